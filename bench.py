@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of the MO vgl hot path on the organic-chain workload.
+
+Workload: 150 nuclei (C:N:O:H 56:10:9:75 on a self-avoiding chain), 1650
+Cartesian AOs up to f, 300 occupied MOs, 600 electrons x 256 walkers,
+eps = 1e-10 radial cutoff; seeded synthetic inputs (no dataset exists here).
+Metric: electron*MO vgl evaluations per second, N_elec * N_walk * N_mo / t,
+one evaluation = value, gradient and Laplacian of one MO at one electron.
+
+A step = new electron coordinates (device, bumps the time stamp) followed by
+the MO vgl evaluation: the ao_vgl kernel and the contraction, every step.
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "organic150: 150 nuclei, 1650 AO (s-f), 300 MO, 600 e- x 256 walkers, eps=1e-10"
+METRIC = "electron·MO vgl evals/s (600 e-, 256 walkers) vs plain FP32 path; % roofline"
+UNIT = "evals/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["bf16x3", "tf32", "fp32", "fp64"], default="bf16x3")
+    ap.add_argument("--no-fp32-line", action="store_true",
+                    help="skip the plain FP32 path measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline ---
+def roofline(mode, mol, ms_per_launch, peaks):
+    """Roofline entries for the two kernels, from algorithmic work per launch."""
+    P, na, nm = mol.point_num, mol.ao_num, mol.mo_num
+    ao_bytes = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode] * 5 * P * na
+    out = {}
+    t_ao = ms_per_launch[0] * 1e-3
+    if t_ao > 0:
+        a = ao_bytes / t_ao / 1e9
+        out["ao_vgl"] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                         "algorithmic_bytes": ao_bytes}
+    t_mo = ms_per_launch[1] * 1e-3
+    dense = 2.0 * 5 * P * nm * na
+    if t_mo > 0:
+        if mode == "bf16x3":
+            fl = 3 * dense
+            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                                     "peak_note": "measured bf16 sustained"}
+        elif mode == "tf32":
+            fl = dense
+            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 0.5
+            out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                                     "peak_note": "measured bf16 sustained x 1/2 (tf32/bf16 "
+                                                  "nominal ratio)"}
+        elif mode == "fp32":
+            fl = dense
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                                     "peak_note": "152 SMs x 128 FP32 FMA/clk x max clock"}
+        else:
+            fl = dense
+            peak = 1.25
+            out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                                     "peak_note": "nominal GB300 FP64"}
+        a = fl / t_mo / 1e12
+        out["mo_contraction"].update({"achieved": a, "frac": a / peak, "algorithmic_flops": fl,
+                                      "dense_flops": dense})
+    return out
+
+
+def traffic_for(kernel, mode):
+    """DRAM bytes per launch from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+        ent = tab.get(f"{kernel}:{mode}")
+        if not ent:
+            return None
+        src = os.path.join(ROOT, ent["source"])
+        import hashlib
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------- our arm ---
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+    mol = synth.make_config(2)
+    peaks, peak_src = load_peaks()
+    coords = torch.from_numpy(mol.coord).cuda()
+    g = torch.Generator(device="cpu").manual_seed(1234 + rank)
+    step_disp = torch.randn(coords.shape, generator=g, dtype=torch.float64).cuda() * 0.05
+    coord_set = [coords, coords + step_disp]        # two electron configurations
+
+    def measure(mode, steps, warmup, timing=True):
+        ctx = qmckl.Context(mode)
+        ctx.set_molecule(mol)
+        ctx.set_points_device(coord_set[0])
+        out = ctx.mo_vgl_device()
+        for i in range(warmup):
+            ctx.set_points_device(coord_set[i % 2])
+            ctx.mo_vgl_device(out)
+        torch.cuda.synchronize()
+        ctx.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ctx.set_timing(timing)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            e0.record(stream)
+            for i in range(steps):
+                ctx.set_points_device(coord_set[i % 2])
+                ctx.mo_vgl_device(out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ctx.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kms, kn = ctx.get_timing() if timing else ([0.0] * 3, [0] * 3)
+        return ctx, out, ms, kms, kn, clk.summary()
+
+    evals_per_step = mol.elec_num * mol.walk_num * mol.mo_num
+    ctx, out, ms, kms, kn, clocks = measure(args.mode, args.steps, args.warmup)
+    ms_step = ms / args.steps
+    value = world * evals_per_step / (ms_step * 1e-3)
+    per_launch = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(3)]
+    roof = roofline(args.mode, mol, per_launch, peaks)
+    dominant = max(roof, key=lambda k: per_launch[0 if k == "ao_vgl" else 1])
+    dom = dict(roof[dominant])
+    dom["kernel"] = dominant
+    dom["traffic"] = traffic_for(dominant, args.mode)
+    dom["peak_source"] = peak_src
+    dom["ms_per_launch"] = per_launch[0 if dominant == "ao_vgl" else 1]
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 (f32 accum)", "tf32": "tf32 (f32 accum)", "fp32": "f32",
+                  "fp64": "f64"}[args.mode],
+        "data": "synthetic (seeded organic-chain molecule, random MO coefficients)",
+        "config": {"workload": WORKLOAD, "mode": args.mode, "points": mol.point_num,
+                   "ao_num": mol.ao_num, "mo_num": mol.mo_num,
+                   "l2": "inputs larger than L2 (AO tensor %.2f GB per step)" % (
+                       5 * mol.point_num * mol.ao_num * 4 / 1e9),
+                   "parallelism": f"walker replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": dom,
+        "kernels": {"ao_vgl_ms": per_launch[0], "contraction_ms": per_launch[1],
+                    "points_ms": per_launch[2], "all": roof},
+        "gpu_launches": int(sum(kn)),
+        "clocks": clocks,
+    }
+
+    # same workload through the plain FP32 path (SIMT ao_vgl + SIMT GEMM)
+    if not args.no_fp32_line and args.mode != "fp32":
+        del ctx
+        c32, _, ms32, k32, n32, clk32 = measure("fp32", max(3, args.steps // 4), 2)
+        ms32_step = ms32 / max(3, args.steps // 4)
+        res["fp32_path"] = {"value": world * evals_per_step / (ms32_step * 1e-3),
+                            "ms_per_step": ms32_step,
+                            "contraction_ms": k32[1] / max(n32[1], 1),
+                            "ao_vgl_ms": k32[0] / max(n32[0], 1), "clocks": clk32}
+        res["speedup_vs_fp32_path"] = res["fp32_path"]["ms_per_step"] / ms_step
+        del c32
+        ctx = None
+
+    # end to end through the host-memory C-ABI calls: H2D of the coordinates
+    # and D2H of the whole MO vgl tensor inside the timed region
+    host_in = torch.empty(coords.shape, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(coords.cpu())
+    host_out = torch.empty((mol.point_num * 5 * mol.mo_num,),
+                           dtype=torch.float64 if args.mode == "fp64" else torch.float32,
+                           pin_memory=True)
+    ce = qmckl.Context(args.mode)
+    ce.set_molecule(mol)
+    hin, hout = host_in.numpy(), host_out.numpy()
+    for _ in range(2):
+        ce.set_points(hin)
+        ce.mo_vgl(hout)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ce.set_points(hin)
+        ce.mo_vgl(hout)
+    torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / args.e2e_steps
+    if dist:
+        t = torch.tensor([te], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    res["e2e"] = {"value": world * evals_per_step / te, "unit": UNIT,
+                  "ms_per_step": te * 1e3,
+                  "h2d_bytes_per_step": int(host_in.numel() * 8),
+                  "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())}
+    gpu_out_w0 = None
+    if rank == 0 and not args.no_cpu_baseline:
+        gpu_out_w0 = hout.reshape(mol.walk_num, mol.elec_num, 5, mol.mo_num)[0].astype(
+            np.float64)
+    ce.close()
+    return res, mol, gpu_out_w0
+
+
+# -------------------------------------------------------- cpu baseline ---
+def oracle_sample(mol, n_points):
+    """Time the FP64 oracle on the first n_points of walker 0."""
+    from oracle import oracle
+    oracle.build()
+    pts = mol.points[:n_points]
+    t0 = time.perf_counter()
+    ref, size = oracle.mo_vgl(mol, points=pts)
+    dt = time.perf_counter() - t0
+    return ref, size, dt
+
+
+def cpu_baseline(mol, gpu_w0):
+    ref, size, dt = oracle_sample(mol, mol.elec_num)
+    out = {"value": mol.elec_num * mol.mo_num / dt, "unit": UNIT, "cores": 1,
+           "kind": "oracle",
+           "sample": f"walker 0 ({mol.elec_num} points) of the 256-walker workload, "
+                     f"screened FP64 oracle with compensated sums, {dt:.1f} s"}
+    if gpu_w0 is not None:
+        import numpy as np
+        e = np.abs(gpu_w0.reshape(ref.shape) - ref) / (size + 1e-300)
+        out["max_err_vs_oracle"] = {"value": float(e[:, 0].max()),
+                                    "gradient": float(e[:, 1:4].max()),
+                                    "laplacian": float(e[:, 4].max()),
+                                    "metric": "normwise |gpu-oracle|/sum|C||chi|, "
+                                              "same sample"}
+    return out
+
+
+def run_reference(args, rank, world):
+    from paper_2512_16677_gb300 import synth
+    if rank != 0:
+        return None
+    mol = synth.make_config(2)
+    n = 48
+    for _ in range(args.warmup):
+        oracle_sample(mol, n)
+    times = []
+    for i in range(args.steps):
+        # each step: a bounded sample of the workload's points
+        sub = mol.with_points(mol.points[(i * n) % mol.point_num:][:n])
+        _, _, dt = oracle_sample(sub, n)
+        times.append(dt)
+    tot = sum(times)
+    value = n * mol.mo_num * args.steps / tot
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": "oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} points per step of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    from paper_2512_16677_gb300 import buildlib
+    if rank == 0 or world == 1:
+        buildlib.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    res, mol, gpu_w0 = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(mol, gpu_w0)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

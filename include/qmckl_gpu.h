@@ -1,0 +1,218 @@
+/*
+ * qmckl_gpu.h -- C ABI of the GB300 (sm_103a) AO/MO "vgl" library.
+ *
+ * The library evaluates, at every electron of a batch of walkers, the values,
+ * gradients and Laplacians ("vgl") of contracted Gaussian atomic orbitals and
+ * of the molecular orbitals built from them, following the QMCkl paper
+ * (arXiv 2512.16677):
+ *
+ *   chi_n(r)  = M_n R_s(r) P_abc(r - R_A)                      Sec. 3.1, Eq. 1
+ *   R_s(r)    = N_s sum_k a_ks f_ks exp(-gamma_ks |r - R_A|^2)  Eq. 2 (p = 2, n_s = 0)
+ *   screening: primitive k is evaluated only if
+ *              gamma_ks |r - R_A|^2 < T,  T = (B-1) ln 2        Eq. 3
+ *   P_abc     = (x-X_A)^a (y-Y_A)^b (z-Z_A)^c                   Eq. 4
+ *   phi_i, grad phi_i, lap phi_i = sum_k C_ik (chi_k, grad chi_k, lap chi_k)
+ *                                                              Sec. 3.2, Eqs. 5-7
+ *
+ * The calling sequence follows the paper's usage (Sec. 2.2 context and
+ * memoisation, Sec. 2.3 C ABI, Sec. 5.1 example): create a context, set the
+ * nuclei, the shells and primitives and the MO coefficients, set the points,
+ * then get the MO vgl.  Units: bohr for lengths, bohr^-2 for exponents.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns a qk_status: QK_SUCCESS (0) or a negative code.
+ *    On failure the context keeps a message, read with qk_last_error.
+ *    Outputs are left untouched when an argument is rejected.
+ *  - Setters copy host inputs; the caller keeps ownership of its arrays.
+ *    The context owns its device tables and frees them in
+ *    qk_context_destroy.
+ *  - Arrays are C order (row-major).  Cartesian components within a shell
+ *    are ordered by descending a, then descending b (l = 2: xx, xy, xz, yy,
+ *    yz, zz).  vgl outputs are [walk][elec][5][n] with the five components
+ *    (value, d/dx, d/dy, d/dz, Laplacian).
+ *  - Element type of AO/MO outputs and of loss weights: double in QK_FP64
+ *    mode, float in every other mode.
+ *  - A context is not thread-safe (Sec. 2.4); separate contexts may be used
+ *    concurrently.  All device work of a context runs on its stream (the
+ *    legacy default stream unless qk_set_stream is called).
+ */
+#ifndef QMCKL_GPU_H
+#define QMCKL_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qk_status;
+
+#define QK_SUCCESS 0
+#define QK_ERR_INVALID_ARG -1      /* a value is out of its domain */
+#define QK_ERR_NULL_POINTER -2     /* a required pointer is NULL */
+#define QK_ERR_BAD_SIZE -3         /* a size argument is too small or inconsistent */
+#define QK_ERR_NOT_PROVIDED -4     /* a required setter has not been called */
+#define QK_ERR_NOT_IMPLEMENTED -5  /* valid input outside what this build supports */
+#define QK_ERR_CUDA -6             /* a CUDA runtime/driver call failed */
+#define QK_ERR_DEVICE_TIMEOUT -7   /* a bounded device-side wait gave up */
+#define QK_ERR_OUT_OF_MEMORY -8    /* device or host allocation failed */
+
+/* Arithmetic of the evaluation (qk_set_compute_mode). */
+#define QK_FP64 0    /* FP64 AOs and FP64 contraction: the accuracy anchor */
+#define QK_FP32 1    /* FP32 AOs (FP64 coordinate differences) and FP32 SIMT contraction */
+#define QK_BF16X3 2  /* FP32 AOs split into bf16 hi+lo, contraction on tcgen05 tensor
+                        cores as hi*hi + hi*lo + lo*hi with FP32 accumulation */
+#define QK_TF32 3    /* FP32 AOs, contraction on tcgen05 tensor cores in TF32 */
+
+typedef struct qk_context_s* qk_context;
+typedef struct qk_batch_s* qk_batch;
+
+/* ----------------------------------------------------------- lifetime --- */
+
+/* Create a context on the current CUDA device (Sec. 2.2: the context holds all
+   inputs, cached intermediates and their time stamps).  *out receives the
+   handle.  Errors: QK_ERR_NULL_POINTER, QK_ERR_OUT_OF_MEMORY, QK_ERR_CUDA. */
+qk_status qk_context_create(qk_context* out);
+
+/* Free the context and every device table it owns.  A NULL handle is
+   QK_ERR_NULL_POINTER.  Caller-owned workspace is not freed. */
+qk_status qk_context_destroy(qk_context ctx);
+
+/* Copy the last error message (NUL-terminated, truncated to size) into buf. */
+qk_status qk_last_error(qk_context ctx, char* buf, int64_t size);
+
+/* ----------------------------------------------------------- settings --- */
+
+/* Precision parameter B of Eq. 3 (default 53): primitives with
+   gamma r^2 >= (B-1) ln 2 are skipped.  2 <= bits <= 53, else
+   QK_ERR_INVALID_ARG.  Clears a cutoff set by qk_set_cutoff. */
+qk_status qk_set_precision(qk_context ctx, int32_t bits);
+
+/* Alternative to B: skip primitives with exp(-gamma r^2) <= eps, i.e.
+   T = ln(1/eps).  0 < eps < 1, else QK_ERR_INVALID_ARG. */
+qk_status qk_set_cutoff(qk_context ctx, double eps);
+
+/* One of QK_FP64, QK_FP32, QK_BF16X3, QK_TF32 (default QK_FP64). */
+qk_status qk_set_compute_mode(qk_context ctx, int32_t mode);
+
+/* ------------------------------------------------------------- system --- */
+
+/* Nuclei (Sec. 3.1): charge [nucl_num] (kept for reference only) and
+   coord [nucl_num][3] in bohr.  nucl_num >= 1.  Non-finite coordinates are
+   QK_ERR_INVALID_ARG.  Resets the basis if nucl_num changed. */
+qk_status qk_set_nucleus(qk_context ctx, int64_t nucl_num, const double* charge,
+                         const double* coord);
+
+/* Contracted Gaussian shells (Eqs. 1, 2, 4).
+   shell_nucleus [shell_num]  nucleus of each shell, 0 <= . < nucl_num
+   shell_ang_mom [shell_num]  l, 0 <= l <= 3 (l > 3: QK_ERR_NOT_IMPLEMENTED)
+   shell_prim_num [shell_num] primitives per shell, >= 1; primitives are
+                              stored shell after shell
+   shell_factor [shell_num]   N_s
+   exponent, coefficient, prim_factor [prim_num]: gamma_ks > 0, a_ks, f_ks
+   ao_num = sum over shells of (l+1)(l+2)/2, else QK_ERR_BAD_SIZE
+   ao_factor [ao_num]         M_n
+   The primitives of each shell are sorted by ascending exponent inside the
+   library (Sec. 3.1); results do not depend on the input order.
+   Requires qk_set_nucleus first (QK_ERR_NOT_PROVIDED). */
+qk_status qk_set_ao_basis(qk_context ctx, int64_t shell_num, int64_t prim_num,
+                          const int64_t* shell_nucleus, const int32_t* shell_ang_mom,
+                          const int64_t* shell_prim_num, const double* shell_factor,
+                          const double* exponent, const double* coefficient,
+                          const double* prim_factor, int64_t ao_num,
+                          const double* ao_factor);
+
+/* MO coefficients C [mo_num][ao_num] (Eqs. 5-7).  Passing only the occupied
+   MOs is the paper's MO-subset selection (Sec. 3.2).  Requires the basis. */
+qk_status qk_set_mo_coefficient(qk_context ctx, int64_t mo_num, const double* coef);
+
+/* ------------------------------------------------------------- points --- */
+
+/* Electron coordinates from host memory.  transp 'N': coord [walk][elec][3];
+   'T': coord [3][walk*elec].  walk_num, elec_num >= 1.  Bumps the context's
+   time stamp, which invalidates every cached intermediate (Sec. 2.2). */
+qk_status qk_set_points(qk_context ctx, char transp, int64_t walk_num, int64_t elec_num,
+                        const double* coord);
+
+/* Same, from device memory (read on the context's stream before return of
+   the next get; the caller keeps the buffer alive until then). */
+qk_status qk_set_points_device(qk_context ctx, char transp, int64_t walk_num,
+                               int64_t elec_num, const double* dcoord);
+
+/* --------------------------------------------------------------- sizes --- */
+
+qk_status qk_get_nucl_num(qk_context ctx, int64_t* n);
+qk_status qk_get_ao_num(qk_context ctx, int64_t* n);
+qk_status qk_get_mo_num(qk_context ctx, int64_t* n);
+qk_status qk_get_point_num(qk_context ctx, int64_t* n);
+
+/* ---------------------------------------------------------- workspace --- */
+
+/* Device bytes the next evaluation needs (points, mode and basis must be
+   set).  The workspace holds the coordinate copies and the AO tensor. */
+qk_status qk_workspace_size(qk_context ctx, size_t* bytes);
+
+/* Caller-owned device workspace (e.g. a torch allocation), 256-byte
+   aligned, at least qk_workspace_size bytes (QK_ERR_BAD_SIZE otherwise).
+   Once set, the library allocates nothing per evaluation.  NULL reverts to
+   library-owned workspace. */
+qk_status qk_set_workspace(qk_context ctx, void* dev, size_t bytes);
+
+/* Stream for all device work of this context (a cudaStream_t). */
+qk_status qk_set_stream(qk_context ctx, void* stream);
+
+/* Synchronise the context's stream and report device-side errors (bounded
+   waits that gave up: QK_ERR_DEVICE_TIMEOUT). */
+qk_status qk_synchronize(qk_context ctx);
+
+/* Profiling aid (no counterpart in the paper): when enabled, the library
+   records a CUDA event pair on the context's stream around every launch,
+   in three classes: 0 = ao_vgl, 1 = MO contraction, 2 = other (point
+   layout).  Enabling or disabling resets the record. */
+qk_status qk_set_timing(qk_context ctx, int32_t enable);
+
+/* Wait for the recorded events and return, for classes 0..n-1, the summed
+   device time in ms and the number of launches since the last reset; then
+   reset.  1 <= n <= 3, else QK_ERR_BAD_SIZE. */
+qk_status qk_get_timing(qk_context ctx, double* ms, int64_t* launches, int32_t n);
+
+/* ----------------------------------------------------------- evaluate --- */
+
+/* AO vgl [walk][elec][5][ao_num] into host memory; size = number of elements
+   the buffer holds (>= point_num*5*ao_num, else QK_ERR_BAD_SIZE).
+   Blocks until the copy is done. */
+qk_status qk_get_ao_vgl(qk_context ctx, void* out, int64_t size);
+
+/* Same into device memory on the context's stream (asynchronous). */
+qk_status qk_get_ao_vgl_device(qk_context ctx, void* dout, int64_t size);
+
+/* MO vgl [walk][elec][5][mo_num] into host memory (Eqs. 5-7); size as above
+   with mo_num.  Blocks until the copy is done. */
+qk_status qk_get_mo_vgl(qk_context ctx, void* out, int64_t size);
+
+/* Same into device memory on the context's stream (asynchronous).  The AO
+   tensor is memoised: a second call at the same time stamp and mode reuses
+   it and runs only the contraction (Sec. 2.2). */
+qk_status qk_get_mo_vgl_device(qk_context ctx, void* dout, int64_t size);
+
+/* ------------------------------------------------------------ adjoint --- */
+
+/* Gradients of L = sum_{p,c,i} W[p][c][i] * mo_vgl[p][c][i] at the current
+   points (Sec. 3.6 needs nuclear derivatives of the orbitals up to third
+   order).  dW has the mo_vgl layout and element type, in device memory.
+   d_dC [mo_num][ao_num] (dL/dC) and d_dR [nucl_num][3] (dL/dR_nuc) are
+   device FP64 arrays; either may be NULL to skip it.  AO values are
+   recomputed (not taken from the forward).  Runs on the context's stream. */
+qk_status qk_mo_vgl_backward_device(qk_context ctx, const void* dW, int64_t size,
+                                    double* d_dC, double* d_dR);
+
+/* Device bytes qk_mo_vgl_backward_device needs beyond the forward workspace
+   (it allocates them itself unless qk_set_workspace covered both sizes). */
+qk_status qk_backward_workspace_size(qk_context ctx, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMCKL_GPU_H */

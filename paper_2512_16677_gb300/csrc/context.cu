@@ -1,0 +1,821 @@
+// context.cu -- the C-ABI context: inputs, device tables, memoisation and
+// dispatch of the AO/MO vgl kernels.
+//
+// Sec. 2.2 of the QMCkl paper: a context holds every input and every cached
+// intermediate with its time stamp; setting new electron coordinates bumps
+// the stamp and a "get" recomputes only what is out of date.  Here the cached
+// intermediate is the AO tensor (the input of the contraction of Eqs. 5-7):
+// it is keyed by (time stamp, compute mode, basis version, workspace).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace qk {
+
+cudaError_t DevBuf::ensure(size_t n) {
+  if (n <= bytes && p) return cudaSuccess;
+  release();
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    bytes = 0;
+    return e;
+  }
+  bytes = n;
+  return cudaSuccess;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+static inline int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
+
+}  // namespace qk
+
+using namespace qk;
+
+// timer classes: 0 = ao_vgl, 1 = contraction, 2 = everything else
+static constexpr int kTimerClasses = 3;
+
+struct qk_context_s {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // settings
+  int bits = 53;
+  double eps = 0.0;  // > 0: explicit cutoff instead of bits
+  int mode = QK_FP64;
+  uint64_t basis_version = 1;
+  // nuclei
+  int64_t nucl_num = 0;
+  std::vector<double> nucl_charge, nucl_coord;
+  // basis, primitives sorted by ascending exponent inside each shell
+  bool has_basis = false;
+  int64_t shell_num = 0, prim_num = 0, ao_num = 0;
+  std::vector<int> shell_nuc, shell_l, shell_prim0, shell_nprim, shell_ao0, ao_shell;
+  std::vector<double> prim_g, prim_c, ao_fac, shell_gmin;
+  std::vector<int4> chunks;
+  DevBuf d_tables;
+  BasisDev bdev{};
+  bool tables_dirty = true;
+  // MO coefficients
+  bool has_mo = false;
+  int64_t mo_num = 0, ldc = 0;
+  std::vector<double> mo_coef;
+  DevBuf d_mo;
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  __nv_bfloat16* c_hi = nullptr;
+  __nv_bfloat16* c_lo = nullptr;
+  bool mo_dirty = true;
+  // points
+  bool has_points = false;
+  int64_t walk_num = 0, elec_num = 0, point_num = 0;
+  uint64_t date = 0;
+  DevBuf d_points, d_raw;
+  PointsDev pdev{};
+  // workspace and memo
+  void* ws_user = nullptr;
+  size_t ws_user_bytes = 0;
+  DevBuf ws_own;
+  uint64_t ao_date = ~0ull, ao_version = 0;
+  int ao_mode = -1;
+  void* ao_ws = nullptr;
+  // host-output staging, device error word, backward scratch
+  DevBuf d_out;
+  DevBuf d_flag;
+  DevBuf bwd_own;
+  // optional per-kernel-class timing with events on the context's stream
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_start[kTimerClasses], ev_stop[kTimerClasses];
+  size_t ev_used[kTimerClasses] = {0, 0, 0};
+  ~qk_context_s() {
+    for (int k = 0; k < kTimerClasses; ++k) {
+      for (auto e : ev_start[k]) cudaEventDestroy(e);
+      for (auto e : ev_stop[k]) cudaEventDestroy(e);
+    }
+  }
+};
+
+namespace {
+
+qk_status fail(qk_context c, qk_status code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+qk_status cuda_fail(qk_context c, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error so later calls start clean
+  if (e == cudaErrorMemoryAllocation)
+    return fail(c, QK_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorNotSupported)
+    return fail(c, QK_ERR_NOT_IMPLEMENTED, "%s: not supported by this build", what);
+  return fail(c, QK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_CTX(c) \
+  if (!(c)) return QK_ERR_NULL_POINTER
+
+// Event pair around one launch of class k (no-op unless timing is on).
+struct TimedLaunch {
+  qk_context c;
+  int k;
+  bool on;
+  TimedLaunch(qk_context c_, int k_) : c(c_), k(k_), on(c_->timing) {
+    if (!on) return;
+    size_t i = c->ev_used[k];
+    if (i == c->ev_start[k].size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        on = false;
+        return;
+      }
+      c->ev_start[k].push_back(a);
+      c->ev_stop[k].push_back(b);
+    }
+    cudaEventRecord(c->ev_start[k][i], c->stream);
+  }
+  ~TimedLaunch() {
+    if (!on) return;
+    cudaEventRecord(c->ev_stop[k][c->ev_used[k]], c->stream);
+    c->ev_used[k]++;
+  }
+};
+
+double threshold(const qk_context c) {
+  if (c->eps > 0.0) return -std::log(c->eps);
+  return (double)(c->bits - 1) * std::log(2.0);
+}
+
+// Upload the basis tables (and the threshold-dependent shell radii).
+qk_status ensure_tables(qk_context c) {
+  if (!c->tables_dirty) return QK_SUCCESS;
+  const double T = threshold(c);
+  const int S = (int)c->shell_num, NP = (int)c->prim_num, NA = (int)c->ao_num,
+            NN = (int)c->nucl_num, NC = (int)c->chunks.size();
+  std::vector<double> r2(S);
+  std::vector<float> r2f(S), gf(NP), cf(NP), af(NA), nhi(3 * NN), nlo(3 * NN);
+  for (int s = 0; s < S; ++s) {
+    // any r^2 >= r2[s] gives fl(gamma_min r^2) > T, so no primitive would pass
+    r2[s] = std::isinf(T) ? INFINITY : T / c->shell_gmin[s] * (1.0 + 1e-13);
+    r2f[s] = std::isinf(T) ? INFINITY : std::nextafter((float)r2[s], INFINITY) * (1.0f + 1e-6f);
+  }
+  for (int k = 0; k < NP; ++k) {
+    gf[k] = (float)c->prim_g[k];
+    cf[k] = (float)c->prim_c[k];
+  }
+  for (int k = 0; k < NA; ++k) af[k] = (float)c->ao_fac[k];
+  for (int k = 0; k < 3 * NN; ++k) {
+    nhi[k] = (float)c->nucl_coord[k];
+    nlo[k] = (float)(c->nucl_coord[k] - (double)nhi[k]);
+  }
+  // pack everything into one allocation, 256-byte aligned pieces
+  struct Piece {
+    const void* src;
+    size_t bytes;
+    size_t off;
+  };
+  std::vector<Piece> pieces = {
+      {c->nucl_coord.data(), sizeof(double) * 3 * NN, 0},
+      {nhi.data(), sizeof(float) * 3 * NN, 0},
+      {nlo.data(), sizeof(float) * 3 * NN, 0},
+      {c->shell_nuc.data(), sizeof(int) * S, 0},
+      {c->shell_l.data(), sizeof(int) * S, 0},
+      {c->shell_prim0.data(), sizeof(int) * S, 0},
+      {c->shell_nprim.data(), sizeof(int) * S, 0},
+      {c->shell_ao0.data(), sizeof(int) * S, 0},
+      {r2.data(), sizeof(double) * S, 0},
+      {r2f.data(), sizeof(float) * S, 0},
+      {c->prim_g.data(), sizeof(double) * NP, 0},
+      {c->prim_c.data(), sizeof(double) * NP, 0},
+      {gf.data(), sizeof(float) * NP, 0},
+      {cf.data(), sizeof(float) * NP, 0},
+      {c->ao_fac.data(), sizeof(double) * NA, 0},
+      {af.data(), sizeof(float) * NA, 0},
+      {c->ao_shell.data(), sizeof(int) * NA, 0},
+      {c->chunks.data(), sizeof(int4) * NC, 0},
+  };
+  size_t total = 0;
+  for (auto& p : pieces) {
+    p.off = total;
+    total = align_up(total + p.bytes, 256);
+  }
+  std::vector<unsigned char> host(total, 0);
+  for (auto& p : pieces)
+    if (p.bytes) std::memcpy(host.data() + p.off, p.src, p.bytes);
+  cudaError_t e = c->d_tables.ensure(total);
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis tables");
+  e = cudaMemcpy(c->d_tables.p, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis tables upload");
+  auto at = [&](int i) { return (void*)((unsigned char*)c->d_tables.p + pieces[i].off); };
+  BasisDev& b = c->bdev;
+  b.nucl_num = NN;
+  b.shell_num = S;
+  b.ao_num = NA;
+  b.prim_num = NP;
+  b.nchunk = NC;
+  b.nucl_xyz = (const double*)at(0);
+  b.nucl_hi = (const float*)at(1);
+  b.nucl_lo = (const float*)at(2);
+  b.shell_nuc = (const int*)at(3);
+  b.shell_l = (const int*)at(4);
+  b.shell_prim0 = (const int*)at(5);
+  b.shell_nprim = (const int*)at(6);
+  b.shell_ao0 = (const int*)at(7);
+  b.shell_r2 = (const double*)at(8);
+  b.shell_r2_f = (const float*)at(9);
+  b.prim_g = (const double*)at(10);
+  b.prim_c = (const double*)at(11);
+  b.prim_g_f = (const float*)at(12);
+  b.prim_c_f = (const float*)at(13);
+  b.ao_fac = (const double*)at(14);
+  b.ao_fac_f = (const float*)at(15);
+  b.ao_shell = (const int*)at(16);
+  b.chunk = (const int4*)at(17);
+  b.T = T;
+  b.T_f = std::isinf(T) ? INFINITY : (float)T;
+  c->tables_dirty = false;
+  return QK_SUCCESS;
+}
+
+qk_status ensure_mo(qk_context c) {
+  if (!c->mo_dirty) return QK_SUCCESS;
+  const int64_t nm = c->mo_num, na = c->ao_num, ldc = round_up8(na);
+  const size_t b64 = align_up(sizeof(double) * nm * na, 256);
+  const size_t b32 = align_up(sizeof(float) * nm * ldc, 256);
+  const size_t b16 = align_up(sizeof(__nv_bfloat16) * nm * ldc, 256);
+  cudaError_t e = c->d_mo.ensure(b64 + b32 + 2 * b16);
+  if (e != cudaSuccess) return cuda_fail(c, e, "MO coefficient tables");
+  unsigned char* base = (unsigned char*)c->d_mo.p;
+  c->c64 = (double*)base;
+  c->c32 = (float*)(base + b64);
+  c->c_hi = (__nv_bfloat16*)(base + b64 + b32);
+  c->c_lo = (__nv_bfloat16*)(base + b64 + b32 + b16);
+  c->ldc = ldc;
+  e = cudaMemcpyAsync(c->c64, c->mo_coef.data(), sizeof(double) * nm * na,
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_to_f32(c->c64, nm, na, ldc, c->c32, c->stream);
+  if (e == cudaSuccess) e = launch_split_bf16(c->c64, nm, na, ldc, c->c_hi, c->c_lo, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "MO coefficient upload");
+  c->mo_dirty = false;
+  return QK_SUCCESS;
+}
+
+size_t ao_tensor_bytes(qk_context c, int mode) {
+  const size_t rows = (size_t)5 * c->point_num;
+  const size_t ld = (size_t)round_up8(c->ao_num);
+  switch (mode) {
+    case QK_FP64:
+      return align_up(rows * ld * sizeof(double), 256);
+    case QK_BF16X3:
+      return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256);
+    default:
+      return align_up(rows * ld * sizeof(float), 256);
+  }
+}
+
+// Bind the context to the current device on first use; allocate the
+// device error word.
+qk_status ensure_device(qk_context c) {
+  if (c->device >= 0) return QK_SUCCESS;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = c->d_flag.ensure(256);
+  if (e == cudaSuccess) e = cudaMemset(c->d_flag.p, 0, 256);
+  if (e != cudaSuccess) return cuda_fail(c, e, "no usable CUDA device");
+  c->device = dev;
+  return QK_SUCCESS;
+}
+
+qk_status require(qk_context c, bool need_mo) {
+  if (c->nucl_num == 0) return fail(c, QK_ERR_NOT_PROVIDED, "nuclei not set");
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "AO basis not set");
+  if (need_mo && !c->has_mo) return fail(c, QK_ERR_NOT_PROVIDED, "MO coefficients not set");
+  if (!c->has_points) return fail(c, QK_ERR_NOT_PROVIDED, "points not set");
+  return ensure_device(c);
+}
+
+// Pointer to a workspace of at least `need` bytes (caller's or the library's).
+qk_status workspace(qk_context c, size_t need, void** out) {
+  if (c->ws_user) {
+    if (c->ws_user_bytes < need)
+      return fail(c, QK_ERR_BAD_SIZE, "workspace holds %zu bytes, %zu needed", c->ws_user_bytes,
+                  need);
+    *out = c->ws_user;
+    return QK_SUCCESS;
+  }
+  cudaError_t e = c->ws_own.ensure(need);
+  if (e != cudaSuccess) return cuda_fail(c, e, "workspace");
+  *out = c->ws_own.p;
+  return QK_SUCCESS;
+}
+
+AOTensor ao_view(qk_context c, void* ws, int mode) {
+  AOTensor t{};
+  t.rows = 5 * c->point_num;
+  t.ld = round_up8(c->ao_num);
+  t.a = ws;
+  if (mode == QK_BF16X3)
+    t.a_lo = (unsigned char*)ws + align_up(t.rows * t.ld * sizeof(__nv_bfloat16), 256);
+  return t;
+}
+
+// Make the AO tensor of the current date/mode valid in the workspace.
+qk_status provide_ao(qk_context c, AOTensor* out) {
+  qk_status st = ensure_tables(c);
+  if (st) return st;
+  void* ws = nullptr;
+  st = workspace(c, ao_tensor_bytes(c, c->mode), &ws);
+  if (st) return st;
+  *out = ao_view(c, ws, c->mode);
+  if (c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
+      c->ao_version == c->basis_version)
+    return QK_SUCCESS;
+  cudaError_t e;
+  {
+    TimedLaunch t(c, 0);
+    e = launch_ao_vgl(c->bdev, c->pdev, c->mode, *out, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
+  c->ao_date = c->date;
+  c->ao_mode = c->mode;
+  c->ao_ws = ws;
+  c->ao_version = c->basis_version;
+  return QK_SUCCESS;
+}
+
+void invalidate(qk_context c) {
+  c->basis_version++;
+  c->tables_dirty = true;
+}
+
+qk_status set_points_common(qk_context c, char transp, int64_t walk_num, int64_t elec_num) {
+  if (transp != 'N' && transp != 'T')
+    return fail(c, QK_ERR_INVALID_ARG, "transp must be 'N' or 'T'");
+  if (walk_num < 1 || elec_num < 1)
+    return fail(c, QK_ERR_BAD_SIZE, "walk_num and elec_num must be >= 1");
+  qk_status st = ensure_device(c);
+  if (st) return st;
+  const int64_t n = walk_num * elec_num;
+  cudaError_t e = c->d_points.ensure(align_up(sizeof(double) * 3 * n, 256) +
+                                     align_up(sizeof(float) * 6 * n, 256));
+  if (e != cudaSuccess) return cuda_fail(c, e, "point buffers");
+  double* base = (double*)c->d_points.p;
+  c->pdev.n = n;
+  c->pdev.x = base;
+  c->pdev.y = base + n;
+  c->pdev.z = base + 2 * n;
+  float* fb = (float*)((unsigned char*)c->d_points.p + align_up(sizeof(double) * 3 * n, 256));
+  c->pdev.hi = fb;
+  c->pdev.lo = fb + 3 * n;
+  c->walk_num = walk_num;
+  c->elec_num = elec_num;
+  c->point_num = n;
+  return QK_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+qk_status qk_context_create(qk_context* out) {
+  if (!out) return QK_ERR_NULL_POINTER;
+  qk_context c = new (std::nothrow) qk_context_s();
+  if (!c) return QK_ERR_OUT_OF_MEMORY;
+  // the device is bound at the first call that touches it, so that the
+  // host-side setters and their validation work without a GPU
+  *out = c;
+  return QK_SUCCESS;
+}
+
+qk_status qk_context_destroy(qk_context c) {
+  CHECK_CTX(c);
+  delete c;
+  return QK_SUCCESS;
+}
+
+qk_status qk_last_error(qk_context c, char* buf, int64_t size) {
+  CHECK_CTX(c);
+  if (!buf) return QK_ERR_NULL_POINTER;
+  if (size < 1) return QK_ERR_BAD_SIZE;
+  const size_t n = std::min((size_t)(size - 1), c->err.size());
+  std::memcpy(buf, c->err.data(), n);
+  buf[n] = '\0';
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_precision(qk_context c, int32_t bits) {
+  CHECK_CTX(c);
+  if (bits < 2 || bits > 53) return fail(c, QK_ERR_INVALID_ARG, "bits must be in [2, 53]");
+  c->bits = bits;
+  c->eps = 0.0;
+  invalidate(c);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_cutoff(qk_context c, double eps) {
+  CHECK_CTX(c);
+  if (!(eps > 0.0 && eps < 1.0)) return fail(c, QK_ERR_INVALID_ARG, "eps must be in (0, 1)");
+  c->eps = eps;
+  invalidate(c);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_compute_mode(qk_context c, int32_t mode) {
+  CHECK_CTX(c);
+  if (mode != QK_FP64 && mode != QK_FP32 && mode != QK_BF16X3 && mode != QK_TF32)
+    return fail(c, QK_ERR_INVALID_ARG, "unknown compute mode %d", mode);
+  c->mode = mode;
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_nucleus(qk_context c, int64_t nucl_num, const double* charge,
+                         const double* coord) {
+  CHECK_CTX(c);
+  if (!charge || !coord) return fail(c, QK_ERR_NULL_POINTER, "charge/coord is NULL");
+  if (nucl_num < 1 || nucl_num > (1 << 30))
+    return fail(c, QK_ERR_BAD_SIZE, "nucl_num must be >= 1");
+  for (int64_t i = 0; i < 3 * nucl_num; ++i)
+    if (!std::isfinite(coord[i])) return fail(c, QK_ERR_INVALID_ARG, "non-finite nuclear coordinate");
+  if (nucl_num != c->nucl_num) {
+    c->has_basis = false;
+    c->has_mo = false;
+  }
+  c->nucl_num = nucl_num;
+  c->nucl_charge.assign(charge, charge + nucl_num);
+  c->nucl_coord.assign(coord, coord + 3 * nucl_num);
+  invalidate(c);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
+                          const int64_t* shell_nucleus, const int32_t* shell_ang_mom,
+                          const int64_t* shell_prim_num, const double* shell_factor,
+                          const double* exponent, const double* coefficient,
+                          const double* prim_factor, int64_t ao_num, const double* ao_factor) {
+  CHECK_CTX(c);
+  if (c->nucl_num == 0) return fail(c, QK_ERR_NOT_PROVIDED, "set the nuclei before the basis");
+  if (!shell_nucleus || !shell_ang_mom || !shell_prim_num || !shell_factor || !exponent ||
+      !coefficient || !prim_factor || !ao_factor)
+    return fail(c, QK_ERR_NULL_POINTER, "a basis array is NULL");
+  if (shell_num < 1 || prim_num < 1 || ao_num < 1 || shell_num > (1 << 30) ||
+      prim_num > (1 << 30) || ao_num > (1 << 30))
+    return fail(c, QK_ERR_BAD_SIZE, "shell/prim/ao counts must be >= 1");
+  int64_t np = 0, na = 0;
+  for (int64_t s = 0; s < shell_num; ++s) {
+    if (shell_nucleus[s] < 0 || shell_nucleus[s] >= c->nucl_num)
+      return fail(c, QK_ERR_INVALID_ARG, "shell %lld: nucleus index out of range", (long long)s);
+    if (shell_ang_mom[s] < 0) return fail(c, QK_ERR_INVALID_ARG, "negative angular momentum");
+    if (shell_ang_mom[s] > kMaxL)
+      return fail(c, QK_ERR_NOT_IMPLEMENTED, "shell %lld: l = %d > 3", (long long)s,
+                  shell_ang_mom[s]);
+    if (shell_prim_num[s] < 1)
+      return fail(c, QK_ERR_INVALID_ARG, "shell %lld has no primitive", (long long)s);
+    np += shell_prim_num[s];
+    na += (shell_ang_mom[s] + 1) * (shell_ang_mom[s] + 2) / 2;
+  }
+  if (np != prim_num) return fail(c, QK_ERR_BAD_SIZE, "prim_num does not match shell_prim_num");
+  if (na != ao_num) return fail(c, QK_ERR_BAD_SIZE, "ao_num does not match the shells");
+  for (int64_t k = 0; k < prim_num; ++k)
+    if (!(exponent[k] > 0.0) || !std::isfinite(exponent[k]) || !std::isfinite(coefficient[k]) ||
+        !std::isfinite(prim_factor[k]))
+      return fail(c, QK_ERR_INVALID_ARG, "primitive %lld: exponent must be > 0 and finite",
+                  (long long)k);
+  for (int64_t s = 0; s < shell_num; ++s)
+    if (!std::isfinite(shell_factor[s])) return fail(c, QK_ERR_INVALID_ARG, "non-finite N_s");
+  for (int64_t k = 0; k < ao_num; ++k)
+    if (!std::isfinite(ao_factor[k])) return fail(c, QK_ERR_INVALID_ARG, "non-finite M_n");
+
+  c->shell_num = shell_num;
+  c->prim_num = prim_num;
+  c->ao_num = ao_num;
+  c->shell_nuc.resize(shell_num);
+  c->shell_l.resize(shell_num);
+  c->shell_prim0.resize(shell_num);
+  c->shell_nprim.resize(shell_num);
+  c->shell_ao0.resize(shell_num);
+  c->shell_gmin.resize(shell_num);
+  c->prim_g.resize(prim_num);
+  c->prim_c.resize(prim_num);
+  c->ao_fac.assign(ao_factor, ao_factor + ao_num);
+  c->ao_shell.resize(ao_num);
+  c->chunks.clear();
+  int64_t p0 = 0, a0 = 0;
+  int4 cur = make_int4(0, 0, 0, 0);
+  for (int64_t s = 0; s < shell_num; ++s) {
+    const int l = shell_ang_mom[s];
+    const int nc = (l + 1) * (l + 2) / 2;
+    const int64_t npr = shell_prim_num[s];
+    std::vector<int64_t> idx(npr);
+    std::iota(idx.begin(), idx.end(), p0);
+    // Sec. 3.1: primitives sorted by ascending exponent, so the first one that
+    // fails Eq. 3 ends the loop
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int64_t x, int64_t y) { return exponent[x] < exponent[y]; });
+    for (int64_t k = 0; k < npr; ++k) {
+      c->prim_g[p0 + k] = exponent[idx[k]];
+      c->prim_c[p0 + k] = shell_factor[s] * coefficient[idx[k]] * prim_factor[idx[k]];
+    }
+    c->shell_nuc[s] = (int)shell_nucleus[s];
+    c->shell_l[s] = l;
+    c->shell_prim0[s] = (int)p0;
+    c->shell_nprim[s] = (int)npr;
+    c->shell_ao0[s] = (int)a0;
+    c->shell_gmin[s] = c->prim_g[p0];
+    for (int j = 0; j < nc; ++j) c->ao_shell[a0 + j] = (int)s;
+    if (cur.w - cur.z + nc > kChunkAO) {
+      c->chunks.push_back(cur);
+      cur = make_int4((int)s, (int)s, (int)a0, (int)a0);
+    }
+    cur.y = (int)s + 1;
+    cur.w = (int)(a0 + nc);
+    p0 += npr;
+    a0 += nc;
+  }
+  c->chunks.push_back(cur);
+  c->has_basis = true;
+  c->has_mo = c->has_mo && c->mo_num > 0 && (int64_t)c->mo_coef.size() == c->mo_num * ao_num;
+  c->mo_dirty = true;
+  invalidate(c);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_mo_coefficient(qk_context c, int64_t mo_num, const double* coef) {
+  CHECK_CTX(c);
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "set the AO basis before the MOs");
+  if (!coef) return fail(c, QK_ERR_NULL_POINTER, "coef is NULL");
+  if (mo_num < 1 || mo_num > (1 << 24)) return fail(c, QK_ERR_BAD_SIZE, "mo_num must be >= 1");
+  for (int64_t i = 0; i < mo_num * c->ao_num; ++i)
+    if (!std::isfinite(coef[i])) return fail(c, QK_ERR_INVALID_ARG, "non-finite MO coefficient");
+  c->mo_num = mo_num;
+  c->mo_coef.assign(coef, coef + mo_num * c->ao_num);
+  c->has_mo = true;
+  c->mo_dirty = true;
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_points(qk_context c, char transp, int64_t walk_num, int64_t elec_num,
+                        const double* coord) {
+  CHECK_CTX(c);
+  if (!coord) return fail(c, QK_ERR_NULL_POINTER, "coord is NULL");
+  qk_status st = set_points_common(c, transp, walk_num, elec_num);
+  if (st) return st;
+  const int64_t n = c->point_num;
+  cudaError_t e = c->d_raw.ensure(sizeof(double) * 3 * n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_raw.p, coord, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = launch_points_soa((const double*)c->d_raw.p, transp, n, (double*)c->pdev.x,
+                          (double*)c->pdev.y, (double*)c->pdev.z, (float*)c->pdev.hi,
+                          (float*)c->pdev.lo, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_points");
+  c->has_points = true;
+  c->date++;
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_points_device(qk_context c, char transp, int64_t walk_num, int64_t elec_num,
+                               const double* dcoord) {
+  CHECK_CTX(c);
+  if (!dcoord) return fail(c, QK_ERR_NULL_POINTER, "dcoord is NULL");
+  qk_status st = set_points_common(c, transp, walk_num, elec_num);
+  if (st) return st;
+  TimedLaunch timer(c, 2);
+  cudaError_t e = launch_points_soa(dcoord, transp, c->point_num, (double*)c->pdev.x,
+                                    (double*)c->pdev.y, (double*)c->pdev.z, (float*)c->pdev.hi,
+                                    (float*)c->pdev.lo, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_points_device");
+  c->has_points = true;
+  c->date++;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_nucl_num(qk_context c, int64_t* n) {
+  CHECK_CTX(c);
+  if (!n) return QK_ERR_NULL_POINTER;
+  if (c->nucl_num == 0) return fail(c, QK_ERR_NOT_PROVIDED, "nuclei not set");
+  *n = c->nucl_num;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_ao_num(qk_context c, int64_t* n) {
+  CHECK_CTX(c);
+  if (!n) return QK_ERR_NULL_POINTER;
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "AO basis not set");
+  *n = c->ao_num;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_mo_num(qk_context c, int64_t* n) {
+  CHECK_CTX(c);
+  if (!n) return QK_ERR_NULL_POINTER;
+  if (!c->has_mo) return fail(c, QK_ERR_NOT_PROVIDED, "MO coefficients not set");
+  *n = c->mo_num;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_point_num(qk_context c, int64_t* n) {
+  CHECK_CTX(c);
+  if (!n) return QK_ERR_NULL_POINTER;
+  if (!c->has_points) return fail(c, QK_ERR_NOT_PROVIDED, "points not set");
+  *n = c->point_num;
+  return QK_SUCCESS;
+}
+
+qk_status qk_workspace_size(qk_context c, size_t* bytes) {
+  CHECK_CTX(c);
+  if (!bytes) return QK_ERR_NULL_POINTER;
+  qk_status st = require(c, false);
+  if (st) return st;
+  *bytes = ao_tensor_bytes(c, c->mode);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_workspace(qk_context c, void* dev, size_t bytes) {
+  CHECK_CTX(c);
+  if (dev && ((uintptr_t)dev % 256 != 0))
+    return fail(c, QK_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  c->ws_user = dev;
+  c->ws_user_bytes = dev ? bytes : 0;
+  if (dev) c->ws_own.release();
+  c->ao_date = ~0ull;  // cached AO tensor lived in the previous workspace
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_stream(qk_context c, void* stream) {
+  CHECK_CTX(c);
+  c->stream = (cudaStream_t)stream;
+  return QK_SUCCESS;
+}
+
+qk_status qk_synchronize(qk_context c) {
+  CHECK_CTX(c);
+  qk_status st = ensure_device(c);
+  if (st) return st;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  int flag = 0;
+  e = cudaMemcpy(&flag, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error flag read");
+  if (flag != 0) {
+    cudaMemset(c->d_flag.p, 0, sizeof(int));
+    return fail(c, QK_ERR_DEVICE_TIMEOUT, "a device-side wait gave up (code %d)", flag);
+  }
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_ao_vgl_device(qk_context c, void* dout, int64_t size) {
+  CHECK_CTX(c);
+  if (!dout) return fail(c, QK_ERR_NULL_POINTER, "dout is NULL");
+  qk_status st = require(c, false);
+  if (st) return st;
+  if (size < 5 * c->point_num * c->ao_num)
+    return fail(c, QK_ERR_BAD_SIZE, "output holds %lld elements, %lld needed", (long long)size,
+                (long long)(5 * c->point_num * c->ao_num));
+  st = ensure_tables(c);
+  if (st) return st;
+  AOTensor t{};
+  t.a = dout;
+  t.rows = 5 * c->point_num;
+  t.ld = c->ao_num;
+  const int m = c->mode == QK_FP64 ? QK_FP64 : QK_FP32;
+  cudaError_t e = launch_ao_vgl(c->bdev, c->pdev, m, t, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_ao_vgl(qk_context c, void* out, int64_t size) {
+  CHECK_CTX(c);
+  if (!out) return fail(c, QK_ERR_NULL_POINTER, "out is NULL");
+  qk_status st = require(c, false);
+  if (st) return st;
+  const int64_t n = 5 * c->point_num * c->ao_num;
+  if (size < n) return fail(c, QK_ERR_BAD_SIZE, "output too small");
+  const size_t es = c->mode == QK_FP64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = c->d_out.ensure(es * n);
+  if (e != cudaSuccess) return cuda_fail(c, e, "output staging");
+  st = qk_get_ao_vgl_device(c, c->d_out.p, n);
+  if (st) return st;
+  e = cudaMemcpyAsync(out, c->d_out.p, es * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_ao_vgl copy");
+  return qk_synchronize(c);
+}
+
+qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
+  CHECK_CTX(c);
+  if (!dout) return fail(c, QK_ERR_NULL_POINTER, "dout is NULL");
+  qk_status st = require(c, true);
+  if (st) return st;
+  const int64_t M = 5 * c->point_num, N = c->mo_num, K = c->ao_num;
+  if (size < M * N)
+    return fail(c, QK_ERR_BAD_SIZE, "output holds %lld elements, %lld needed", (long long)size,
+                (long long)(M * N));
+  st = ensure_mo(c);
+  if (st) return st;
+  AOTensor ao{};
+  st = provide_ao(c, &ao);
+  if (st) return st;
+  cudaError_t e = cudaSuccess;
+  TimedLaunch timer(c, 1);
+  switch (c->mode) {
+    case QK_FP64:
+      e = launch_gemm_f64(M, N, K, (const double*)ao.a, ao.ld, 1, c->c64, K, 1, (double*)dout, N,
+                          1, c->stream);
+      break;
+    case QK_FP32:
+      e = launch_gemm_f32(M, N, K, (const float*)ao.a, ao.ld, 1, c->c32, c->ldc, 1, (float*)dout,
+                          N, 1, c->stream);
+      break;
+    default: {
+      const bool split = c->mode == QK_BF16X3;
+      e = launch_mo_tc(c->mode, ao, K, split ? (const void*)c->c_hi : (const void*)c->c32,
+                       split ? (const void*)c->c_lo : nullptr, c->ldc, N, (float*)dout,
+                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "mo_vgl contraction");
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
+  CHECK_CTX(c);
+  if (!out) return fail(c, QK_ERR_NULL_POINTER, "out is NULL");
+  qk_status st = require(c, true);
+  if (st) return st;
+  const int64_t n = 5 * c->point_num * c->mo_num;
+  if (size < n) return fail(c, QK_ERR_BAD_SIZE, "output too small");
+  const size_t es = c->mode == QK_FP64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = c->d_out.ensure(es * n);
+  if (e != cudaSuccess) return cuda_fail(c, e, "output staging");
+  st = qk_get_mo_vgl_device(c, c->d_out.p, n);
+  if (st) return st;
+  e = cudaMemcpyAsync(out, c->d_out.p, es * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl copy");
+  return qk_synchronize(c);
+}
+
+qk_status qk_set_timing(qk_context c, int32_t enable) {
+  CHECK_CTX(c);
+  c->timing = enable != 0;
+  for (int k = 0; k < kTimerClasses; ++k) c->ev_used[k] = 0;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_timing(qk_context c, double* ms, int64_t* launches, int32_t n) {
+  CHECK_CTX(c);
+  if (!ms || !launches) return fail(c, QK_ERR_NULL_POINTER, "ms/launches is NULL");
+  if (n < 1 || n > kTimerClasses) return fail(c, QK_ERR_BAD_SIZE, "n must be in [1, 3]");
+  for (int k = 0; k < n; ++k) {
+    double tot = 0.0;
+    for (size_t i = 0; i < c->ev_used[k]; ++i) {
+      cudaError_t e = cudaEventSynchronize(c->ev_stop[k][i]);
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, c->ev_start[k][i], c->ev_stop[k][i]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "timing events");
+      tot += t;
+    }
+    ms[k] = tot;
+    launches[k] = (int64_t)c->ev_used[k];
+    c->ev_used[k] = 0;
+  }
+  return QK_SUCCESS;
+}
+
+qk_status qk_backward_workspace_size(qk_context c, size_t* bytes) {
+  CHECK_CTX(c);
+  if (!bytes) return QK_ERR_NULL_POINTER;
+  return fail(c, QK_ERR_NOT_IMPLEMENTED, "backward not built yet");
+}
+
+qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, double* d_dC,
+                                    double* d_dR) {
+  CHECK_CTX(c);
+  (void)dW;
+  (void)size;
+  (void)d_dC;
+  (void)d_dR;
+  return fail(c, QK_ERR_NOT_IMPLEMENTED, "backward not built yet");
+}
+
+}  // extern "C"

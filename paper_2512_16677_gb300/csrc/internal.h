@@ -1,0 +1,130 @@
+// internal.h -- declarations shared by the library's translation units.
+// Not part of the public ABI (include/qmckl_gpu.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qmckl_gpu.h"
+
+namespace qk {
+
+// Largest angular momentum handled by the kernels (f shells).
+constexpr int kMaxL = 3;
+// AOs per ao_vgl column chunk; chunks end on shell boundaries.
+constexpr int kChunkAO = 64;
+
+// Device-side basis tables, passed to kernels by value.  Every pointer
+// points into one allocation owned by the context.  Primitives of each
+// shell are sorted by ascending exponent.
+struct BasisDev {
+  int nucl_num, shell_num, ao_num, prim_num, nchunk;
+  const double* nucl_xyz;   // [nucl][3]
+  const float* nucl_hi;     // [nucl][3] float(x)
+  const float* nucl_lo;     // [nucl][3] float(x - float(x))
+  const int* shell_nuc;     // [shell]
+  const int* shell_l;       // [shell]
+  const int* shell_prim0;   // [shell] first primitive
+  const int* shell_nprim;   // [shell]
+  const int* shell_ao0;     // [shell] first AO
+  const double* shell_r2;   // [shell] T / gamma_min: r^2 at or beyond it screens every primitive
+  const float* shell_r2_f;  // [shell] same, rounded up to float
+  const double* prim_g;     // [prim] gamma
+  const double* prim_c;     // [prim] N_s * a * f
+  const float* prim_g_f;
+  const float* prim_c_f;
+  const double* ao_fac;     // [ao] M_n
+  const float* ao_fac_f;
+  const int* ao_shell;      // [ao] shell of each AO
+  const int4* chunk;        // [nchunk] (shell_begin, shell_end, ao_begin, ao_end)
+  double T;                 // Eq. 3 threshold on gamma r^2
+  float T_f;
+};
+
+// Points in structure-of-arrays form (device, library-owned).
+struct PointsDev {
+  int64_t n;
+  const double* x;  // [n] each
+  const double* y;
+  const double* z;
+  const float* hi;  // [3][n] float(x), float(y), float(z)
+  const float* lo;  // [3][n] residuals
+};
+
+// Layout of the AO tensor handed to the contraction: rows are (point,
+// component) pairs, row r = 5*p + c, ld elements apart; AOs contiguous.
+struct AOTensor {
+  void* a;       // FP64 / FP32 values, or bf16 "hi" plane
+  void* a_lo;    // bf16 "lo" plane (QK_BF16X3 only)
+  int64_t rows;  // 5 * point_num
+  int64_t ld;    // row stride in elements (multiple of 8)
+};
+
+// A device allocation owned by the library.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n);
+  void release();
+  ~DevBuf() { release(); }
+};
+
+// ---------------------------------------------------------------- kernels --
+// All launchers return the launch status (cudaGetLastError) and run on `s`.
+
+// AO vgl at every point.  out_mode: QK_FP64 -> double, QK_FP32/QK_TF32 ->
+// float, QK_BF16X3 -> bf16 hi/lo planes.
+cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
+                          const AOTensor& out, cudaStream_t s);
+
+// Point coordinates [n][3] ('N') or [3][n] ('T') -> SoA + hi/lo floats.
+cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double* x,
+                              double* y, double* z, float* hi, float* lo, cudaStream_t s);
+
+// Split an FP64 matrix [rows][cols] into bf16 hi and lo planes (ld columns,
+// padding zeroed), or convert it to FP32.
+cudaError_t launch_split_bf16(const double* src, int64_t rows, int64_t cols, int64_t ld,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, int64_t rows, int64_t cols, int64_t ld,
+                          float* dst, cudaStream_t s);
+
+// SIMT contraction D[M][N] = sum_k A[m][k] B[n][k] (FP32 or FP64), with
+// generic strides: element (m,k) of A at A[m*sam + k*sak], (n,k) of B at
+// B[n*sbn + k*sbk], D[m*ldd + n].  k_split > 1 writes k_split partial
+// results D + z*M*ldd.
+cudaError_t launch_gemm_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t sam,
+                            int64_t sak, const float* B, int64_t sbn, int64_t sbk, float* D,
+                            int64_t ldd, int k_split, cudaStream_t s);
+cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t sam,
+                            int64_t sak, const double* B, int64_t sbn, int64_t sbk, double* D,
+                            int64_t ldd, int k_split, cudaStream_t s);
+// Sum k_split partials [k_split][n] into dst (FP64 out).
+cudaError_t launch_reduce_partials_f32(const float* part, int k_split, int64_t n, double* dst,
+                                       cudaStream_t s);
+cudaError_t launch_reduce_partials_f64(const double* part, int k_split, int64_t n, double* dst,
+                                       cudaStream_t s);
+
+// tcgen05 contraction (QK_BF16X3 / QK_TF32): D[rows][mo] float.
+struct TcConfig {
+  int bn;      // MMA N per instruction (multiple of 16, <= 256)
+  int nsub;    // MMA instructions along N per CTA
+  int stages;  // shared-memory pipeline depth
+};
+cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
+                         const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
+                         const TcConfig& cfg, int* err_flag, cudaStream_t s);
+// Default tile configuration for a problem shape.
+TcConfig tc_default_config(int mode, int64_t mo_num);
+
+// Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
+// points, reduced into d_dR [nucl][3] (FP64).
+cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
+                              const void* abar, int64_t ld, double* partial, double* d_dR,
+                              cudaStream_t s);
+size_t adjoint_dR_partial_bytes(const BasisDev& b, int64_t point_num);
+
+}  // namespace qk

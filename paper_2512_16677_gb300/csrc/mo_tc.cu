@@ -1,0 +1,486 @@
+// mo_tc.cu -- MO contraction on the 5th-generation (tcgen05) tensor cores.
+//
+// Eqs. 5-7 of the QMCkl paper as one product over the concatenated
+// (point, component) rows (Sec. 3.2):  D[5P x N_mo] = AO[5P x N_ao] . C^T.
+//
+// Arithmetic:
+//   QK_BF16X3  AO and C are each split into bf16 hi + lo (x = hi + lo + r,
+//              |r| <= 2^-18 |x|) and D accumulates hi*hi + hi*lo + lo*hi in
+//              FP32 (tcgen05.mma kind::f16, bf16 inputs, f32 accumulator).
+//   QK_TF32    FP32 AO and C read as TF32 (kind::tf32), one product.
+//
+// Design: one CTA computes a 128-row x (NSUB*BN)-column tile of D.
+//   warp 4     TMA producer: 128B-swizzled K-major tiles of AO and C into a
+//              STAGES-deep shared-memory ring (mbarrier complete_tx).
+//   warp 5     allocates TMEM; one thread issues the MMAs for each stage and
+//              commits them to the stage's "empty" barrier.
+//   warps 0-3  epilogue: wait for the last commit, read the FP32 accumulator
+//              from TMEM (warp w owns TMEM lanes 32w..32w+31 = rows) and store
+//              row segments of D.
+// Every wait is bounded (clock64); a wait that gives up records a code in the
+// caller's error word, stops the pipeline, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+
+#include "internal.h"
+
+namespace qk {
+namespace {
+
+constexpr int kBM = 128;            // MMA M (TMEM lanes)
+constexpr int kRowBytes = 128;      // one K block = one 128-byte swizzle row
+constexpr int kUmmaKBytes = 32;     // bytes of K consumed by one MMA
+constexpr int kThreads = 192;       // 4 epilogue warps + producer + MMA
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+template <int MODE>
+struct TcTraits;
+template <>
+struct TcTraits<QK_BF16X3> {
+  static constexpr int kBK = 64;      // bf16 elements per K block
+  static constexpr int kPlanes = 2;   // hi and lo
+  static constexpr uint32_t kFmt = 1; // BF16
+};
+template <>
+struct TcTraits<QK_TF32> {
+  static constexpr int kBK = 32;
+  static constexpr int kPlanes = 1;
+  static constexpr uint32_t kFmt = 2; // TF32
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up or
+// another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), start address in 16-byte units; descriptor
+// version 1 (bits 46-47); layout type 2 = SWIZZLE_128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: f32 accumulator, A/B format, K-major A and B,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int m, int n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if constexpr (MODE == QK_BF16X3) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void flag_error(int* err_flag, volatile int* abort_flag, int code) {
+  *abort_flag = 1;
+  atomicCAS(err_flag, 0, code);
+}
+
+template <int BNT>
+constexpr uint32_t tmem_cols() {
+  return BNT <= 32 ? 32 : BNT <= 64 ? 64 : BNT <= 128 ? 128 : BNT <= 256 ? 256 : 512;
+}
+
+template <int MODE, int BN, int NSUB, int STAGES>
+struct TcShape {
+  using TR = TcTraits<MODE>;
+  static constexpr int BNT = BN * NSUB;
+  static constexpr uint32_t A_BYTES = kBM * kRowBytes;
+  static constexpr uint32_t B_BYTES = BNT * kRowBytes;
+  static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + B_BYTES);
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1);
+  static constexpr uint32_t TMEM_COLS = tmem_cols<BNT>();
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N must be 16..256, step 16");
+  static_assert(BNT <= 512, "accumulator exceeds TMEM");
+};
+
+template <int MODE, int BN, int NSUB, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    mo_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_a_lo,
+                 const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_b_lo,
+                 float* __restrict__ D, int64_t M, int64_t N, int num_kb, int64_t m_tiles,
+                 int* err_flag) {
+  using S = TcShape<MODE, BN, NSUB, STAGES>;
+  using TR = TcTraits<MODE>;
+  constexpr int BNT = S::BNT;
+  constexpr uint32_t idesc = make_idesc(TR::kFmt, kBM, BN);
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+  const uint32_t bar0 = base + STAGES * S::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  const uint32_t done_bar = bar0 + 8u * (2 * STAGES);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  volatile int* abort_v = &abort_flag;
+
+  // TMEM for the accumulator, once per CTA (no allocation after relinquish)
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  for (int64_t mt = blockIdx.y; mt < m_tiles; mt += gridDim.y) {
+    const int64_t m0 = mt * kBM;
+    const int n0 = blockIdx.x * BNT;
+    // barriers are (re)initialised per tile: every phase of the previous tile
+    // has completed once its epilogue passed the block barrier below
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(full_bar(s), 1);
+        mbar_init(empty_bar(s), 1);
+      }
+      mbar_init(done_bar, 1);
+      abort_flag = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 4 && lane == 0) {
+      // ------------------------------------------------ TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
+          flag_error(err_flag, abort_v, 1);
+          break;
+        }
+        const uint32_t st = base + s * S::STAGE_BYTES;
+        mbar_expect_tx(full_bar(s), S::STAGE_BYTES);
+        const int kc = kb * TR::kBK;
+        tma_load_2d(st, &tm_a, full_bar(s), kc, (int)m0);
+        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, &tm_a_lo, full_bar(s), kc, (int)m0);
+        const uint32_t bst = st + TR::kPlanes * S::A_BYTES;
+#pragma unroll
+        for (int j = 0; j < NSUB; ++j) {
+          tma_load_2d(bst + j * BN * kRowBytes, &tm_b, full_bar(s), kc, n0 + j * BN);
+          if constexpr (TR::kPlanes == 2)
+            tma_load_2d(bst + S::B_BYTES + j * BN * kRowBytes, &tm_b_lo, full_bar(s), kc,
+                        n0 + j * BN);
+        }
+        ++issued;
+      }
+      if (*abort_v) {
+        // drain: let the copies already issued land before the CTA leaves
+        const int first = issued > STAGES ? issued - STAGES : 0;
+        for (int kb = first; kb < issued; ++kb) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(full_bar(kb % STAGES), (uint32_t)(kb / STAGES) & 1u) &&
+                 clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    } else if (warp == 5 && lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(full_bar(s), ph, abort_v)) {
+          flag_error(err_flag, abort_v, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + s * S::STAGE_BYTES;
+        const uint32_t a_hi = st;
+        const uint32_t a_lo = st + S::A_BYTES;
+        const uint32_t b_hi = st + TR::kPlanes * S::A_BYTES;
+        const uint32_t b_lo = b_hi + S::B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
+          const uint32_t koff = kk * kUmmaKBytes;
+#pragma unroll
+          for (int j = 0; j < NSUB; ++j) {
+            const uint32_t d = tmem + j * BN;
+            const uint32_t boff = j * BN * kRowBytes + koff;
+            const uint32_t acc = (kb | kk) != 0;
+            umma<MODE>(d, sw128_desc(a_hi + koff), sw128_desc(b_hi + boff), idesc, acc);
+            if constexpr (MODE == QK_BF16X3) {
+              umma<MODE>(d, sw128_desc(a_hi + koff), sw128_desc(b_lo + boff), idesc, 1u);
+              umma<MODE>(d, sw128_desc(a_lo + koff), sw128_desc(b_hi + boff), idesc, 1u);
+            }
+          }
+        }
+        umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
+      }
+      umma_commit(done_bar);  // accumulator complete (also on abort: drains MMAs)
+    }
+
+    if (warp < 4) {
+      // ------------------------------------------------ epilogue
+      // wait for the final commit even after an abort, so that no MMA is
+      // still writing TMEM when it is freed
+      const long long t0 = clock64();
+      bool ok = true;
+      while (!mbar_try_wait(done_bar, 0)) {
+        if (clock64() - t0 > kWaitCycles) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) flag_error(err_flag, abort_v, 3);
+      ok = __all_sync(0xffffffffu, ok) && !*abort_v;
+      __syncwarp();
+      tc_fence_after();
+      if (ok) {
+        const int64_t row = m0 + warp * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        float* drow = D + row * N;
+        const bool vec = (N % 4) == 0;
+#pragma unroll 1
+        for (int c = 0; c < BNT; c += 16) {
+          float v[16];
+          tmem_ld16(tbase + c, v);
+          if (row < M) {
+            const int64_t n = n0 + c;
+            if (vec && n + 16 <= N) {
+              float4* p = reinterpret_cast<float4*>(drow + n);
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (n + q < N) drow[n + q] = v[q];
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_v) break;
+  }
+  if (warp == 5) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------------- host ---
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D tiled map over a row-major [outer][ld] matrix with `inner` valid
+// columns; box = box_inner x box_outer, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* m, const void* ptr, bool f32, int64_t inner, int64_t outer,
+              int64_t ld, int box_inner, int box_outer) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int es = f32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+             const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, int BN, int NSUB, int STAGES>
+cudaError_t launch_cfg(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                       int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
+  using S = TcShape<MODE, BN, NSUB, STAGES>;
+  using TR = TcTraits<MODE>;
+  static_assert(S::SMEM <= 232448, "shared memory budget");
+  const bool f32 = MODE == QK_TF32;
+  const int64_t M = ao.rows;
+  if (M == 0 || N == 0) return cudaSuccess;
+  if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
+  CUtensorMap ta, ta_lo, tb, tb_lo;
+  if (!make_map(&ta, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+  if (TR::kPlanes == 2) {
+    if (!make_map(&ta_lo, ao.a_lo, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&tb_lo, c_lo, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+  } else {
+    ta_lo = ta;
+    tb_lo = tb;
+  }
+  auto kern = mo_tc_kernel<MODE, BN, NSUB, STAGES>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  // TMEM is not oversubscribed: resident CTAs x columns <= 512
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, S::SMEM);
+  if (e != cudaSuccess) return e;
+  if (occ < 1 || occ * (int)S::TMEM_COLS > 512) return cudaErrorInvalidConfiguration;
+  const int num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
+  const int64_t m_tiles = (M + kBM - 1) / kBM;
+  const int64_t n_tiles = (N + S::BNT - 1) / S::BNT;
+  dim3 grid((unsigned)n_tiles, (unsigned)(m_tiles < 65535 ? m_tiles : 65535));
+  kern<<<grid, kThreads, S::SMEM, s>>>(ta, ta_lo, tb, tb_lo, out, M, N, num_kb, m_tiles,
+                                       err_flag);
+  return cudaGetLastError();
+}
+
+constexpr int stages_for(int mode, int bn) {
+  // fill ~220 KB of shared memory, at most 8 stages
+  return (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes)) > 8
+             ? 8
+             : (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes));
+}
+
+template <int MODE, int BN>
+cudaError_t launch_bn(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                      int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
+  constexpr int ST = stages_for(MODE, BN);
+  return launch_cfg<MODE, BN, 1, ST>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+}
+
+template <int MODE>
+cudaError_t launch_mode(const TcConfig& cfg, const AOTensor& ao, int64_t K, const void* c_hi,
+                        const void* c_lo, int64_t ldc, int64_t N, float* out, int* err_flag,
+                        cudaStream_t s) {
+  switch (cfg.bn) {
+    case 16: return launch_bn<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 32: return launch_bn<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 64: return launch_bn<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 96: return launch_bn<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 128: return launch_bn<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 160: return launch_bn<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 192: return launch_bn<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 256: return launch_bn<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+TcConfig tc_default_config(int mode, int64_t mo_num) {
+  (void)mode;
+  static const int bns[] = {16, 32, 64, 96, 128, 160, 192, 256};
+  const int64_t tiles = (mo_num + 255) / 256;
+  const int64_t per = (mo_num + tiles - 1) / tiles;
+  int bn = 256;
+  for (int b : bns)
+    if (b >= per) {
+      bn = b;
+      break;
+    }
+  return TcConfig{bn, 1, 0};
+}
+
+cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
+                         const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
+                         const TcConfig& cfg, int* err_flag, cudaStream_t s) {
+  if (mode == QK_BF16X3)
+    return launch_mode<QK_BF16X3>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, err_flag, s);
+  if (mode == QK_TF32)
+    return launch_mode<QK_TF32>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, err_flag, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qk

@@ -1,0 +1,328 @@
+"""Thin Python binding of the C ABI in include/qmckl_gpu.h.
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library ``libqmckl_gpu.so``.  Host arrays are numpy; device buffers and
+streams come from PyTorch (``tensor.data_ptr()``, ``stream.cuda_stream``).
+There is no CPU fallback: if the library is missing, loading it raises.
+
+Usage, following the paper's example (Sec. 5.1)::
+
+    ctx = Context(mode="bf16x3")
+    ctx.set_molecule(mol)              # nuclei, shells, primitives, MOs, cutoff
+    ctx.set_points_device(coord)       # [walk][elec][3] float64 CUDA tensor
+    out = ctx.mo_vgl_device()          # [walk][elec][5][mo] CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqmckl_gpu.so")
+
+QK_SUCCESS = 0
+STATUS_NAMES = {
+    0: "QK_SUCCESS", -1: "QK_ERR_INVALID_ARG", -2: "QK_ERR_NULL_POINTER",
+    -3: "QK_ERR_BAD_SIZE", -4: "QK_ERR_NOT_PROVIDED", -5: "QK_ERR_NOT_IMPLEMENTED",
+    -6: "QK_ERR_CUDA", -7: "QK_ERR_DEVICE_TIMEOUT", -8: "QK_ERR_OUT_OF_MEMORY",
+}
+MODES = {"fp64": 0, "fp32": 1, "bf16x3": 2, "tf32": 3}
+
+# every exported symbol with its ctypes signature (restype is qk_status unless noted)
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+SIGNATURES = {
+    "qk_context_create": [ctypes.POINTER(_P)],
+    "qk_context_destroy": [_P],
+    "qk_last_error": [_P, ctypes.c_char_p, _I64],
+    "qk_set_precision": [_P, _I32],
+    "qk_set_cutoff": [_P, _D],
+    "qk_set_compute_mode": [_P, _I32],
+    "qk_set_nucleus": [_P, _I64, _P, _P],
+    "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
+    "qk_set_mo_coefficient": [_P, _I64, _P],
+    "qk_set_points": [_P, ctypes.c_char, _I64, _I64, _P],
+    "qk_set_points_device": [_P, ctypes.c_char, _I64, _I64, _P],
+    "qk_get_nucl_num": [_P, ctypes.POINTER(_I64)],
+    "qk_get_ao_num": [_P, ctypes.POINTER(_I64)],
+    "qk_get_mo_num": [_P, ctypes.POINTER(_I64)],
+    "qk_get_point_num": [_P, ctypes.POINTER(_I64)],
+    "qk_workspace_size": [_P, ctypes.POINTER(_SZ)],
+    "qk_set_workspace": [_P, _P, _SZ],
+    "qk_set_stream": [_P, _P],
+    "qk_synchronize": [_P],
+    "qk_get_ao_vgl": [_P, _P, _I64],
+    "qk_get_ao_vgl_device": [_P, _P, _I64],
+    "qk_get_mo_vgl": [_P, _P, _I64],
+    "qk_get_mo_vgl_device": [_P, _P, _I64],
+    "qk_mo_vgl_backward_device": [_P, _P, _I64, _P, _P],
+    "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
+    "qk_set_timing": [_P, _I32],
+    "qk_get_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32],
+}
+
+_lib = None
+
+
+class QmcklError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with paper_2512_16677_gb300.build() "
+                "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int32
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One QMCkl-style context (not thread-safe; use one per thread)."""
+
+    def __init__(self, mode: str = "fp64"):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.qk_context_create(ctypes.byref(h))
+        if st != QK_SUCCESS:
+            raise QmcklError(st, "qk_context_create failed")
+        self.h = h
+        self._ws = None
+        self._keep = []
+        self._walk_elec_shape = (0, 0)
+        self.mode = mode
+        self.set_compute_mode(mode)
+
+    # ----------------------------------------------------------- plumbing
+    def _check(self, st: int, what: str):
+        if st != QK_SUCCESS:
+            buf = ctypes.create_string_buffer(512)
+            self.lib.qk_last_error(self.h, buf, 512)
+            raise QmcklError(st, f"{what}: {buf.value.decode(errors='replace')}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.qk_context_destroy(self.h)
+            self.h = ctypes.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ settings
+    def set_precision(self, bits: int):
+        self._check(self.lib.qk_set_precision(self.h, bits), "set_precision")
+
+    def set_cutoff(self, eps: float):
+        self._check(self.lib.qk_set_cutoff(self.h, eps), "set_cutoff")
+
+    def set_compute_mode(self, mode: str):
+        self._check(self.lib.qk_set_compute_mode(self.h, MODES[mode]), "set_compute_mode")
+        self.mode = mode
+
+    @property
+    def dtype_np(self):
+        return np.float64 if self.mode == "fp64" else np.float32
+
+    @property
+    def dtype_torch(self):
+        import torch
+        return torch.float64 if self.mode == "fp64" else torch.float32
+
+    # -------------------------------------------------------------- system
+    def set_nucleus(self, charge, coord):
+        charge, coord = _f64(charge), _f64(coord).reshape(-1, 3)
+        self._check(self.lib.qk_set_nucleus(self.h, charge.shape[0], _ptr(charge), _ptr(coord)),
+                    "set_nucleus")
+
+    def set_ao_basis(self, shell_nucleus, shell_ang_mom, shell_prim_num, shell_factor,
+                     exponent, coefficient, prim_factor, ao_factor):
+        sn = np.ascontiguousarray(shell_nucleus, dtype=np.int64)
+        sl = np.ascontiguousarray(shell_ang_mom, dtype=np.int32)
+        sp = np.ascontiguousarray(shell_prim_num, dtype=np.int64)
+        sf, ex, co, pf, af = map(_f64, (shell_factor, exponent, coefficient, prim_factor,
+                                        ao_factor))
+        self._check(self.lib.qk_set_ao_basis(
+            self.h, sn.shape[0], ex.shape[0], _ptr(sn), _ptr(sl), _ptr(sp), _ptr(sf), _ptr(ex),
+            _ptr(co), _ptr(pf), af.shape[0], _ptr(af)), "set_ao_basis")
+
+    def set_mo_coefficient(self, C):
+        C = _f64(C)
+        self._check(self.lib.qk_set_mo_coefficient(self.h, C.shape[0], _ptr(C)),
+                    "set_mo_coefficient")
+
+    def set_molecule(self, mol, points: bool = False):
+        """Nuclei, basis, MO coefficients and cutoff of a synth.Molecule."""
+        self.set_nucleus(mol.nucl_charge, mol.nucl_coord)
+        self.set_ao_basis(mol.shell_nucleus, mol.shell_ang_mom, mol.shell_prim_num,
+                          mol.shell_factor, mol.exponent, mol.coefficient, mol.prim_factor,
+                          mol.ao_factor)
+        self.set_mo_coefficient(mol.mo_coef)
+        if getattr(mol, "eps", None) is not None:
+            self.set_cutoff(mol.eps)
+        else:
+            self.set_precision(int(mol.bits))
+        if points:
+            self.set_points(mol.coord)
+
+    # -------------------------------------------------------------- points
+    def set_points(self, coord, transp: str = "N"):
+        """Host coordinates [walk][elec][3] ('N') or [3][walk*elec] ('T')."""
+        c = _f64(coord)
+        if transp == "N":
+            c3 = c.reshape(-1, c.shape[-2], 3) if c.ndim == 3 else c.reshape(1, -1, 3)
+            w, e = c3.shape[0], c3.shape[1]
+        else:
+            w, e = 1, c.size // 3
+        self._check(self.lib.qk_set_points(self.h, transp.encode(), w, e, _ptr(c)), "set_points")
+        self._walk_elec_shape = (w, e)
+
+    def set_points_device(self, coord, transp: str = "N", walk_num=None, elec_num=None):
+        """CUDA float64 tensor [walk][elec][3] (or [3][n] with transp='T')."""
+        self._bind_stream()
+        if walk_num is None:
+            if transp == "N":
+                walk_num, elec_num = (coord.shape[0], coord.shape[1]) if coord.dim() == 3 \
+                    else (1, coord.shape[0])
+            else:
+                walk_num, elec_num = 1, coord.numel() // 3
+        assert coord.is_cuda and coord.is_contiguous() and str(coord.dtype) == "torch.float64"
+        self._keep = [coord]
+        self._check(self.lib.qk_set_points_device(self.h, transp.encode(), walk_num, elec_num,
+                                                  _tptr(coord)), "set_points_device")
+        self._walk_elec_shape = (walk_num, elec_num)
+
+    # --------------------------------------------------------------- sizes
+    def _get_i64(self, fn, what):
+        v = ctypes.c_int64()
+        self._check(fn(self.h, ctypes.byref(v)), what)
+        return v.value
+
+    @property
+    def nucl_num(self):
+        return self._get_i64(self.lib.qk_get_nucl_num, "get_nucl_num")
+
+    @property
+    def ao_num(self):
+        return self._get_i64(self.lib.qk_get_ao_num, "get_ao_num")
+
+    @property
+    def mo_num(self):
+        return self._get_i64(self.lib.qk_get_mo_num, "get_mo_num")
+
+    @property
+    def point_num(self):
+        return self._get_i64(self.lib.qk_get_point_num, "get_point_num")
+
+    # ----------------------------------------------------- device plumbing
+    def _bind_stream(self):
+        import torch
+        self._check(self.lib.qk_set_stream(self.h, ctypes.c_void_p(
+            torch.cuda.current_stream().cuda_stream)), "set_stream")
+
+    def workspace_size(self) -> int:
+        v = ctypes.c_size_t()
+        self._check(self.lib.qk_workspace_size(self.h, ctypes.byref(v)), "workspace_size")
+        return v.value
+
+    def ensure_workspace(self, extra: int = 0):
+        """Caller-owned workspace from the torch allocator (grown as needed)."""
+        import torch
+        need = self.workspace_size() + extra
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            off = (-base) % 256
+            self._check(self.lib.qk_set_workspace(self.h, ctypes.c_void_p(base + off),
+                                                  need + 256 - off), "set_workspace")
+        return self._ws
+
+    def set_timing(self, enable: bool):
+        self._check(self.lib.qk_set_timing(self.h, 1 if enable else 0), "set_timing")
+
+    def get_timing(self):
+        """(ms per class, launches per class) for ao_vgl, contraction, other."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        self._check(self.lib.qk_get_timing(self.h, ms, n, 3), "get_timing")
+        return list(ms), list(n)
+
+    def synchronize(self):
+        self._check(self.lib.qk_synchronize(self.h), "synchronize")
+
+    # ------------------------------------------------------------ evaluate
+    def mo_vgl_device(self, out=None):
+        """MO vgl [walk][elec][5][mo] as a CUDA tensor (async on torch's stream)."""
+        import torch
+        self._bind_stream()
+        self.ensure_workspace()
+        w, e = self._walk_elec()
+        if out is None:
+            out = torch.empty((w, e, 5, self.mo_num), dtype=self.dtype_torch, device="cuda")
+        self._check(self.lib.qk_get_mo_vgl_device(self.h, _tptr(out), out.numel()),
+                    "get_mo_vgl_device")
+        return out
+
+    def ao_vgl_device(self, out=None):
+        import torch
+        self._bind_stream()
+        w, e = self._walk_elec()
+        if out is None:
+            out = torch.empty((w, e, 5, self.ao_num), dtype=self.dtype_torch, device="cuda")
+        self._check(self.lib.qk_get_ao_vgl_device(self.h, _tptr(out), out.numel()),
+                    "get_ao_vgl_device")
+        return out
+
+    def mo_vgl(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """MO vgl into host memory (blocking)."""
+        n = self.point_num * 5 * self.mo_num
+        if out is None:
+            out = np.empty(n, dtype=self.dtype_np)
+        self._check(self.lib.qk_get_mo_vgl(self.h, _ptr(out), out.size), "get_mo_vgl")
+        return out.reshape(self.point_num, 5, self.mo_num)
+
+    def ao_vgl(self) -> np.ndarray:
+        n = self.point_num * 5 * self.ao_num
+        out = np.empty(n, dtype=self.dtype_np)
+        self._check(self.lib.qk_get_ao_vgl(self.h, _ptr(out), out.size), "get_ao_vgl")
+        return out.reshape(self.point_num, 5, self.ao_num)
+
+    def _walk_elec(self):
+        return self._walk_elec_shape

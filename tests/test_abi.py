@@ -1,0 +1,120 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol include/qmckl_gpu.h declares; host-side validation of the setters
+runs without touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_16677_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qmckl_gpu.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_16677_gb300 import buildlib, qmckl
+    buildlib.build()
+    return qmckl.load()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\bqk_status\s+(qk_\w+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in the header but not exported"
+
+
+def test_binding_covers_header():
+    from paper_2512_16677_gb300 import qmckl
+    assert set(_declared()) <= set(qmckl.SIGNATURES), \
+        set(_declared()) - set(qmckl.SIGNATURES)
+
+
+def _ctx():
+    from paper_2512_16677_gb300 import qmckl
+    return qmckl.Context("fp64")
+
+
+def test_null_and_status_codes(lib):
+    assert lib.qk_context_destroy(None) == -2
+    assert lib.qk_set_precision(None, 53) == -2
+    from paper_2512_16677_gb300 import qmckl
+    c = _ctx()
+    for bad in (1, 54):
+        with pytest.raises(qmckl.QmcklError) as e:
+            c.set_precision(bad)
+        assert e.value.status == -1
+    with pytest.raises(qmckl.QmcklError) as e:
+        c.set_cutoff(0.0)
+    assert e.value.status == -1
+    with pytest.raises(qmckl.QmcklError) as e:
+        c.lib.qk_set_compute_mode(c.h, 7) and c._check(c.lib.qk_set_compute_mode(c.h, 7), "m")
+    assert e.value.status == -1
+
+
+def test_setter_order_and_validation():
+    from paper_2512_16677_gb300 import qmckl
+    m = synth.make_config(1, walk_num=1)
+    c = _ctx()
+    with pytest.raises(qmckl.QmcklError) as e:      # basis before nuclei
+        c.set_ao_basis(m.shell_nucleus, m.shell_ang_mom, m.shell_prim_num, m.shell_factor,
+                       m.exponent, m.coefficient, m.prim_factor, m.ao_factor)
+    assert e.value.status == -4
+    c.set_nucleus(m.nucl_charge, m.nucl_coord)
+    bad = m.nucl_coord.copy()
+    bad[1, 2] = np.nan
+    with pytest.raises(qmckl.QmcklError) as e:
+        c.set_nucleus(m.nucl_charge, bad)
+    assert e.value.status == -1
+    with pytest.raises(qmckl.QmcklError) as e:      # MOs before basis
+        c.set_mo_coefficient(m.mo_coef)
+    assert e.value.status == -4
+
+    def basis(**over):
+        kw = dict(shell_nucleus=m.shell_nucleus, shell_ang_mom=m.shell_ang_mom,
+                  shell_prim_num=m.shell_prim_num, shell_factor=m.shell_factor,
+                  exponent=m.exponent, coefficient=m.coefficient, prim_factor=m.prim_factor,
+                  ao_factor=m.ao_factor)
+        kw.update(over)
+        c.set_ao_basis(**kw)
+
+    cases = [
+        (dict(shell_nucleus=m.shell_nucleus + 5), -1),                  # nucleus out of range
+        (dict(exponent=-m.exponent), -1),                               # gamma <= 0
+        (dict(ao_factor=m.ao_factor[:-1]), -3),                         # ao_num mismatch
+        (dict(shell_ang_mom=np.where(m.shell_ang_mom == 2, 4, m.shell_ang_mom)), -5),  # g shell
+    ]
+    for over, code in cases:
+        with pytest.raises(qmckl.QmcklError) as e:
+            basis(**over)
+        assert e.value.status == code, (over.keys(), e.value)
+    basis()
+    assert c.ao_num == m.ao_num
+    c.set_mo_coefficient(m.mo_coef)
+    assert c.mo_num == m.mo_num
+    with pytest.raises(qmckl.QmcklError) as e:      # nothing evaluated without points
+        c.workspace_size()
+    assert e.value.status == -4
+    c.close()
+
+
+def test_last_error_truncates(lib):
+    from paper_2512_16677_gb300 import qmckl
+    c = _ctx()
+    try:
+        c.set_precision(99)
+    except qmckl.QmcklError:
+        pass
+    buf = ctypes.create_string_buffer(8)
+    assert lib.qk_last_error(c.h, buf, 8) == 0
+    assert len(buf.value) == 7
+    assert lib.qk_last_error(c.h, buf, 0) == -3

@@ -1,0 +1,200 @@
+"""GPU parity of the forward AO/MO vgl path against the FP64 CPU oracle.
+
+Every test calls the CUDA library through its C ABI (ctypes binding) and
+compares with the oracle element by element with the normwise metric of
+tests/tolerances.py.  Small cases span several tiles and ragged tails in
+every dimension; the full organic workload (600 e- x 256 walkers, 300 MOs,
+1650 AOs) runs in the benchmark's launch configuration and is checked on
+sampled points.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2512_16677_gb300 import synth
+from tolerances import TOL, assert_within, component_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODES = ["fp64", "fp32", "bf16x3", "tf32"]
+REPORT = os.environ.get("QK_PARITY_REPORT")
+
+
+def _report(name, mode, errs):
+    if REPORT:
+        with open(REPORT, "a") as f:
+            f.write(json.dumps({"case": name, "mode": mode, "value": errs[0],
+                                "gradient": errs[1], "laplacian": errs[2]}) + "\n")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2512_16677_gb300 import buildlib
+    buildlib.build()
+
+
+def _ctx(mol, mode):
+    from paper_2512_16677_gb300 import qmckl
+    c = qmckl.Context(mode)
+    c.set_molecule(mol)
+    c.set_points_device(torch.from_numpy(mol.coord).cuda())
+    return c
+
+
+def _run(mol, mode):
+    from paper_2512_16677_gb300 import qmckl
+    c = _ctx(mol, mode)
+    try:
+        out = c.mo_vgl_device()
+    except qmckl.QmcklError as e:
+        if e.status == -5:
+            pytest.skip(f"{mode} not built: {e}")
+        raise
+    torch.cuda.synchronize()
+    c.synchronize()
+    return c, out.double().cpu().numpy().reshape(-1, 5, mol.mo_num)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_water_all_points(orc, cfg, mode):
+    """Water: all 640 points, 25 AOs, 5 MOs."""
+    m = cfg(1)
+    ref, size = orc.mo_vgl(m)
+    _, got = _run(m, mode)
+    _report("water", mode, assert_within(mode, got, ref, size, "water"))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_water_ao_vgl(orc, cfg, mode):
+    """AO tensor itself (qk_get_ao_vgl_device) against the oracle's AOs."""
+    m = cfg(1)
+    ref, size = orc.ao_vgl(m)
+    c = _ctx(m, mode)
+    ao = c.ao_vgl_device()
+    torch.cuda.synchronize()
+    got = ao.double().cpu().numpy().reshape(ref.shape)
+    errs = assert_within(mode, got, ref, size, "water AO")
+    _report("water_ao", mode, errs)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_chain_two_walkers(orc, cfg, mode):
+    """C/H chain, 2 walkers x 200 e- (400 points), 500 AOs, 100 MOs: several
+    tiles along points, AOs and MOs, with ragged tails in each."""
+    m = cfg(3, walk_num=2)
+    ref, size = orc.mo_vgl(m)
+    _, got = _run(m, mode)
+    _report("chain50_2w", mode, assert_within(mode, got, ref, size, "chain"))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_organic_one_walker(orc, cfg, mode):
+    """Organic chain, 1 walker (600 points), 1650 AOs up to f, 300 MOs,
+    eps = 1e-10 cutoff."""
+    m = cfg(2, walk_num=1)
+    pts = m.points[::3]          # 200 points, still ragged against every tile
+    mm = m.with_points(pts)
+    ref, size = orc.mo_vgl(mm)
+    _, got = _run(mm, mode)
+    _report("organic150_1w", mode, assert_within(mode, got, ref, size, "organic"))
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "fp32", "fp64"])
+def test_organic_full_size_sampled(orc, cfg, mode):
+    """Full benchmark workload (153 600 points), sampled outputs."""
+    m = cfg(2)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(m.point_num, 96, replace=False))
+    idx[0], idx[-1] = 0, m.point_num - 1          # first and last rows of the launch
+    ref, size = orc.mo_vgl(m, points=m.points[idx])
+    c, got = _run(m, mode)
+    errs = assert_within(mode, got[idx], ref, size, "organic full")
+    _report("organic150_full_sampled", mode, errs)
+    assert np.all(np.isfinite(got))
+
+
+def test_edge_single_point_and_far_points(orc, cfg):
+    """One point; points far from every nucleus give exact zeros."""
+    m = cfg(1)
+    one = m.with_points(m.points[:1])
+    ref, size = orc.mo_vgl(one)
+    _, got = _run(one, "fp64")
+    assert_within("fp64", got, ref, size, "single point")
+    far = m.with_points(np.array([[80.0, 0.0, 0.0], [0.0, -95.0, 3.0], [1e3, 1e3, 1e3]]))
+    for mode in ("fp64", "fp32"):
+        _, got = _run(far, mode)
+        assert np.all(got == 0.0)
+
+
+def test_transposed_points_and_host_api(orc, cfg):
+    """'T' layout and the host-memory calls give the device results."""
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(3, walk_num=1)
+    c, dev = _run(m, "fp64")
+    c2 = qmckl.Context("fp64")
+    c2.set_molecule(m)
+    c2.set_points(np.ascontiguousarray(m.points.T), transp="T")
+    host = c2.mo_vgl()
+    np.testing.assert_array_equal(host, dev)
+    ao = c2.ao_vgl()
+    ref, size = orc.ao_vgl(m)
+    assert_within("fp64", ao, ref, size, "host ao")
+
+
+def test_memoisation_and_time_stamp(cfg):
+    """Same time stamp: the AO tensor is reused (one ao_vgl launch); new
+    points bump the stamp and the result changes."""
+    m = cfg(1)
+    c = _ctx(m, "fp32")
+    c.set_timing(True)
+    a = c.mo_vgl_device().clone()
+    b = c.mo_vgl_device().clone()
+    torch.cuda.synchronize()
+    ms, n = c.get_timing()
+    assert n[0] == 1 and n[1] == 2
+    assert torch.equal(a, b)
+    c.set_points_device(torch.from_numpy(m.coord[::-1].copy()).cuda())
+    d = c.mo_vgl_device()
+    torch.cuda.synchronize()
+    assert not torch.equal(a, d)
+    ms, n = c.get_timing()
+    assert n[0] == 1
+
+
+def test_errors_on_device_calls(cfg):
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(1, walk_num=1)
+    c = _ctx(m, "fp64")
+    small = torch.empty(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(qmckl.QmcklError) as e:
+        c.lib.qk_get_mo_vgl_device(c.h, small.data_ptr(), 10) and \
+            c._check(c.lib.qk_get_mo_vgl_device(c.h, small.data_ptr(), 10), "x")
+    assert e.value.status == -3
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    c._check(c.lib.qk_set_workspace(c.h, ws.data_ptr(), 1024), "ws")
+    with pytest.raises(qmckl.QmcklError) as e:
+        out = torch.empty(m.point_num * 5 * m.mo_num, dtype=torch.float64, device="cuda")
+        c._check(c.lib.qk_get_mo_vgl_device(c.h, out.data_ptr(), out.numel()), "x")
+    assert e.value.status == -3
+
+
+def test_primitive_order_invariance_gpu(cfg):
+    """The library sorts primitives itself: permuted input, same FP64 output."""
+    m = cfg(1, walk_num=4)
+    rng = np.random.default_rng(8)
+    perm, start = [], 0
+    for npr in m.shell_prim_num:
+        perm.extend((start + rng.permutation(int(npr))).tolist())
+        start += int(npr)
+    perm = np.array(perm)
+    m2 = synth.Molecule(**{**m.__dict__, "exponent": m.exponent[perm],
+                           "coefficient": m.coefficient[perm],
+                           "prim_factor": m.prim_factor[perm]})
+    _, a = _run(m, "fp64")
+    _, b = _run(m2, "fp64")
+    np.testing.assert_array_equal(a, b)
