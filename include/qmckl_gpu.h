@@ -196,6 +196,18 @@ qk_status qk_get_mo_vgl(qk_context ctx, void* out, int64_t size);
    it and runs only the contraction (Sec. 2.2). */
 qk_status qk_get_mo_vgl_device(qk_context ctx, void* dout, int64_t size);
 
+/* The contraction of Eqs. 5-7 on a caller-supplied tensor, without a
+   context: D[m][n] = sum_k A[m][k] B[n][k], A [M][K], B [N][K], D [M][N]
+   row-major in device memory; double in QK_FP64 mode, float otherwise.
+   mode selects the kernel (QK_BF16X3 splits A and B into bf16 hi/lo planes
+   first).  Runs on `stream` (a cudaStream_t, NULL = legacy default);
+   tensor-core modes synchronise the stream to read the device error word.
+   Scratch is library-owned and shared by all calls: not thread-safe.
+   Errors: QK_ERR_NULL_POINTER, QK_ERR_BAD_SIZE (K < 1 or a negative size),
+   QK_ERR_INVALID_ARG (mode), QK_ERR_DEVICE_TIMEOUT, QK_ERR_CUDA. */
+qk_status qk_contract_device(int32_t mode, int64_t M, int64_t N, int64_t K, const void* A,
+                             const void* B, void* D, void* stream);
+
 /* ------------------------------------------------------------ adjoint --- */
 
 /* Gradients of L = sum_{p,c,i} W[p][c][i] * mo_vgl[p][c][i] at the current

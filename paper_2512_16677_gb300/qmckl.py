@@ -64,6 +64,7 @@ SIGNATURES = {
     "qk_mo_vgl_backward_device": [_P, _P, _I64, _P, _P],
     "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "qk_set_timing": [_P, _I32],
+    "qk_contract_device": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
     "qk_get_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32],
 }
 
@@ -103,6 +104,23 @@ def _ptr(a):
 
 def _tptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def contract_device(A, B, mode: str = "fp32", out=None):
+    """D = A @ B.T on the GPU with the kernel of `mode` (CUDA tensors)."""
+    import torch
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    dt = torch.float64 if mode == "fp64" else torch.float32
+    assert A.dtype == dt and B.dtype == dt and A.is_contiguous() and B.is_contiguous()
+    if out is None:
+        out = torch.empty((M, N), dtype=dt, device=A.device)
+    st = lib.qk_contract_device(MODES[mode], M, N, K, _tptr(A), _tptr(B), _tptr(out),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != QK_SUCCESS:
+        raise QmcklError(st, "qk_contract_device")
+    return out
 
 
 class Context:
