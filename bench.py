@@ -45,6 +45,8 @@ def parse_args():
                     help="skip the plain FP32 path measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--walkers", type=int, default=None,
+                    help="fewer walkers than the workload's 256 (profiling captures only)")
     return ap.parse_args()
 
 
@@ -187,7 +189,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist  # noqa: F811
-    mol = synth.make_config(2)
+    mol = synth.make_config(2, walk_num=args.walkers)
     peaks, peak_src = load_peaks()
     coords = torch.from_numpy(mol.coord).cuda()
     g = torch.Generator(device="cpu").manual_seed(1234 + rank)
@@ -249,7 +251,9 @@ def run_ours(args, rank, world, local_rank):
         "dtype": {"bf16x3": "bf16x3 (f32 accum)", "tf32": "tf32 (f32 accum)", "fp32": "f32",
                   "fp64": "f64"}[args.mode],
         "data": "synthetic (seeded organic-chain molecule, random MO coefficients)",
-        "config": {"workload": WORKLOAD, "mode": args.mode, "points": mol.point_num,
+        "config": {"workload": WORKLOAD if args.walkers is None else
+                   WORKLOAD.replace("x 256 walkers", f"x {mol.walk_num} walkers"),
+                   "mode": args.mode, "points": mol.point_num,
                    "ao_num": mol.ao_num, "mo_num": mol.mo_num,
                    "l2": "inputs larger than L2 (AO tensor %.2f GB per step)" % (
                        5 * mol.point_num * mol.ao_num * 4 / 1e9),
