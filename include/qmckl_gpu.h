@@ -208,6 +208,28 @@ qk_status qk_get_mo_vgl_device(qk_context ctx, void* dout, int64_t size);
 qk_status qk_contract_device(int32_t mode, int64_t M, int64_t N, int64_t K, const void* A,
                              const void* B, void* D, void* stream);
 
+/* Allocation-free variant of qk_contract_device for the tensor-core modes.
+   The paper has no counterpart: this entry point exists for callers that
+   cannot call cudaMalloc (a framework or memory pool owns the device memory
+   budget, a latency-critical loop cannot take the synchronisation that
+   cudaMalloc/cudaFree imply, or the caller must not fail for lack of memory
+   once started).  Same arguments and result as qk_contract_device, with
+   mode QK_BF16X3 or QK_TF32 (else QK_ERR_INVALID_ARG) and float data.
+   Scratch: a fixed 32 MiB device array inside the library, which every GPU
+   that loads the library holds until the process exits.  Limit:
+     256 + planes * (round256(M*ld*es) + round256(N*ld*es)) <= 32 MiB,
+   ld = K rounded up to a multiple of 8; bf16x3: planes 2, es 2; tf32:
+   planes 1, es 4; so about (M + N) * ld <= 8.38e6.  Larger problems are
+   refused with QK_ERR_BAD_SIZE before any work is queued.
+   The first call on a device looks up the array's device address (once per
+   device, with that device current); make that first call before any stream
+   capture.  All calls share the one array and it keeps the previous call's
+   contents (the error word is cleared on every call): calls that overlap on
+   the GPU race, so serialise them (one stream, or events).  Synchronises
+   `stream` to read the error word.  Allocates no device or host memory. */
+qk_status qk_contract_device_noalloc(int32_t mode, int64_t M, int64_t N, int64_t K,
+                                     const float* A, const float* B, float* D, void* stream);
+
 /* ------------------------------------------------------------ adjoint --- */
 
 /* Gradients of L = sum_{p,c,i} W[p][c][i] * mo_vgl[p][c][i] at the current

@@ -65,6 +65,7 @@ SIGNATURES = {
     "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "qk_set_timing": [_P, _I32],
     "qk_contract_device": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
+    "qk_contract_device_noalloc": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
     "qk_get_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32],
 }
 
