@@ -287,23 +287,31 @@ static void init_adj_orders(void) {
  * and since an AO on A depends on r - R_A only, d/dR_Aj = -d/dr_j:
  *   c = value -> -d_j chi; c = d_i -> -d_j d_i chi; c = lap -> -d_j lap chi.
  * W [n][5][mo]; dC [mo][ao]; dR [nucl][3].  Either output may be NULL.
+ * dC_size, dR_size (optional, same shapes): the same sums with every factor
+ * replaced by the absolute size of its terms (|W|, sum_i |W||C| for Abar,
+ * and the term-wise size of each AO derivative): the scale against which a
+ * rounding error of the sum is measured.
  */
 int oracle_adjoint(const oracle_basis_t* b, double T, int64_t mo_num, const double* C,
                    int64_t n, const double* coord, const double* W,
-                   double* dC, double* dR) {
+                   double* dC, double* dR, double* dC_size, double* dR_size) {
   int rc = check_basis(b);
   if (rc) return rc;
   init_adj_orders();
   const int64_t na = b->ao_num;
   double* d = (double*)malloc(sizeof(double) * 20 * (size_t)(na ? na : 1));
+  double* z = (double*)malloc(sizeof(double) * 20 * (size_t)(na ? na : 1));
   double* abar = (double*)malloc(sizeof(double) * 5 * (size_t)(na ? na : 1));
+  double* abar_sz = (double*)malloc(sizeof(double) * 5 * (size_t)(na ? na : 1));
   dot2_t* accC = dC ? (dot2_t*)calloc((size_t)mo_num * (na ? na : 1), sizeof(dot2_t)) : NULL;
   dot2_t* accR = (dot2_t*)calloc((size_t)3 * (b->nucl_num ? b->nucl_num : 1), sizeof(dot2_t));
   int64_t* ao_nuc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(na ? na : 1));
-  if (!d || !abar || (dC && !accC) || !accR || !ao_nuc) {
-    free(d); free(abar); free(accC); free(accR); free(ao_nuc);
+  if (!d || !z || !abar || !abar_sz || (dC && !accC) || !accR || !ao_nuc) {
+    free(d); free(z); free(abar); free(abar_sz); free(accC); free(accR); free(ao_nuc);
     return -9;
   }
+  if (dC_size) memset(dC_size, 0, sizeof(double) * (size_t)mo_num * na);
+  if (dR_size) memset(dR_size, 0, sizeof(double) * 3 * (size_t)b->nucl_num);
   {
     int64_t ao0 = 0;
     for (int64_t s = 0; s < b->shell_num; ++s) {
@@ -313,24 +321,35 @@ int oracle_adjoint(const oracle_basis_t* b, double T, int64_t mo_num, const doub
     }
   }
   for (int64_t p = 0; p < n; ++p) {
-    ao_derivs_point(b, T, coord + 3 * p, 20, (const int (*)[3])ADJ_ORDERS, d, NULL);
+    ao_derivs_point(b, T, coord + 3 * p, 20, (const int (*)[3])ADJ_ORDERS, d, z);
     const double* w = W + (size_t)p * 5 * mo_num;
     /* AO vgl at this point, component c, AO k: from the derivative table */
 #define DV(ix, iy, iz, k) d[(size_t)order_index(ix, iy, iz) * na + (k)]
+#define DZ(ix, iy, iz, k) z[(size_t)order_index(ix, iy, iz) * na + (k)]
     for (int64_t k = 0; k < na; ++k) {
-      double ao_c[5];
+      double ao_c[5], ao_z[5];
       ao_c[0] = DV(0, 0, 0, k);
       ao_c[1] = DV(1, 0, 0, k);
       ao_c[2] = DV(0, 1, 0, k);
       ao_c[3] = DV(0, 0, 1, k);
       ao_c[4] = DV(2, 0, 0, k) + DV(0, 2, 0, k) + DV(0, 0, 2, k);
+      ao_z[0] = DZ(0, 0, 0, k);
+      ao_z[1] = DZ(1, 0, 0, k);
+      ao_z[2] = DZ(0, 1, 0, k);
+      ao_z[3] = DZ(0, 0, 1, k);
+      ao_z[4] = DZ(2, 0, 0, k) + DZ(0, 2, 0, k) + DZ(0, 0, 2, k);
       for (int c = 0; c < 5; ++c) {
         dot2_t acc = {0.0, 0.0};
+        double asz = 0.0;
         for (int64_t i = 0; i < mo_num; ++i) {
-          dot2_add(&acc, w[(size_t)c * mo_num + i], C[(size_t)i * na + k]);
-          if (accC) dot2_add(&accC[(size_t)i * na + k], w[(size_t)c * mo_num + i], ao_c[c]);
+          const double wv = w[(size_t)c * mo_num + i];
+          dot2_add(&acc, wv, C[(size_t)i * na + k]);
+          asz += fabs(wv) * fabs(C[(size_t)i * na + k]);
+          if (accC) dot2_add(&accC[(size_t)i * na + k], wv, ao_c[c]);
+          if (dC_size) dC_size[(size_t)i * na + k] += fabs(wv) * ao_z[c];
         }
         abar[(size_t)c * na + k] = dot2_value(&acc);
+        abar_sz[(size_t)c * na + k] = asz;
       }
     }
     if (dR) {
@@ -347,16 +366,27 @@ int oracle_adjoint(const oracle_basis_t* b, double T, int64_t mo_num, const doub
           g[4] = DV(2 + e[0], e[1], e[2], k) + DV(e[0], 2 + e[1], e[2], k) +
                  DV(e[0], e[1], 2 + e[2], k);
           for (int c = 0; c < 5; ++c) dot2_add(&accR[3 * A + j], -abar[(size_t)c * na + k], g[c]);
+          if (dR_size) {
+            double gz[5];
+            gz[0] = DZ(e[0], e[1], e[2], k);
+            gz[1] = DZ(1 + e[0], e[1], e[2], k);
+            gz[2] = DZ(e[0], 1 + e[1], e[2], k);
+            gz[3] = DZ(e[0], e[1], 1 + e[2], k);
+            gz[4] = DZ(2 + e[0], e[1], e[2], k) + DZ(e[0], 2 + e[1], e[2], k) +
+                    DZ(e[0], e[1], 2 + e[2], k);
+            for (int c = 0; c < 5; ++c) dR_size[3 * A + j] += abar_sz[(size_t)c * na + k] * gz[c];
+          }
         }
       }
     }
 #undef DV
+#undef DZ
   }
   if (dC)
     for (size_t t = 0; t < (size_t)mo_num * na; ++t) dC[t] = dot2_value(&accC[t]);
   if (dR)
     for (int64_t t = 0; t < 3 * b->nucl_num; ++t) dR[t] = dot2_value(&accR[t]);
-  free(d); free(abar); free(accC); free(accR); free(ao_nuc);
+  free(d); free(z); free(abar); free(abar_sz); free(accC); free(accR); free(ao_nuc);
   return 0;
 }
 

@@ -77,7 +77,7 @@ def _load():
         lib.oracle_ao_vgl.argtypes = [P, D, I, P, P, P]
         lib.oracle_mo_vgl.argtypes = [I, I, P, I, P, P, P, P]
         lib.oracle_mo_vgl_points.argtypes = [P, D, I, P, I, P, P, P]
-        lib.oracle_adjoint.argtypes = [P, D, I, P, I, P, P, P, P]
+        lib.oracle_adjoint.argtypes = [P, D, I, P, I, P, P, P, P, P, P]
         lib.oracle_screen_counts.argtypes = [P, D, I, P, P]
         for f in ("oracle_ao_vgl", "oracle_mo_vgl", "oracle_mo_vgl_points",
                   "oracle_adjoint", "oracle_screen_counts"):
@@ -193,8 +193,12 @@ def mo_vgl(mol, points=None, screened: bool = True, C=None,
 
 
 def adjoint(mol, W: np.ndarray, points=None, screened: bool = True, C=None,
-            nucl_coord=None) -> Tuple[np.ndarray, np.ndarray]:
-    """dL/dC [mo][ao] and dL/dR_nuc [nucl][3] for L = sum W * mo_vgl."""
+            nucl_coord=None, sizes: bool = False):
+    """dL/dC [mo][ao] and dL/dR_nuc [nucl][3] for L = sum W * mo_vgl.
+
+    With sizes=True also returns the term-wise sizes of both sums (the scale
+    of their rounding error): (dC, dR, dC_size, dR_size).
+    """
     lib = _load()
     b = _BasisRef(mol, nucl_coord)
     pts = _points(mol, points)
@@ -204,10 +208,15 @@ def adjoint(mol, W: np.ndarray, points=None, screened: bool = True, C=None,
     nm = C.shape[0]
     if W.shape != (n, 5, nm):
         raise ValueError(f"W has shape {W.shape}, expected {(n, 5, nm)}")
+    nn = b.arrs["nucl_coord"].shape[0]
     dC = np.zeros((nm, b.ao_num))
-    dR = np.zeros((b.arrs["nucl_coord"].shape[0], 3))
+    dR = np.zeros((nn, 3))
+    dCs = np.zeros((nm, b.ao_num)) if sizes else None
+    dRs = np.zeros((nn, 3)) if sizes else None
     _check(lib.oracle_adjoint(b.ref, threshold(mol, screened), nm, _ptr(C), n, _ptr(pts),
-                              _ptr(W), _ptr(dC), _ptr(dR)), "adjoint")
+                              _ptr(W), _ptr(dC), _ptr(dR), _ptr(dCs), _ptr(dRs)), "adjoint")
+    if sizes:
+        return dC, dR, dCs, dRs
     return dC, dR
 
 

@@ -802,20 +802,124 @@ qk_status qk_get_timing(qk_context c, double* ms, int64_t* launches, int32_t n) 
   return QK_SUCCESS;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Layout of the backward scratch: recomputed AO tensor, Abar (both
+// [5P][ld]), split-K partials of dL/dC, then the dR partials.
+struct BwdLayout {
+  size_t ao, abar, dc, dr, total;
+  int k_split;
+};
+
+BwdLayout bwd_layout(qk_context c) {
+  BwdLayout L{};
+  const bool f64 = c->mode == QK_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  const int64_t rows = 5 * c->point_num, ld = round_up8(c->ao_num);
+  // enough split-K blocks to fill the GPU: SIMT tiles are 64x64 (FP64) or
+  // 128x128 (FP32); keep >= 1024 rows per split
+  const int64_t tile = f64 ? 64 : 128;
+  const int64_t tiles = ((c->mo_num + tile - 1) / tile) * ((c->ao_num + tile - 1) / tile);
+  int64_t ks = (304 + tiles - 1) / tiles;
+  const int64_t kmax = (rows + 1023) / 1024;
+  if (ks > kmax) ks = kmax;
+  if (ks < 1) ks = 1;
+  L.k_split = (int)ks;
+  L.ao = 0;
+  L.abar = align_up(rows * ld * es, 256);
+  L.dc = L.abar + align_up(rows * ld * es, 256);
+  L.dr = L.dc + align_up((size_t)ks * c->mo_num * c->ao_num * es, 256);
+  L.total = L.dr + align_up(adjoint_dR_partial_bytes(c->bdev, c->point_num), 256);
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
 qk_status qk_backward_workspace_size(qk_context c, size_t* bytes) {
   CHECK_CTX(c);
   if (!bytes) return QK_ERR_NULL_POINTER;
-  return fail(c, QK_ERR_NOT_IMPLEMENTED, "backward not built yet");
+  qk_status st = require(c, true);
+  if (st) return st;
+  st = ensure_tables(c);
+  if (st) return st;
+  *bytes = bwd_layout(c).total;
+  return QK_SUCCESS;
 }
 
 qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, double* d_dC,
                                     double* d_dR) {
   CHECK_CTX(c);
-  (void)dW;
-  (void)size;
-  (void)d_dC;
-  (void)d_dR;
-  return fail(c, QK_ERR_NOT_IMPLEMENTED, "backward not built yet");
+  if (!dW) return fail(c, QK_ERR_NULL_POINTER, "dW is NULL");
+  qk_status st = require(c, true);
+  if (st) return st;
+  const int64_t rows = 5 * c->point_num, N = c->mo_num, K = c->ao_num;
+  if (size < rows * N)
+    return fail(c, QK_ERR_BAD_SIZE, "dW holds %lld elements, %lld needed", (long long)size,
+                (long long)(rows * N));
+  st = ensure_tables(c);
+  if (st) return st;
+  st = ensure_mo(c);
+  if (st) return st;
+  const BwdLayout L = bwd_layout(c);
+  // scratch: behind the forward's AO tensor in the caller's workspace when it
+  // is large enough, else library-owned
+  unsigned char* base = nullptr;
+  const size_t fwd = ao_tensor_bytes(c, c->mode);
+  if (c->ws_user && c->ws_user_bytes >= fwd + L.total) {
+    base = (unsigned char*)c->ws_user + fwd;
+  } else {
+    cudaError_t e = c->bwd_own.ensure(L.total);
+    if (e != cudaSuccess) return cuda_fail(c, e, "backward scratch");
+    base = (unsigned char*)c->bwd_own.p;
+  }
+  const bool f64 = c->mode == QK_FP64;
+  const int64_t ld = round_up8(K);
+  AOTensor ao{};
+  ao.a = base + L.ao;
+  ao.rows = rows;
+  ao.ld = ld;
+  void* abar = base + L.abar;
+  void* dcp = base + L.dc;
+  double* drp = (double*)(base + L.dr);
+  cudaError_t e;
+  TimedLaunch timer(c, 2);
+  // 1. AO values recomputed, not kept from the forward pass
+  e = launch_ao_vgl(c->bdev, c->pdev, f64 ? QK_FP64 : QK_FP32, ao, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward ao_vgl");
+  // 2. Abar[row][k] = sum_i W[row][i] C[i][k]
+  if (f64)
+    e = launch_gemm_f64(rows, K, N, (const double*)dW, N, 1, c->c64, 1, K, (double*)abar, ld, 1,
+                        c->stream);
+  else
+    e = launch_gemm_f32(rows, K, N, (const float*)dW, N, 1, c->c32, 1, c->ldc, (float*)abar, ld,
+                        1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward Abar");
+  // 3. dL/dC[i][k] = sum_row W[row][i] AO[row][k], split over rows
+  if (d_dC) {
+    if (f64) {
+      e = launch_gemm_f64(N, K, rows, (const double*)dW, 1, N, (const double*)ao.a, 1, ld,
+                          (double*)dcp, K, L.k_split, c->stream);
+      if (e == cudaSuccess)
+        e = launch_reduce_partials_f64((const double*)dcp, L.k_split, N * K, d_dC, c->stream);
+    } else {
+      e = launch_gemm_f32(N, K, rows, (const float*)dW, 1, N, (const float*)ao.a, 1, ld,
+                          (float*)dcp, K, L.k_split, c->stream);
+      if (e == cudaSuccess)
+        e = launch_reduce_partials_f32((const float*)dcp, L.k_split, N * K, d_dC, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "backward dL/dC");
+  }
+  // 4. dL/dR_nuc from Abar and third-order AO derivatives
+  if (d_dR) {
+    e = launch_adjoint_dR(c->bdev, c->pdev, f64 ? QK_FP64 : QK_FP32, abar, ld, drp, d_dR,
+                          c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "backward dL/dR");
+  }
+  return QK_SUCCESS;
 }
 
 }  // extern "C"

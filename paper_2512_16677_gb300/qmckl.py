@@ -137,6 +137,7 @@ class Context:
         self._ws = None
         self._keep = []
         self._walk_elec_shape = (0, 0)
+        self.charges = None
         self.mode = mode
         self.set_compute_mode(mode)
 
@@ -188,6 +189,7 @@ class Context:
     # -------------------------------------------------------------- system
     def set_nucleus(self, charge, coord):
         charge, coord = _f64(charge), _f64(coord).reshape(-1, 3)
+        self.charges = charge
         self._check(self.lib.qk_set_nucleus(self.h, charge.shape[0], _ptr(charge), _ptr(coord)),
                     "set_nucleus")
 
@@ -281,6 +283,12 @@ class Context:
         self._check(self.lib.qk_workspace_size(self.h, ctypes.byref(v)), "workspace_size")
         return v.value
 
+    def backward_workspace_size(self) -> int:
+        v = ctypes.c_size_t()
+        self._check(self.lib.qk_backward_workspace_size(self.h, ctypes.byref(v)),
+                    "backward_workspace_size")
+        return v.value
+
     def ensure_workspace(self, extra: int = 0):
         """Caller-owned workspace from the torch allocator (grown as needed)."""
         import torch
@@ -318,6 +326,22 @@ class Context:
         self._check(self.lib.qk_get_mo_vgl_device(self.h, _tptr(out), out.numel()),
                     "get_mo_vgl_device")
         return out
+
+    def backward_device(self, dW, need_dC: bool = True, need_dR: bool = True):
+        """(dL/dC [mo][ao], dL/dR [nucl][3]) as CUDA float64 tensors for
+        L = sum(dW * mo_vgl) at the current points (async on torch's stream)."""
+        import torch
+        self._bind_stream()
+        self.ensure_workspace(extra=self.backward_workspace_size())
+        assert dW.is_cuda and dW.is_contiguous() and dW.dtype == self.dtype_torch
+        dC = torch.empty((self.mo_num, self.ao_num), dtype=torch.float64, device="cuda") \
+            if need_dC else None
+        dR = torch.empty((self.nucl_num, 3), dtype=torch.float64, device="cuda") \
+            if need_dR else None
+        self._check(self.lib.qk_mo_vgl_backward_device(
+            self.h, _tptr(dW), dW.numel(), _tptr(dC) if dC is not None else None,
+            _tptr(dR) if dR is not None else None), "mo_vgl_backward_device")
+        return dC, dR
 
     def ao_vgl_device(self, out=None):
         import torch
