@@ -2,7 +2,7 @@
 //
 // Sec. 3.1 of the QMCkl paper: chi_n = M_n R_s P_abc (Eq. 1), a contracted
 // Gaussian radial part (Eq. 2, p = 2), primitives skipped when
-// gamma r^2 >= T (Eq. 3), Cartesian polynomial (Eq. 4) built from iterated
+// gamma r^2 >= T (Eq. 3), Cartesian polynomial (Eq. 4) built from repeated
 // products of the coordinate differences.
 //
 // For one (point, shell) the radial part and its derivatives need only
@@ -13,178 +13,318 @@
 //   d_i   = M (d_iP S_0 - 2 d_i P S_1)
 //   lap   = M (lapP S_0 - 2 (2l+3) P S_1 + 4 r^2 P S_2)
 //
-// One CTA covers PT points x one column chunk of <= 64 AOs (chunks end on
-// shell boundaries).  Phase 1: threads over (point, shell) pairs compute
-// d = r - R_A, apply the per-shell radius (r^2 >= T/gamma_min screens the
-// whole shell) and then the per-primitive test of Eq. 3 on primitives
-// sorted by ascending exponent (the first screened primitive ends the loop),
-// leaving S_0..S_2 and d in shared memory.  Phase 2: threads over
-// (point, AO) pairs, consecutive lanes on consecutive AOs, assemble the five
-// components and store them as coalesced row segments of the AO tensor
-// [5*point][ld] (row 5p + c).
+// Work decomposition.  The AOs are cut into column chunks of at most 64 AOs
+// and 32 shells that end on shell boundaries.  A CTA owns one chunk and
+// loops over tiles of 32 points (persistent in the point direction), with the
+// chunk's shell, primitive and AO tables staged once in shared memory:
+//   phase 0  the tile's point coordinates -> shared memory
+//   phase 1  one warp per shell, one lane per point: d = r - R_A, the shell
+//            radius test (r^2 >= T/gamma_min screens every primitive), then
+//            the Eq. 3 test on primitives sorted by ascending exponent (the
+//            first screened one ends the loop); S_0..S_2 and d -> shared
+//   phase 2  one lane per pair of AOs, one warp per point: assemble the five
+//            components and store them.
+// In the contraction layout (AOTensor::chunked) chunk q owns the 64 columns
+// [64q, 64q + 64) of the AO tensor, padding included, so each warp store is
+// one aligned 128-byte (bf16 plane) / 256-byte (FP32) / 512-byte (FP64) row
+// segment, and the contraction's K blocks coincide with the chunks.  The
+// caller-facing layout writes the AOs densely (column = AO index).
 //
 // Precision: FP64 mode does everything in FP64 and forms r^2 and gamma r^2
 // without fused multiply-adds, so its screening decisions are those of the
 // plain definition.  The reduced modes form d from float hi/lo pairs of the
-// coordinates (exact-ish difference, then FP32), and run exp and the
-// assembly in FP32.
+// coordinates, then run exp and the assembly in FP32.
 #include "ao_common.cuh"
 
 namespace qk {
-
-// Output writers: plain element type, or bf16 hi/lo planes.
-template <typename T>
-struct StorePlain {
-  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int col, T v) {
-    static_cast<T*>(o.a)[row * o.ld + col] = v;
-  }
-};
-struct StoreSplit {
-  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int col, float v) {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    static_cast<__nv_bfloat16*>(o.a)[row * o.ld + col] = hi;
-    static_cast<__nv_bfloat16*>(o.a_lo)[row * o.ld + col] = lo;
-  }
-};
+namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPT = 32;  // points per tile: one lane per point in phase 1
 
+// Shared memory of one CTA (templated on the arithmetic type).
+template <typename T>
+struct AOShared {
+  // chunk tables (loaded once)
+  T nuc[kMaxShellsChunk][3];     // FP64: R_A; FP32: float(R_A)
+  T nuc_lo[kMaxShellsChunk][3];  // FP32: residual R_A - float(R_A)
+  T r2max[kMaxShellsChunk];
+  int prim0[kMaxShellsChunk];    // first primitive, local to the chunk
+  int nprim[kMaxShellsChunk];
+  int lmom[kMaxShellsChunk];
+  T g[kMaxPrimsChunk];
+  T c[kMaxPrimsChunk];
+  T M[kChunkAO];
+  unsigned char ao_shell[kChunkAO];  // local shell of each local AO
+  unsigned char ao_j[kChunkAO];      // Cartesian component index
+  // per tile
+  T pt[kPT][3];
+  T pt_lo[kPT][3];
+  T d[3][kMaxShellsChunk][kPT];
+  T S[3][kMaxShellsChunk][kPT];
+};
 
-// shared layout: 6 arrays [PT][kChunkAO] of T: dx, dy, dz, S0, S1, S2
-template <int PT, typename T>
-constexpr size_t ao_smem_bytes() {
-  return sizeof(T) * 6 * PT * kChunkAO;
+// Two adjacent AOs (local columns 2q, 2q+1) of one component row.
+template <typename T, bool kSplit>
+struct PairStore;
+
+template <typename T>
+struct PairStore<T, false> {
+  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int64_t col, T v0,
+                                             T v1) {
+    T* p = static_cast<T*>(o.a) + row * o.ld + col;
+    if constexpr (sizeof(T) == 8)
+      *reinterpret_cast<double2*>(p) = make_double2(v0, v1);
+    else
+      *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
+  }
+};
+
+template <>
+struct PairStore<float, true> {
+  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int64_t col, float v0,
+                                             float v1) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+    const int64_t off = row * o.ld + col;
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a) + off) =
+        __halves2bfloat162(h0, h1);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a_lo) + off) =
+        __halves2bfloat162(l0, l1);
+  }
+};
+
+// The five components of local AO `al` at tile point `pl`.
+template <typename T>
+__device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, T out[5]) {
+  const int sl = sh.ao_shell[al];
+  const T S0 = sh.S[0][sl][pl], S1 = sh.S[1][sl][pl], S2 = sh.S[2][sl][pl];
+  if (S0 == T(0) && S1 == T(0) && S2 == T(0)) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] = T(0);
+    return;
+  }
+  const int l = sh.lmom[sl];
+  const int j = sh.ao_j[al];
+  const T dx = sh.d[0][sl][pl], dy = sh.d[1][sl][pl], dz = sh.d[2][sl][pl];
+  const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
+  const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
+  const T X = sel4(a, T(1), dx, x2, x2 * dx);
+  const T Y = sel4(bb, T(1), dy, y2, y2 * dy);
+  const T Z = sel4(c, T(1), dz, z2, z2 * dz);
+  const T X1 = sel4(a, T(0), T(1), T(2) * dx, T(3) * x2);
+  const T Y1 = sel4(bb, T(0), T(1), T(2) * dy, T(3) * y2);
+  const T Z1 = sel4(c, T(0), T(1), T(2) * dz, T(3) * z2);
+  const T X2 = sel4(a, T(0), T(0), T(2), T(6) * dx);
+  const T Y2 = sel4(bb, T(0), T(0), T(2), T(6) * dy);
+  const T Z2 = sel4(c, T(0), T(0), T(2), T(6) * dz);
+  const T P = X * Y * Z;
+  const T M = sh.M[al];
+  const T r2 = x2 + y2 + z2;
+  const T MS0 = M * S0;
+  const T MS1x2 = T(2) * M * S1;
+  out[0] = MS0 * P;
+  out[1] = MS0 * (X1 * Y * Z) - MS1x2 * dx * P;
+  out[2] = MS0 * (X * Y1 * Z) - MS1x2 * dy * P;
+  out[3] = MS0 * (X * Y * Z1) - MS1x2 * dz * P;
+  const T lapP = X2 * Y * Z + X * Y2 * Z + X * Y * Z2;
+  out[4] = M * (lapP * S0 - T(2 * (2 * l + 3)) * P * S1 + T(4) * r2 * P * S2);
 }
 
-template <int PT, typename T, typename Store>
+template <typename T, bool kSplit, bool kChunked>
 __global__ void __launch_bounds__(kThreads)
     ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
   using A = Arith<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  T* s_dx = sm;
-  T* s_dy = sm + 1 * PT * kChunkAO;
-  T* s_dz = sm + 2 * PT * kChunkAO;
-  T* s_S0 = sm + 3 * PT * kChunkAO;
-  T* s_S1 = sm + 4 * PT * kChunkAO;
-  T* s_S2 = sm + 5 * PT * kChunkAO;
-
-  const int4 ch = b.chunk[blockIdx.x];
+  AOShared<T>& sh = *reinterpret_cast<AOShared<T>*>(smem_raw);
+  const int q = blockIdx.x;
+  const int4 ch = b.chunk[q];
   const int ns = ch.y - ch.x;
   const int na = ch.w - ch.z;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+
+  // ---- chunk tables, once per CTA
+  const int p_first = b.shell_prim0[ch.x];
+  for (int i = tid; i < ns; i += kThreads) {
+    const int s = ch.x + i;
+    const int A_ = b.shell_nuc[s];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sh.nuc[i][k] = b.nucl_xyz[3 * A_ + k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sh.nuc[i][k] = b.nucl_hi[3 * A_ + k];
+        sh.nuc_lo[i][k] = b.nucl_lo[3 * A_ + k];
+      }
+    }
+    sh.r2max[i] = A::r2max(b, s);
+    sh.prim0[i] = b.shell_prim0[s] - p_first;
+    sh.nprim[i] = b.shell_nprim[s];
+    sh.lmom[i] = b.shell_l[s];
+  }
+  const int np_chunk = b.shell_prim0[ch.y - 1] + b.shell_nprim[ch.y - 1] - p_first;
+  for (int i = tid; i < np_chunk; i += kThreads) {
+    sh.g[i] = A::gam(b, p_first + i);
+    sh.c[i] = A::coef(b, p_first + i);
+  }
+  for (int i = tid; i < na; i += kThreads) {
+    const int ao = ch.z + i;
+    const int s = b.ao_shell[ao];
+    sh.ao_shell[i] = (unsigned char)(s - ch.x);
+    sh.ao_j[i] = (unsigned char)(ao - b.shell_ao0[s]);
+    sh.M[i] = A::aofac(b, ao);
+  }
   const T Tthr = A::thr(b);
+  const int64_t n = pts.n;
+  const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
 
   for (int64_t ptile = blockIdx.y; ptile < n_ptiles; ptile += gridDim.y) {
-    const int64_t p0 = ptile * PT;
-    // ---- phase 1: radial sums per (point, shell)
-    for (int idx = threadIdx.x; idx < PT * ns; idx += kThreads) {
-      const int pl = idx % PT;
-      const int sl = idx / PT;
-      const int64_t ip = p0 + pl;
-      const int s = ch.x + sl;
-      T dx = T(0), dy = T(0), dz = T(0), S0 = T(0), S1 = T(0), S2 = T(0);
-      if (ip < pts.n) {
-        A::diff(b, pts, ip, b.shell_nuc[s], dx, dy, dz);
-        const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
-        if (r2 < A::r2max(b, s)) {
-          const int k0 = b.shell_prim0[s];
-          const int k1 = k0 + b.shell_nprim[s];
-          for (int k = k0; k < k1; ++k) {
-            const T g = A::gam(b, k);
-            const T t = A::mul(g, r2);
-            if (!(t < Tthr)) break;  // ascending exponents: the rest is screened too
-            const T ce = A::coef(b, k) * A::ex(-t);
-            S0 += ce;
-            S1 += g * ce;
-            S2 += g * g * ce;
+    const int64_t p0 = ptile * kPT;
+    __syncthreads();  // tables ready / previous tile's phase 2 done with shared data
+    // ---- phase 0: the tile's points
+    if (tid < kPT) {
+      const int64_t ip = p0 + tid;
+      if (ip < n) {
+        if constexpr (sizeof(T) == 8) {
+          sh.pt[tid][0] = pts.x[ip];
+          sh.pt[tid][1] = pts.y[ip];
+          sh.pt[tid][2] = pts.z[ip];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            sh.pt[tid][k] = pts.hi[k * n + ip];
+            sh.pt_lo[tid][k] = pts.lo[k * n + ip];
           }
         }
       }
-      const int o = pl * kChunkAO + sl;
-      s_dx[o] = dx;
-      s_dy[o] = dy;
-      s_dz[o] = dz;
-      s_S0[o] = S0;
-      s_S1[o] = S1;
-      s_S2[o] = S2;
     }
     __syncthreads();
-    // ---- phase 2: Cartesian assembly per (point, AO), lanes along AOs
-    for (int idx = threadIdx.x; idx < PT * kChunkAO; idx += kThreads) {
-      const int al = idx % kChunkAO;
-      const int pl = idx / kChunkAO;
+    // ---- phase 1: one warp per shell, lanes over the tile's points
+    for (int sl = warp; sl < ns; sl += kThreads / 32) {
+      const int pl = lane;
+      T dx = T(0), dy = T(0), dz = T(0), S0 = T(0), S1 = T(0), S2 = T(0);
+      if (p0 + pl < n) {
+        if constexpr (sizeof(T) == 8) {
+          dx = __dsub_rn(sh.pt[pl][0], sh.nuc[sl][0]);
+          dy = __dsub_rn(sh.pt[pl][1], sh.nuc[sl][1]);
+          dz = __dsub_rn(sh.pt[pl][2], sh.nuc[sl][2]);
+        } else {
+          // hi parts cancel exactly when close; the residuals restore FP32
+          // accuracy of the difference
+          dx = (sh.pt[pl][0] - sh.nuc[sl][0]) + (sh.pt_lo[pl][0] - sh.nuc_lo[sl][0]);
+          dy = (sh.pt[pl][1] - sh.nuc[sl][1]) + (sh.pt_lo[pl][1] - sh.nuc_lo[sl][1]);
+          dz = (sh.pt[pl][2] - sh.nuc[sl][2]) + (sh.pt_lo[pl][2] - sh.nuc_lo[sl][2]);
+        }
+        const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
+        if (r2 < sh.r2max[sl]) {
+          const int k0 = sh.prim0[sl];
+          const int k1 = k0 + sh.nprim[sl];
+          for (int k = k0; k < k1; ++k) {
+            const T gm = sh.g[k];
+            const T t = A::mul(gm, r2);
+            if (!(t < Tthr)) break;  // ascending exponents: the rest is screened too
+            const T ce = sh.c[k] * A::ex(-t);
+            S0 += ce;
+            S1 += gm * ce;
+            S2 += gm * gm * ce;
+          }
+        }
+      }
+      sh.d[0][sl][pl] = dx;
+      sh.d[1][sl][pl] = dy;
+      sh.d[2][sl][pl] = dz;
+      sh.S[0][sl][pl] = S0;
+      sh.S[1][sl][pl] = S1;
+      sh.S[2][sl][pl] = S2;
+    }
+    __syncthreads();
+    // ---- phase 2: one warp per point, lane = AO pair (2 lane, 2 lane + 1)
+    for (int pl = warp; pl < kPT; pl += kThreads / 32) {
       const int64_t ip = p0 + pl;
-      if (al >= na || ip >= pts.n) continue;
-      const int ao = ch.z + al;
-      const int s = b.ao_shell[ao];
-      const int l = b.shell_l[s];
-      const int j = ao - b.shell_ao0[s];
-      const int o = pl * kChunkAO + (s - ch.x);
-      const T S0 = s_S0[o], S1 = s_S1[o], S2 = s_S2[o];
-      T v = T(0), gx = T(0), gy = T(0), gz = T(0), lap = T(0);
-      if (S0 != T(0) || S1 != T(0) || S2 != T(0)) {
-        const T dx = s_dx[o], dy = s_dy[o], dz = s_dz[o];
-        const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
-        // iterated powers d^0..d^3 (Eq. 4 without pow), picked by selects so
-        // that they stay in registers
-        const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
-        const T X = sel4(a, T(1), dx, x2, x2 * dx);
-        const T Y = sel4(bb, T(1), dy, y2, y2 * dy);
-        const T Z = sel4(c, T(1), dz, z2, z2 * dz);
-        const T X1 = sel4(a, T(0), T(1), T(2) * dx, T(3) * x2);
-        const T Y1 = sel4(bb, T(0), T(1), T(2) * dy, T(3) * y2);
-        const T Z1 = sel4(c, T(0), T(1), T(2) * dz, T(3) * z2);
-        const T X2 = sel4(a, T(0), T(0), T(2), T(6) * dx);
-        const T Y2 = sel4(bb, T(0), T(0), T(2), T(6) * dy);
-        const T Z2 = sel4(c, T(0), T(0), T(2), T(6) * dz);
-        const T P = X * Y * Z;
-        const T M = A::aofac(b, ao);
-        const T r2 = x2 + y2 + z2;
-        const T MS1x2 = T(2) * M * S1;
-        v = M * P * S0;
-        gx = M * (X1 * Y * Z) * S0 - MS1x2 * dx * P;
-        gy = M * (X * Y1 * Z) * S0 - MS1x2 * dy * P;
-        gz = M * (X * Y * Z1) * S0 - MS1x2 * dz * P;
-        const T lapP = X2 * Y * Z + X * Y2 * Z + X * Y * Z2;
-        lap = M * (lapP * S0 - T(2 * (2 * l + 3)) * P * S1 + T(4) * r2 * P * S2);
+      if (ip >= n) break;
+      const int a0 = 2 * lane, a1 = 2 * lane + 1;
+      T v0[5], v1[5];
+      if (a0 < na) {
+        assemble(sh, a0, pl, v0);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v0[c] = T(0);
+      }
+      if (a1 < na) {
+        assemble(sh, a1, pl, v1);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v1[c] = T(0);
       }
       const int64_t row = 5 * ip;
-      Store::put(out, row + 0, ao, v);
-      Store::put(out, row + 1, ao, gx);
-      Store::put(out, row + 2, ao, gy);
-      Store::put(out, row + 3, ao, gz);
-      Store::put(out, row + 4, ao, lap);
+      if constexpr (kChunked) {
+        // chunk window: padding columns are written as zeros
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          PairStore<T, kSplit>::put(out, row + c, col0 + a0, v0[c], v1[c]);
+      } else {
+        T* o = static_cast<T*>(out.a);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (a0 < na) o[(row + c) * out.ld + col0 + a0] = v0[c];
+          if (a1 < na) o[(row + c) * out.ld + col0 + a1] = v1[c];
+        }
+      }
     }
-    __syncthreads();
   }
 }
 
-template <int PT, typename T, typename Store>
-static cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
-                             cudaStream_t s) {
-  constexpr size_t smem = ao_smem_bytes<PT, T>();
-  auto kern = ao_vgl_kernel<PT, T, Store>;
+template <typename T, bool kSplit, bool kChunked>
+cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
+                      cudaStream_t s) {
+  constexpr size_t smem = sizeof(AOShared<T>);
+  auto kern = ao_vgl_kernel<T, kSplit, kChunked>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t n_ptiles = (p.n + PT - 1) / PT;
+  const int64_t n_ptiles = (p.n + kPT - 1) / kPT;
   if (n_ptiles == 0 || b.nchunk == 0) return cudaSuccess;
-  dim3 grid((unsigned)b.nchunk, (unsigned)(n_ptiles < 65535 ? n_ptiles : 65535));
+  int occ = 1, sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (occ < 1) occ = 1;
+  // about four waves of resident CTAs, each CTA walking several point tiles
+  int64_t gy = ((int64_t)sms * occ * 4 + b.nchunk - 1) / b.nchunk;
+  if (gy > n_ptiles) gy = n_ptiles;
+  if (gy > 65535) gy = 65535;
+  dim3 grid((unsigned)b.nchunk, (unsigned)gy);
   kern<<<grid, kThreads, smem, s>>>(b, p, out, n_ptiles);
   return cudaGetLastError();
 }
 
+}  // namespace
+
 cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s) {
+  if (out.chunked) {
+    switch (out_mode) {
+      case QK_FP64:
+        return launch_ao<double, false, true>(b, p, out, s);
+      case QK_FP32:
+      case QK_TF32:
+        return launch_ao<float, false, true>(b, p, out, s);
+      case QK_BF16X3:
+        return launch_ao<float, true, true>(b, p, out, s);
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
   switch (out_mode) {
     case QK_FP64:
-      return launch_ao<16, double, StorePlain<double>>(b, p, out, s);
+      return launch_ao<double, false, false>(b, p, out, s);
     case QK_FP32:
     case QK_TF32:
-      return launch_ao<32, float, StorePlain<float>>(b, p, out, s);
-    case QK_BF16X3:
-      return launch_ao<32, float, StoreSplit>(b, p, out, s);
+      return launch_ao<float, false, false>(b, p, out, s);
     default:
       return cudaErrorInvalidValue;
   }
@@ -224,6 +364,38 @@ cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double*
   const int64_t blocks = (n + 255) / 256;
   points_soa_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(raw, transp, n, x,
                                                                               y, z, hi, lo);
+  return cudaGetLastError();
+}
+
+// C [rows][cols] (FP64) -> the contraction's chunked column layout
+// ([rows][nchunk*64], padding zeroed) as FP64, FP32 and bf16 hi/lo planes.
+__global__ void mo_chunked_kernel(const double* src, int64_t rows, int64_t cols,
+                                  const int4* chunk, int nchunk, double* d64, float* d32,
+                                  __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const int64_t ld = (int64_t)nchunk * kChunkAO;
+  const int64_t n = rows * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ld, col = i % ld;
+    const int q = (int)(col / kChunkAO), loc = (int)(col % kChunkAO);
+    const int4 ch = chunk[q];
+    const double v = loc < ch.w - ch.z ? src[r * cols + ch.z + loc] : 0.0;
+    d64[i] = v;
+    d32[i] = __double2float_rn(v);
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi[i] = h;
+    lo[i] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+cudaError_t launch_mo_chunked(const double* src, int64_t rows, int64_t cols, const int4* chunk,
+                              int nchunk, double* d64, float* d32, __nv_bfloat16* hi,
+                              __nv_bfloat16* lo, cudaStream_t s) {
+  const int64_t n = rows * (int64_t)nchunk * kChunkAO;
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  mo_chunked_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(
+      src, rows, cols, chunk, nchunk, d64, d32, hi, lo);
   return cudaGetLastError();
 }
 

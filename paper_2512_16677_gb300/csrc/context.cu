@@ -73,10 +73,13 @@ struct qk_context_s {
   int64_t mo_num = 0, ldc = 0;
   std::vector<double> mo_coef;
   DevBuf d_mo;
-  double* c64 = nullptr;
-  float* c32 = nullptr;
+  double* c64 = nullptr;   // [mo][ao]     dense (adjoint)
+  float* c32 = nullptr;    // [mo][ldc]    dense (adjoint)
+  double* c64p = nullptr;  // [mo][kpad]   chunked column layout (contraction)
+  float* c32p = nullptr;
   __nv_bfloat16* c_hi = nullptr;
   __nv_bfloat16* c_lo = nullptr;
+  int64_t kpad = 0;
   bool mo_dirty = true;
   // points
   bool has_points = false;
@@ -257,31 +260,44 @@ qk_status ensure_tables(qk_context c) {
 
 qk_status ensure_mo(qk_context c) {
   if (!c->mo_dirty) return QK_SUCCESS;
+  qk_status st = ensure_tables(c);  // the chunk table defines the padded layout
+  if (st) return st;
   const int64_t nm = c->mo_num, na = c->ao_num, ldc = round_up8(na);
+  const int64_t kp = (int64_t)c->chunks.size() * kChunkAO;
   const size_t b64 = align_up(sizeof(double) * nm * na, 256);
   const size_t b32 = align_up(sizeof(float) * nm * ldc, 256);
-  const size_t b16 = align_up(sizeof(__nv_bfloat16) * nm * ldc, 256);
-  cudaError_t e = c->d_mo.ensure(b64 + b32 + 2 * b16);
+  const size_t b64p = align_up(sizeof(double) * nm * kp, 256);
+  const size_t b32p = align_up(sizeof(float) * nm * kp, 256);
+  const size_t b16 = align_up(sizeof(__nv_bfloat16) * nm * kp, 256);
+  cudaError_t e = c->d_mo.ensure(b64 + b32 + b64p + b32p + 2 * b16);
   if (e != cudaSuccess) return cuda_fail(c, e, "MO coefficient tables");
   unsigned char* base = (unsigned char*)c->d_mo.p;
   c->c64 = (double*)base;
   c->c32 = (float*)(base + b64);
-  c->c_hi = (__nv_bfloat16*)(base + b64 + b32);
-  c->c_lo = (__nv_bfloat16*)(base + b64 + b32 + b16);
+  c->c64p = (double*)(base + b64 + b32);
+  c->c32p = (float*)(base + b64 + b32 + b64p);
+  c->c_hi = (__nv_bfloat16*)(base + b64 + b32 + b64p + b32p);
+  c->c_lo = (__nv_bfloat16*)(base + b64 + b32 + b64p + b32p + b16);
   c->ldc = ldc;
+  c->kpad = kp;
   e = cudaMemcpyAsync(c->c64, c->mo_coef.data(), sizeof(double) * nm * na,
                       cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = launch_to_f32(c->c64, nm, na, ldc, c->c32, c->stream);
-  if (e == cudaSuccess) e = launch_split_bf16(c->c64, nm, na, ldc, c->c_hi, c->c_lo, c->stream);
+  if (e == cudaSuccess)
+    e = launch_mo_chunked(c->c64, nm, na, c->bdev.chunk, c->bdev.nchunk, c->c64p, c->c32p,
+                          c->c_hi, c->c_lo, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "MO coefficient upload");
   c->mo_dirty = false;
   return QK_SUCCESS;
 }
 
+// Columns of the contraction's AO tensor: one 64-wide window per chunk.
+int64_t kpad_of(qk_context c) { return (int64_t)c->chunks.size() * kChunkAO; }
+
 size_t ao_tensor_bytes(qk_context c, int mode) {
   const size_t rows = (size_t)5 * c->point_num;
-  const size_t ld = (size_t)round_up8(c->ao_num);
+  const size_t ld = (size_t)kpad_of(c);
   switch (mode) {
     case QK_FP64:
       return align_up(rows * ld * sizeof(double), 256);
@@ -331,7 +347,8 @@ qk_status workspace(qk_context c, size_t need, void** out) {
 AOTensor ao_view(qk_context c, void* ws, int mode) {
   AOTensor t{};
   t.rows = 5 * c->point_num;
-  t.ld = round_up8(c->ao_num);
+  t.ld = kpad_of(c);
+  t.chunked = true;
   t.a = ws;
   if (mode == QK_BF16X3)
     t.a_lo = (unsigned char*)ws + align_up(t.rows * t.ld * sizeof(__nv_bfloat16), 256);
@@ -489,6 +506,9 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
                   shell_ang_mom[s]);
     if (shell_prim_num[s] < 1)
       return fail(c, QK_ERR_INVALID_ARG, "shell %lld has no primitive", (long long)s);
+    if (shell_prim_num[s] > kMaxPrimsChunk)
+      return fail(c, QK_ERR_NOT_IMPLEMENTED, "shell %lld has more than %d primitives",
+                  (long long)s, kMaxPrimsChunk);
     np += shell_prim_num[s];
     na += (shell_ang_mom[s] + 1) * (shell_ang_mom[s] + 2) / 2;
   }
@@ -518,7 +538,7 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
   c->ao_fac.assign(ao_factor, ao_factor + ao_num);
   c->ao_shell.resize(ao_num);
   c->chunks.clear();
-  int64_t p0 = 0, a0 = 0;
+  int64_t p0 = 0, a0 = 0, chunk_prims = 0;
   int4 cur = make_int4(0, 0, 0, 0);
   for (int64_t s = 0; s < shell_num; ++s) {
     const int l = shell_ang_mom[s];
@@ -541,10 +561,13 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
     c->shell_ao0[s] = (int)a0;
     c->shell_gmin[s] = c->prim_g[p0];
     for (int j = 0; j < nc; ++j) c->ao_shell[a0 + j] = (int)s;
-    if (cur.w - cur.z + nc > kChunkAO) {
+    if (cur.w - cur.z + nc > kChunkAO || cur.y - cur.x + 1 > kMaxShellsChunk ||
+        chunk_prims + npr > kMaxPrimsChunk) {
       c->chunks.push_back(cur);
       cur = make_int4((int)s, (int)s, (int)a0, (int)a0);
+      chunk_prims = 0;
     }
+    chunk_prims += npr;
     cur.y = (int)s + 1;
     cur.w = (int)(a0 + nc);
     p0 += npr;
@@ -726,7 +749,7 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
   if (!dout) return fail(c, QK_ERR_NULL_POINTER, "dout is NULL");
   qk_status st = require(c, true);
   if (st) return st;
-  const int64_t M = 5 * c->point_num, N = c->mo_num, K = c->ao_num;
+  const int64_t M = 5 * c->point_num, N = c->mo_num;
   if (size < M * N)
     return fail(c, QK_ERR_BAD_SIZE, "output holds %lld elements, %lld needed", (long long)size,
                 (long long)(M * N));
@@ -735,21 +758,22 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
   AOTensor ao{};
   st = provide_ao(c, &ao);
   if (st) return st;
+  const int64_t KP = c->kpad;  // contraction runs over the chunked columns
   cudaError_t e = cudaSuccess;
   TimedLaunch timer(c, 1);
   switch (c->mode) {
     case QK_FP64:
-      e = launch_gemm_f64(M, N, K, (const double*)ao.a, ao.ld, 1, c->c64, K, 1, (double*)dout, N,
-                          1, c->stream);
+      e = launch_gemm_f64(M, N, KP, (const double*)ao.a, ao.ld, 1, c->c64p, KP, 1, (double*)dout,
+                          N, 1, c->stream);
       break;
     case QK_FP32:
-      e = launch_gemm_f32(M, N, K, (const float*)ao.a, ao.ld, 1, c->c32, c->ldc, 1, (float*)dout,
+      e = launch_gemm_f32(M, N, KP, (const float*)ao.a, ao.ld, 1, c->c32p, KP, 1, (float*)dout,
                           N, 1, c->stream);
       break;
     default: {
       const bool split = c->mode == QK_BF16X3;
-      e = launch_mo_tc(c->mode, ao, K, split ? (const void*)c->c_hi : (const void*)c->c32,
-                       split ? (const void*)c->c_lo : nullptr, c->ldc, N, (float*)dout,
+      e = launch_mo_tc(c->mode, ao, KP, split ? (const void*)c->c_hi : (const void*)c->c32p,
+                       split ? (const void*)c->c_lo : nullptr, KP, N, (float*)dout,
                        tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream);
     }
   }
@@ -882,6 +906,7 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
   ao.a = base + L.ao;
   ao.rows = rows;
   ao.ld = ld;
+  ao.chunked = false;
   void* abar = base + L.abar;
   void* dcp = base + L.dc;
   double* drp = (double*)(base + L.dr);

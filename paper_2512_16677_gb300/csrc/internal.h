@@ -15,8 +15,12 @@ namespace qk {
 
 // Largest angular momentum handled by the kernels (f shells).
 constexpr int kMaxL = 3;
-// AOs per ao_vgl column chunk; chunks end on shell boundaries.
+// AOs per ao_vgl column chunk; chunks end on shell boundaries and also hold
+// at most kMaxShellsChunk shells and kMaxPrimsChunk primitives.  In the
+// contraction layout chunk q owns AO-tensor columns [64q, 64q + 64).
 constexpr int kChunkAO = 64;
+constexpr int kMaxShellsChunk = 32;
+constexpr int kMaxPrimsChunk = 256;
 
 // Device-side basis tables, passed to kernels by value.  Every pointer
 // points into one allocation owned by the context.  Primitives of each
@@ -55,13 +59,16 @@ struct PointsDev {
   const float* lo;  // [3][n] residuals
 };
 
-// Layout of the AO tensor handed to the contraction: rows are (point,
-// component) pairs, row r = 5*p + c, ld elements apart; AOs contiguous.
+// Layout of the AO tensor: rows are (point, component) pairs, row r = 5p + c,
+// ld elements apart.  chunked: AO n of chunk q sits in column
+// 64q + (n - first AO of q) and the padding columns hold zeros (the layout the
+// contraction reads); otherwise column = AO index.
 struct AOTensor {
   void* a;       // FP64 / FP32 values, or bf16 "hi" plane
   void* a_lo;    // bf16 "lo" plane (QK_BF16X3 only)
   int64_t rows;  // 5 * point_num
-  int64_t ld;    // row stride in elements (multiple of 8)
+  int64_t ld;    // row stride in elements
+  bool chunked;
 };
 
 // A device allocation owned by the library.
@@ -84,6 +91,12 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 // Point coordinates [n][3] ('N') or [3][n] ('T') -> SoA + hi/lo floats.
 cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double* x,
                               double* y, double* z, float* hi, float* lo, cudaStream_t s);
+
+// C [rows][cols] (FP64) -> chunked column layout [rows][nchunk*64] in FP64,
+// FP32 and bf16 hi/lo planes (padding zeroed).
+cudaError_t launch_mo_chunked(const double* src, int64_t rows, int64_t cols, const int4* chunk,
+                              int nchunk, double* d64, float* d32, __nv_bfloat16* hi,
+                              __nv_bfloat16* lo, cudaStream_t s);
 
 // Split an FP64 matrix [rows][cols] into bf16 hi and lo planes (ld columns,
 // padding zeroed), or convert it to FP32.

@@ -169,22 +169,36 @@ struct TcShape {
   static constexpr uint32_t A_BYTES = kBM * kRowBytes;
   static constexpr uint32_t B_BYTES = BNT * kRowBytes;
   static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + B_BYTES);
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1);
-  static constexpr uint32_t TMEM_COLS = tmem_cols<BNT>();
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 4);
+  static constexpr uint32_t TMEM_COLS = tmem_cols<BNT>();  // per accumulator buffer (two)
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N must be 16..256, step 16");
-  static_assert(BNT <= 512, "accumulator exceeds TMEM");
+  static_assert(BNT <= 256, "two accumulator buffers must fit the 512 TMEM columns");
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: CTA c walks tiles t = c, c + gridDim.x, ... with
+// (m, n) = (t / n_tiles, t % n_tiles).  The shared-memory ring runs on a
+// k-block counter that continues across tiles; the accumulator alternates
+// between two TMEM buffers so that the epilogue of tile i overlaps the MMAs
+// of tile i + 1.
+//   full[s]   TMA bytes of stage s landed        (producer -> MMA)
+//   empty[s]  MMAs reading stage s finished      (MMA -> producer, commit)
+//   tfull[b]  accumulator b complete             (MMA -> epilogue, commit)
+//   tempty[b] accumulator b drained to global    (epilogue warps -> MMA)
 template <int MODE, int BN, int NSUB, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     mo_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_a_lo,
                  const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_b_lo,
                  float* __restrict__ D, int64_t M, int64_t N, int num_kb, int64_t m_tiles,
-                 int* err_flag) {
+                 int n_tiles, int* err_flag) {
   using S = TcShape<MODE, BN, NSUB, STAGES>;
   using TR = TcTraits<MODE>;
   constexpr int BNT = S::BNT;
   constexpr uint32_t idesc = make_idesc(TR::kFmt, kBM, BN);
+  constexpr uint32_t ACC = S::TMEM_COLS;  // columns of one accumulator buffer
 
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
@@ -194,55 +208,58 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bar0 = base + STAGES * S::STAGE_BYTES;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-  const uint32_t done_bar = bar0 + 8u * (2 * STAGES);
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   volatile int* abort_v = &abort_flag;
+  const int64_t total = m_tiles * (int64_t)n_tiles;
 
-  // TMEM for the accumulator, once per CTA (no allocation after relinquish)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);  // one arrival per epilogue warp
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(S::TMEM_COLS)
+                 "r"(2 * ACC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
 
-  for (int64_t mt = blockIdx.y; mt < m_tiles; mt += gridDim.y) {
-    const int64_t m0 = mt * kBM;
-    const int n0 = blockIdx.x * BNT;
-    // barriers are (re)initialised per tile: every phase of the previous tile
-    // has completed once its epilogue passed the block barrier below
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < STAGES; ++s) {
-        mbar_init(full_bar(s), 1);
-        mbar_init(empty_bar(s), 1);
-      }
-      mbar_init(done_bar, 1);
-      abort_flag = 0;
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-
-    if (warp == 4 && lane == 0) {
-      // ------------------------------------------------ TMA producer
-      int issued = 0;
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+  if (warp == 4 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int m0 = (int)((t / n_tiles) * kBM);
+      const int n0 = (int)((t % n_tiles) * BNT);
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
         if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
           flag_error(err_flag, abort_v, 1);
+          ok = false;
           break;
         }
         const uint32_t st = base + s * S::STAGE_BYTES;
         mbar_expect_tx(full_bar(s), S::STAGE_BYTES);
         const int kc = kb * TR::kBK;
-        tma_load_2d(st, &tm_a, full_bar(s), kc, (int)m0);
-        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, &tm_a_lo, full_bar(s), kc, (int)m0);
+        tma_load_2d(st, &tm_a, full_bar(s), kc, m0);
+        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, &tm_a_lo, full_bar(s), kc, m0);
         const uint32_t bst = st + TR::kPlanes * S::A_BYTES;
 #pragma unroll
         for (int j = 0; j < NSUB; ++j) {
@@ -251,25 +268,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(bst + S::B_BYTES + j * BN * kRowBytes, &tm_b_lo, full_bar(s), kc,
                         n0 + j * BN);
         }
-        ++issued;
       }
-      if (*abort_v) {
-        // drain: let the copies already issued land before the CTA leaves
-        const int first = issued > STAGES ? issued - STAGES : 0;
-        for (int kb = first; kb < issued; ++kb) {
-          const long long t0 = clock64();
-          while (!mbar_try_wait(full_bar(kb % STAGES), (uint32_t)(kb / STAGES) & 1u) &&
-                 clock64() - t0 < kWaitCycles) {
-          }
+    }
+    if (*abort_v) {
+      // drain: let the copies already issued land before the CTA leaves
+      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      for (uint32_t k = first; k < it; ++k) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full_bar(k % STAGES), (k / STAGES) & 1u) &&
+               clock64() - t0 < kWaitCycles) {
         }
       }
-    } else if (warp == 5 && lane == 0) {
-      // ------------------------------------------------ MMA issuer
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+    }
+  } else if (warp == 5 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    uint32_t it = 0, i = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+      const uint32_t b = i & 1u;
+      if (!mbar_wait(tempty_bar(b), ((i >> 1) & 1u) ^ 1u, abort_v)) {
+        flag_error(err_flag, abort_v, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dacc = tmem + b * ACC;
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
         if (!mbar_wait(full_bar(s), ph, abort_v)) {
           flag_error(err_flag, abort_v, 2);
+          ok = false;
           break;
         }
         tc_fence_after();
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t koff = kk * kUmmaKBytes;
 #pragma unroll
           for (int j = 0; j < NSUB; ++j) {
-            const uint32_t d = tmem + j * BN;
+            const uint32_t d = dacc + j * BN;
             const uint32_t boff = j * BN * kRowBytes + koff;
             const uint32_t acc = (kb | kk) != 0;
             umma<MODE>(d, sw128_desc(a_hi + koff), sw128_desc(b_hi + boff), idesc, acc);
@@ -295,16 +323,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
       }
-      umma_commit(done_bar);  // accumulator complete (also on abort: drains MMAs)
+      // accumulator b complete (after an abort this still waits for the MMAs
+      // already issued, so the epilogue never reads a buffer being written)
+      umma_commit(tfull_bar(b));
+      if (!ok) {
+        // aborted: wait for the MMAs in flight before TMEM can be freed
+        const long long t0 = clock64();
+        while (!mbar_try_wait(tfull_bar(b), (i >> 1) & 1u) && clock64() - t0 < kWaitCycles) {
+        }
+      }
     }
-
-    if (warp < 4) {
-      // ------------------------------------------------ epilogue
-      // wait for the final commit even after an abort, so that no MMA is
-      // still writing TMEM when it is freed
+  } else if (warp < 4) {
+    // ------------------------------------------------ epilogue
+    uint32_t i = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const uint32_t b = i & 1u;
       const long long t0 = clock64();
       bool ok = true;
-      while (!mbar_try_wait(done_bar, 0)) {
+      while (!mbar_try_wait(tfull_bar(b), (i >> 1) & 1u)) {
         if (clock64() - t0 > kWaitCycles) {
           ok = false;
           break;
@@ -313,40 +349,43 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) flag_error(err_flag, abort_v, 3);
       ok = __all_sync(0xffffffffu, ok) && !*abort_v;
       __syncwarp();
+      if (!ok) break;
       tc_fence_after();
-      if (ok) {
-        const int64_t row = m0 + warp * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        float* drow = D + row * N;
-        const bool vec = (N % 4) == 0;
+      const int64_t m0 = (t / n_tiles) * kBM;
+      const int64_t n0 = (t % n_tiles) * BNT;
+      const int64_t row = m0 + warp * 32 + lane;
+      const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
+      float* drow = D + row * N;
+      const bool vec = (N % 4) == 0;
 #pragma unroll 1
-        for (int c = 0; c < BNT; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + c, v);
-          if (row < M) {
-            const int64_t n = n0 + c;
-            if (vec && n + 16 <= N) {
-              float4* p = reinterpret_cast<float4*>(drow + n);
+      for (int c = 0; c < BNT; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + c, v);
+        if (row < M) {
+          const int64_t n = n0 + c;
+          if (vec && n + 16 <= N) {
+            float4* p = reinterpret_cast<float4*>(drow + n);
 #pragma unroll
-              for (int q = 0; q < 4; ++q)
-                p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            } else {
+            for (int q = 0; q < 4; ++q)
+              p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (n + q < N) drow[n + q] = v[q];
-            }
+            for (int q = 0; q < 16; ++q)
+              if (n + q < N) drow[n + q] = v[q];
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(b));
     }
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_v) break;
   }
+  tc_fence_before();
+  __syncthreads();
   if (warp == 5) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
-                 "r"(S::TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * ACC)
                  : "memory");
   }
 }
@@ -416,13 +455,17 @@ cudaError_t launch_cfg(const AOTensor& ao, int64_t K, const void* c_hi, const vo
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, S::SMEM);
   if (e != cudaSuccess) return e;
-  if (occ < 1 || occ * (int)S::TMEM_COLS > 512) return cudaErrorInvalidConfiguration;
+  if (occ < 1 || occ * 2 * (int)S::TMEM_COLS > 512) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
   const int64_t m_tiles = (M + kBM - 1) / kBM;
   const int64_t n_tiles = (N + S::BNT - 1) / S::BNT;
-  dim3 grid((unsigned)n_tiles, (unsigned)(m_tiles < 65535 ? m_tiles : 65535));
-  kern<<<grid, kThreads, S::SMEM, s>>>(ta, ta_lo, tb, tb_lo, out, M, N, num_kb, m_tiles,
-                                       err_flag);
+  const int64_t total = m_tiles * n_tiles;
+  const int64_t grid = total < (int64_t)sms * occ ? total : (int64_t)sms * occ;
+  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(ta, ta_lo, tb, tb_lo, out, M, N, num_kb, m_tiles,
+                                                 (int)n_tiles, err_flag);
   return cudaGetLastError();
 }
 
