@@ -245,6 +245,51 @@ qk_status qk_mo_vgl_backward_device(qk_context ctx, const void* dW, int64_t size
    (it allocates them itself unless qk_set_workspace covered both sizes). */
 qk_status qk_backward_workspace_size(qk_context ctx, size_t* bytes);
 
+/* ------------------------------------------------------------- batch --- */
+/* Walkers of several molecules of uneven sizes, evaluated together: one
+   persistent ao_vgl launch over (molecule, AO chunk, point tiles) items and
+   one persistent tcgen05 contraction over (molecule, M tile, N tile) items,
+   each ordered longest first, captured once in a CUDA graph and replayed.
+   The paper evaluates one system per context (Sec. 2.2); a batch runs the
+   same Eqs. 1-7 for each of its contexts. */
+
+/* Create a batch over n_ctx contexts, each with nuclei, basis, MO
+   coefficients and points set, all in QK_BF16X3 or all in QK_TF32 mode
+   (else QK_ERR_INVALID_ARG; unset inputs: QK_ERR_NOT_PROVIDED).  The batch
+   keeps the handles, not copies: the contexts must outlive it, and their
+   points may be updated between runs (qk_set_points*). */
+qk_status qk_batch_create(qk_batch* out, int32_t n_ctx, const qk_context* ctxs);
+qk_status qk_batch_destroy(qk_batch b);
+qk_status qk_batch_last_error(qk_batch b, char* buf, int64_t size);
+
+/* Stream for the batch's launches (a cudaStream_t; NULL = legacy default).
+   Point updates of the contexts must be ordered before a run on it. */
+qk_status qk_batch_set_stream(qk_batch b, void* stream);
+
+/* 1 (default): capture the two launches in a CUDA graph on the first run and
+   replay it; 0: plain launches. */
+qk_status qk_batch_set_graph(qk_batch b, int32_t enable);
+
+/* Largest MMA N of the contraction (64, 96, 128, 160, 192 or 256; default
+   160).  Each molecule uses the smallest multiple of 16 that covers its MOs
+   in the fewest N tiles under this bound. */
+qk_status qk_batch_set_tile(qk_batch b, int32_t bn_max);
+qk_status qk_batch_get_tile(qk_batch b, int32_t* bn_max);
+
+/* Evaluate the MO vgl of every context: douts[i] is a device float array
+   [walk][elec][5][mo] of context i holding at least sizes[i] elements
+   (sizes may be NULL).  Asynchronous on the batch stream. */
+qk_status qk_batch_run(qk_batch b, float* const* douts, const int64_t* sizes);
+
+/* Wait for the batch stream; QK_ERR_DEVICE_TIMEOUT if a bounded device wait
+   gave up. */
+qk_status qk_batch_synchronize(qk_batch b);
+
+/* Autotuner: time the contraction for every instantiated bn_max on this
+   batch (reps timed launches each, after one warm-up) and keep the fastest;
+   *best_ms (optional) receives its time per launch.  Writes douts. */
+qk_status qk_batch_autotune(qk_batch b, float* const* douts, int32_t reps, double* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

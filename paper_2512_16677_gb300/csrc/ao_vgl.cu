@@ -41,6 +41,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPT = 32;  // points per tile: one lane per point in phase 1
+static_assert(kPT == kAOTilePoints, "tile size shared with the batch work list");
 
 // Shared memory of one CTA (templated on the arithmetic type).
 template <typename T>
@@ -132,13 +133,14 @@ __device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, 
   out[4] = M * (lapP * S0 - T(2 * (2 * l + 3)) * P * S1 + T(4) * r2 * P * S2);
 }
 
+// Chunk q of one problem over point tiles t_begin, t_begin + t_step, ...
+// below t_end (the whole CTA calls this; it starts with a block barrier).
 template <typename T, bool kSplit, bool kChunked>
-__global__ void __launch_bounds__(kThreads)
-    ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
+__device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDev& pts,
+                                               const AOTensor& out, int q, int64_t t_begin,
+                                               int64_t t_end, int64_t t_step, AOShared<T>& sh) {
   using A = Arith<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  AOShared<T>& sh = *reinterpret_cast<AOShared<T>*>(smem_raw);
-  const int q = blockIdx.x;
+  __syncthreads();  // the previous call's readers of the shared tables are done
   const int4 ch = b.chunk[q];
   const int ns = ch.y - ch.x;
   const int na = ch.w - ch.z;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t n = pts.n;
   const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
 
-  for (int64_t ptile = blockIdx.y; ptile < n_ptiles; ptile += gridDim.y) {
+  for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
     const int64_t p0 = ptile * kPT;
     __syncthreads();  // tables ready / previous tile's phase 2 done with shared data
     // ---- phase 0: the tile's points
@@ -279,6 +281,30 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename T, bool kSplit, bool kChunked>
+__global__ void __launch_bounds__(kThreads)
+    ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AOShared<T>& sh = *reinterpret_cast<AOShared<T>*>(smem_raw);
+  ao_chunk_tiles<T, kSplit, kChunked>(b, pts, out, blockIdx.x, blockIdx.y, n_ptiles, gridDim.y,
+                                      sh);
+}
+
+// Several problems in one persistent launch: CTAs stride over a work list of
+// (problem, chunk, first tile, end tile), longest first.
+template <bool kSplit>
+__global__ void __launch_bounds__(kThreads)
+    ao_vgl_batch_kernel(const AOProblem* __restrict__ probs, const int4* __restrict__ items,
+                        int64_t n_items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AOShared<float>& sh = *reinterpret_cast<AOShared<float>*>(smem_raw);
+  for (int64_t i = blockIdx.x; i < n_items; i += gridDim.x) {
+    const int4 w = items[i];
+    const AOProblem& P = probs[w.x];
+    ao_chunk_tiles<float, kSplit, true>(P.b, P.p, P.out, w.y, w.z, w.w, 1, sh);
+  }
+}
+
+template <typename T, bool kSplit, bool kChunked>
 cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
                       cudaStream_t s) {
   constexpr size_t smem = sizeof(AOShared<T>);
@@ -302,7 +328,32 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   return cudaGetLastError();
 }
 
+template <bool kSplit>
+cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n_items,
+                            cudaStream_t s) {
+  constexpr size_t smem = sizeof(AOShared<float>);
+  auto kern = ao_vgl_batch_kernel<kSplit>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_items == 0) return cudaSuccess;
+  int occ = 1, sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (occ < 1) occ = 1;
+  const int64_t grid = n_items < (int64_t)sms * occ ? n_items : (int64_t)sms * occ;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(probs, items, n_items);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
+                                int64_t n_items, cudaStream_t s) {
+  return split ? launch_ao_batch<true>(probs, items, n_items, s)
+               : launch_ao_batch<false>(probs, items, n_items, s);
+}
 
 cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s) {

@@ -948,3 +948,43 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
 }
 
 }  // extern "C"
+
+namespace qk {
+
+qk_status context_fail(qk_context c, qk_status code, const char* msg) {
+  return fail(c, code, "%s", msg);
+}
+
+qk_status context_forward_views(qk_context c, ForwardViews* v) {
+  CHECK_CTX(c);
+  qk_status st = require(c, true);
+  if (st) return st;
+  st = ensure_tables(c);
+  if (st) return st;
+  st = ensure_mo(c);
+  if (st) return st;
+  void* ws = nullptr;
+  st = workspace(c, ao_tensor_bytes(c, c->mode), &ws);
+  if (st) return st;
+  v->b = c->bdev;
+  v->p = c->pdev;
+  v->ao = ao_view(c, ws, c->mode);
+  const bool split = c->mode == QK_BF16X3;
+  v->c_hi = split ? (const void*)c->c_hi : (const void*)c->c32p;
+  v->c_lo = split ? (const void*)c->c_lo : nullptr;
+  v->kpad = c->kpad;
+  v->mo_num = c->mo_num;
+  v->walk_num = c->walk_num;
+  v->elec_num = c->elec_num;
+  v->mode = c->mode;
+  return QK_SUCCESS;
+}
+
+void context_mark_ao_valid(qk_context c) {
+  c->ao_date = c->date;
+  c->ao_mode = c->mode;
+  c->ao_ws = c->ws_user ? c->ws_user : c->ws_own.p;
+  c->ao_version = c->basis_version;
+}
+
+}  // namespace qk

@@ -2,8 +2,9 @@
 // Not part of the public ABI (include/qmckl_gpu.h is).
 #pragma once
 
-#include <cuda_runtime.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
@@ -133,11 +134,59 @@ cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const voi
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
 
+// One contraction problem of a multi-problem launch (device-resident; the
+// tensor maps, 64-byte aligned by their type, are written by the host
+// before the launch).
+struct TcProblem {
+  CUtensorMap a, a_lo, b, b_lo;  // AO hi / lo, C hi / lo (lo = hi for TF32)
+  float* D;                      // [M][N] output
+  int64_t M, N;
+  int num_kb;                    // K blocks
+  int bn;                        // MMA N (multiple of 16, <= the launch's bn_max)
+};
+// BN_MAX values instantiated for multi-problem launches.
+extern const int kBatchBnMax[6];
+// Fill a TcProblem (host): tensor maps over the AO tensor and C planes.
+bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                     int64_t ldc, int64_t N, float* out, int bn, TcProblem* p);
+// Persistent launch over a work list of int4 (problem, m tile, n tile, 0).
+cudaError_t launch_mo_tc_batch(int mode, int bn_max, const TcProblem* probs, const int4* items,
+                               int64_t n_items, int* err_flag, cudaStream_t s);
+
+// One AO problem of a multi-problem ao_vgl launch.
+struct AOProblem {
+  BasisDev b;
+  PointsDev p;
+  AOTensor out;  // chunked layout
+};
+// Persistent ao_vgl over a work list of int4 (problem, chunk, first tile,
+// end tile); tiles are 32 points.  split: bf16 hi/lo planes, else FP32.
+cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
+                                int64_t n_items, cudaStream_t s);
+constexpr int kAOTilePoints = 32;
+
 // Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
 // points, reduced into d_dR [nucl][3] (FP64).
 cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
                               const void* abar, int64_t ld, double* partial, double* d_dR,
                               cudaStream_t s);
 size_t adjoint_dR_partial_bytes(const BasisDev& b, int64_t point_num);
+
+// What a multi-molecule launch needs from one context (context.cu): makes
+// the tables, MO planes and AO workspace of the current state valid and
+// returns views of them.
+struct ForwardViews {
+  BasisDev b;
+  PointsDev p;
+  AOTensor ao;          // chunked
+  const void* c_hi;     // contraction B planes (c_lo NULL for TF32)
+  const void* c_lo;
+  int64_t kpad, mo_num, walk_num, elec_num;
+  int mode;
+};
+qk_status context_forward_views(qk_context c, ForwardViews* v);
+// Record that the AO tensor of the current time stamp is now in the workspace.
+void context_mark_ao_valid(qk_context c);
+qk_status context_fail(qk_context c, qk_status code, const char* msg);
 
 }  // namespace qk

@@ -162,42 +162,99 @@ constexpr uint32_t tmem_cols() {
   return BNT <= 32 ? 32 : BNT <= 64 ? 64 : BNT <= 128 ? 128 : BNT <= 256 ? 256 : 512;
 }
 
-template <int MODE, int BN, int NSUB, int STAGES>
+template <int MODE, int BN_MAX, int STAGES>
 struct TcShape {
   using TR = TcTraits<MODE>;
-  static constexpr int BNT = BN * NSUB;
   static constexpr uint32_t A_BYTES = kBM * kRowBytes;
-  static constexpr uint32_t B_BYTES = BNT * kRowBytes;
+  static constexpr uint32_t B_BYTES = BN_MAX * kRowBytes;  // room for the widest B tile
   static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + B_BYTES);
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 4);
-  static constexpr uint32_t TMEM_COLS = tmem_cols<BNT>();  // per accumulator buffer (two)
-  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N must be 16..256, step 16");
-  static_assert(BNT <= 256, "two accumulator buffers must fit the 512 TMEM columns");
+  static constexpr uint32_t TMEM_COLS = tmem_cols<BN_MAX>();  // per accumulator buffer (two)
+  static_assert(BN_MAX % 16 == 0 && BN_MAX >= 16 && BN_MAX <= 256, "MMA N: 16..256, step 16");
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Persistent: CTA c walks tiles t = c, c + gridDim.x, ... with
-// (m, n) = (t / n_tiles, t % n_tiles).  The shared-memory ring runs on a
-// k-block counter that continues across tiles; the accumulator alternates
-// between two TMEM buffers so that the epilogue of tile i overlaps the MMAs
-// of tile i + 1.
+// One output tile as the three roles see it.
+struct TileInfo {
+  const CUtensorMap* a;
+  const CUtensorMap* a_lo;
+  const CUtensorMap* b;
+  const CUtensorMap* b_lo;
+  float* D;
+  int64_t M, N;
+  int m0, n0;
+  int num_kb;
+  int bn;  // MMA N of this problem (multiple of 16, <= BN_MAX)
+};
+
+// One problem: tile t -> (m, n) = (t / n_tiles, t % n_tiles), N tile fastest
+// so that the N tiles of one M tile run together and share A through L2.
+template <int BN>
+struct SingleSched {
+  CUtensorMap a, a_lo, b, b_lo;
+  float* D;
+  int64_t M, N, total;
+  int num_kb, n_tiles;
+  __device__ __forceinline__ int64_t count() const { return total; }
+  __device__ __forceinline__ TileInfo tile(int64_t t) const {
+    TileInfo x;
+    x.a = &a;
+    x.a_lo = &a_lo;
+    x.b = &b;
+    x.b_lo = &b_lo;
+    x.D = D;
+    x.M = M;
+    x.N = N;
+    x.m0 = (int)((t / n_tiles) * kBM);
+    x.n0 = (int)((t % n_tiles) * BN);
+    x.num_kb = num_kb;
+    x.bn = BN;
+    return x;
+  }
+};
+
+// Several problems: a work list of (problem, m tile, n tile) over descriptors
+// in global memory (tensor maps written by the host before the launch).
+struct BatchSched {
+  const TcProblem* probs;
+  const int4* items;
+  int64_t n_items;
+  __device__ __forceinline__ int64_t count() const { return n_items; }
+  __device__ __forceinline__ TileInfo tile(int64_t t) const {
+    const int4 it = items[t];
+    const TcProblem& p = probs[it.x];
+    TileInfo x;
+    x.a = &p.a;
+    x.a_lo = &p.a_lo;
+    x.b = &p.b;
+    x.b_lo = &p.b_lo;
+    x.D = p.D;
+    x.M = p.M;
+    x.N = p.N;
+    x.m0 = it.y * kBM;
+    x.n0 = it.z * p.bn;
+    x.num_kb = p.num_kb;
+    x.bn = p.bn;
+    return x;
+  }
+};
+
+// Persistent: CTA c walks tiles t = c, c + gridDim.x, ...  The shared-memory
+// ring runs on a k-block counter that continues across tiles; the
+// accumulator alternates between two TMEM buffers so that the epilogue of
+// tile i overlaps the MMAs of tile i + 1.
 //   full[s]   TMA bytes of stage s landed        (producer -> MMA)
 //   empty[s]  MMAs reading stage s finished      (MMA -> producer, commit)
 //   tfull[b]  accumulator b complete             (MMA -> epilogue, commit)
 //   tempty[b] accumulator b drained to global    (epilogue warps -> MMA)
-template <int MODE, int BN, int NSUB, int STAGES>
+template <int MODE, int BN_MAX, int STAGES, class Sched>
 __global__ void __launch_bounds__(kThreads, 1)
-    mo_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_a_lo,
-                 const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_b_lo,
-                 float* __restrict__ D, int64_t M, int64_t N, int num_kb, int64_t m_tiles,
-                 int n_tiles, int* err_flag) {
-  using S = TcShape<MODE, BN, NSUB, STAGES>;
+    mo_tc_kernel(const __grid_constant__ Sched sched, int* err_flag) {
+  using S = TcShape<MODE, BN_MAX, STAGES>;
   using TR = TcTraits<MODE>;
-  constexpr int BNT = S::BNT;
-  constexpr uint32_t idesc = make_idesc(TR::kFmt, kBM, BN);
   constexpr uint32_t ACC = S::TMEM_COLS;  // columns of one accumulator buffer
 
   extern __shared__ unsigned char smem_raw[];
@@ -214,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   volatile int* abort_v = &abort_flag;
-  const int64_t total = m_tiles * (int64_t)n_tiles;
+  const int64_t total = sched.count();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -245,9 +302,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int m0 = (int)((t / n_tiles) * kBM);
-      const int n0 = (int)((t % n_tiles) * BNT);
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      const TileInfo x = sched.tile(t);
+      const uint32_t bytes = TR::kPlanes * (S::A_BYTES + (uint32_t)x.bn * kRowBytes);
+      for (int kb = 0; kb < x.num_kb; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
@@ -256,18 +313,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         const uint32_t st = base + s * S::STAGE_BYTES;
-        mbar_expect_tx(full_bar(s), S::STAGE_BYTES);
+        mbar_expect_tx(full_bar(s), bytes);
         const int kc = kb * TR::kBK;
-        tma_load_2d(st, &tm_a, full_bar(s), kc, m0);
-        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, &tm_a_lo, full_bar(s), kc, m0);
+        tma_load_2d(st, x.a, full_bar(s), kc, x.m0);
+        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, x.a_lo, full_bar(s), kc, x.m0);
         const uint32_t bst = st + TR::kPlanes * S::A_BYTES;
-#pragma unroll
-        for (int j = 0; j < NSUB; ++j) {
-          tma_load_2d(bst + j * BN * kRowBytes, &tm_b, full_bar(s), kc, n0 + j * BN);
-          if constexpr (TR::kPlanes == 2)
-            tma_load_2d(bst + S::B_BYTES + j * BN * kRowBytes, &tm_b_lo, full_bar(s), kc,
-                        n0 + j * BN);
-        }
+        tma_load_2d(bst, x.b, full_bar(s), kc, x.n0);
+        if constexpr (TR::kPlanes == 2) tma_load_2d(bst + S::B_BYTES, x.b_lo, full_bar(s), kc, x.n0);
       }
     }
     if (*abort_v) {
@@ -285,6 +337,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t it = 0, i = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+      const TileInfo x = sched.tile(t);
+      const uint32_t idesc = make_idesc(TR::kFmt, kBM, x.bn);
       const uint32_t b = i & 1u;
       if (!mbar_wait(tempty_bar(b), ((i >> 1) & 1u) ^ 1u, abort_v)) {
         flag_error(err_flag, abort_v, 2);
@@ -292,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t dacc = tmem + b * ACC;
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      for (int kb = 0; kb < x.num_kb; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         if (!mbar_wait(full_bar(s), ph, abort_v)) {
@@ -309,16 +363,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
           const uint32_t koff = kk * kUmmaKBytes;
-#pragma unroll
-          for (int j = 0; j < NSUB; ++j) {
-            const uint32_t d = dacc + j * BN;
-            const uint32_t boff = j * BN * kRowBytes + koff;
-            const uint32_t acc = (kb | kk) != 0;
-            umma<MODE>(d, sw128_desc(a_hi + koff), sw128_desc(b_hi + boff), idesc, acc);
-            if constexpr (MODE == QK_BF16X3) {
-              umma<MODE>(d, sw128_desc(a_hi + koff), sw128_desc(b_lo + boff), idesc, 1u);
-              umma<MODE>(d, sw128_desc(a_lo + koff), sw128_desc(b_hi + boff), idesc, 1u);
-            }
+          const uint32_t acc = (kb | kk) != 0;
+          umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_hi + koff), idesc, acc);
+          if constexpr (MODE == QK_BF16X3) {
+            umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_lo + koff), idesc, 1u);
+            umma<MODE>(dacc, sw128_desc(a_lo + koff), sw128_desc(b_hi + koff), idesc, 1u);
           }
         }
         umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
@@ -351,18 +400,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      const int64_t m0 = (t / n_tiles) * kBM;
-      const int64_t n0 = (t % n_tiles) * BNT;
-      const int64_t row = m0 + warp * 32 + lane;
+      const TileInfo x = sched.tile(t);
+      const int64_t row = x.m0 + warp * 32 + lane;
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
-      float* drow = D + row * N;
+      const int64_t N = x.N;
+      float* drow = x.D + row * N;
       const bool vec = (N % 4) == 0;
 #pragma unroll 1
-      for (int c = 0; c < BNT; c += 16) {
+      for (int c = 0; c < x.bn; c += 16) {
         float v[16];
         tmem_ld16(tbase + c, v);
-        if (row < M) {
-          const int64_t n = n0 + c;
+        if (row < x.M) {
+          const int64_t n = x.n0 + c;
           if (vec && n + 16 <= N) {
             float4* p = reinterpret_cast<float4*>(drow + n);
 #pragma unroll
@@ -427,48 +476,6 @@ bool make_map(CUtensorMap* m, const void* ptr, bool f32, int64_t inner, int64_t 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, int BN, int NSUB, int STAGES>
-cudaError_t launch_cfg(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                       int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
-  using S = TcShape<MODE, BN, NSUB, STAGES>;
-  using TR = TcTraits<MODE>;
-  static_assert(S::SMEM <= 232448, "shared memory budget");
-  const bool f32 = MODE == QK_TF32;
-  const int64_t M = ao.rows;
-  if (M == 0 || N == 0) return cudaSuccess;
-  if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
-  CUtensorMap ta, ta_lo, tb, tb_lo;
-  if (!make_map(&ta, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
-  if (TR::kPlanes == 2) {
-    if (!make_map(&ta_lo, ao.a_lo, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
-    if (!make_map(&tb_lo, c_lo, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
-  } else {
-    ta_lo = ta;
-    tb_lo = tb;
-  }
-  auto kern = mo_tc_kernel<MODE, BN, NSUB, STAGES>;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-  if (e != cudaSuccess) return e;
-  // TMEM is not oversubscribed: resident CTAs x columns <= 512
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, S::SMEM);
-  if (e != cudaSuccess) return e;
-  if (occ < 1 || occ * 2 * (int)S::TMEM_COLS > 512) return cudaErrorInvalidConfiguration;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
-  const int64_t m_tiles = (M + kBM - 1) / kBM;
-  const int64_t n_tiles = (N + S::BNT - 1) / S::BNT;
-  const int64_t total = m_tiles * n_tiles;
-  const int64_t grid = total < (int64_t)sms * occ ? total : (int64_t)sms * occ;
-  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(ta, ta_lo, tb, tb_lo, out, M, N, num_kb, m_tiles,
-                                                 (int)n_tiles, err_flag);
-  return cudaGetLastError();
-}
-
 constexpr int stages_for(int mode, int bn) {
   // fill ~220 KB of shared memory, at most 8 stages
   return (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes)) > 8
@@ -476,11 +483,57 @@ constexpr int stages_for(int mode, int bn) {
              : (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes));
 }
 
+// Grid of resident CTAs for a kernel instance (TMEM never oversubscribed).
+template <class Kern>
+cudaError_t persistent_grid(Kern kern, size_t smem, uint32_t tmem_cols, int64_t work,
+                            int64_t* grid) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1 || occ * 2 * (int)tmem_cols > 512) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *grid = work < (int64_t)sms * occ ? work : (int64_t)sms * occ;
+  return cudaSuccess;
+}
+
 template <int MODE, int BN>
-cudaError_t launch_bn(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                      int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
+cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                          int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
   constexpr int ST = stages_for(MODE, BN);
-  return launch_cfg<MODE, BN, 1, ST>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+  using S = TcShape<MODE, BN, ST>;
+  using TR = TcTraits<MODE>;
+  static_assert(S::SMEM <= 232448, "shared memory budget");
+  const bool f32 = MODE == QK_TF32;
+  const int64_t M = ao.rows;
+  if (M == 0 || N == 0) return cudaSuccess;
+  if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
+  SingleSched<BN> sc;
+  if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+  if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+  if (TR::kPlanes == 2) {
+    if (!make_map(&sc.a_lo, ao.a_lo, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&sc.b_lo, c_lo, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+  } else {
+    sc.a_lo = sc.a;
+    sc.b_lo = sc.b;
+  }
+  sc.D = out;
+  sc.M = M;
+  sc.N = N;
+  sc.num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
+  sc.n_tiles = (int)((N + BN - 1) / BN);
+  sc.total = ((M + kBM - 1) / kBM) * sc.n_tiles;
+  auto kern = mo_tc_kernel<MODE, BN, ST, SingleSched<BN>>;
+  int64_t grid = 0;
+  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_COLS, sc.total, &grid);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
+  return cudaGetLastError();
 }
 
 template <int MODE>
@@ -488,14 +541,44 @@ cudaError_t launch_mode(const TcConfig& cfg, const AOTensor& ao, int64_t K, cons
                         const void* c_lo, int64_t ldc, int64_t N, float* out, int* err_flag,
                         cudaStream_t s) {
   switch (cfg.bn) {
-    case 16: return launch_bn<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 32: return launch_bn<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 64: return launch_bn<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 96: return launch_bn<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 128: return launch_bn<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 160: return launch_bn<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 192: return launch_bn<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 256: return launch_bn<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 16: return launch_single<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 32: return launch_single<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 64: return launch_single<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 96: return launch_single<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 128: return launch_single<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 160: return launch_single<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 192: return launch_single<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 256: return launch_single<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE, int BN_MAX>
+cudaError_t launch_batch_bn(const TcProblem* probs, const int4* items, int64_t n_items,
+                            int* err_flag, cudaStream_t s) {
+  constexpr int ST = stages_for(MODE, BN_MAX);
+  using S = TcShape<MODE, BN_MAX, ST>;
+  static_assert(S::SMEM <= 232448, "shared memory budget");
+  if (n_items == 0) return cudaSuccess;
+  BatchSched sc{probs, items, n_items};
+  auto kern = mo_tc_kernel<MODE, BN_MAX, ST, BatchSched>;
+  int64_t grid = 0;
+  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_COLS, n_items, &grid);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_batch_mode(int bn_max, const TcProblem* probs, const int4* items,
+                              int64_t n_items, int* err_flag, cudaStream_t s) {
+  switch (bn_max) {
+    case 64: return launch_batch_bn<MODE, 64>(probs, items, n_items, err_flag, s);
+    case 96: return launch_batch_bn<MODE, 96>(probs, items, n_items, err_flag, s);
+    case 128: return launch_batch_bn<MODE, 128>(probs, items, n_items, err_flag, s);
+    case 160: return launch_batch_bn<MODE, 160>(probs, items, n_items, err_flag, s);
+    case 192: return launch_batch_bn<MODE, 192>(probs, items, n_items, err_flag, s);
+    case 256: return launch_batch_bn<MODE, 256>(probs, items, n_items, err_flag, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -514,6 +597,40 @@ TcConfig tc_default_config(int mode, int64_t mo_num) {
       break;
     }
   return TcConfig{bn, 1, 0};
+}
+
+const int kBatchBnMax[] = {64, 96, 128, 160, 192, 256};
+
+bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                     int64_t ldc, int64_t N, float* out, int bn, TcProblem* p) {
+  const bool f32 = mode == QK_TF32;
+  const int bk = f32 ? TcTraits<QK_TF32>::kBK : TcTraits<QK_BF16X3>::kBK;
+  if (bn % 16 != 0 || bn < 16 || bn > 256) return false;
+  if (ao.rows > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return false;
+  if (!make_map(&p->a, ao.a, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
+  if (!make_map(&p->b, c_hi, f32, K, N, ldc, bk, bn)) return false;
+  if (!f32) {
+    if (!make_map(&p->a_lo, ao.a_lo, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
+    if (!make_map(&p->b_lo, c_lo, f32, K, N, ldc, bk, bn)) return false;
+  } else {
+    p->a_lo = p->a;
+    p->b_lo = p->b;
+  }
+  p->D = out;
+  p->M = ao.rows;
+  p->N = N;
+  p->num_kb = (int)((K + bk - 1) / bk);
+  p->bn = bn;
+  return true;
+}
+
+cudaError_t launch_mo_tc_batch(int mode, int bn_max, const TcProblem* probs, const int4* items,
+                               int64_t n_items, int* err_flag, cudaStream_t s) {
+  if (mode == QK_BF16X3)
+    return launch_batch_mode<QK_BF16X3>(bn_max, probs, items, n_items, err_flag, s);
+  if (mode == QK_TF32)
+    return launch_batch_mode<QK_TF32>(bn_max, probs, items, n_items, err_flag, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,

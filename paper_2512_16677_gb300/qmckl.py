@@ -64,6 +64,16 @@ SIGNATURES = {
     "qk_mo_vgl_backward_device": [_P, _P, _I64, _P, _P],
     "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "qk_set_timing": [_P, _I32],
+    "qk_batch_create": [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)],
+    "qk_batch_destroy": [_P],
+    "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
+    "qk_batch_set_stream": [_P, _P],
+    "qk_batch_set_graph": [_P, _I32],
+    "qk_batch_set_tile": [_P, _I32],
+    "qk_batch_get_tile": [_P, ctypes.POINTER(_I32)],
+    "qk_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
+    "qk_batch_synchronize": [_P],
+    "qk_batch_autotune": [_P, ctypes.POINTER(_P), _I32, ctypes.POINTER(_D)],
     "qk_contract_device": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
     "qk_contract_device_noalloc": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
     "qk_get_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32],
@@ -369,3 +379,87 @@ class Context:
 
     def _walk_elec(self):
         return self._walk_elec_shape
+
+
+class Batch:
+    """Several contexts (molecules of uneven sizes) evaluated by two
+    persistent launches captured in a CUDA graph (qk_batch_* calls)."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        for c in self.contexts:
+            c.ensure_workspace()
+        st = self.lib.qk_batch_create(ctypes.byref(h), len(self.contexts), arr)
+        if st != QK_SUCCESS:
+            raise QmcklError(st, "qk_batch_create: contexts must be set and share a "
+                                 "tensor-core mode")
+        self.h = h
+        self._outs = None
+
+    def _check(self, st, what):
+        if st != QK_SUCCESS:
+            buf = ctypes.create_string_buffer(512)
+            self.lib.qk_batch_last_error(self.h, buf, 512)
+            raise QmcklError(st, f"{what}: {buf.value.decode(errors='replace')}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.qk_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        import torch
+        self._check(self.lib.qk_batch_set_stream(self.h, ctypes.c_void_p(
+            torch.cuda.current_stream().cuda_stream)), "set_stream")
+
+    def set_graph(self, enable: bool):
+        self._check(self.lib.qk_batch_set_graph(self.h, 1 if enable else 0), "set_graph")
+
+    def set_tile(self, bn_max: int):
+        self._check(self.lib.qk_batch_set_tile(self.h, bn_max), "set_tile")
+
+    @property
+    def tile(self) -> int:
+        v = ctypes.c_int32()
+        self._check(self.lib.qk_batch_get_tile(self.h, ctypes.byref(v)), "get_tile")
+        return v.value
+
+    def outputs(self):
+        """One float32 CUDA tensor [walk][elec][5][mo] per context (kept)."""
+        import torch
+        if self._outs is None:
+            self._outs = [torch.empty((c._walk_elec_shape[0], c._walk_elec_shape[1], 5, c.mo_num),
+                                      dtype=torch.float32, device="cuda")
+                          for c in self.contexts]
+        return self._outs
+
+    def _ptrs(self, outs):
+        return (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+
+    def run(self, outs=None):
+        self._bind_stream()
+        outs = self.outputs() if outs is None else outs
+        sizes = (ctypes.c_int64 * len(outs))(*[o.numel() for o in outs])
+        self._check(self.lib.qk_batch_run(self.h, self._ptrs(outs), sizes), "batch_run")
+        return outs
+
+    def synchronize(self):
+        self._check(self.lib.qk_batch_synchronize(self.h), "batch_synchronize")
+
+    def autotune(self, reps: int = 3):
+        """Time every instantiated tile width on this batch; keep the fastest.
+        Returns (bn_max, ms per contraction launch)."""
+        self._bind_stream()
+        best = ctypes.c_double()
+        self._check(self.lib.qk_batch_autotune(self.h, self._ptrs(self.outputs()), reps,
+                                               ctypes.byref(best)), "batch_autotune")
+        return self.tile, best.value
