@@ -41,7 +41,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPT = 32;  // points per tile: one lane per point in phase 1
-static_assert(kPT == kAOTilePoints, "tile size shared with the batch work list");
+static_assert(kTilePoints <= kPT, "a tiled tile fits the 32 lanes of phase 1");
 
 // Shared memory of one CTA (templated on the arithmetic type).
 template <typename T>
@@ -52,17 +52,16 @@ struct AOShared {
   T r2max[kMaxShellsChunk];
   int prim0[kMaxShellsChunk];    // first primitive, local to the chunk
   int nprim[kMaxShellsChunk];
-  int lmom[kMaxShellsChunk];
   T g[kMaxPrimsChunk];
   T c[kMaxPrimsChunk];
   T M[kChunkAO];
-  unsigned char ao_shell[kChunkAO];  // local shell of each local AO
-  unsigned char ao_j[kChunkAO];      // Cartesian component index
-  // per tile
+  int ao_info[kChunkAO];  // local shell | l << 8 | Cartesian index << 12
+  // per tile: [point][shell] with one pad column, so that phase 1 (lanes over
+  // points) and phase 2 (lanes over AOs of one point) hit distinct banks
   T pt[kPT][3];
   T pt_lo[kPT][3];
-  T d[3][kMaxShellsChunk][kPT];
-  T S[3][kMaxShellsChunk][kPT];
+  T d[3][kPT][kMaxShellsChunk + 1];
+  T S[3][kPT][kMaxShellsChunk + 1];
 };
 
 // Two adjacent AOs (local columns 2q, 2q+1) of one component row.
@@ -99,16 +98,17 @@ struct PairStore<float, true> {
 // The five components of local AO `al` at tile point `pl`.
 template <typename T>
 __device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, T out[5]) {
-  const int sl = sh.ao_shell[al];
-  const T S0 = sh.S[0][sl][pl], S1 = sh.S[1][sl][pl], S2 = sh.S[2][sl][pl];
+  const int info = sh.ao_info[al];
+  const int sl = info & 0xff;
+  const T S0 = sh.S[0][pl][sl], S1 = sh.S[1][pl][sl], S2 = sh.S[2][pl][sl];
   if (S0 == T(0) && S1 == T(0) && S2 == T(0)) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c] = T(0);
     return;
   }
-  const int l = sh.lmom[sl];
-  const int j = sh.ao_j[al];
-  const T dx = sh.d[0][sl][pl], dy = sh.d[1][sl][pl], dz = sh.d[2][sl][pl];
+  const int l = (info >> 8) & 0xf;
+  const int j = info >> 12;
+  const T dx = sh.d[0][pl][sl], dy = sh.d[1][pl][sl], dz = sh.d[2][pl][sl];
   const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
   const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
   const T X = sel4(a, T(1), dx, x2, x2 * dx);
@@ -135,10 +135,11 @@ __device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, 
 
 // Chunk q of one problem over point tiles t_begin, t_begin + t_step, ...
 // below t_end (the whole CTA calls this; it starts with a block barrier).
-template <typename T, bool kSplit, bool kChunked>
+template <typename T, bool kSplit, bool kChunked, bool kTiled>
 __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDev& pts,
                                                const AOTensor& out, int q, int64_t t_begin,
                                                int64_t t_end, int64_t t_step, AOShared<T>& sh) {
+  constexpr int TP = kTiled ? kTilePoints : kPT;  // points per tile
   using A = Arith<T>;
   __syncthreads();  // the previous call's readers of the shared tables are done
   const int4 ch = b.chunk[q];
@@ -166,7 +167,6 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
     sh.r2max[i] = A::r2max(b, s);
     sh.prim0[i] = b.shell_prim0[s] - p_first;
     sh.nprim[i] = b.shell_nprim[s];
-    sh.lmom[i] = b.shell_l[s];
   }
   const int np_chunk = b.shell_prim0[ch.y - 1] + b.shell_nprim[ch.y - 1] - p_first;
   for (int i = tid; i < np_chunk; i += kThreads) {
@@ -176,8 +176,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   for (int i = tid; i < na; i += kThreads) {
     const int ao = ch.z + i;
     const int s = b.ao_shell[ao];
-    sh.ao_shell[i] = (unsigned char)(s - ch.x);
-    sh.ao_j[i] = (unsigned char)(ao - b.shell_ao0[s]);
+    sh.ao_info[i] = (s - ch.x) | (b.shell_l[s] << 8) | ((ao - b.shell_ao0[s]) << 12);
     sh.M[i] = A::aofac(b, ao);
   }
   const T Tthr = A::thr(b);
@@ -185,10 +184,10 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
 
   for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
-    const int64_t p0 = ptile * kPT;
+    const int64_t p0 = ptile * TP;
     __syncthreads();  // tables ready / previous tile's phase 2 done with shared data
     // ---- phase 0: the tile's points
-    if (tid < kPT) {
+    if (tid < TP) {
       const int64_t ip = p0 + tid;
       if (ip < n) {
         if constexpr (sizeof(T) == 8) {
@@ -206,10 +205,11 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
     }
     __syncthreads();
     // ---- phase 1: one warp per shell, lanes over the tile's points
+    int live = 0;
     for (int sl = warp; sl < ns; sl += kThreads / 32) {
       const int pl = lane;
       T dx = T(0), dy = T(0), dz = T(0), S0 = T(0), S1 = T(0), S2 = T(0);
-      if (p0 + pl < n) {
+      if (pl < TP && p0 + pl < n) {
         if constexpr (sizeof(T) == 8) {
           dx = __dsub_rn(sh.pt[pl][0], sh.nuc[sl][0]);
           dy = __dsub_rn(sh.pt[pl][1], sh.nuc[sl][1]);
@@ -236,16 +236,28 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
           }
         }
       }
-      sh.d[0][sl][pl] = dx;
-      sh.d[1][sl][pl] = dy;
-      sh.d[2][sl][pl] = dz;
-      sh.S[0][sl][pl] = S0;
-      sh.S[1][sl][pl] = S1;
-      sh.S[2][sl][pl] = S2;
+      sh.d[0][pl][sl] = dx;
+      sh.d[1][pl][sl] = dy;
+      sh.d[2][pl][sl] = dz;
+      sh.S[0][pl][sl] = S0;
+      sh.S[1][pl][sl] = S1;
+      sh.S[2][pl][sl] = S2;
+      live |= (S0 != T(0) || S1 != T(0) || S2 != T(0));
     }
-    __syncthreads();
+    // block barrier; in the tiled layout it also tells whether any entry of
+    // block (tile, chunk) survived screening
+    live = __syncthreads_or(live);
+    if constexpr (kTiled) {
+      if (tid == 0) out.mask[ptile * out.nchunk + q] = live ? 1 : 0;
+      if (!live) continue;  // not written: the contraction skips this block
+      // rows 125..127 of the tile are zero
+      if (warp < kTileRows - 5 * kTilePoints) {
+        const int64_t prow = ptile * kTileRows + 5 * kTilePoints + warp;
+        PairStore<T, kSplit>::put(out, prow, col0 + 2 * lane, T(0), T(0));
+      }
+    }
     // ---- phase 2: one warp per point, lane = AO pair (2 lane, 2 lane + 1)
-    for (int pl = warp; pl < kPT; pl += kThreads / 32) {
+    for (int pl = warp; pl < TP; pl += kThreads / 32) {
       const int64_t ip = p0 + pl;
       if (ip >= n) break;
       const int a0 = 2 * lane, a1 = 2 * lane + 1;
@@ -262,7 +274,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
 #pragma unroll
         for (int c = 0; c < 5; ++c) v1[c] = T(0);
       }
-      const int64_t row = 5 * ip;
+      const int64_t row = kTiled ? ptile * kTileRows + 5 * pl : 5 * ip;
       if constexpr (kChunked) {
         // chunk window: padding columns are written as zeros
 #pragma unroll
@@ -280,13 +292,13 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   }
 }
 
-template <typename T, bool kSplit, bool kChunked>
+template <typename T, bool kSplit, bool kChunked, bool kTiled>
 __global__ void __launch_bounds__(kThreads)
     ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AOShared<T>& sh = *reinterpret_cast<AOShared<T>*>(smem_raw);
-  ao_chunk_tiles<T, kSplit, kChunked>(b, pts, out, blockIdx.x, blockIdx.y, n_ptiles, gridDim.y,
-                                      sh);
+  ao_chunk_tiles<T, kSplit, kChunked, kTiled>(b, pts, out, blockIdx.x, blockIdx.y, n_ptiles,
+                                              gridDim.y, sh);
 }
 
 // Several problems in one persistent launch: CTAs stride over a work list of
@@ -300,19 +312,20 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int4 w = items[i];
     const AOProblem& P = probs[w.x];
-    ao_chunk_tiles<float, kSplit, true>(P.b, P.p, P.out, w.y, w.z, w.w, 1, sh);
+    ao_chunk_tiles<float, kSplit, true, true>(P.b, P.p, P.out, w.y, w.z, w.w, 1, sh);
   }
 }
 
-template <typename T, bool kSplit, bool kChunked>
+template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
 cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
                       cudaStream_t s) {
   constexpr size_t smem = sizeof(AOShared<T>);
-  auto kern = ao_vgl_kernel<T, kSplit, kChunked>;
+  constexpr int TP = kTiled ? kTilePoints : kPT;
+  auto kern = ao_vgl_kernel<T, kSplit, kChunked, kTiled>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t n_ptiles = (p.n + kPT - 1) / kPT;
+  const int64_t n_ptiles = (p.n + TP - 1) / TP;
   if (n_ptiles == 0 || b.nchunk == 0) return cudaSuccess;
   int occ = 1, sms = 1, dev = 0;
   cudaGetDevice(&dev);
@@ -357,6 +370,17 @@ cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* 
 
 cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s) {
+  if (out.tiled) {
+    switch (out_mode) {
+      case QK_FP32:
+      case QK_TF32:
+        return launch_ao<float, false, true, true>(b, p, out, s);
+      case QK_BF16X3:
+        return launch_ao<float, true, true, true>(b, p, out, s);
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
   if (out.chunked) {
     switch (out_mode) {
       case QK_FP64:

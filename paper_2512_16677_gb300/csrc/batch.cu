@@ -75,10 +75,10 @@ qk_status build(qk_batch b, float* const* outs) {
     aop[i].out = v.ao;
     const int bn = pick_bn(v.mo_num, b->bn_max);
     if (!tc_make_problem(b->mode, v.ao, v.kpad, v.c_hi, v.c_lo, v.kpad, v.mo_num, outs[i], bn,
-                         &tcp[i]))
+                         5 * v.p.n, &tcp[i]))
       return bfail(b, QK_ERR_CUDA, "tensor map encoding failed");
     // ao items: 8 point tiles of one chunk each
-    const int64_t tiles = (v.p.n + kAOTilePoints - 1) / kAOTilePoints;
+    const int64_t tiles = (v.p.n + kTilePoints - 1) / kTilePoints;
     const int64_t per = 8;
     for (int q = 0; q < v.b.nchunk; ++q)
       for (int64_t t = 0; t < tiles; t += per) {
@@ -87,7 +87,7 @@ qk_status build(qk_batch b, float* const* outs) {
         ao_cost.push_back((double)(e - t));
       }
     // contraction items: every (M tile, N tile); cost ~ K blocks x MMA N
-    const int64_t mt = (v.ao.rows + 127) / 128, nt = (v.mo_num + bn - 1) / bn;
+    const int64_t mt = v.ao.rows / kTileRows, nt = (v.mo_num + bn - 1) / bn;
     for (int64_t m = 0; m < mt; ++m)
       for (int64_t k = 0; k < nt; ++k) {
         tc_items.push_back(make_int4(i, (int)m, (int)k, 0));
@@ -137,6 +137,7 @@ qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig)
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
     sig->push_back((uintptr_t)v.ao.a);
     sig->push_back((uintptr_t)v.ao.a_lo);
+    sig->push_back((uintptr_t)v.ao.mask);
     sig->push_back((uintptr_t)v.p.x);
     sig->push_back((uintptr_t)v.p.n);
     sig->push_back((uintptr_t)v.b.chunk);
@@ -163,7 +164,7 @@ qk_status prepare(qk_batch b, float* const* outs, const int64_t* sizes) {
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
     if (v.mode != b->mode)
       return bfail(b, QK_ERR_INVALID_ARG, "context " + std::to_string(i) + " changed mode");
-    if (sizes && sizes[i] < v.ao.rows * v.mo_num)
+    if (sizes && sizes[i] < 5 * v.p.n * v.mo_num)
       return bfail(b, QK_ERR_BAD_SIZE, "output " + std::to_string(i) + " too small");
   }
   std::vector<uintptr_t> sig;

@@ -295,17 +295,22 @@ qk_status ensure_mo(qk_context c) {
 // Columns of the contraction's AO tensor: one 64-wide window per chunk.
 int64_t kpad_of(qk_context c) { return (int64_t)c->chunks.size() * kChunkAO; }
 
+// Tensor-core modes use the tiled layout: kTilePoints points per 128-row
+// tile, plus one live-block byte per (tile, chunk).
+bool tiled_mode(int mode) { return mode == QK_BF16X3 || mode == QK_TF32; }
+int64_t ao_tiles(qk_context c) { return (c->point_num + kTilePoints - 1) / kTilePoints; }
+
 size_t ao_tensor_bytes(qk_context c, int mode) {
-  const size_t rows = (size_t)5 * c->point_num;
   const size_t ld = (size_t)kpad_of(c);
-  switch (mode) {
-    case QK_FP64:
-      return align_up(rows * ld * sizeof(double), 256);
-    case QK_BF16X3:
-      return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256);
-    default:
-      return align_up(rows * ld * sizeof(float), 256);
+  if (tiled_mode(mode)) {
+    const size_t rows = (size_t)ao_tiles(c) * kTileRows;
+    const size_t mask = align_up((size_t)ao_tiles(c) * c->chunks.size(), 256);
+    if (mode == QK_BF16X3) return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256) + mask;
+    return align_up(rows * ld * sizeof(float), 256) + mask;
   }
+  const size_t rows = (size_t)5 * c->point_num;
+  if (mode == QK_FP64) return align_up(rows * ld * sizeof(double), 256);
+  return align_up(rows * ld * sizeof(float), 256);
 }
 
 // Bind the context to the current device on first use; allocate the
@@ -346,12 +351,24 @@ qk_status workspace(qk_context c, size_t need, void** out) {
 
 AOTensor ao_view(qk_context c, void* ws, int mode) {
   AOTensor t{};
-  t.rows = 5 * c->point_num;
   t.ld = kpad_of(c);
   t.chunked = true;
+  t.nchunk = (int)c->chunks.size();
   t.a = ws;
-  if (mode == QK_BF16X3)
-    t.a_lo = (unsigned char*)ws + align_up(t.rows * t.ld * sizeof(__nv_bfloat16), 256);
+  if (tiled_mode(mode)) {
+    t.tiled = true;
+    t.rows = ao_tiles(c) * kTileRows;
+    const size_t es = mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float);
+    const size_t plane = align_up((size_t)t.rows * t.ld * es, 256);
+    unsigned char* p = (unsigned char*)ws + plane;
+    if (mode == QK_BF16X3) {
+      t.a_lo = p;
+      p += plane;
+    }
+    t.mask = p;
+  } else {
+    t.rows = 5 * c->point_num;
+  }
   return t;
 }
 
@@ -774,7 +791,7 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
       const bool split = c->mode == QK_BF16X3;
       e = launch_mo_tc(c->mode, ao, KP, split ? (const void*)c->c_hi : (const void*)c->c32p,
                        split ? (const void*)c->c_lo : nullptr, KP, N, (float*)dout,
-                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream);
+                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream, M);
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "mo_vgl contraction");

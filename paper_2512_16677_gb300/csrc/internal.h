@@ -64,13 +64,25 @@ struct PointsDev {
 // ld elements apart.  chunked: AO n of chunk q sits in column
 // 64q + (n - first AO of q) and the padding columns hold zeros (the layout the
 // contraction reads); otherwise column = AO index.
+//
+// tiled (tensor-core modes): points go in tiles of kTilePoints; the 125
+// (point, component) rows of tile t are rows 128 t .. 128 t + 124, rows
+// 125..127 of each tile are zero, and mask[t * nchunk + q] says whether
+// block (t, q) holds any entry that survived screening.  Blocks with a zero
+// mask byte are not written and the contraction skips them (the sparse-AO
+// MO product of Sec. 3.2 at tile granularity).
 struct AOTensor {
-  void* a;       // FP64 / FP32 values, or bf16 "hi" plane
-  void* a_lo;    // bf16 "lo" plane (QK_BF16X3 only)
-  int64_t rows;  // 5 * point_num
-  int64_t ld;    // row stride in elements
+  void* a;        // FP64 / FP32 values, or bf16 "hi" plane
+  void* a_lo;     // bf16 "lo" plane (QK_BF16X3 only)
+  int64_t rows;   // rows of the tensor: 5 * point_num, or 128 * tiles when tiled
+  int64_t ld;     // row stride in elements
   bool chunked;
+  bool tiled;
+  uint8_t* mask;  // [tiles][nchunk] when tiled
+  int nchunk;
 };
+constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
+constexpr int kTileRows = 128;
 
 // A device allocation owned by the library.
 struct DevBuf {
@@ -128,9 +140,11 @@ struct TcConfig {
   int nsub;    // MMA instructions along N per CTA
   int stages;  // shared-memory pipeline depth
 };
+// out_rows: rows of D (5 * points); -1 = ao.rows (dense layout).
 cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
                          const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
-                         const TcConfig& cfg, int* err_flag, cudaStream_t s);
+                         const TcConfig& cfg, int* err_flag, cudaStream_t s,
+                         int64_t out_rows = -1);
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
 
@@ -140,15 +154,18 @@ TcConfig tc_default_config(int mode, int64_t mo_num);
 struct TcProblem {
   CUtensorMap a, a_lo, b, b_lo;  // AO hi / lo, C hi / lo (lo = hi for TF32)
   float* D;                      // [M][N] output
-  int64_t M, N;
+  const uint8_t* mask;           // tiled AO tensor: [tiles][nchunk] live blocks (else NULL)
+  int64_t M, N;                  // output rows (5 * points) and columns
   int num_kb;                    // K blocks
   int bn;                        // MMA N (multiple of 16, <= the launch's bn_max)
+  int nchunk;
 };
 // BN_MAX values instantiated for multi-problem launches.
 extern const int kBatchBnMax[6];
 // Fill a TcProblem (host): tensor maps over the AO tensor and C planes.
 bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                     int64_t ldc, int64_t N, float* out, int bn, TcProblem* p);
+                     int64_t ldc, int64_t N, float* out, int bn, int64_t out_rows,
+                     TcProblem* p);
 // Persistent launch over a work list of int4 (problem, m tile, n tile, 0).
 cudaError_t launch_mo_tc_batch(int mode, int bn_max, const TcProblem* probs, const int4* items,
                                int64_t n_items, int* err_flag, cudaStream_t s);
@@ -160,10 +177,10 @@ struct AOProblem {
   AOTensor out;  // chunked layout
 };
 // Persistent ao_vgl over a work list of int4 (problem, chunk, first tile,
-// end tile); tiles are 32 points.  split: bf16 hi/lo planes, else FP32.
+// end tile) on tiled AO tensors (kTilePoints points per tile).  split: bf16
+// hi/lo planes, else FP32.
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s);
-constexpr int kAOTilePoints = 32;
 
 // Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
 // points, reduced into d_dR [nucl][3] (FP64).

@@ -184,11 +184,20 @@ struct TileInfo {
   const CUtensorMap* b;
   const CUtensorMap* b_lo;
   float* D;
-  int64_t M, N;
-  int m0, n0;
+  const uint8_t* kmask;  // live 64-column chunks of this M tile (NULL: all live)
+  int64_t M, N;          // output rows and columns
+  int m0, n0;            // AO-tensor row and output column of the tile
   int num_kb;
-  int bn;  // MMA N of this problem (multiple of 16, <= BN_MAX)
+  int bn;                // MMA N of this problem (multiple of 16, <= BN_MAX)
+  bool tiled;            // rows: 125 live of 128, output row = 125 (m0/128) + local
 };
+
+template <int MODE>
+__device__ __forceinline__ bool kb_live(const TileInfo& x, int kb) {
+  // K blocks of 64 bf16 or 32 TF32 elements; the mask is per 64-column chunk
+  constexpr int kShift = TcTraits<MODE>::kBK == 64 ? 0 : 1;
+  return x.kmask == nullptr || x.kmask[kb >> kShift] != 0;
+}
 
 // One problem: tile t -> (m, n) = (t / n_tiles, t % n_tiles), N tile fastest
 // so that the N tiles of one M tile run together and share A through L2.
@@ -196,22 +205,27 @@ template <int BN>
 struct SingleSched {
   CUtensorMap a, a_lo, b, b_lo;
   float* D;
+  const uint8_t* mask;  // [m tiles][nchunk] when tiled
   int64_t M, N, total;
-  int num_kb, n_tiles;
+  int num_kb, n_tiles, nchunk;
+  bool tiled;
   __device__ __forceinline__ int64_t count() const { return total; }
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
     TileInfo x;
+    const int64_t mt = t / n_tiles;
     x.a = &a;
     x.a_lo = &a_lo;
     x.b = &b;
     x.b_lo = &b_lo;
     x.D = D;
+    x.kmask = tiled ? mask + mt * nchunk : nullptr;
     x.M = M;
     x.N = N;
-    x.m0 = (int)((t / n_tiles) * kBM);
+    x.m0 = (int)(mt * kBM);
     x.n0 = (int)((t % n_tiles) * BN);
     x.num_kb = num_kb;
     x.bn = BN;
+    x.tiled = tiled;
     return x;
   }
 };
@@ -232,12 +246,14 @@ struct BatchSched {
     x.b = &p.b;
     x.b_lo = &p.b_lo;
     x.D = p.D;
+    x.kmask = p.mask ? p.mask + (int64_t)it.y * p.nchunk : nullptr;
     x.M = p.M;
     x.N = p.N;
     x.m0 = it.y * kBM;
     x.n0 = it.z * p.bn;
     x.num_kb = p.num_kb;
     x.bn = p.bn;
+    x.tiled = p.mask != nullptr;
     return x;
   }
 };
@@ -304,9 +320,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const TileInfo x = sched.tile(t);
       const uint32_t bytes = TR::kPlanes * (S::A_BYTES + (uint32_t)x.bn * kRowBytes);
-      for (int kb = 0; kb < x.num_kb; ++kb, ++it) {
+      for (int kb = 0; kb < x.num_kb; ++kb) {
+        if (!kb_live<MODE>(x, kb)) continue;  // block of screened AOs: never read
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
+        ++it;
         if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
           flag_error(err_flag, abort_v, 1);
           ok = false;
@@ -346,9 +364,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t dacc = tmem + b * ACC;
-      for (int kb = 0; kb < x.num_kb; ++kb, ++it) {
+      uint32_t issued = 0;
+      for (int kb = 0; kb < x.num_kb; ++kb) {
+        if (!kb_live<MODE>(x, kb)) continue;
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
+        ++it;
         if (!mbar_wait(full_bar(s), ph, abort_v)) {
           flag_error(err_flag, abort_v, 2);
           ok = false;
@@ -363,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
           const uint32_t koff = kk * kUmmaKBytes;
-          const uint32_t acc = (kb | kk) != 0;
+          const uint32_t acc = (issued | (uint32_t)kk) != 0;  // first live block overwrites
           umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_hi + koff), idesc, acc);
           if constexpr (MODE == QK_BF16X3) {
             umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_lo + koff), idesc, 1u);
@@ -371,6 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
+        ++issued;
       }
       // accumulator b complete (after an abort this still waits for the MMAs
       // already issued, so the epilogue never reads a buffer being written)
@@ -401,7 +423,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       tc_fence_after();
       const TileInfo x = sched.tile(t);
-      const int64_t row = x.m0 + warp * 32 + lane;
+      const int local = warp * 32 + lane;
+      const int64_t row = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) + local
+                                  : (int64_t)x.m0 + local;
+      const bool row_ok = row < x.M && (!x.tiled || local < 5 * kTilePoints);
+      bool any_live = x.kmask == nullptr;
+      for (int kb = 0; kb < x.num_kb && !any_live; ++kb) any_live = kb_live<MODE>(x, kb);
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
       const int64_t N = x.N;
       float* drow = x.D + row * N;
@@ -409,8 +436,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int c = 0; c < x.bn; c += 16) {
         float v[16];
-        tmem_ld16(tbase + c, v);
-        if (row < x.M) {
+        if (any_live) {
+          tmem_ld16(tbase + c, v);
+        } else {  // every AO of the tile was screened: the MOs are exactly zero
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+        }
+        if (row_ok) {
           const int64_t n = x.n0 + c;
           if (vec && n + 16 <= N) {
             float4* p = reinterpret_cast<float4*>(drow + n);
@@ -503,7 +535,8 @@ cudaError_t persistent_grid(Kern kern, size_t smem, uint32_t tmem_cols, int64_t 
 
 template <int MODE, int BN>
 cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                          int64_t ldc, int64_t N, float* out, int* err_flag, cudaStream_t s) {
+                          int64_t ldc, int64_t N, float* out, int64_t out_rows, int* err_flag,
+                          cudaStream_t s) {
   constexpr int ST = stages_for(MODE, BN);
   using S = TcShape<MODE, BN, ST>;
   using TR = TcTraits<MODE>;
@@ -512,6 +545,7 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   const int64_t M = ao.rows;
   if (M == 0 || N == 0) return cudaSuccess;
   if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
+  if (ao.tiled && M % kBM != 0) return cudaErrorInvalidValue;
   SingleSched<BN> sc;
   if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
   if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
@@ -523,7 +557,10 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
     sc.b_lo = sc.b;
   }
   sc.D = out;
-  sc.M = M;
+  sc.mask = ao.tiled ? ao.mask : nullptr;
+  sc.tiled = ao.tiled;
+  sc.nchunk = ao.nchunk;
+  sc.M = ao.tiled ? out_rows : M;
   sc.N = N;
   sc.num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
   sc.n_tiles = (int)((N + BN - 1) / BN);
@@ -538,17 +575,17 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
 
 template <int MODE>
 cudaError_t launch_mode(const TcConfig& cfg, const AOTensor& ao, int64_t K, const void* c_hi,
-                        const void* c_lo, int64_t ldc, int64_t N, float* out, int* err_flag,
-                        cudaStream_t s) {
+                        const void* c_lo, int64_t ldc, int64_t N, float* out, int64_t out_rows,
+                        int* err_flag, cudaStream_t s) {
   switch (cfg.bn) {
-    case 16: return launch_single<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 32: return launch_single<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 64: return launch_single<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 96: return launch_single<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 128: return launch_single<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 160: return launch_single<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 192: return launch_single<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
-    case 256: return launch_single<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, err_flag, s);
+    case 16: return launch_single<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 32: return launch_single<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 64: return launch_single<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 96: return launch_single<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 128: return launch_single<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 160: return launch_single<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 192: return launch_single<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 256: return launch_single<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -602,7 +639,8 @@ TcConfig tc_default_config(int mode, int64_t mo_num) {
 const int kBatchBnMax[] = {64, 96, 128, 160, 192, 256};
 
 bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                     int64_t ldc, int64_t N, float* out, int bn, TcProblem* p) {
+                     int64_t ldc, int64_t N, float* out, int bn, int64_t out_rows,
+                     TcProblem* p) {
   const bool f32 = mode == QK_TF32;
   const int bk = f32 ? TcTraits<QK_TF32>::kBK : TcTraits<QK_BF16X3>::kBK;
   if (bn % 16 != 0 || bn < 16 || bn > 256) return false;
@@ -617,7 +655,9 @@ bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, 
     p->b_lo = p->b;
   }
   p->D = out;
-  p->M = ao.rows;
+  p->mask = ao.tiled ? ao.mask : nullptr;
+  p->nchunk = ao.nchunk;
+  p->M = out_rows;
   p->N = N;
   p->num_kb = (int)((K + bk - 1) / bk);
   p->bn = bn;
@@ -635,11 +675,14 @@ cudaError_t launch_mo_tc_batch(int mode, int bn_max, const TcProblem* probs, con
 
 cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
                          const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
-                         const TcConfig& cfg, int* err_flag, cudaStream_t s) {
+                         const TcConfig& cfg, int* err_flag, cudaStream_t s, int64_t out_rows) {
+  if (out_rows < 0) out_rows = ao.rows;
   if (mode == QK_BF16X3)
-    return launch_mode<QK_BF16X3>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, err_flag, s);
+    return launch_mode<QK_BF16X3>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows,
+                                  err_flag, s);
   if (mode == QK_TF32)
-    return launch_mode<QK_TF32>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, err_flag, s);
+    return launch_mode<QK_TF32>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows,
+                                err_flag, s);
   return cudaErrorInvalidValue;
 }
 

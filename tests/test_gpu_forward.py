@@ -126,9 +126,24 @@ def test_edge_single_point_and_far_points(orc, cfg):
     _, got = _run(one, "fp64")
     assert_within("fp64", got, ref, size, "single point")
     far = m.with_points(np.array([[80.0, 0.0, 0.0], [0.0, -95.0, 3.0], [1e3, 1e3, 1e3]]))
-    for mode in ("fp64", "fp32"):
+    for mode in MODES:
         _, got = _run(far, mode)
         assert np.all(got == 0.0)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_sparse_tiles_mixed(orc, cfg, mode):
+    """Tensor-core modes skip blocks of screened AOs: a point set where whole
+    25-point tiles are far from every nucleus, others near, others mixed."""
+    m = cfg(2, walk_num=1)
+    near = m.points[:100]
+    far = near + np.array([300.0, 0.0, 0.0])
+    mixed = np.concatenate([near[:40], far[:60], near[40:90], far[60:73]])
+    mm = m.with_points(mixed)
+    ref, size = orc.mo_vgl(mm)
+    _, got = _run(mm, mode)
+    assert np.all(got[40:100] == 0.0)
+    assert_within(mode, got, ref, size, "mixed tiles")
 
 
 def test_transposed_points_and_host_api(orc, cfg):
