@@ -121,44 +121,63 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ roofline ---
-def roofline(mode, mol, ms_per_launch, peaks):
-    """Roofline entries for the two kernels, from algorithmic work per launch."""
+def roofline(mode, mol, ms_per_launch, peaks, stats=None):
+    """Roofline entries for the two kernels, from algorithmic work per launch.
+
+    Dense modes: every (point, AO) entry.  Tensor-core modes skip blocks of
+    screened AOs, so their algorithmic work is that of the live blocks only
+    (stats = (live blocks, all blocks, live (point, AO) entries)); the padded
+    work the kernels actually move or issue is reported beside it.
+    """
     P, na, nm = mol.point_num, mol.ao_num, mol.mo_num
-    ao_bytes = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode] * 5 * P * na
+    es = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode]
+    entries = P * na if stats is None else stats[2]
+    ao_bytes = es * 5 * entries
+    dense = 2.0 * 5 * P * nm * na
+    useful = 2.0 * 5 * entries * nm
     out = {}
     t_ao = ms_per_launch[0] * 1e-3
     if t_ao > 0:
         a = ao_bytes / t_ao / 1e9
         out["ao_vgl"] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
-                         "algorithmic_bytes": ao_bytes}
+                         "algorithmic_bytes": ao_bytes,
+                         "dense_equivalent_bytes": es * 5 * P * na}
+        if stats is not None:
+            out["ao_vgl"]["written_bytes"] = stats[0] * 128 * 64 * es + stats[1]
+            out["ao_vgl"]["live_block_fraction"] = stats[0] / stats[1]
     t_mo = ms_per_launch[1] * 1e-3
-    dense = 2.0 * 5 * P * nm * na
     if t_mo > 0:
         if mode == "bf16x3":
-            fl = 3 * dense
+            fl = 3 * useful
             peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
             out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                                      "peak_note": "measured bf16 sustained"}
         elif mode == "tf32":
-            fl = dense
+            fl = useful
             peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 0.5
             out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                                      "peak_note": "measured bf16 sustained x 1/2 (tf32/bf16 "
                                                   "nominal ratio)"}
         elif mode == "fp32":
-            fl = dense
+            fl = useful
             peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                                      "peak_note": "152 SMs x 128 FP32 FMA/clk x max clock"}
         else:
-            fl = dense
+            fl = useful
             peak = 1.25
             out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                                      "peak_note": "nominal GB300 FP64"}
         a = fl / t_mo / 1e12
         out["mo_contraction"].update({"achieved": a, "frac": a / peak, "algorithmic_flops": fl,
-                                      "dense_flops": dense})
+                                      "dense_equivalent_flops": dense * (3 if mode == "bf16x3"
+                                                                          else 1)})
+        if stats is not None:
+            n_pad = -(-nm // 160) * 160
+            issued = stats[0] * 128 * 64 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
+            out["mo_contraction"]["issued_flops"] = issued
+            out["mo_contraction"]["issued_tflops"] = issued / t_mo / 1e12
     return out
 
 
@@ -238,7 +257,8 @@ def run_ours(args, rank, world, local_rank):
     ms_step = ms / args.steps
     value = world * evals_per_step / (ms_step * 1e-3)
     per_launch = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(3)]
-    roof = roofline(args.mode, mol, per_launch, peaks)
+    stats = ctx.block_stats() if args.mode in ("bf16x3", "tf32") else None
+    roof = roofline(args.mode, mol, per_launch, peaks, stats)
     dominant = max(roof, key=lambda k: per_launch[0 if k == "ao_vgl" else 1])
     dom = dict(roof[dominant])
     dom["kernel"] = dominant

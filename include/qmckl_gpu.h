@@ -96,6 +96,12 @@ qk_status qk_set_cutoff(qk_context ctx, double eps);
 /* One of QK_FP64, QK_FP32, QK_BF16X3, QK_TF32 (default QK_FP64). */
 qk_status qk_set_compute_mode(qk_context ctx, int32_t mode);
 
+/* QK_BF16X3 only: 1 builds the AO blocks inside the tensor-core contraction
+   kernel, in shared memory, so no AO tensor goes through HBM; 0 (default)
+   runs ao_vgl and the contraction as two kernels through an AO tensor in the
+   workspace.  Both give the same arithmetic.  Other modes ignore it. */
+qk_status qk_set_fusion(qk_context ctx, int32_t enable);
+
 /* ------------------------------------------------------------- system --- */
 
 /* Nuclei (Sec. 3.1): charge [nucl_num] (kept for reference only) and
@@ -176,6 +182,15 @@ qk_status qk_set_timing(qk_context ctx, int32_t enable);
    device time in ms and the number of launches since the last reset; then
    reset.  1 <= n <= 3, else QK_ERR_BAD_SIZE. */
 qk_status qk_get_timing(qk_context ctx, double* ms, int64_t* launches, int32_t n);
+
+/* Block sparsity of the AO tensor of the current points (tensor-core modes,
+   after a get_mo_vgl at this time stamp; else QK_ERR_NOT_PROVIDED).  Points
+   are grouped in tiles of 25 and AOs in chunks of <= 64; a block is live
+   when any primitive of its shells passed Eq. 3 at any of its points.
+   live_entries = sum over live blocks of (points x AOs) of the block: the
+   (point, AO) pairs the contraction multiplies.  Synchronises the stream. */
+qk_status qk_get_block_stats(qk_context ctx, int64_t* live_blocks, int64_t* total_blocks,
+                             int64_t* live_entries);
 
 /* ----------------------------------------------------------- evaluate --- */
 

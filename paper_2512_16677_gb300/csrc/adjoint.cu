@@ -27,7 +27,7 @@
 namespace qk {
 namespace {
 
-constexpr int kPT = 32;
+
 constexpr int kThreads = 256;
 constexpr int kMaxTileBlocks = 512;
 

@@ -62,4 +62,155 @@ __device__ __forceinline__ T sel4(int i, T v0, T v1, T v2, T v3) {
   return i == 0 ? v0 : (i == 1 ? v1 : (i == 2 ? v2 : v3));
 }
 
+constexpr int kPT = 32;  // points per tile slot: one lane per point in the radial phase
+
+// Shared memory of one CTA (templated on the arithmetic type).
+template <typename T>
+struct AOShared {
+  // chunk tables (loaded once)
+  T nuc[kMaxShellsChunk][3];     // FP64: R_A; FP32: float(R_A)
+  T nuc_lo[kMaxShellsChunk][3];  // FP32: residual R_A - float(R_A)
+  T r2max[kMaxShellsChunk];
+  int prim0[kMaxShellsChunk];    // first primitive, local to the chunk
+  int nprim[kMaxShellsChunk];
+  T g[kMaxPrimsChunk];
+  T c[kMaxPrimsChunk];
+  T M[kChunkAO];
+  int ao_info[kChunkAO];  // local shell | l << 8 | Cartesian index << 12
+  // per tile: [point][shell] with one pad column, so that phase 1 (lanes over
+  // points) and phase 2 (lanes over AOs of one point) hit distinct banks
+  T pt[kPT][3];
+  T pt_lo[kPT][3];
+  T d[3][kPT][kMaxShellsChunk + 1];
+  T S[3][kPT][kMaxShellsChunk + 1];
+};
+
+// The chunk's shell, primitive and AO tables into shared memory (threads
+// tid = 0..nthreads-1 of the calling group share the work).
+template <typename T>
+__device__ __forceinline__ void load_chunk_tables(const BasisDev& b, int q, AOShared<T>& sh,
+                                                  int tid, int nthreads) {
+  using A = Arith<T>;
+  const int4 ch = b.chunk[q];
+  const int ns = ch.y - ch.x;
+  const int na = ch.w - ch.z;
+  const int p_first = b.shell_prim0[ch.x];
+  for (int i = tid; i < ns; i += nthreads) {
+    const int s = ch.x + i;
+    const int A_ = b.shell_nuc[s];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sh.nuc[i][k] = b.nucl_xyz[3 * A_ + k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sh.nuc[i][k] = b.nucl_hi[3 * A_ + k];
+        sh.nuc_lo[i][k] = b.nucl_lo[3 * A_ + k];
+      }
+    }
+    sh.r2max[i] = A::r2max(b, s);
+    sh.prim0[i] = b.shell_prim0[s] - p_first;
+    sh.nprim[i] = b.shell_nprim[s];
+  }
+  const int np_chunk = b.shell_prim0[ch.y - 1] + b.shell_nprim[ch.y - 1] - p_first;
+  for (int i = tid; i < np_chunk; i += nthreads) {
+    sh.g[i] = A::gam(b, p_first + i);
+    sh.c[i] = A::coef(b, p_first + i);
+  }
+  for (int i = tid; i < na; i += nthreads) {
+    const int ao = ch.z + i;
+    const int s = b.ao_shell[ao];
+    sh.ao_info[i] = (s - ch.x) | (b.shell_l[s] << 8) | ((ao - b.shell_ao0[s]) << 12);
+    sh.M[i] = A::aofac(b, ao);
+  }
+}
+
+// Radial phase for one tile: warp w of `nwarps` takes shells w, w + nwarps,
+// ...; lane pl < tp is point p0 + pl.  Leaves d and S_0..S_2 in shared
+// memory; returns whether this thread saw a nonzero S.
+template <typename T>
+__device__ __forceinline__ int radial_phase(AOShared<T>& sh, int ns, int warp, int nwarps,
+                                            int lane, int tp, int64_t p0, int64_t n, T Tthr) {
+  using A = Arith<T>;
+  int live = 0;
+  for (int sl = warp; sl < ns; sl += nwarps) {
+    const int pl = lane;
+    T dx = T(0), dy = T(0), dz = T(0), S0 = T(0), S1 = T(0), S2 = T(0);
+    if (pl < tp && p0 + pl < n) {
+      if constexpr (sizeof(T) == 8) {
+        dx = __dsub_rn(sh.pt[pl][0], sh.nuc[sl][0]);
+        dy = __dsub_rn(sh.pt[pl][1], sh.nuc[sl][1]);
+        dz = __dsub_rn(sh.pt[pl][2], sh.nuc[sl][2]);
+      } else {
+        // hi parts cancel exactly when close; the residuals restore FP32
+        // accuracy of the difference
+        dx = (sh.pt[pl][0] - sh.nuc[sl][0]) + (sh.pt_lo[pl][0] - sh.nuc_lo[sl][0]);
+        dy = (sh.pt[pl][1] - sh.nuc[sl][1]) + (sh.pt_lo[pl][1] - sh.nuc_lo[sl][1]);
+        dz = (sh.pt[pl][2] - sh.nuc[sl][2]) + (sh.pt_lo[pl][2] - sh.nuc_lo[sl][2]);
+      }
+      const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
+      if (r2 < sh.r2max[sl]) {
+        const int k0 = sh.prim0[sl];
+        const int k1 = k0 + sh.nprim[sl];
+        for (int k = k0; k < k1; ++k) {
+          const T gm = sh.g[k];
+          const T t = A::mul(gm, r2);
+          if (!(t < Tthr)) break;  // ascending exponents: the rest is screened too
+          const T ce = sh.c[k] * A::ex(-t);
+          S0 += ce;
+          S1 += gm * ce;
+          S2 += gm * gm * ce;
+        }
+      }
+    }
+    sh.d[0][pl][sl] = dx;
+    sh.d[1][pl][sl] = dy;
+    sh.d[2][pl][sl] = dz;
+    sh.S[0][pl][sl] = S0;
+    sh.S[1][pl][sl] = S1;
+    sh.S[2][pl][sl] = S2;
+    live |= (S0 != T(0) || S1 != T(0) || S2 != T(0));
+  }
+  return live;
+}
+
+// The five components of local AO `al` at tile point `pl`.
+template <typename T>
+__device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, T out[5]) {
+  const int info = sh.ao_info[al];
+  const int sl = info & 0xff;
+  const T S0 = sh.S[0][pl][sl], S1 = sh.S[1][pl][sl], S2 = sh.S[2][pl][sl];
+  if (S0 == T(0) && S1 == T(0) && S2 == T(0)) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] = T(0);
+    return;
+  }
+  const int l = (info >> 8) & 0xf;
+  const int j = info >> 12;
+  const T dx = sh.d[0][pl][sl], dy = sh.d[1][pl][sl], dz = sh.d[2][pl][sl];
+  const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
+  const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
+  const T X = sel4(a, T(1), dx, x2, x2 * dx);
+  const T Y = sel4(bb, T(1), dy, y2, y2 * dy);
+  const T Z = sel4(c, T(1), dz, z2, z2 * dz);
+  const T X1 = sel4(a, T(0), T(1), T(2) * dx, T(3) * x2);
+  const T Y1 = sel4(bb, T(0), T(1), T(2) * dy, T(3) * y2);
+  const T Z1 = sel4(c, T(0), T(1), T(2) * dz, T(3) * z2);
+  const T X2 = sel4(a, T(0), T(0), T(2), T(6) * dx);
+  const T Y2 = sel4(bb, T(0), T(0), T(2), T(6) * dy);
+  const T Z2 = sel4(c, T(0), T(0), T(2), T(6) * dz);
+  const T P = X * Y * Z;
+  const T M = sh.M[al];
+  const T r2 = x2 + y2 + z2;
+  const T MS0 = M * S0;
+  const T MS1x2 = T(2) * M * S1;
+  out[0] = MS0 * P;
+  out[1] = MS0 * (X1 * Y * Z) - MS1x2 * dx * P;
+  out[2] = MS0 * (X * Y1 * Z) - MS1x2 * dy * P;
+  out[3] = MS0 * (X * Y * Z1) - MS1x2 * dz * P;
+  const T lapP = X2 * Y * Z + X * Y2 * Z + X * Y * Z2;
+  out[4] = M * (lapP * S0 - T(2 * (2 * l + 3)) * P * S1 + T(4) * r2 * P * S2);
+}
+
+
 }  // namespace qk

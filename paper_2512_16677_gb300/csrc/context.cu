@@ -55,6 +55,7 @@ struct qk_context_s {
   int bits = 53;
   double eps = 0.0;  // > 0: explicit cutoff instead of bits
   int mode = QK_FP64;
+  bool fused = false;  // split-bf16: AO blocks built inside the contraction kernel
   uint64_t basis_version = 1;
   // nuclei
   int64_t nucl_num = 0;
@@ -92,6 +93,8 @@ struct qk_context_s {
   size_t ws_user_bytes = 0;
   DevBuf ws_own;
   uint64_t ao_date = ~0ull, ao_version = 0;
+  uint64_t fused_date = ~0ull;             // time stamp of the last fused evaluation
+  unsigned char* fused_lists = nullptr;    // its live-chunk lists
   int ao_mode = -1;
   void* ao_ws = nullptr;
   // host-output staging, device error word, backward scratch
@@ -175,6 +178,9 @@ qk_status ensure_tables(qk_context c) {
             NN = (int)c->nucl_num, NC = (int)c->chunks.size();
   std::vector<double> r2(S);
   std::vector<float> r2f(S), gf(NP), cf(NP), af(NA), nhi(3 * NN), nlo(3 * NN);
+  std::vector<int> sch(S);
+  for (int q = 0; q < NC; ++q)
+    for (int sh = c->chunks[q].x; sh < c->chunks[q].y; ++sh) sch[sh] = q;
   for (int s = 0; s < S; ++s) {
     // any r^2 >= r2[s] gives fl(gamma_min r^2) > T, so no primitive would pass
     r2[s] = std::isinf(T) ? INFINITY : T / c->shell_gmin[s] * (1.0 + 1e-13);
@@ -214,6 +220,7 @@ qk_status ensure_tables(qk_context c) {
       {af.data(), sizeof(float) * NA, 0},
       {c->ao_shell.data(), sizeof(int) * NA, 0},
       {c->chunks.data(), sizeof(int4) * NC, 0},
+      {sch.data(), sizeof(int) * S, 0},
   };
   size_t total = 0;
   for (auto& p : pieces) {
@@ -252,6 +259,7 @@ qk_status ensure_tables(qk_context c) {
   b.ao_fac_f = (const float*)at(15);
   b.ao_shell = (const int*)at(16);
   b.chunk = (const int4*)at(17);
+  b.shell_chunk = (const int*)at(18);
   b.T = T;
   b.T_f = std::isinf(T) ? INFINITY : (float)T;
   c->tables_dirty = false;
@@ -299,6 +307,8 @@ int64_t kpad_of(qk_context c) { return (int64_t)c->chunks.size() * kChunkAO; }
 // tile, plus one live-block byte per (tile, chunk).
 bool tiled_mode(int mode) { return mode == QK_BF16X3 || mode == QK_TF32; }
 int64_t ao_tiles(qk_context c) { return (c->point_num + kTilePoints - 1) / kTilePoints; }
+
+bool use_fused(qk_context c) { return c->mode == QK_BF16X3 && c->fused; }
 
 size_t ao_tensor_bytes(qk_context c, int mode) {
   const size_t ld = (size_t)kpad_of(c);
@@ -686,7 +696,17 @@ qk_status qk_workspace_size(qk_context c, size_t* bytes) {
   if (!bytes) return QK_ERR_NULL_POINTER;
   qk_status st = require(c, false);
   if (st) return st;
-  *bytes = ao_tensor_bytes(c, c->mode);
+  // room for both the fused path's live lists and the two-kernel path's AO
+  // tensor, so that switching qk_set_fusion needs no new workspace
+  *bytes = ao_tensor_bytes(c, c->mode) +
+           (c->mode == QK_BF16X3 ? fused_workspace_bytes(c->point_num, (int)c->chunks.size())
+                                 : 0);
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_fusion(qk_context c, int32_t enable) {
+  CHECK_CTX(c);
+  c->fused = enable != 0;
   return QK_SUCCESS;
 }
 
@@ -772,6 +792,33 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
                 (long long)(M * N));
   st = ensure_mo(c);
   if (st) return st;
+  if (use_fused(c)) {
+    void* ws = nullptr;
+    const size_t fb = fused_workspace_bytes(c->point_num, (int)c->chunks.size());
+    st = workspace(c, ao_tensor_bytes(c, c->mode) + fb, &ws);
+    if (st) return st;
+    // the live lists sit behind the (unused here) AO tensor area
+    unsigned char* lp = (unsigned char*)ws + ao_tensor_bytes(c, c->mode);
+    const int64_t tiles = ao_tiles(c);
+    int* live_count = (int*)lp;
+    uint16_t* live_list = (uint16_t*)(lp + align_up((size_t)tiles * 4, 256));
+    cudaError_t e;
+    {
+      TimedLaunch t0(c, 0);
+      e = launch_fused_live(c->bdev, c->pdev, live_count, live_list, c->stream);
+    }
+    if (e == cudaSuccess) {
+      TimedLaunch t1(c, 1);
+      e = launch_mo_fused(tc_default_config(c->mode, N).bn, c->bdev, c->pdev, c->c_hi, c->c_lo,
+                          c->kpad, N, (float*)dout, live_count, live_list, (int*)c->d_flag.p,
+                          c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "fused mo_vgl");
+    c->fused_date = c->date;
+    c->fused_lists = lp;
+    c->ao_date = ~0ull;  // no AO tensor was written
+    return QK_SUCCESS;
+  }
   AOTensor ao{};
   st = provide_ao(c, &ao);
   if (st) return st;
@@ -879,6 +926,61 @@ BwdLayout bwd_layout(qk_context c) {
 }  // namespace
 
 extern "C" {
+
+qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_blocks,
+                             int64_t* live_entries) {
+  CHECK_CTX(c);
+  if (!live_blocks || !total_blocks || !live_entries)
+    return fail(c, QK_ERR_NULL_POINTER, "output pointer is NULL");
+  if (c->fused_date == c->date && c->fused_lists && use_fused(c)) {
+    const int64_t tiles = ao_tiles(c), nq = (int64_t)c->chunks.size();
+    std::vector<int> cnt((size_t)tiles);
+    std::vector<uint16_t> lst((size_t)(tiles * nq));
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(cnt.data(), c->fused_lists, sizeof(int) * tiles, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(lst.data(), c->fused_lists + align_up((size_t)tiles * 4, 256),
+                     sizeof(uint16_t) * lst.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "live list read");
+    int64_t live = 0, entries = 0;
+    for (int64_t ti = 0; ti < tiles; ++ti) {
+      const int64_t pts = std::min<int64_t>(kTilePoints, c->point_num - ti * kTilePoints);
+      for (int i = 0; i < cnt[ti]; ++i) {
+        const int4 ch = c->chunks[lst[ti * nq + i]];
+        ++live;
+        entries += pts * (ch.w - ch.z);
+      }
+    }
+    *live_blocks = live;
+    *total_blocks = tiles * nq;
+    *live_entries = entries;
+    return QK_SUCCESS;
+  }
+  if (!tiled_mode(c->ao_mode) || c->ao_ws == nullptr || c->ao_date != c->date)
+    return fail(c, QK_ERR_NOT_PROVIDED,
+                "no AO tensor of the current points in a tensor-core mode");
+  const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
+  const int64_t tiles = ao_tiles(c), nq = t.nchunk;
+  std::vector<uint8_t> mask((size_t)(tiles * nq));
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(mask.data(), t.mask, mask.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "block mask read");
+  int64_t live = 0, entries = 0;
+  for (int64_t ti = 0; ti < tiles; ++ti) {
+    const int64_t pts = std::min<int64_t>(kTilePoints, c->point_num - ti * kTilePoints);
+    for (int64_t q = 0; q < nq; ++q)
+      if (mask[ti * nq + q]) {
+        ++live;
+        entries += pts * (c->chunks[q].w - c->chunks[q].z);
+      }
+  }
+  *live_blocks = live;
+  *total_blocks = tiles * nq;
+  *live_entries = entries;
+  return QK_SUCCESS;
+}
 
 qk_status qk_backward_workspace_size(qk_context c, size_t* bytes) {
   CHECK_CTX(c);

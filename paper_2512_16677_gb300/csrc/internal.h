@@ -46,6 +46,7 @@ struct BasisDev {
   const float* ao_fac_f;
   const int* ao_shell;      // [ao] shell of each AO
   const int4* chunk;        // [nchunk] (shell_begin, shell_end, ao_begin, ao_end)
+  const int* shell_chunk;   // [shell] chunk holding each shell
   double T;                 // Eq. 3 threshold on gamma r^2
   float T_f;
 };
@@ -188,6 +189,17 @@ cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
                               const void* abar, int64_t ld, double* partial, double* d_dR,
                               cudaStream_t s);
 size_t adjoint_dR_partial_bytes(const BasisDev& b, int64_t point_num);
+
+// Fused AO + MO evaluation (split-bf16): live-chunk lists per 25-point tile,
+// then one persistent kernel that builds AO blocks in shared memory and
+// multiplies them on the tensor cores.
+size_t fused_workspace_bytes(int64_t point_num, int nchunk);
+cudaError_t launch_fused_live(const BasisDev& b, const PointsDev& p, int* live_count,
+                              uint16_t* live_list, cudaStream_t s);
+cudaError_t launch_mo_fused(int bn, const BasisDev& b, const PointsDev& p, const void* c_hi,
+                            const void* c_lo, int64_t kpad, int64_t N, float* out,
+                            const int* live_count, const uint16_t* live_list, int* err_flag,
+                            cudaStream_t s);
 
 // What a multi-molecule launch needs from one context (context.cu): makes
 // the tables, MO planes and AO workspace of the current state valid and

@@ -44,6 +44,7 @@ SIGNATURES = {
     "qk_set_precision": [_P, _I32],
     "qk_set_cutoff": [_P, _D],
     "qk_set_compute_mode": [_P, _I32],
+    "qk_set_fusion": [_P, _I32],
     "qk_set_nucleus": [_P, _I64, _P, _P],
     "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
     "qk_set_mo_coefficient": [_P, _I64, _P],
@@ -64,6 +65,8 @@ SIGNATURES = {
     "qk_mo_vgl_backward_device": [_P, _P, _I64, _P, _P],
     "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "qk_set_timing": [_P, _I32],
+    "qk_get_block_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                           ctypes.POINTER(_I64)],
     "qk_batch_create": [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)],
     "qk_batch_destroy": [_P],
     "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
@@ -182,6 +185,11 @@ class Context:
 
     def set_cutoff(self, eps: float):
         self._check(self.lib.qk_set_cutoff(self.h, eps), "set_cutoff")
+
+    def set_fusion(self, enable: bool):
+        """split-bf16: build AO blocks inside the contraction kernel (default
+        off: ao_vgl and the contraction run as two kernels)."""
+        self._check(self.lib.qk_set_fusion(self.h, 1 if enable else 0), "set_fusion")
 
     def set_compute_mode(self, mode: str):
         self._check(self.lib.qk_set_compute_mode(self.h, MODES[mode]), "set_compute_mode")
@@ -323,6 +331,14 @@ class Context:
 
     def synchronize(self):
         self._check(self.lib.qk_synchronize(self.h), "synchronize")
+
+    def block_stats(self):
+        """(live blocks, all blocks, live (point, AO) entries) of the current
+        AO tensor in a tensor-core mode."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.qk_get_block_stats(self.h, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c)), "get_block_stats")
+        return a.value, b.value, c.value
 
     # ------------------------------------------------------------ evaluate
     def mo_vgl_device(self, out=None):

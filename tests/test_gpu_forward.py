@@ -213,3 +213,22 @@ def test_primitive_order_invariance_gpu(cfg):
     _, a = _run(m, "fp64")
     _, b = _run(m2, "fp64")
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["water", "chain", "organic"])
+def test_bf16x3_fused_matches_two_kernel_path(orc, cfg, case):
+    """split-bf16 with AO blocks built inside the contraction kernel
+    (qk_set_fusion(1)) and through an AO tensor in HBM (the default) use the
+    same arithmetic; both meet the bar against the oracle."""
+    m = {"water": cfg(1), "chain": cfg(3, walk_num=2), "organic": cfg(2, walk_num=1)}[case]
+    ref, size = orc.mo_vgl(m)
+    outs = []
+    for fused in (True, False):
+        c = _ctx(m, "bf16x3")
+        c.set_fusion(fused)
+        o = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        c.synchronize()
+        outs.append(o.double().cpu().numpy().reshape(-1, 5, m.mo_num))
+        assert_within("bf16x3", outs[-1], ref, size, f"{case} fused={fused}")
+    assert np.max(np.abs(outs[0] - outs[1])) <= 1e-6 * np.max(np.abs(outs[1]))
