@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the uneven multi-molecule batch measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the large-cluster and adjoint measurements")
     ap.add_argument("--walkers", type=int, default=None,
                     help="fewer walkers than the workload's 256 (profiling captures only)")
     return ap.parse_args()
@@ -302,6 +304,9 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_batch:
         res["batch"] = measure_batch(args, world)
+    if not args.no_extra:
+        res["large"] = measure_large(args, world)
+        res["adjoint"] = measure_adjoint(args)
 
     # end to end through the host-memory C-ABI calls: H2D of the coordinates
     # and D2H of the whole MO vgl tensor inside the timed region
@@ -384,6 +389,83 @@ def measure_batch(args, world):
             "ms_per_step": ms, "value": world * evals / (ms * 1e-3), "unit": UNIT,
             "autotuned_bn_max": bn, "autotune_contraction_ms": tune_ms, "cuda_graph": True,
             "launches_per_step": 2 + len(mols)}
+
+
+def _time_steps(fn, steps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.current_stream()
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_large(args, world):
+    """1000-nucleus cluster, 10 000 AOs, 2000 MOs, 4000 e- x 16 walkers:
+    split-bf16 (block-sparse) against the plain FP32 path (dense)."""
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+    mol = synth.make_config(5)
+    coords = [torch.from_numpy(mol.coord).cuda()]
+    coords.append(coords[0] + 0.05)
+    evals = mol.elec_num * mol.walk_num * mol.mo_num
+    out = {"workload": "cluster1000: 1000 nuclei, 10000 AO, 2000 MO, 4000 e- x 16 walkers, "
+                       "eps=1e-10", "evals_per_step": evals}
+    for mode, steps in (("bf16x3", max(3, args.steps // 2)), ("fp32", 2)):
+        ctx = qmckl.Context(mode)
+        ctx.set_molecule(mol)
+        ctx.set_points_device(coords[0])
+        o = ctx.mo_vgl_device()
+        k = [0]
+
+        def step():
+            k[0] += 1
+            ctx.set_points_device(coords[k[0] % 2])
+            ctx.mo_vgl_device(o)
+        ms = _time_steps(step, steps, warmup=1)
+        ent = {"ms_per_step": ms, "value": world * evals / (ms * 1e-3)}
+        if mode == "bf16x3":
+            live, total, entries = ctx.block_stats()
+            ent["live_block_fraction"] = live / total
+            ent["live_entry_fraction"] = entries / (mol.point_num * mol.ao_num)
+        out[mode] = ent
+        del ctx, o
+        torch.cuda.empty_cache()
+    out["speedup_vs_fp32_path"] = out["fp32"]["ms_per_step"] / out["bf16x3"]["ms_per_step"]
+    return out
+
+
+def measure_adjoint(args):
+    """C/H chain, 50 nuclei, 500 AOs, 100 MOs, 200 e- x 128 walkers: forward
+    plus backward (dL/dC and dL/dR_nuc) per step, FP64 and split-bf16 forward
+    with the FP32 adjoint."""
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+    mol = synth.make_config(3)
+    coord = torch.from_numpy(mol.coord).cuda()
+    res = {"workload": "chain50: 50 nuclei, 500 AO, 100 MO, 200 e- x 128 walkers"}
+    for mode, steps in (("fp64", 3), ("bf16x3", 10)):
+        ctx = qmckl.Context(mode)
+        ctx.set_molecule(mol)
+        ctx.set_points_device(coord)
+        o = ctx.mo_vgl_device()
+        W = torch.randn(o.shape, dtype=o.dtype, device="cuda")
+
+        def fwd_bwd():
+            ctx.set_points_device(coord)
+            ctx.mo_vgl_device(o)
+            ctx.backward_device(W)
+        ms = _time_steps(fwd_bwd, steps, warmup=1)
+        res[mode] = {"ms_per_fwd_bwd": ms,
+                     "evals_per_s": mol.elec_num * mol.walk_num * mol.mo_num / (ms * 1e-3)}
+    return res
 
 
 # -------------------------------------------------------- cpu baseline ---

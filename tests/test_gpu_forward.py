@@ -104,7 +104,7 @@ def test_organic_one_walker(orc, cfg, mode):
     _report("organic150_1w", mode, assert_within(mode, got, ref, size, "organic"))
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "fp32", "fp64"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32", "fp32", "fp64"])
 def test_organic_full_size_sampled(orc, cfg, mode):
     """Full benchmark workload (153 600 points), sampled outputs."""
     m = cfg(2)
