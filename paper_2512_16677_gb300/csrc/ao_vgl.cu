@@ -62,14 +62,13 @@ template <>
 struct PairStore<float, true> {
   static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int64_t col, float v0,
                                              float v1) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+    // packed conversions: hi = rn(v), lo = rn(v - hi), two lanes at once
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
     const int64_t off = row * o.ld + col;
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a) + off) =
-        __halves2bfloat162(h0, h1);
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a_lo) + off) =
-        __halves2bfloat162(l0, l1);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a) + off) = h;
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a_lo) + off) = l;
   }
 };
 
