@@ -212,5 +212,225 @@ __device__ __forceinline__ void assemble(const AOShared<T>& sh, int al, int pl, 
   out[4] = M * (lapP * S0 - T(2 * (2 * l + 3)) * P * S1 + T(4) * r2 * P * S2);
 }
 
+// ------------------------------------------------------------------------
+// Shell-major evaluation.  One warp takes one shell, one lane one point: the
+// radial sums S_0..S_2 and the 1-D power tables of d are formed once per
+// (point, shell) and every Cartesian component of the shell follows with
+// its exponents known at compile time.  Results land in a shared staging
+// tile [5 * points][kStagePitch] (row 5 p + c, column = AO in the chunk);
+// the odd pitch keeps both the column writes (lanes over points) and the
+// row reads (lanes over AOs) free of bank conflicts.  kLanes point lanes
+// own staging rows; lanes at or past kLanes - 1 share the last lane's rows
+// (with 25-point tiles, kLanes = 26 leaves zeros in rows 125..129).
+constexpr int kStagePitch = kChunkAO + 1;
+
+// (a, b, c) of Cartesian component j of momentum l: a from l down to 0, then
+// b from l - a down to 0 (the order of the c_pow table).
+__host__ __device__ constexpr int cart_exp(int l, int j, int axis) {
+  int idx = 0;
+  for (int a = l; a >= 0; --a)
+    for (int b = l - a; b >= 0; --b) {
+      if (idx == j) return axis == 0 ? a : (axis == 1 ? b : l - a - b);
+      ++idx;
+    }
+  return 0;
+}
+
+template <typename T, int kLanes>
+struct AOStageSmem {
+  T nuc[kMaxShellsChunk][3];     // FP64: R_A; FP32: float(R_A)
+  T nuc_lo[kMaxShellsChunk][3];  // FP32: residual R_A - float(R_A)
+  T r2max[kMaxShellsChunk];
+  T g[kMaxPrimsChunk];
+  T c[kMaxPrimsChunk];
+  T M[kChunkAO];
+  T pt[kPT][3];
+  T pt_lo[kPT][3];
+  int prim0[kMaxShellsChunk];  // first primitive, local to the chunk
+  int nprim[kMaxShellsChunk];
+  int col[kMaxShellsChunk];    // first column of the shell in the chunk
+  int lsh[kMaxShellsChunk];
+  int order[kMaxShellsChunk];  // shells by descending estimated cost
+  int next;                    // next entry of `order` to hand out
+  T stage[5 * kLanes][kStagePitch];
+};
+
+// Chunk tables into shared memory and zeros into the staging columns past
+// the chunk's last AO (nothing else writes them).
+template <typename T, int kLanes>
+__device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q,
+                                                  AOStageSmem<T, kLanes>& sh,
+                                                  int tid, int nthreads) {
+  using A = Arith<T>;
+  const int4 ch = b.chunk[q];
+  const int ns = ch.y - ch.x;
+  const int na = ch.w - ch.z;
+  const int p_first = b.shell_prim0[ch.x];
+  for (int i = tid; i < ns; i += nthreads) {
+    const int s = ch.x + i;
+    const int A_ = b.shell_nuc[s];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sh.nuc[i][k] = b.nucl_xyz[3 * A_ + k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sh.nuc[i][k] = b.nucl_hi[3 * A_ + k];
+        sh.nuc_lo[i][k] = b.nucl_lo[3 * A_ + k];
+      }
+    }
+    sh.r2max[i] = A::r2max(b, s);
+    sh.prim0[i] = b.shell_prim0[s] - p_first;
+    sh.nprim[i] = b.shell_nprim[s];
+    sh.col[i] = b.shell_ao0[s] - ch.z;
+    const int l = b.shell_l[s];
+    sh.lsh[i] = l;
+    // cost ~ primitives (radial sums) + Cartesian components (assembly);
+    // rank by descending cost, ties by position
+    auto cost = [&](int ss) {
+      const int ll = b.shell_l[ss];
+      return 8 * b.shell_nprim[ss] + 15 * (ll + 1) * (ll + 2);
+    };
+    const int ci = cost(s);
+    int rank = 0;
+    for (int j = 0; j < ns; ++j) {
+      const int cj = cost(ch.x + j);
+      rank += (cj > ci) || (cj == ci && j < i);
+    }
+    sh.order[rank] = i;
+  }
+  const int np_chunk = b.shell_prim0[ch.y - 1] + b.shell_nprim[ch.y - 1] - p_first;
+  for (int i = tid; i < np_chunk; i += nthreads) {
+    sh.g[i] = A::gam(b, p_first + i);
+    sh.c[i] = A::coef(b, p_first + i);
+  }
+  for (int i = tid; i < na; i += nthreads) sh.M[i] = A::aofac(b, ch.z + i);
+  const int npad = kChunkAO - na;
+  for (int i = tid; i < 5 * kLanes * npad; i += nthreads)
+    sh.stage[i / npad][na + i % npad] = T(0);
+}
+
+// Cartesian component J of a momentum-L shell at one point:
+//   chi = M S0 P,  d_i chi = M (S0 d_iP - 2 S1 d_i P),
+//   lap chi = M (S0 lapP + (4 r^2 S2 - 2 (2L+3) S1) P),
+// with u_i = 2 S1 d_i and Lr = 4 r^2 S2 - 2 (2L+3) S1 formed once per shell.
+template <typename T, int L, int J>
+__device__ __forceinline__ void cart_component(const T (&px)[4], const T (&py)[4],
+                                               const T (&pz)[4], const T* M, T S0, T ux, T uy,
+                                               T uz, T Lr, T* st) {
+  if constexpr (J < (L + 1) * (L + 2) / 2) {
+    constexpr int a = cart_exp(L, J, 0), b = cart_exp(L, J, 1), c = cart_exp(L, J, 2);
+    const T P = px[a] * py[b] * pz[c];
+    const T mS0 = M[J] * S0;
+    const T mP = M[J] * P;
+    st[J] = mS0 * P;
+    if constexpr (a > 0)
+      st[kStagePitch + J] = mS0 * (T(a) * px[a > 0 ? a - 1 : 0] * py[b] * pz[c]) - ux * mP;
+    else
+      st[kStagePitch + J] = -(ux * mP);
+    if constexpr (b > 0)
+      st[2 * kStagePitch + J] = mS0 * (T(b) * px[a] * py[b > 0 ? b - 1 : 0] * pz[c]) - uy * mP;
+    else
+      st[2 * kStagePitch + J] = -(uy * mP);
+    if constexpr (c > 0)
+      st[3 * kStagePitch + J] = mS0 * (T(c) * px[a] * py[b] * pz[c > 0 ? c - 1 : 0]) - uz * mP;
+    else
+      st[3 * kStagePitch + J] = -(uz * mP);
+    if constexpr (a > 1 || b > 1 || c > 1) {
+      T lapP = T(0);
+      bool first = true;
+      if constexpr (a > 1) {
+        lapP = T(a * (a - 1)) * px[a > 1 ? a - 2 : 0] * py[b] * pz[c];
+        first = false;
+      }
+      if constexpr (b > 1) {
+        const T t = T(b * (b - 1)) * px[a] * py[b > 1 ? b - 2 : 0] * pz[c];
+        lapP = first ? t : lapP + t;
+        first = false;
+      }
+      if constexpr (c > 1) {
+        const T t = T(c * (c - 1)) * px[a] * py[b] * pz[c > 1 ? c - 2 : 0];
+        lapP = first ? t : lapP + t;
+      }
+      st[4 * kStagePitch + J] = mS0 * lapP + Lr * mP;
+    } else {
+      st[4 * kStagePitch + J] = Lr * mP;
+    }
+    cart_component<T, L, J + 1>(px, py, pz, M, S0, ux, uy, uz, Lr, st);
+  }
+}
+
+// All components of a momentum-L shell at one point into the staging rows
+// st[c * kStagePitch + j] (c = value, d/dx, d/dy, d/dz, Laplacian).
+template <typename T, int L>
+__device__ __forceinline__ void shell_components(T dx, T dy, T dz, T S0, T S1, T S2, const T* M,
+                                                 T* st) {
+  const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
+  const T px[4] = {T(1), dx, x2, x2 * dx};
+  const T py[4] = {T(1), dy, y2, y2 * dy};
+  const T pz[4] = {T(1), dz, z2, z2 * dz};
+  const T r2 = x2 + y2 + z2;
+  const T S1x2 = T(2) * S1;
+  const T Lr = T(4) * r2 * S2 - T(2 * (2 * L + 3)) * S1;
+  cart_component<T, L, 0>(px, py, pz, M, S0, S1x2 * dx, S1x2 * dy, S1x2 * dz, Lr, st);
+}
+
+// Radial sums and every component of shell `sl` at tile point `lane` (valid
+// lanes only; the others get zeros), written to the staging tile.  Returns
+// whether this lane's S were nonzero.
+template <typename T, int kLanes>
+__device__ __forceinline__ bool shell_at_point(AOStageSmem<T, kLanes>& sh, int sl, int lane,
+                                               bool valid, T Tthr) {
+  using A = Arith<T>;
+  T dx = T(0), dy = T(0), dz = T(0), S0 = T(0), S1 = T(0), S2 = T(0);
+  if (valid) {
+    if constexpr (sizeof(T) == 8) {
+      dx = __dsub_rn(sh.pt[lane][0], sh.nuc[sl][0]);
+      dy = __dsub_rn(sh.pt[lane][1], sh.nuc[sl][1]);
+      dz = __dsub_rn(sh.pt[lane][2], sh.nuc[sl][2]);
+    } else {
+      // hi parts cancel exactly when close; the residuals restore FP32
+      // accuracy of the difference
+      dx = (sh.pt[lane][0] - sh.nuc[sl][0]) + (sh.pt_lo[lane][0] - sh.nuc_lo[sl][0]);
+      dy = (sh.pt[lane][1] - sh.nuc[sl][1]) + (sh.pt_lo[lane][1] - sh.nuc_lo[sl][1]);
+      dz = (sh.pt[lane][2] - sh.nuc[sl][2]) + (sh.pt_lo[lane][2] - sh.nuc_lo[sl][2]);
+    }
+    const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
+    if (r2 < sh.r2max[sl]) {
+      const int k0 = sh.prim0[sl];
+      const int k1 = k0 + sh.nprim[sl];
+      for (int k = k0; k < k1; ++k) {
+        const T gm = sh.g[k];
+        const T t = A::mul(gm, r2);
+        if (!(t < Tthr)) break;  // ascending exponents: the rest is screened too
+        const T ce = sh.c[k] * A::ex(-t);
+        S0 += ce;
+        S1 += gm * ce;
+        S2 += gm * gm * ce;
+      }
+    }
+  }
+  const bool nz = S0 != T(0) || S1 != T(0) || S2 != T(0);
+  const int c0 = sh.col[sl];
+  const int l = sh.lsh[sl];
+  T* st = &sh.stage[5 * (lane < kLanes ? lane : kLanes - 1)][c0];
+  if (__any_sync(0xffffffffu, nz)) {
+    const T* M = &sh.M[c0];
+    switch (l) {
+      case 0: shell_components<T, 0>(dx, dy, dz, S0, S1, S2, M, st); break;
+      case 1: shell_components<T, 1>(dx, dy, dz, S0, S1, S2, M, st); break;
+      case 2: shell_components<T, 2>(dx, dy, dz, S0, S1, S2, M, st); break;
+      default: shell_components<T, 3>(dx, dy, dz, S0, S1, S2, M, st); break;
+    }
+  } else {
+    const int nc = (l + 1) * (l + 2) / 2;
+    for (int j = 0; j < nc; ++j) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st[c * kStagePitch + j] = T(0);
+    }
+  }
+  return nz;
+}
+
 
 }  // namespace qk

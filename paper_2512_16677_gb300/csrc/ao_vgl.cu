@@ -15,20 +15,23 @@
 //
 // Work decomposition.  The AOs are cut into column chunks of at most 64 AOs
 // and 32 shells that end on shell boundaries.  A CTA owns one chunk and
-// loops over tiles of 32 points (persistent in the point direction), with the
+// loops over tiles of points (persistent in the point direction), with the
 // chunk's shell, primitive and AO tables staged once in shared memory:
 //   phase 0  the tile's point coordinates -> shared memory
-//   phase 1  one warp per shell, one lane per point: d = r - R_A, the shell
-//            radius test (r^2 >= T/gamma_min screens every primitive), then
-//            the Eq. 3 test on primitives sorted by ascending exponent (the
-//            first screened one ends the loop); S_0..S_2 and d -> shared
-//   phase 2  one lane per pair of AOs, one warp per point: assemble the five
-//            components and store them.
+//   phase 1  warps take shells from a shared counter, costliest first; one
+//            lane per point: d = r - R_A, the shell radius test
+//            (r^2 >= T/gamma_min screens every primitive), then the Eq. 3
+//            test on primitives sorted by ascending exponent (the first
+//            screened one ends the loop) gives S_0..S_2, and every Cartesian
+//            component of the shell follows with compile-time exponents
+//            into a shared staging tile [5 points][64 AOs]
+//   phase 2  copy-out: one warp per (point, component) row, lanes over the
+//            64 columns, converted to the output type.
 // In the contraction layout (AOTensor::chunked) chunk q owns the 64 columns
 // [64q, 64q + 64) of the AO tensor, padding included, so each warp store is
-// one aligned 128-byte (bf16 plane) / 256-byte (FP32) / 512-byte (FP64) row
-// segment, and the contraction's K blocks coincide with the chunks.  The
-// caller-facing layout writes the AOs densely (column = AO index).
+// an aligned row segment, and the contraction's K blocks coincide with the
+// chunks.  The caller-facing layout writes the AOs densely (column = AO
+// index).
 //
 // Precision: FP64 mode does everything in FP64 and forms r^2 and gamma r^2
 // without fused multiply-adds, so its screening decisions are those of the
@@ -40,45 +43,26 @@ namespace qk {
 namespace {
 
 constexpr int kThreads = 256;
-static_assert(kTilePoints <= kPT, "a tiled tile fits the 32 lanes of phase 1");
+static_assert(kTilePoints < kPT, "a tiled tile fits the 32 lanes of phase 1");
 
-// Two adjacent AOs (local columns 2q, 2q+1) of one component row.
-template <typename T, bool kSplit>
-struct PairStore;
-
-template <typename T>
-struct PairStore<T, false> {
-  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int64_t col, T v0,
-                                             T v1) {
-    T* p = static_cast<T*>(o.a) + row * o.ld + col;
-    if constexpr (sizeof(T) == 8)
-      *reinterpret_cast<double2*>(p) = make_double2(v0, v1);
-    else
-      *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
-  }
-};
-
-template <>
-struct PairStore<float, true> {
-  static __device__ __forceinline__ void put(const AOTensor& o, int64_t row, int64_t col, float v0,
-                                             float v1) {
-    // packed conversions: hi = rn(v), lo = rn(v - hi), two lanes at once
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-    const int64_t off = row * o.ld + col;
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a) + off) = h;
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o.a_lo) + off) = l;
-  }
-};
+// Point lanes that own staging rows: 32-point tiles use every lane; 25-point
+// tiles use 26, lane 25's zero rows doubling as the tile's rows 125..127.
+template <bool kTiled>
+constexpr int stage_lanes() {
+  return kTiled ? kTilePoints + 1 : kPT;
+}
+template <typename T, bool kTiled>
+using StageOf = AOStageSmem<T, stage_lanes<kTiled>()>;
 
 // Chunk q of one problem over point tiles t_begin, t_begin + t_step, ...
 // below t_end (the whole CTA calls this; it starts with a block barrier).
 template <typename T, bool kSplit, bool kChunked, bool kTiled>
 __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDev& pts,
                                                const AOTensor& out, int q, int64_t t_begin,
-                                               int64_t t_end, int64_t t_step, AOShared<T>& sh) {
+                                               int64_t t_end, int64_t t_step,
+                                               StageOf<T, kTiled>& sh) {
   constexpr int TP = kTiled ? kTilePoints : kPT;  // points per tile
+  constexpr int kWarps = kThreads / 32;
   using A = Arith<T>;
   __syncthreads();  // the previous call's readers of the shared tables are done
   const int4 ch = b.chunk[q];
@@ -89,14 +73,14 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   const int warp = tid >> 5;
 
   // ---- chunk tables, once per call
-  load_chunk_tables<T>(b, q, sh, tid, kThreads);
+  load_stage_tables(b, q, sh, tid, kThreads);
   const T Tthr = A::thr(b);
   const int64_t n = pts.n;
   const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
 
   for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
     const int64_t p0 = ptile * TP;
-    __syncthreads();  // tables ready / previous tile's phase 2 done with shared data
+    __syncthreads();  // tables ready / previous tile's copy-out done with the stage
     // ---- phase 0: the tile's points
     if (tid < TP) {
       const int64_t ip = p0 + tid;
@@ -114,51 +98,59 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
         }
       }
     }
+    if (tid == 0) sh.next = 0;
     __syncthreads();
-    // ---- phase 1: one warp per shell, lanes over the tile's points
-    const int live = radial_phase<T>(sh, ns, warp, kThreads / 32, lane, TP, p0, n, Tthr);
+    // ---- phase 1: warps take shells (costliest first), lanes are points
+    const bool valid = lane < TP && p0 + lane < n;
+    int live = 0;
+    for (;;) {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(&sh.next, 1);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= ns) break;
+      live |= shell_at_point(sh, sh.order[k], lane, valid, Tthr);
+    }
     // block barrier; in the tiled layout it also tells whether any entry of
     // block (tile, chunk) survived screening
     const int any_live = __syncthreads_or(live);
     if constexpr (kTiled) {
       if (tid == 0) out.mask[ptile * out.nchunk + q] = any_live ? 1 : 0;
       if (!any_live) continue;  // not written: the contraction skips this block
-      // rows 125..127 of the tile are zero
-      if (warp < kTileRows - 5 * kTilePoints) {
-        const int64_t prow = ptile * kTileRows + 5 * kTilePoints + warp;
-        PairStore<T, kSplit>::put(out, prow, col0 + 2 * lane, T(0), T(0));
-      }
     }
-    // ---- phase 2: one warp per point, lane = AO pair (2 lane, 2 lane + 1)
-    for (int pl = warp; pl < TP; pl += kThreads / 32) {
-      const int64_t ip = p0 + pl;
-      if (ip >= n) break;
-      const int a0 = 2 * lane, a1 = 2 * lane + 1;
-      T v0[5], v1[5];
-      if (a0 < na) {
-        assemble(sh, a0, pl, v0);
+    // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
+    // lane + 32.  Tiled: all 128 rows (stage rows 125..127 belong to the
+    // lane past the tile and hold zeros).
+    constexpr int kRows = kTiled ? kTileRows : 5 * kPT;
+    for (int r = warp; r < kRows; r += kWarps) {
+      int64_t grow;
+      if constexpr (kTiled) {
+        grow = ptile * kTileRows + r;
       } else {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) v0[c] = T(0);
+        if (p0 + r / 5 >= n) break;
+        grow = 5 * p0 + r;
       }
-      if (a1 < na) {
-        assemble(sh, a1, pl, v1);
+      const T v0 = sh.stage[r][lane];
+      const T v1 = sh.stage[r][lane + 32];
+      if constexpr (kSplit) {
+        // hi = rn(v), lo = rn(v - hi), both columns at once
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(out.a) + grow * out.ld + col0;
+        __nv_bfloat16* ol = static_cast<__nv_bfloat16*>(out.a_lo) + grow * out.ld + col0;
+        oh[lane] = h.x;
+        oh[lane + 32] = h.y;
+        ol[lane] = l.x;
+        ol[lane + 32] = l.y;
       } else {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) v1[c] = T(0);
-      }
-      const int64_t row = kTiled ? ptile * kTileRows + 5 * pl : 5 * ip;
-      if constexpr (kChunked) {
-        // chunk window: padding columns are written as zeros
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-          PairStore<T, kSplit>::put(out, row + c, col0 + a0, v0[c], v1[c]);
-      } else {
-        T* o = static_cast<T*>(out.a);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          if (a0 < na) o[(row + c) * out.ld + col0 + a0] = v0[c];
-          if (a1 < na) o[(row + c) * out.ld + col0 + a1] = v1[c];
+        T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
+        if constexpr (kChunked) {
+          // chunk window: padding columns are written as zeros
+          o[lane] = v0;
+          o[lane + 32] = v1;
+        } else {
+          if (lane < na) o[lane] = v0;
+          if (lane + 32 < na) o[lane + 32] = v1;
         }
       }
     }
@@ -169,7 +161,7 @@ template <typename T, bool kSplit, bool kChunked, bool kTiled>
 __global__ void __launch_bounds__(kThreads)
     ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  AOShared<T>& sh = *reinterpret_cast<AOShared<T>*>(smem_raw);
+  auto& sh = *reinterpret_cast<StageOf<T, kTiled>*>(smem_raw);
   ao_chunk_tiles<T, kSplit, kChunked, kTiled>(b, pts, out, blockIdx.x, blockIdx.y, n_ptiles,
                                               gridDim.y, sh);
 }
@@ -181,7 +173,7 @@ __global__ void __launch_bounds__(kThreads)
     ao_vgl_batch_kernel(const AOProblem* __restrict__ probs, const int4* __restrict__ items,
                         int64_t n_items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  AOShared<float>& sh = *reinterpret_cast<AOShared<float>*>(smem_raw);
+  auto& sh = *reinterpret_cast<StageOf<float, true>*>(smem_raw);
   for (int64_t i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int4 w = items[i];
     const AOProblem& P = probs[w.x];
@@ -192,7 +184,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
 cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
                       cudaStream_t s) {
-  constexpr size_t smem = sizeof(AOShared<T>);
+  constexpr size_t smem = sizeof(StageOf<T, kTiled>);
   constexpr int TP = kTiled ? kTilePoints : kPT;
   auto kern = ao_vgl_kernel<T, kSplit, kChunked, kTiled>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -217,7 +209,7 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
 template <bool kSplit>
 cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n_items,
                             cudaStream_t s) {
-  constexpr size_t smem = sizeof(AOShared<float>);
+  constexpr size_t smem = sizeof(StageOf<float, true>);
   auto kern = ao_vgl_batch_kernel<kSplit>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

@@ -9,13 +9,14 @@
 //     points, as an ascending list; only those K blocks are multiplied (the
 //     sparse-AO MO product of Sec. 3.2 at tile granularity).
 //  2. mo_fused_kernel, persistent over (tile, N tile) items, 13 warps:
-//       warps 5-12  AO producers: for each live chunk, the radial sums of
-//                   Eq. 2 with the Eq. 3 screen (one warp per shell, one lane
-//                   per point), then the Cartesian assembly of Eqs. 1 and 4
-//                   (one warp per point, one lane per AO pair), split into
-//                   bf16 hi + lo and written straight into the MMA's shared
-//                   memory stage in the 128-byte swizzled K-major layout; the
-//                   group leader also loads the matching C chunk by TMA
+//       warps 5-12  AO producers: for each live chunk, the shell-major AO
+//                   evaluation of ao_vgl (one warp per shell, one lane per
+//                   point: radial sums of Eq. 2 with the Eq. 3 screen, then
+//                   every Cartesian component of Eqs. 1 and 4) into an FP32
+//                   staging tile, then split into bf16 hi + lo and written
+//                   into the MMA's shared memory stage in the 128-byte
+//                   swizzled K-major layout; the group leader also loads the
+//                   matching C chunk by TMA
 //       warp 4      one thread issues hi*hi + hi*lo + lo*hi MMAs into a
 //                   double-buffered TMEM accumulator
 //       warps 0-3   epilogue: TMEM -> registers -> rows of the MO vgl output
@@ -36,13 +37,15 @@ constexpr int kProdThreads = 32 * kProdWarps;
 constexpr int kFThreads = 32 * (kProdWarp0 + kProdWarps);  // 416
 constexpr int kStages = 2;
 constexpr uint32_t kABytes = kBM * kRowBytes;  // one bf16 plane of a 128 x 64 block
+// staging rows of lanes 0..25; lane 25 is past the tile, so rows 125..127
+// read back as zeros
+using FusedStage = AOStageSmem<float, kTilePoints + 1>;
+// MMA N of the fused kernel: the AO staging tile leaves room for two stages
+// of B up to 192 columns
+constexpr int kFusedBnMax = 192;
 
 __device__ __forceinline__ void prod_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
 struct FusedParams {
@@ -62,7 +65,7 @@ struct FusedShape {
   static constexpr uint32_t STAGE_BYTES = 2 * (kABytes + B_BYTES);
   static constexpr uint32_t RING = kStages * STAGE_BYTES;
   static constexpr uint32_t TMEM_COLS = tmem_cols<BN>();  // per accumulator buffer (two)
-  static constexpr size_t SMEM = 1024 + RING + sizeof(AOShared<float>);
+  static constexpr size_t SMEM = 1024 + RING + sizeof(FusedStage);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N: 16..256, step 16");
 };
 
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   unsigned char* gbase = smem_raw + (base - raw);
-  AOShared<float>& sh = *reinterpret_cast<AOShared<float>*>(gbase + Sh::RING);
+  FusedStage& sh = *reinterpret_cast<FusedStage*>(gbase + Sh::RING);
   auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
   auto empty_bar = [&](int s) { return smem_u32(&bars[kStages + s]); };
   auto tfull_bar = [&](int b) { return smem_u32(&bars[2 * kStages + b]); };
@@ -141,13 +144,22 @@ __global__ void __launch_bounds__(kFThreads, 1)
           }
         }
       }
+      const bool valid = lane < kTilePoints && p0 + lane < n;
       for (int i = 0; i < cnt; ++i) {
         const int q = forced ? 0 : (int)lst[i];
-        prod_sync();  // previous block's assembly done with the tables and S / d
-        load_chunk_tables<float>(prm.b, q, sh, ptid, kProdThreads);
+        prod_sync();  // previous block's conversion done with the tables and staging tile
+        load_stage_tables(prm.b, q, sh, ptid, kProdThreads);
+        if (ptid == 0) sh.next = 0;
         prod_sync();
         const int4 ch = prm.b.chunk[q];
-        radial_phase<float>(sh, ch.y - ch.x, pw, kProdWarps, lane, kTilePoints, p0, n, Tthr);
+        const int ns = ch.y - ch.x;
+        for (;;) {
+          int k = 0;
+          if (lane == 0) k = atomicAdd(&sh.next, 1);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if (k >= ns) break;
+          shell_at_point(sh, sh.order[k], lane, valid, Tthr);
+        }
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1u;
         ++it;
@@ -163,50 +175,24 @@ __global__ void __launch_bounds__(kFThreads, 1)
             tma_load_2d(bst + Sh::B_BYTES, &prm.c_lo, full_bar(s), q * kChunkAO, n0);
           }
         }
-        prod_sync();  // radial results visible, stage granted
+        prod_sync();  // staging tile complete, stage granted
         if (!prod_ok) {
           alive = false;
           break;
         }
-        // assembly: rows 5 pl + c of both planes in the SWIZZLE_128B layout
-        // (16-byte chunk j of row r at chunk j ^ (r & 7))
+        // rows r of both planes in the SWIZZLE_128B layout (16-byte chunk j
+        // of row r at chunk j ^ (r & 7)); lane = AO pair (2 lane, 2 lane + 1)
         unsigned char* a_hi = gbase + s * Sh::STAGE_BYTES;
         unsigned char* a_lo = a_hi + kABytes;
-        const int na = ch.w - ch.z;
-        const int a0 = 2 * lane, a1 = 2 * lane + 1;
-        for (int pl = pw; pl < kTilePoints; pl += kProdWarps) {
-          float v0[5], v1[5];
-          const bool valid = p0 + pl < n;
-          if (valid && a0 < na) {
-            assemble(sh, a0, pl, v0);
-          } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) v0[c] = 0.0f;
-          }
-          if (valid && a1 < na) {
-            assemble(sh, a1, pl, v1);
-          } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) v1[c] = 0.0f;
-          }
-#pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            const int r = 5 * pl + c;
-            const uint32_t off = r * kRowBytes + ((((uint32_t)lane >> 2) ^ (r & 7)) << 4) +
-                                 (((uint32_t)lane & 3) << 2);
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0[c]), h1 = __float2bfloat16_rn(v1[c]);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(v0[c] - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(v1[c] - __bfloat162float(h1));
-            *reinterpret_cast<uint32_t*>(a_hi + off) = pack_bf16x2(h0, h1);
-            *reinterpret_cast<uint32_t*>(a_lo + off) = pack_bf16x2(l0, l1);
-          }
-        }
-        if (pw < kTileRows - 5 * kTilePoints) {  // rows 125..127 are zero
-          const int r = 5 * kTilePoints + pw;
+        for (int r = pw; r < kTileRows; r += kProdWarps) {
+          const float v0 = sh.stage[r][2 * lane], v1 = sh.stage[r][2 * lane + 1];
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
           const uint32_t off = r * kRowBytes + ((((uint32_t)lane >> 2) ^ (r & 7)) << 4) +
                                (((uint32_t)lane & 3) << 2);
-          *reinterpret_cast<uint32_t*>(a_hi + off) = 0u;
-          *reinterpret_cast<uint32_t*>(a_lo + off) = 0u;
+          *reinterpret_cast<__nv_bfloat162*>(a_hi + off) = h;
+          *reinterpret_cast<__nv_bfloat162*>(a_lo + off) = l;
         }
         // generic-proxy writes must be visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -434,6 +420,18 @@ cudaError_t launch_mo_fused(int bn, const BasisDev& b, const PointsDev& p, const
                             const void* c_lo, int64_t kpad, int64_t N, float* out,
                             const int* live_count, const uint16_t* live_list, int* err_flag,
                             cudaStream_t s) {
+  if (bn > kFusedBnMax) {
+    // the fewest N tiles of at most kFusedBnMax columns, each as narrow as it can be
+    static const int bns[] = {16, 32, 64, 96, 128, 160, 192};
+    const int64_t tiles = (N + kFusedBnMax - 1) / kFusedBnMax;
+    const int64_t per = (N + tiles - 1) / tiles;
+    bn = kFusedBnMax;
+    for (int c : bns)
+      if (c >= per) {
+        bn = c;
+        break;
+      }
+  }
   switch (bn) {
     case 16: return launch_fused_bn<16>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
     case 32: return launch_fused_bn<32>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
@@ -442,7 +440,6 @@ cudaError_t launch_mo_fused(int bn, const BasisDev& b, const PointsDev& p, const
     case 128: return launch_fused_bn<128>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
     case 160: return launch_fused_bn<160>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
     case 192: return launch_fused_bn<192>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
-    case 256: return launch_fused_bn<256>(b, p, c_hi, c_lo, kpad, N, out, live_count, live_list, err_flag, s);
     default: return cudaErrorInvalidValue;
   }
 }
