@@ -184,7 +184,8 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None):
 
 
 def traffic_for(kernel, mode):
-    """DRAM bytes per launch from the committed ncu summary, if current."""
+    """DRAM bytes per launch from the committed ncu summary, if every source
+    file of the kernel still hashes to what was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -194,10 +195,13 @@ def traffic_for(kernel, mode):
         ent = tab.get(f"{kernel}:{mode}")
         if not ent:
             return None
-        src = os.path.join(ROOT, ent["source"])
         import hashlib
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+        srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+        hsh = hashlib.sha256()
+        for src in srcs:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                hsh.update(f.read())
+        return ent["bytes_per_launch"] if hsh.hexdigest()[:16] == ent["source_sha"] else None
     except Exception:
         return None
 
