@@ -251,7 +251,11 @@ struct AOStageSmem {
   int col[kMaxShellsChunk];    // first column of the shell in the chunk
   int lsh[kMaxShellsChunk];
   int order[kMaxShellsChunk];  // shells by descending estimated cost
-  int next;                    // next entry of `order` to hand out
+  int work[kMaxShellsChunk];   // this tile's shells to visit, in `order` order
+  unsigned char dirty[kMaxShellsChunk];  // staging columns of the shell may be nonzero
+  unsigned reach;              // bit s: shell s may reach a point of the tile
+  int nwork;
+  int next;                    // next entry of `work` to hand out
   T stage[5 * kLanes][kStagePitch];
 };
 
@@ -285,6 +289,7 @@ __device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q,
     sh.col[i] = b.shell_ao0[s] - ch.z;
     const int l = b.shell_l[s];
     sh.lsh[i] = l;
+    sh.dirty[i] = 1;  // columns hold whatever the previous chunk left
     // cost ~ primitives (radial sums) + Cartesian components (assembly);
     // rank by descending cost, ties by position
     auto cost = [&](int ss) {
@@ -375,6 +380,92 @@ __device__ __forceinline__ void shell_components(T dx, T dy, T dz, T S0, T S1, T
   cart_component<T, L, 0>(px, py, pz, M, S0, S1x2 * dx, S1x2 * dy, S1x2 * dz, Lr, st);
 }
 
+// Zeros into the staging columns of shell `sl` if they may hold values of
+// an earlier tile (whole warp; only this warp touches the shell this tile).
+template <typename T, int kLanes>
+__device__ __forceinline__ void shell_zero_columns(AOStageSmem<T, kLanes>& sh, int sl, int lane) {
+  if (!sh.dirty[sl]) return;
+  const int l = sh.lsh[sl];
+  const int nc = (l + 1) * (l + 2) / 2;
+  T* st = &sh.stage[5 * (lane < kLanes ? lane : kLanes - 1)][sh.col[sl]];
+  for (int j = 0; j < nc; ++j) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) st[c * kStagePitch + j] = T(0);
+  }
+  __syncwarp();
+  if (lane == 0) sh.dirty[sl] = 0;
+}
+
+// Phase 0 of a tile, one warp: lane p < tp with p0 + p < n loads point p
+// into shared memory.  The tile's bounding box then culls shells whose
+// screening sphere (r^2 < r2max) cannot reach it: the squared distance from
+// R_A to the box bounds r^2 from below for every point, so a shell is kept
+// unless that bound, less a relative and absolute margin for the rounding of
+// both sides, is at least r2max.  Writes sh.reach, the list of shells to
+// visit (kept ones, and culled ones whose staging columns are dirty) in
+// `order` order, and resets the work counter.
+template <typename T, int kLanes>
+__device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const PointsDev& pts,
+                                           int ns, int lane, int tp, int64_t p0) {
+  const int64_t n = pts.n;
+  const int64_t ip = p0 + lane;
+  const bool pv = lane < tp && ip < n;
+  T x = T(0), y = T(0), z = T(0);
+  if (pv) {
+    if constexpr (sizeof(T) == 8) {
+      x = pts.x[ip];
+      y = pts.y[ip];
+      z = pts.z[ip];
+    } else {
+      x = pts.hi[ip];
+      y = pts.hi[n + ip];
+      z = pts.hi[2 * n + ip];
+      sh.pt_lo[lane][0] = pts.lo[ip];
+      sh.pt_lo[lane][1] = pts.lo[n + ip];
+      sh.pt_lo[lane][2] = pts.lo[2 * n + ip];
+    }
+    sh.pt[lane][0] = x;
+    sh.pt[lane][1] = y;
+    sh.pt[lane][2] = z;
+  }
+  const T big = T(3.0e38);
+  T lo[3] = {pv ? x : big, pv ? y : big, pv ? z : big};
+  T hi[3] = {pv ? x : -big, pv ? y : -big, pv ? z : -big};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  bool keep = false;
+  if (lane < ns) {
+    T d2 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T c = sh.nuc[lane][k];
+      const T e = max(T(0), max(lo[k] - c, c - hi[k]));
+      d2 += e * e;
+    }
+    keep = d2 * T(0.9999) - T(1e-3) < sh.r2max[lane];
+  }
+  const unsigned reach = __ballot_sync(0xffffffffu, keep);
+  bool visit = false;
+  int sl = 0;
+  if (lane < ns) {
+    sl = sh.order[lane];
+    visit = ((reach >> sl) & 1u) || sh.dirty[sl];
+  }
+  const unsigned vm = __ballot_sync(0xffffffffu, visit);
+  if (visit) sh.work[__popc(vm & ((1u << lane) - 1u))] = sl;
+  if (lane == 0) {
+    sh.reach = reach;
+    sh.nwork = __popc(vm);
+    sh.next = 0;
+  }
+}
+
 // Radial sums and every component of shell `sl` at tile point `lane` (valid
 // lanes only; the others get zeros), written to the staging tile.  Returns
 // whether this lane's S were nonzero.
@@ -411,23 +502,19 @@ __device__ __forceinline__ bool shell_at_point(AOStageSmem<T, kLanes>& sh, int s
     }
   }
   const bool nz = S0 != T(0) || S1 != T(0) || S2 != T(0);
-  const int c0 = sh.col[sl];
-  const int l = sh.lsh[sl];
-  T* st = &sh.stage[5 * (lane < kLanes ? lane : kLanes - 1)][c0];
   if (__any_sync(0xffffffffu, nz)) {
+    const int c0 = sh.col[sl];
+    T* st = &sh.stage[5 * (lane < kLanes ? lane : kLanes - 1)][c0];
     const T* M = &sh.M[c0];
-    switch (l) {
+    switch (sh.lsh[sl]) {
       case 0: shell_components<T, 0>(dx, dy, dz, S0, S1, S2, M, st); break;
       case 1: shell_components<T, 1>(dx, dy, dz, S0, S1, S2, M, st); break;
       case 2: shell_components<T, 2>(dx, dy, dz, S0, S1, S2, M, st); break;
       default: shell_components<T, 3>(dx, dy, dz, S0, S1, S2, M, st); break;
     }
+    if (lane == 0) sh.dirty[sl] = 1;
   } else {
-    const int nc = (l + 1) * (l + 2) / 2;
-    for (int j = 0; j < nc; ++j) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) st[c * kStagePitch + j] = T(0);
-    }
+    shell_zero_columns(sh, sl, lane);
   }
   return nz;
 }

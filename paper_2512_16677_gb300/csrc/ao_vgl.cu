@@ -81,34 +81,32 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
     const int64_t p0 = ptile * TP;
     __syncthreads();  // tables ready / previous tile's copy-out done with the stage
-    // ---- phase 0: the tile's points
-    if (tid < TP) {
-      const int64_t ip = p0 + tid;
-      if (ip < n) {
-        if constexpr (sizeof(T) == 8) {
-          sh.pt[tid][0] = pts.x[ip];
-          sh.pt[tid][1] = pts.y[ip];
-          sh.pt[tid][2] = pts.z[ip];
-        } else {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            sh.pt[tid][k] = pts.hi[k * n + ip];
-            sh.pt_lo[tid][k] = pts.lo[k * n + ip];
-          }
-        }
+    // ---- phase 0 (warp 0): the tile's points, its bounding box and the
+    // shells that may reach it
+    if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0);
+    __syncthreads();
+    const unsigned reach = sh.reach;
+    if constexpr (kTiled) {
+      if (reach == 0u) {  // no shell reaches the tile: block not written
+        if (tid == 0) out.mask[ptile * out.nchunk + q] = 0;
+        continue;
       }
     }
-    if (tid == 0) sh.next = 0;
-    __syncthreads();
-    // ---- phase 1: warps take shells (costliest first), lanes are points
+    // ---- phase 1: warps take shells (costliest first), lanes are points;
+    // culled shells only get their staging columns cleared
     const bool valid = lane < TP && p0 + lane < n;
+    const int nwork = sh.nwork;
     int live = 0;
     for (;;) {
       int k = 0;
       if (lane == 0) k = atomicAdd(&sh.next, 1);
       k = __shfl_sync(0xffffffffu, k, 0);
-      if (k >= ns) break;
-      live |= shell_at_point(sh, sh.order[k], lane, valid, Tthr);
+      if (k >= nwork) break;
+      const int sl = sh.work[k];
+      if ((reach >> sl) & 1u)
+        live |= shell_at_point(sh, sl, lane, valid, Tthr);
+      else
+        shell_zero_columns(sh, sl, lane);
     }
     // block barrier; in the tiled layout it also tells whether any entry of
     // block (tile, chunk) survived screening
