@@ -19,7 +19,8 @@
 //                   matching C chunk by TMA
 //       warp 4      one thread issues hi*hi + hi*lo + lo*hi MMAs into a
 //                   double-buffered TMEM accumulator
-//       warps 0-3   epilogue: TMEM -> registers -> rows of the MO vgl output
+//       warps 0-3   epilogue: TMEM -> registers -> shared memory (32 x 16
+//                   slices turned around) -> whole row segments of the output
 // The producer group synchronises on named barrier 1.  Every wait is bounded
 // and a wait that gives up records a code in the caller's error word.
 #include "ao_common.cuh"
@@ -43,6 +44,9 @@ using FusedStage = AOStageSmem<float, kTilePoints + 1>;
 // MMA N of the fused kernel: the AO staging tile leaves room for two stages
 // of B up to 192 columns
 constexpr int kFusedBnMax = 192;
+// epilogue staging, as in the two-kernel contraction: per warp a 32 x 16
+// accumulator slice with an odd pitch
+constexpr int kEpiPitch = 17;
 
 __device__ __forceinline__ void prod_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
@@ -80,6 +84,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __shared__ int abort_flag;
   __shared__ int stage_last[kStages];
   __shared__ int prod_ok;
+  __shared__ float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   unsigned char* gbase = smem_raw + (base - raw);
@@ -269,30 +274,30 @@ __global__ void __launch_bounds__(kFThreads, 1)
       tc_fence_after();
       const int64_t mt = t / prm.n_tiles;
       const int64_t n0 = (t % prm.n_tiles) * BN;
-      const int local = warp * 32 + lane;
-      const int64_t row = mt * (5 * kTilePoints) + local;
-      const bool row_ok = local < 5 * kTilePoints && row < 5 * prm.P;
       const int64_t N = prm.N;
-      float* drow = prm.D + row * N;
-      const bool vec = (N % 4) == 0;
+      const int64_t M = 5 * prm.P;
       const uint32_t tbase = tmem + b * Sh::TMEM_COLS + ((uint32_t)(warp * 32) << 16);
+      // each 32 x 16 slice turned around in shared memory: lane -> row
+      // 2 i + lane / 16 of the warp's 32, column lane % 16
+      const int cl = lane & 15;
+      const int rsub = lane >> 4;
+      float(*stg)[kEpiPitch] = epi[warp];
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(tbase + c, v);
-        if (row_ok) {
-          const int64_t col = n0 + c;
-          if (vec && col + 16 <= N) {
-            float4* p = reinterpret_cast<float4*>(drow + col);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (col + q < N) drow[col + q] = v[q];
-          }
+        for (int q = 0; q < 16; ++q) stg[lane][q] = v[q];
+        __syncwarp();
+        const int64_t col = n0 + c + cl;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+          const int r = 2 * i + rsub;
+          const int loc = warp * 32 + r;
+          const int64_t row = mt * (5 * kTilePoints) + loc;
+          if (loc < 5 * kTilePoints && row < M && col < N) prm.D[row * N + col] = stg[r][cl];
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -364,7 +369,8 @@ cudaError_t launch_fused_bn(const BasisDev& b, const PointsDev& p, const void* c
                             const int* live_count, const uint16_t* live_list, int* err_flag,
                             cudaStream_t s) {
   using Sh = FusedShape<BN>;
-  static_assert(Sh::SMEM <= 232448 - 1024, "shared memory budget");
+  static_assert(Sh::SMEM + sizeof(float) * 4 * 32 * kEpiPitch + 1024 <= 232448,
+                "shared memory budget");
   FusedParams prm;
   prm.b = b;
   prm.p = p;

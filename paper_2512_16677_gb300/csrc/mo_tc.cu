@@ -15,8 +15,9 @@
 //   warp 5     allocates TMEM; one thread issues the MMAs for each stage and
 //              commits them to the stage's "empty" barrier.
 //   warps 0-3  epilogue: wait for the last commit, read the FP32 accumulator
-//              from TMEM (warp w owns TMEM lanes 32w..32w+31 = rows) and store
-//              row segments of D.
+//              from TMEM (warp w owns TMEM lanes 32w..32w+31 = rows), turn
+//              each 32 x 16 slice around in shared memory and store it as
+//              whole 64-byte row segments of D.
 // Every wait is bounded (clock64); a wait that gives up records a code in the
 // caller's error word, stops the pipeline, drains its own copies and MMAs,
 // frees TMEM and returns.
@@ -30,6 +31,14 @@ namespace {
 using namespace tc;
 
 constexpr int kThreads = 192;       // 4 epilogue warps + producer + MMA
+// Epilogue staging: each epilogue warp turns a 32-row x 16-column slice of
+// the accumulator (one row per lane) around in shared memory so that its
+// global stores cover whole 64-byte row segments; the odd pitch keeps both
+// directions free of bank conflicts.
+constexpr int kEpiCols = 16;
+constexpr int kEpiPitch = kEpiCols + 1;
+constexpr size_t kEpiBytes = 4 * 32 * kEpiPitch * sizeof(float);
+constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block
 
 template <int MODE, int BN_MAX, int STAGES>
 struct TcShape {
@@ -38,6 +47,7 @@ struct TcShape {
   static constexpr uint32_t B_BYTES = BN_MAX * kRowBytes;  // room for the widest B tile
   static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + B_BYTES);
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 4);
+  static_assert(SMEM + kEpiBytes + 64 <= kSmemLimit, "shared memory budget");
   static constexpr uint32_t TMEM_COLS = tmem_cols<BN_MAX>();  // per accumulator buffer (two)
   static_assert(BN_MAX % 16 == 0 && BN_MAX >= 16 && BN_MAX <= 256, "MMA N: 16..256, step 16");
 };
@@ -141,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   const uint32_t bar0 = base + STAGES * S::STAGE_BYTES;
@@ -288,18 +299,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       tc_fence_after();
       const TileInfo x = sched.tile(t);
-      const int local = warp * 32 + lane;
-      const int64_t row = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) + local
-                                  : (int64_t)x.m0 + local;
-      const bool row_ok = row < x.M && (!x.tiled || local < 5 * kTilePoints);
       bool any_live = x.kmask == nullptr;
       for (int kb = 0; kb < x.num_kb && !any_live; ++kb) any_live = kb_live<MODE>(x, kb);
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
       const int64_t N = x.N;
-      float* drow = x.D + row * N;
-      const bool vec = (N % 4) == 0;
+      // store phase: lane -> row 2 i + lane / 16 of the warp's 32, column lane % 16
+      const int cl = lane & 15;
+      const int rsub = lane >> 4;
+      const int64_t row0 = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) : (int64_t)x.m0;
+      const int rows_here = x.tiled ? 5 * kTilePoints : kBM;  // tile rows that exist in D
+      float(*stg)[kEpiPitch] = epi[warp];
 #pragma unroll 1
-      for (int c = 0; c < x.bn; c += 16) {
+      for (int c = 0; c < x.bn; c += kEpiCols) {
         float v[16];
         if (any_live) {
           tmem_ld16(tbase + c, v);
@@ -307,19 +318,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < 16; ++q) v[q] = 0.0f;
         }
-        if (row_ok) {
-          const int64_t n = x.n0 + c;
-          if (vec && n + 16 <= N) {
-            float4* p = reinterpret_cast<float4*>(drow + n);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (n + q < N) drow[n + q] = v[q];
-          }
+        for (int q = 0; q < 16; ++q) stg[lane][q] = v[q];
+        __syncwarp();
+        const int64_t col = x.n0 + c + cl;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+          const int r = 2 * i + rsub;
+          const int loc = warp * 32 + r;
+          const int64_t row = row0 + loc;
+          if (loc < rows_here && row < x.M && col < N) x.D[row * N + col] = stg[r][cl];
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -339,10 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ----------------------------------------------------------------- host ---
 
 constexpr int stages_for(int mode, int bn) {
-  // fill ~220 KB of shared memory, at most 8 stages
-  return (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes)) > 8
+  // as many stages as the shared memory left by the epilogue staging holds, at most 8
+  return (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+               ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes)) > 8
              ? 8
-             : (int)((220 * 1024) / ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes));
+             : (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+                     ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn) * kRowBytes));
 }
 
 // Grid of resident CTAs for a kernel instance (TMEM never oversubscribed).
