@@ -45,8 +45,8 @@ using FusedStage = AOStageSmem<float, kTilePoints + 1>;
 // of B up to 192 columns
 constexpr int kFusedBnMax = 192;
 // epilogue staging, as in the two-kernel contraction: per warp a 32 x 16
-// accumulator slice with an odd pitch
-constexpr int kEpiPitch = 17;
+// accumulator slice, 16-byte chunk q of row r at chunk q ^ ((r / 2) % 4)
+constexpr int kEpiPitch = 16;
 
 __device__ __forceinline__ void prod_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __shared__ int abort_flag;
   __shared__ int stage_last[kStages];
   __shared__ int prod_ok;
-  __shared__ float epi[4][32][kEpiPitch];
+  __shared__ __align__(16) float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   unsigned char* gbase = smem_raw + (base - raw);
@@ -277,25 +277,41 @@ __global__ void __launch_bounds__(kFThreads, 1)
       const int64_t N = prm.N;
       const int64_t M = 5 * prm.P;
       const uint32_t tbase = tmem + b * Sh::TMEM_COLS + ((uint32_t)(warp * 32) << 16);
-      // each 32 x 16 slice turned around in shared memory: lane -> row
-      // 2 i + lane / 16 of the warp's 32, column lane % 16
-      const int cl = lane & 15;
-      const int rsub = lane >> 4;
+      // store phase: lane -> row 8 i + lane / 4 of the warp's 32, columns
+      // 4 (lane % 4) .. + 3 of the slice
+      const int rq = lane >> 2;
+      const int cq = (lane & 3) * 4;
+      const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(prm.D) & 15) == 0;
       float(*stg)[kEpiPitch] = epi[warp];
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(tbase + c, v);
+        float4* srow = reinterpret_cast<float4*>(&stg[lane][0]);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stg[lane][q] = v[q];
+        for (int q = 0; q < 4; ++q)
+          srow[q ^ ((lane >> 1) & 3)] =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         __syncwarp();
-        const int64_t col = n0 + c + cl;
-#pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
-          const int r = 2 * i + rsub;
+        const int64_t col = n0 + c + cq;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 8 * i + rq;
           const int loc = warp * 32 + r;
           const int64_t row = mt * (5 * kTilePoints) + loc;
-          if (loc < 5 * kTilePoints && row < M && col < N) prm.D[row * N + col] = stg[r][cl];
+          if (loc < 5 * kTilePoints && row < M) {
+            const float4 w =
+                reinterpret_cast<const float4*>(&stg[r][0])[(lane & 3) ^ ((r >> 1) & 3)];
+            float* dst = prm.D + row * N + col;
+            if (vec && col + 3 < N) {
+              *reinterpret_cast<float4*>(dst) = w;
+            } else {
+              if (col < N) dst[0] = w.x;
+              if (col + 1 < N) dst[1] = w.y;
+              if (col + 2 < N) dst[2] = w.z;
+              if (col + 3 < N) dst[3] = w.w;
+            }
+          }
         }
         __syncwarp();
       }

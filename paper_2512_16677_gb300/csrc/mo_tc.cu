@@ -17,7 +17,7 @@
 //   warps 0-3  epilogue: wait for the last commit, read the FP32 accumulator
 //              from TMEM (warp w owns TMEM lanes 32w..32w+31 = rows), turn
 //              each 32 x 16 slice around in shared memory and store it as
-//              whole 64-byte row segments of D.
+//              64-byte row segments of D, 8 rows per instruction.
 // Every wait is bounded (clock64); a wait that gives up records a code in the
 // caller's error word, stops the pipeline, drains its own copies and MMAs,
 // frees TMEM and returns.
@@ -32,11 +32,13 @@ using namespace tc;
 
 constexpr int kThreads = 192;       // 4 epilogue warps + producer + MMA
 // Epilogue staging: each epilogue warp turns a 32-row x 16-column slice of
-// the accumulator (one row per lane) around in shared memory so that its
-// global stores cover whole 64-byte row segments; the odd pitch keeps both
-// directions free of bank conflicts.
+// the accumulator (one row per lane) around in shared memory so that each
+// 16-byte global store instruction covers 8 rows x 64 contiguous bytes.
+// 16-byte chunk q of row r sits at chunk q ^ ((r / 2) % 4): row writes (8
+// lanes = 8 rows per phase) and row-pair reads are both free of bank
+// conflicts.
 constexpr int kEpiCols = 16;
-constexpr int kEpiPitch = kEpiCols + 1;
+constexpr int kEpiPitch = kEpiCols;
 constexpr size_t kEpiBytes = 4 * 32 * kEpiPitch * sizeof(float);
 constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block
 
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ float epi[4][32][kEpiPitch];
+  __shared__ __align__(16) float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   const uint32_t bar0 = base + STAGES * S::STAGE_BYTES;
@@ -303,14 +305,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < x.num_kb && !any_live; ++kb) any_live = kb_live<MODE>(x, kb);
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
       const int64_t N = x.N;
-      // store phase: lane -> row 2 i + lane / 16 of the warp's 32, column lane % 16
-      const int cl = lane & 15;
-      const int rsub = lane >> 4;
+      // store phase: lane -> row 8 i + lane / 4 of the warp's 32, columns
+      // 4 (lane % 4) .. + 3 of the slice
+      const int rq = lane >> 2;
+      const int cq = (lane & 3) * 4;
+      const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(x.D) & 15) == 0;
       const int64_t row0 = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) : (int64_t)x.m0;
       const int rows_here = x.tiled ? 5 * kTilePoints : kBM;  // tile rows that exist in D
       float(*stg)[kEpiPitch] = epi[warp];
 #pragma unroll 1
-      for (int c = 0; c < x.bn; c += kEpiCols) {
+      for (int c = 0; c < x.bn; c += 16) {
         float v[16];
         if (any_live) {
           tmem_ld16(tbase + c, v);
@@ -318,16 +322,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < 16; ++q) v[q] = 0.0f;
         }
+        float4* srow = reinterpret_cast<float4*>(&stg[lane][0]);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stg[lane][q] = v[q];
+        for (int q = 0; q < 4; ++q)
+          srow[q ^ ((lane >> 1) & 3)] =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         __syncwarp();
-        const int64_t col = x.n0 + c + cl;
-#pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
-          const int r = 2 * i + rsub;
+        const int64_t col = x.n0 + c + cq;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 8 * i + rq;
           const int loc = warp * 32 + r;
           const int64_t row = row0 + loc;
-          if (loc < rows_here && row < x.M && col < N) x.D[row * N + col] = stg[r][cl];
+          if (loc < rows_here && row < x.M) {
+            const float4 w =
+                reinterpret_cast<const float4*>(&stg[r][0])[(lane & 3) ^ ((r >> 1) & 3)];
+            float* dst = x.D + row * N + col;
+            if (vec && col + 3 < N) {
+              *reinterpret_cast<float4*>(dst) = w;
+            } else {
+              if (col < N) dst[0] = w.x;
+              if (col + 1 < N) dst[1] = w.y;
+              if (col + 2 < N) dst[2] = w.z;
+              if (col + 3 < N) dst[3] = w.w;
+            }
+          }
         }
         __syncwarp();
       }
