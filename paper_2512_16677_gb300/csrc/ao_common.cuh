@@ -43,7 +43,7 @@ struct Arith<float> {
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
   static __device__ __forceinline__ void diff(const BasisDev& b, const PointsDev& p, int64_t ip,
                                               int a, float& dx, float& dy, float& dz) {
-    const int64_t n = p.n;
+    const int64_t n = p.ld;
     // (x_hi - X_hi) is exact when the two are close (Sterbenz) and otherwise
     // rounds once; adding the residual difference restores FP32 accuracy of d.
     dx = (p.hi[ip] - b.nucl_hi[3 * a + 0]) + (p.lo[ip] - b.nucl_lo[3 * a + 0]);
@@ -417,12 +417,13 @@ __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const Poi
       y = pts.y[ip];
       z = pts.z[ip];
     } else {
+      const int64_t ld = pts.ld;
       x = pts.hi[ip];
-      y = pts.hi[n + ip];
-      z = pts.hi[2 * n + ip];
+      y = pts.hi[ld + ip];
+      z = pts.hi[2 * ld + ip];
       sh.pt_lo[lane][0] = pts.lo[ip];
-      sh.pt_lo[lane][1] = pts.lo[n + ip];
-      sh.pt_lo[lane][2] = pts.lo[2 * n + ip];
+      sh.pt_lo[lane][1] = pts.lo[ld + ip];
+      sh.pt_lo[lane][2] = pts.lo[2 * ld + ip];
     }
     sh.pt[lane][0] = x;
     sh.pt[lane][1] = y;

@@ -99,6 +99,8 @@ struct qk_context_s {
   void* ao_ws = nullptr;
   // host-output staging, device error word, backward scratch
   DevBuf d_out;
+  cudaStream_t copy_stream = nullptr;   // device -> host copies of output ranges
+  std::vector<cudaEvent_t> range_done;  // one per output range of a host call
   DevBuf d_flag;
   DevBuf bwd_own;
   // optional per-kernel-class timing with events on the context's stream
@@ -106,6 +108,8 @@ struct qk_context_s {
   std::vector<cudaEvent_t> ev_start[kTimerClasses], ev_stop[kTimerClasses];
   size_t ev_used[kTimerClasses] = {0, 0, 0};
   ~qk_context_s() {
+    for (auto e : range_done) cudaEventDestroy(e);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     for (int k = 0; k < kTimerClasses; ++k) {
       for (auto e : ev_start[k]) cudaEventDestroy(e);
       for (auto e : ev_stop[k]) cudaEventDestroy(e);
@@ -382,28 +386,111 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
   return t;
 }
 
-// Make the AO tensor of the current date/mode valid in the workspace.
-qk_status provide_ao(qk_context c, AOTensor* out) {
+// The AO tensor's place in the workspace; *valid says whether it already
+// holds the current date/mode/basis.
+qk_status ao_workspace(qk_context c, AOTensor* out, bool* valid) {
   qk_status st = ensure_tables(c);
   if (st) return st;
   void* ws = nullptr;
   st = workspace(c, ao_tensor_bytes(c, c->mode), &ws);
   if (st) return st;
   *out = ao_view(c, ws, c->mode);
-  if (c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
-      c->ao_version == c->basis_version)
-    return QK_SUCCESS;
+  *valid = c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
+           c->ao_version == c->basis_version;
+  return QK_SUCCESS;
+}
+
+void mark_ao(qk_context c, const AOTensor& ao) {
+  c->ao_date = c->date;
+  c->ao_mode = c->mode;
+  c->ao_ws = ao.a;
+  c->ao_version = c->basis_version;
+}
+
+// Points [p0, p1) and the matching rows of the AO tensor (p0 a multiple of
+// the layout's point tile).
+PointsDev points_range(const PointsDev& p, int64_t p0, int64_t p1) {
+  PointsDev v = p;
+  v.n = p1 - p0;
+  v.x += p0;
+  v.y += p0;
+  v.z += p0;
+  v.hi += p0;
+  v.lo += p0;
+  return v;
+}
+
+AOTensor ao_range(const AOTensor& t, int mode, int64_t p0, int64_t p1) {
+  AOTensor v = t;
+  const size_t es = mode == QK_FP64 ? sizeof(double)
+                                    : (mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
+  int64_t r0;
+  if (t.tiled) {
+    const int64_t t0 = p0 / kTilePoints;
+    r0 = t0 * kTileRows;
+    v.rows = (p1 - p0 + kTilePoints - 1) / kTilePoints * kTileRows;
+    v.mask = t.mask + t0 * t.nchunk;
+  } else {
+    r0 = 5 * p0;
+    v.rows = 5 * (p1 - p0);
+  }
+  v.a = (unsigned char*)t.a + (size_t)r0 * t.ld * es;
+  if (t.a_lo) v.a_lo = (unsigned char*)t.a_lo + (size_t)r0 * t.ld * es;
+  return v;
+}
+
+// Make the AO tensor of the current date/mode valid in the workspace.
+qk_status provide_ao(qk_context c, AOTensor* out) {
+  bool valid = false;
+  qk_status st = ao_workspace(c, out, &valid);
+  if (st || valid) return st;
   cudaError_t e;
   {
     TimedLaunch t(c, 0);
     e = launch_ao_vgl(c->bdev, c->pdev, c->mode, *out, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
-  c->ao_date = c->date;
-  c->ao_mode = c->mode;
-  c->ao_ws = ws;
-  c->ao_version = c->basis_version;
+  mark_ao(c, *out);
   return QK_SUCCESS;
+}
+
+// D[M][mo] = AO rows . C^T for the AO rows of `ao` (M = 5 x its points).
+qk_status contract(qk_context c, const AOTensor& ao, int64_t M, void* dout) {
+  const int64_t N = c->mo_num;
+  const int64_t KP = c->kpad;  // the contraction runs over the chunked columns
+  cudaError_t e = cudaSuccess;
+  TimedLaunch timer(c, 1);
+  switch (c->mode) {
+    case QK_FP64:
+      e = launch_gemm_f64(M, N, KP, (const double*)ao.a, ao.ld, 1, c->c64p, KP, 1, (double*)dout,
+                          N, 1, c->stream);
+      break;
+    case QK_FP32:
+      e = launch_gemm_f32(M, N, KP, (const float*)ao.a, ao.ld, 1, c->c32p, KP, 1, (float*)dout,
+                          N, 1, c->stream);
+      break;
+    default: {
+      const bool split = c->mode == QK_BF16X3;
+      e = launch_mo_tc(c->mode, ao, KP, split ? (const void*)c->c_hi : (const void*)c->c32p,
+                       split ? (const void*)c->c_lo : nullptr, KP, N, (float*)dout,
+                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream, M);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "mo_vgl contraction");
+  return QK_SUCCESS;
+}
+
+// Output ranges of a host-memory MO call: enough points per range for full
+// launches, at most 8 ranges, each a multiple of 800 points (whole 25- and
+// 32-point tiles, so every range sees the tiles of the one-launch path).
+constexpr int64_t kRangeQuantum = 800;
+constexpr int64_t kMinRangePoints = 9600;
+int64_t host_range_points(qk_context c) {
+  int64_t parts = c->point_num / kMinRangePoints;
+  if (parts > 8) parts = 8;
+  if (parts < 2) return c->point_num;
+  const int64_t per = (c->point_num + parts - 1) / parts;
+  return (per + kRangeQuantum - 1) / kRangeQuantum * kRangeQuantum;
 }
 
 void invalidate(qk_context c) {
@@ -430,6 +517,7 @@ qk_status set_points_common(qk_context c, char transp, int64_t walk_num, int64_t
   float* fb = (float*)((unsigned char*)c->d_points.p + align_up(sizeof(double) * 3 * n, 256));
   c->pdev.hi = fb;
   c->pdev.lo = fb + 3 * n;
+  c->pdev.ld = n;
   c->walk_num = walk_num;
   c->elec_num = elec_num;
   c->point_num = n;
@@ -822,27 +910,7 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
   AOTensor ao{};
   st = provide_ao(c, &ao);
   if (st) return st;
-  const int64_t KP = c->kpad;  // contraction runs over the chunked columns
-  cudaError_t e = cudaSuccess;
-  TimedLaunch timer(c, 1);
-  switch (c->mode) {
-    case QK_FP64:
-      e = launch_gemm_f64(M, N, KP, (const double*)ao.a, ao.ld, 1, c->c64p, KP, 1, (double*)dout,
-                          N, 1, c->stream);
-      break;
-    case QK_FP32:
-      e = launch_gemm_f32(M, N, KP, (const float*)ao.a, ao.ld, 1, c->c32p, KP, 1, (float*)dout,
-                          N, 1, c->stream);
-      break;
-    default: {
-      const bool split = c->mode == QK_BF16X3;
-      e = launch_mo_tc(c->mode, ao, KP, split ? (const void*)c->c_hi : (const void*)c->c32p,
-                       split ? (const void*)c->c_lo : nullptr, KP, N, (float*)dout,
-                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream, M);
-    }
-  }
-  if (e != cudaSuccess) return cuda_fail(c, e, "mo_vgl contraction");
-  return QK_SUCCESS;
+  return contract(c, ao, M, dout);
 }
 
 qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
@@ -855,10 +923,58 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
   const size_t es = c->mode == QK_FP64 ? sizeof(double) : sizeof(float);
   cudaError_t e = c->d_out.ensure(es * n);
   if (e != cudaSuccess) return cuda_fail(c, e, "output staging");
-  st = qk_get_mo_vgl_device(c, c->d_out.p, n);
+  const int64_t per = host_range_points(c);
+  if (per >= c->point_num || use_fused(c)) {
+    st = qk_get_mo_vgl_device(c, c->d_out.p, n);
+    if (st) return st;
+    e = cudaMemcpyAsync(out, c->d_out.p, es * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl copy");
+    return qk_synchronize(c);
+  }
+  // Point ranges in turn: range r's output goes to the host on a second
+  // stream while range r + 1 is evaluated (the copy link is the slower part).
+  st = ensure_mo(c);
   if (st) return st;
-  e = cudaMemcpyAsync(out, c->d_out.p, es * n, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  AOTensor ao{};
+  bool have_ao = false;
+  st = ao_workspace(c, &ao, &have_ao);
+  if (st) return st;
+  if (!c->copy_stream) {
+    e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy stream");
+  }
+  const int64_t N = c->mo_num;
+  const int64_t ranges = (c->point_num + per - 1) / per;
+  while ((int64_t)c->range_done.size() < ranges) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e, "range events");
+    c->range_done.push_back(ev);
+  }
+  unsigned char* dbase = (unsigned char*)c->d_out.p;
+  unsigned char* hbase = (unsigned char*)out;
+  for (int64_t r = 0; r < ranges; ++r) {
+    const int64_t p0 = r * per;
+    const int64_t p1 = p0 + per < c->point_num ? p0 + per : c->point_num;
+    const AOTensor av = ao_range(ao, c->mode, p0, p1);
+    if (!have_ao) {
+      TimedLaunch t(c, 0);
+      e = launch_ao_vgl(c->bdev, points_range(c->pdev, p0, p1), c->mode, av, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
+    }
+    const size_t off = (size_t)5 * p0 * N * es;
+    st = contract(c, av, 5 * (p1 - p0), dbase + off);
+    if (st) return st;
+    e = cudaEventRecord(c->range_done[r], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->range_done[r], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hbase + off, dbase + off, (size_t)5 * (p1 - p0) * N * es,
+                          cudaMemcpyDeviceToHost, c->copy_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl range copy");
+  }
+  if (!have_ao) mark_ao(c, ao);
+  e = cudaStreamSynchronize(c->copy_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl copy");
   return qk_synchronize(c);
 }

@@ -51,14 +51,16 @@ struct BasisDev {
   float T_f;
 };
 
-// Points in structure-of-arrays form (device, library-owned).
+// Points in structure-of-arrays form (device, library-owned).  A view of a
+// contiguous range of points offsets every pointer and keeps ld.
 struct PointsDev {
   int64_t n;
   const double* x;  // [n] each
   const double* y;
   const double* z;
-  const float* hi;  // [3][n] float(x), float(y), float(z)
-  const float* lo;  // [3][n] residuals
+  const float* hi;  // [3][ld] float(x), float(y), float(z)
+  const float* lo;  // [3][ld] residuals
+  int64_t ld;       // distance between the coordinate planes of hi and lo
 };
 
 // Layout of the AO tensor: rows are (point, component) pairs, row r = 5p + c,

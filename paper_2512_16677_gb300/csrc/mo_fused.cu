@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
         if (ip < n) {
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            sh.pt[ptid][k] = prm.p.hi[k * n + ip];
-            sh.pt_lo[ptid][k] = prm.p.lo[k * n + ip];
+            sh.pt[ptid][k] = prm.p.hi[k * prm.p.ld + ip];
+            sh.pt_lo[ptid][k] = prm.p.lo[k * prm.p.ld + ip];
           }
         }
       }
@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(256)
     if (tid < np) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        pt[tid][k] = p.hi[k * n + p0 + tid];
-        pt_lo[tid][k] = p.lo[k * n + p0 + tid];
+        pt[tid][k] = p.hi[k * p.ld + p0 + tid];
+        pt_lo[tid][k] = p.lo[k * p.ld + p0 + tid];
       }
     }
     __syncthreads();

@@ -232,3 +232,24 @@ def test_bf16x3_fused_matches_two_kernel_path(orc, cfg, case):
         outs.append(o.double().cpu().numpy().reshape(-1, 5, m.mo_num))
         assert_within("bf16x3", outs[-1], ref, size, f"{case} fused={fused}")
     assert np.max(np.abs(outs[0] - outs[1])) <= 1e-6 * np.max(np.abs(outs[1]))
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32", "fp32", "fp64"])
+def test_host_output_ranges_match_device(cfg, mode):
+    """The host-memory MO call evaluates and copies back point ranges in turn
+    (19 200 points: two ranges); the result is bit-identical to the device
+    call, both when it evaluates the AOs itself and when it reuses them."""
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(2, walk_num=32)
+    _, dev = _run(m, mode)
+    c = qmckl.Context(mode)
+    c.set_molecule(m)
+    c.set_points(m.points)
+    pinned = torch.empty(m.point_num * 5 * m.mo_num, dtype=torch.float64 if mode == "fp64"
+                         else torch.float32, pin_memory=True)
+    first = c.mo_vgl(pinned.numpy()).copy()
+    again = c.mo_vgl(pinned.numpy())          # AO tensor reused from the first call
+    np.testing.assert_array_equal(first, dev)
+    np.testing.assert_array_equal(again, dev)
+    pageable = c.mo_vgl()                     # plain numpy output buffer
+    np.testing.assert_array_equal(pageable, dev)
