@@ -396,17 +396,54 @@ __device__ __forceinline__ void shell_zero_columns(AOStageSmem<T, kLanes>& sh, i
   if (lane == 0) sh.dirty[sl] = 0;
 }
 
+// Whether a shell centred at c with screening radius^2 r2max may reach a
+// point of the box [lo, hi]: the squared distance from c to the box bounds
+// r^2 from below for every point in it, so the shell is kept unless that
+// bound, less a relative and absolute margin for the rounding of both
+// sides, is at least r2max.
+template <typename T>
+__device__ __forceinline__ bool shell_reaches_box(const T (&lo)[3], const T (&hi)[3], T cx, T cy,
+                                                  T cz, T r2max) {
+  const T c[3] = {cx, cy, cz};
+  T d2 = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T e = max(T(0), max(lo[k] - c[k], c[k] - hi[k]));
+    d2 += e * e;
+  }
+  return d2 * T(0.9999) - T(1e-3) < r2max;
+}
+
+// Bounding box of the valid points held one per lane (whole warp).
+template <typename T>
+__device__ __forceinline__ void warp_box(bool pv, T x, T y, T z, T (&lo)[3], T (&hi)[3]) {
+  const T big = T(3.0e38);
+  lo[0] = pv ? x : big;
+  lo[1] = pv ? y : big;
+  lo[2] = pv ? z : big;
+  hi[0] = pv ? x : -big;
+  hi[1] = pv ? y : -big;
+  hi[2] = pv ? z : -big;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+}
+
 // Phase 0 of a tile, one warp: lane p < tp with p0 + p < n loads point p
-// into shared memory.  The tile's bounding box then culls shells whose
-// screening sphere (r^2 < r2max) cannot reach it: the squared distance from
-// R_A to the box bounds r^2 from below for every point, so a shell is kept
-// unless that bound, less a relative and absolute margin for the rounding of
-// both sides, is at least r2max.  Writes sh.reach, the list of shells to
-// visit (kept ones, and culled ones whose staging columns are dirty) in
-// `order` order, and resets the work counter.
+// into shared memory.  Shells that cannot reach the tile's bounding box
+// (shell_reaches_box) are culled, from `pre` when a pre-pass worked that
+// out (pre != ~0u) or from the box here.  Writes sh.reach, the list of
+// shells to visit (kept ones, and culled ones whose staging columns are
+// dirty) in `order` order, and resets the work counter.
 template <typename T, int kLanes>
 __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const PointsDev& pts,
-                                           int ns, int lane, int tp, int64_t p0) {
+                                           int ns, int lane, int tp, int64_t p0,
+                                           unsigned pre = ~0u) {
   const int64_t n = pts.n;
   const int64_t ip = p0 + lane;
   const bool pv = lane < tp && ip < n;
@@ -429,29 +466,14 @@ __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const Poi
     sh.pt[lane][1] = y;
     sh.pt[lane][2] = z;
   }
-  const T big = T(3.0e38);
-  T lo[3] = {pv ? x : big, pv ? y : big, pv ? z : big};
-  T hi[3] = {pv ? x : -big, pv ? y : -big, pv ? z : -big};
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-    }
+  unsigned reach = pre;
+  if (pre == ~0u) {
+    T lo[3], hi[3];
+    warp_box(pv, x, y, z, lo, hi);
+    const bool keep = lane < ns && shell_reaches_box(lo, hi, sh.nuc[lane][0], sh.nuc[lane][1],
+                                                     sh.nuc[lane][2], sh.r2max[lane]);
+    reach = __ballot_sync(0xffffffffu, keep);
   }
-  bool keep = false;
-  if (lane < ns) {
-    T d2 = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const T c = sh.nuc[lane][k];
-      const T e = max(T(0), max(lo[k] - c, c - hi[k]));
-      d2 += e * e;
-    }
-    keep = d2 * T(0.9999) - T(1e-3) < sh.r2max[lane];
-  }
-  const unsigned reach = __ballot_sync(0xffffffffu, keep);
   bool visit = false;
   int sl = 0;
   if (lane < ns) {

@@ -80,10 +80,20 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
 
   for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
     const int64_t p0 = ptile * TP;
+    unsigned pre = ~0u;
+    if constexpr (kTiled) {
+      if (out.reach) {  // the pre-pass's culling: unreached blocks cost no barrier
+        pre = out.reach[ptile * out.nchunk + q];
+        if (pre == 0u) {
+          if (tid == 0) out.mask[ptile * out.nchunk + q] = 0;
+          continue;
+        }
+      }
+    }
     __syncthreads();  // tables ready / previous tile's copy-out done with the stage
     // ---- phase 0 (warp 0): the tile's points, its bounding box and the
     // shells that may reach it
-    if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0);
+    if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0, pre);
     __syncthreads();
     const unsigned reach = sh.reach;
     if constexpr (kTiled) {
@@ -179,6 +189,41 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Pre-pass of the tiled layout: one warp per 25-point tile forms the tile's
+// bounding box (float hi parts of the coordinates) and, for every chunk,
+// the bit mask of the chunk's shells that may reach it (shell_reaches_box,
+// the test ao_vgl applies itself when no table is given).
+__global__ void __launch_bounds__(256)
+    tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles;
+       t += wstep) {
+    const int64_t ip = t * kTilePoints + lane;
+    const bool pv = lane < kTilePoints && ip < pts.n;
+    float x = 0.0f, y = 0.0f, z = 0.0f;
+    if (pv) {
+      x = pts.hi[ip];
+      y = pts.hi[pts.ld + ip];
+      z = pts.hi[2 * pts.ld + ip];
+    }
+    float lo[3], hi[3];
+    warp_box(pv, x, y, z, lo, hi);
+    for (int q = 0; q < b.nchunk; ++q) {
+      const int4 ch = b.chunk[q];
+      const int s = ch.x + lane;
+      bool keep = false;
+      if (s < ch.y) {
+        const int A = b.shell_nuc[s];
+        keep = shell_reaches_box(lo, hi, b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1],
+                                 b.nucl_hi[3 * A + 2], b.shell_r2_f[s]);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) reach[t * b.nchunk + q] = m;
+    }
+  }
+}
+
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
 cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
                       cudaStream_t s) {
@@ -190,6 +235,13 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   if (e != cudaSuccess) return e;
   const int64_t n_ptiles = (p.n + TP - 1) / TP;
   if (n_ptiles == 0 || b.nchunk == 0) return cudaSuccess;
+  if (kTiled && out.reach) {
+    const int64_t blocks = (n_ptiles + 7) / 8;
+    tile_reach_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(b, p, out.reach,
+                                                                                n_ptiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   int occ = 1, sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -73,6 +73,7 @@ qk_status build(qk_batch b, float* const* outs) {
     aop[i].b = v.b;
     aop[i].p = v.p;
     aop[i].out = v.ao;
+    aop[i].out.reach = nullptr;  // the multi-problem ao_vgl culls tiles itself
     const int bn = pick_bn(v.mo_num, b->bn_max);
     if (!tc_make_problem(b->mode, v.ao, v.kpad, v.c_hi, v.c_lo, v.kpad, v.mo_num, outs[i], bn,
                          5 * v.p.n, &tcp[i]))

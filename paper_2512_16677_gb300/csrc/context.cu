@@ -318,7 +318,8 @@ size_t ao_tensor_bytes(qk_context c, int mode) {
   const size_t ld = (size_t)kpad_of(c);
   if (tiled_mode(mode)) {
     const size_t rows = (size_t)ao_tiles(c) * kTileRows;
-    const size_t mask = align_up((size_t)ao_tiles(c) * c->chunks.size(), 256);
+    const size_t mask = align_up((size_t)ao_tiles(c) * c->chunks.size(), 256) +
+                        align_up((size_t)ao_tiles(c) * c->chunks.size() * sizeof(uint32_t), 256);
     if (mode == QK_BF16X3) return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256) + mask;
     return align_up(rows * ld * sizeof(float), 256) + mask;
   }
@@ -380,6 +381,7 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
       p += plane;
     }
     t.mask = p;
+    t.reach = (uint32_t*)(p + align_up((size_t)ao_tiles(c) * c->chunks.size(), 256));
   } else {
     t.rows = 5 * c->point_num;
   }
@@ -430,6 +432,7 @@ AOTensor ao_range(const AOTensor& t, int mode, int64_t p0, int64_t p1) {
     r0 = t0 * kTileRows;
     v.rows = (p1 - p0 + kTilePoints - 1) / kTilePoints * kTileRows;
     v.mask = t.mask + t0 * t.nchunk;
+    if (t.reach) v.reach = t.reach + t0 * t.nchunk;
   } else {
     r0 = 5 * p0;
     v.rows = 5 * (p1 - p0);

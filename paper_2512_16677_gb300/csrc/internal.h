@@ -83,6 +83,10 @@ struct AOTensor {
   bool tiled;
   uint8_t* mask;  // [tiles][nchunk] when tiled
   int nchunk;
+  // tiled, optional: [tiles][nchunk] bit s set when shell s of the chunk may
+  // reach a point of the tile (filled by a pre-pass in launch_ao_vgl; NULL:
+  // each ao_vgl tile works it out itself)
+  uint32_t* reach;
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
