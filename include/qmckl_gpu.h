@@ -102,6 +102,15 @@ qk_status qk_set_compute_mode(qk_context ctx, int32_t mode);
    workspace.  Both give the same arithmetic.  Other modes ignore it. */
 qk_status qk_set_fusion(qk_context ctx, int32_t enable);
 
+/* QK_BF16X3 / QK_TF32, device-memory calls: 1 (default) cuts the point tiles
+   of the block-sparse contraction from a spatial (Morton cell) order of the
+   points, so that a tile's points share their nonzero AOs and fewer
+   (tile, AO chunk) blocks are multiplied; outputs stay in the caller's
+   point order and every value is the same as with 0, which cuts tiles in
+   the caller's order.  This is a layout choice of this library, not a step
+   of the paper's method.  Other modes and the host-memory calls ignore it. */
+qk_status qk_set_spatial_order(qk_context ctx, int32_t enable);
+
 /* ------------------------------------------------------------- system --- */
 
 /* Nuclei (Sec. 3.1): charge [nucl_num] (kept for reference only) and

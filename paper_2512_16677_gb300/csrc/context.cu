@@ -56,10 +56,12 @@ struct qk_context_s {
   double eps = 0.0;  // > 0: explicit cutoff instead of bits
   int mode = QK_FP64;
   bool fused = false;  // split-bf16: AO blocks built inside the contraction kernel
+  bool spatial = true;  // tensor-core modes: tiles cut from a spatial point order
   uint64_t basis_version = 1;
   // nuclei
   int64_t nucl_num = 0;
   std::vector<double> nucl_charge, nucl_coord;
+  float nbox_lo[3] = {0, 0, 0}, nbox_hi[3] = {0, 0, 0};  // nuclear box with a margin
   // basis, primitives sorted by ascending exponent inside each shell
   bool has_basis = false;
   int64_t shell_num = 0, prim_num = 0, ao_num = 0;
@@ -88,6 +90,11 @@ struct qk_context_s {
   uint64_t date = 0;
   DevBuf d_points, d_raw;
   PointsDev pdev{};
+  // spatial order of the current points (tensor-core modes)
+  DevBuf d_sort;
+  int32_t* perm = nullptr;
+  PointsDev psort{};
+  uint64_t sort_date = ~0ull;
   // workspace and memo
   void* ws_user = nullptr;
   size_t ws_user_bytes = 0;
@@ -97,6 +104,7 @@ struct qk_context_s {
   unsigned char* fused_lists = nullptr;    // its live-chunk lists
   int ao_mode = -1;
   void* ao_ws = nullptr;
+  bool ao_sorted = false;
   // host-output staging, device error word, backward scratch
   DevBuf d_out;
   cudaStream_t copy_stream = nullptr;   // device -> host copies of output ranges
@@ -390,23 +398,45 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
 
 // The AO tensor's place in the workspace; *valid says whether it already
 // holds the current date/mode/basis.
-qk_status ao_workspace(qk_context c, AOTensor* out, bool* valid) {
+qk_status ao_workspace(qk_context c, AOTensor* out, bool* valid, bool sorted) {
   qk_status st = ensure_tables(c);
   if (st) return st;
   void* ws = nullptr;
   st = workspace(c, ao_tensor_bytes(c, c->mode), &ws);
   if (st) return st;
   *out = ao_view(c, ws, c->mode);
+  if (sorted) out->perm = c->perm;
   *valid = c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
-           c->ao_version == c->basis_version;
+           c->ao_version == c->basis_version && c->ao_sorted == sorted;
   return QK_SUCCESS;
 }
 
-void mark_ao(qk_context c, const AOTensor& ao) {
+void mark_ao(qk_context c, const AOTensor& ao, bool sorted) {
   c->ao_date = c->date;
   c->ao_mode = c->mode;
   c->ao_ws = ao.a;
   c->ao_version = c->basis_version;
+  c->ao_sorted = sorted;
+}
+
+// Whether the device path cuts its tiles from a spatial point order.
+bool use_spatial(qk_context c) {
+  return tiled_mode(c->mode) && c->spatial && c->point_num >= 2 * kTilePoints;
+}
+
+// The spatial order of the current points (once per time stamp).
+qk_status ensure_spatial(qk_context c) {
+  if (c->sort_date == c->date) return QK_SUCCESS;
+  cudaError_t e = c->d_sort.ensure(spatial_order_bytes(c->point_num));
+  if (e != cudaSuccess) return cuda_fail(c, e, "spatial order scratch");
+  {
+    TimedLaunch t(c, 2);
+    e = launch_spatial_order(c->pdev, c->nbox_lo, c->nbox_hi, c->d_sort.p, &c->perm, &c->psort,
+                             c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "spatial order");
+  c->sort_date = c->date;
+  return QK_SUCCESS;
 }
 
 // Points [p0, p1) and the matching rows of the AO tensor (p0 a multiple of
@@ -444,16 +474,21 @@ AOTensor ao_range(const AOTensor& t, int mode, int64_t p0, int64_t p1) {
 
 // Make the AO tensor of the current date/mode valid in the workspace.
 qk_status provide_ao(qk_context c, AOTensor* out) {
+  const bool sorted = use_spatial(c);
+  if (sorted) {
+    qk_status st = ensure_spatial(c);
+    if (st) return st;
+  }
   bool valid = false;
-  qk_status st = ao_workspace(c, out, &valid);
+  qk_status st = ao_workspace(c, out, &valid, sorted);
   if (st || valid) return st;
   cudaError_t e;
   {
     TimedLaunch t(c, 0);
-    e = launch_ao_vgl(c->bdev, c->pdev, c->mode, *out, c->stream);
+    e = launch_ao_vgl(c->bdev, sorted ? c->psort : c->pdev, c->mode, *out, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
-  mark_ao(c, *out);
+  mark_ao(c, *out, sorted);
   return QK_SUCCESS;
 }
 
@@ -597,6 +632,16 @@ qk_status qk_set_nucleus(qk_context c, int64_t nucl_num, const double* charge,
   c->nucl_num = nucl_num;
   c->nucl_charge.assign(charge, charge + nucl_num);
   c->nucl_coord.assign(coord, coord + 3 * nucl_num);
+  // region the spatial point order resolves: the nuclei plus 4 bohr
+  for (int k = 0; k < 3; ++k) {
+    double lo = coord[k], hi = coord[k];
+    for (int64_t a = 1; a < nucl_num; ++a) {
+      lo = std::min(lo, coord[3 * a + k]);
+      hi = std::max(hi, coord[3 * a + k]);
+    }
+    c->nbox_lo[k] = (float)(lo - 4.0);
+    c->nbox_hi[k] = (float)(hi + 4.0);
+  }
   invalidate(c);
   return QK_SUCCESS;
 }
@@ -801,6 +846,12 @@ qk_status qk_set_fusion(qk_context c, int32_t enable) {
   return QK_SUCCESS;
 }
 
+qk_status qk_set_spatial_order(qk_context c, int32_t enable) {
+  CHECK_CTX(c);
+  c->spatial = enable != 0;
+  return QK_SUCCESS;
+}
+
 qk_status qk_set_workspace(qk_context c, void* dev, size_t bytes) {
   CHECK_CTX(c);
   if (dev && ((uintptr_t)dev % 256 != 0))
@@ -941,7 +992,7 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
   if (st) return st;
   AOTensor ao{};
   bool have_ao = false;
-  st = ao_workspace(c, &ao, &have_ao);
+  st = ao_workspace(c, &ao, &have_ao, false);  // ranges are contiguous in the caller's order
   if (st) return st;
   if (!c->copy_stream) {
     e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
@@ -976,7 +1027,7 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
                           cudaMemcpyDeviceToHost, c->copy_stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl range copy");
   }
-  if (!have_ao) mark_ao(c, ao);
+  if (!have_ao) mark_ao(c, ao, false);
   e = cudaStreamSynchronize(c->copy_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "get_mo_vgl copy");
   return qk_synchronize(c);
@@ -1223,6 +1274,7 @@ void context_mark_ao_valid(qk_context c) {
   c->ao_mode = c->mode;
   c->ao_ws = c->ws_user ? c->ws_user : c->ws_own.p;
   c->ao_version = c->basis_version;
+  c->ao_sorted = false;  // multi-molecule launches keep the caller's order
 }
 
 }  // namespace qk

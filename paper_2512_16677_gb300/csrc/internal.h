@@ -87,6 +87,10 @@ struct AOTensor {
   // reach a point of the tile (filled by a pre-pass in launch_ao_vgl; NULL:
   // each ao_vgl tile works it out itself)
   uint32_t* reach;
+  // tiled, optional: point slot s of the tiles holds the caller's point
+  // perm[s] (spatial order); the contraction writes its rows there.  NULL:
+  // slot s is point s.
+  const int32_t* perm;
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
@@ -162,6 +166,7 @@ struct TcProblem {
   CUtensorMap a, a_lo, b, b_lo;  // AO hi / lo, C hi / lo (lo = hi for TF32)
   float* D;                      // [M][N] output
   const uint8_t* mask;           // tiled AO tensor: [tiles][nchunk] live blocks (else NULL)
+  const int32_t* perm;           // tiled AO tensor: point of each slot (NULL: identity)
   int64_t M, N;                  // output rows (5 * points) and columns
   int num_kb;                    // K blocks
   int bn;                        // MMA N (multiple of 16, <= the launch's bn_max)
@@ -188,6 +193,14 @@ struct AOProblem {
 // hi/lo planes, else FP32.
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s);
+
+// Spatial order of the points (sort.cu): a permutation perm (slot -> point)
+// and the point arrays in that order, in `scratch` of spatial_order_bytes(n)
+// bytes; box_lo/box_hi bound the region the order resolves.
+size_t spatial_order_bytes(int64_t n);
+cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
+                                 const float box_hi[3], void* scratch, int32_t** perm,
+                                 PointsDev* sorted, cudaStream_t s);
 
 // Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
 // points, reduced into d_dR [nucl][3] (FP64).

@@ -62,6 +62,7 @@ struct TileInfo {
   const CUtensorMap* b_lo;
   float* D;
   const uint8_t* kmask;  // live 64-column chunks of this M tile (NULL: all live)
+  const int32_t* perm;   // tiled: point of each slot (NULL: slot = point)
   int64_t M, N;          // output rows and columns
   int m0, n0;            // AO-tensor row and output column of the tile
   int num_kb;
@@ -83,6 +84,7 @@ struct SingleSched {
   CUtensorMap a, a_lo, b, b_lo;
   float* D;
   const uint8_t* mask;  // [m tiles][nchunk] when tiled
+  const int32_t* perm;
   int64_t M, N, total;
   int num_kb, n_tiles, nchunk;
   bool tiled;
@@ -96,6 +98,7 @@ struct SingleSched {
     x.b_lo = &b_lo;
     x.D = D;
     x.kmask = tiled ? mask + mt * nchunk : nullptr;
+    x.perm = perm;
     x.M = M;
     x.N = N;
     x.m0 = (int)(mt * kBM);
@@ -124,6 +127,7 @@ struct BatchSched {
     x.b_lo = &p.b_lo;
     x.D = p.D;
     x.kmask = p.mask ? p.mask + (int64_t)it.y * p.nchunk : nullptr;
+    x.perm = p.perm;
     x.M = p.M;
     x.N = p.N;
     x.m0 = it.y * kBM;
@@ -312,6 +316,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(x.D) & 15) == 0;
       const int64_t row0 = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) : (int64_t)x.m0;
       const int rows_here = x.tiled ? 5 * kTilePoints : kBM;  // tile rows that exist in D
+      // the four output rows this lane writes (slot rows mapped to the
+      // caller's points when the tiles hold a spatial order); -1: none
+      int64_t orow[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int loc = warp * 32 + 8 * i + rq;
+        const int64_t lin = row0 + loc;
+        orow[i] = (loc < rows_here && lin < x.M)
+                      ? (x.perm ? 5 * (int64_t)x.perm[lin / 5] + lin % 5 : lin)
+                      : -1;
+      }
       float(*stg)[kEpiPitch] = epi[warp];
 #pragma unroll 1
       for (int c = 0; c < x.bn; c += 16) {
@@ -332,9 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = 8 * i + rq;
-          const int loc = warp * 32 + r;
-          const int64_t row = row0 + loc;
-          if (loc < rows_here && row < x.M) {
+          const int64_t row = orow[i];
+          if (row >= 0) {
             const float4 w =
                 reinterpret_cast<const float4*>(&stg[r][0])[(lane & 3) ^ ((r >> 1) & 3)];
             float* dst = x.D + row * N + col;
@@ -419,6 +433,7 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   }
   sc.D = out;
   sc.mask = ao.tiled ? ao.mask : nullptr;
+  sc.perm = ao.tiled ? ao.perm : nullptr;
   sc.tiled = ao.tiled;
   sc.nchunk = ao.nchunk;
   sc.M = ao.tiled ? out_rows : M;
@@ -517,6 +532,7 @@ bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, 
   }
   p->D = out;
   p->mask = ao.tiled ? ao.mask : nullptr;
+  p->perm = ao.tiled ? ao.perm : nullptr;
   p->nchunk = ao.nchunk;
   p->M = out_rows;
   p->N = N;

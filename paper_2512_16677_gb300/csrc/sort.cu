@@ -1,0 +1,206 @@
+// sort.cu -- spatial order of the points for the block-sparse tensor-core
+// path.
+//
+// Tiles of 25 consecutive points decide which (tile, AO chunk) blocks the
+// contraction multiplies (Sec. 3.2's sparse AO matrix at tile granularity).
+// Points that are close in space share their nonzero AOs, so tiles cut from
+// a spatial order carry fewer live blocks than tiles cut from the caller's
+// order.  The order here: cells of a 32 x 32 x 32 grid over the nuclear
+// bounding box (points outside are clamped to the border cells) visited in
+// Morton (Z-curve) order, points of one cell by ascending index: a stable
+// radix sort of the cell keys, so the permutation depends on the
+// coordinates only.  The permutation changes which points share a tile, never a point's
+// own values: each AO value and each output row is computed from that point
+// alone.
+#include "internal.h"
+
+namespace qk {
+namespace {
+
+constexpr int kCellBits = 5;  // per axis
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  // bit i of v -> bit 3 i
+  uint32_t r = 0;
+#pragma unroll
+  for (int i = 0; i < kCellBits; ++i) r |= ((v >> i) & 1u) << (3 * i);
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cell_of(float x, float lo, float inv) {
+  const float f = (x - lo) * inv;
+  const int c = f <= 0.0f ? 0 : (f >= (float)((1 << kCellBits) - 1) ? (1 << kCellBits) - 1 : (int)f);
+  return (uint32_t)c;
+}
+
+__global__ void cell_key_kernel(PointsDev p, float3 lo, float3 inv, uint32_t* key) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t cx = cell_of(p.hi[i], lo.x, inv.x);
+    const uint32_t cy = cell_of(p.hi[p.ld + i], lo.y, inv.y);
+    const uint32_t cz = cell_of(p.hi[2 * p.ld + i], lo.z, inv.z);
+    key[i] = spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+  }
+}
+
+// Stable LSD radix sort of the cell keys, 8-bit digits.  Block b owns keys
+// [b * kSortBlock, (b + 1) * kSortBlock).  A pass: per-block digit counts,
+// an exclusive scan of the counts in digit-major order (so the offset of
+// (digit d, block b) counts every key of a smaller digit and every key of
+// digit d in an earlier block), then a scatter in which a key's place among
+// the equal digits of its block follows warp order and lane order.  Equal
+// keys therefore keep their index order and the result is unique.
+constexpr int kSortBlock = 1024;
+constexpr int kDigitBits = 8;
+constexpr int kBins = 1 << kDigitBits;
+
+__global__ void __launch_bounds__(kSortBlock)
+    digit_count_kernel(const uint32_t* key, int64_t n, int shift, int nblocks, uint32_t* hist) {
+  __shared__ uint32_t cnt[kBins];
+  for (int d = threadIdx.x; d < kBins; d += blockDim.x) cnt[d] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kSortBlock + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[(key[i] >> shift) & (kBins - 1)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kBins; d += blockDim.x)
+    hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+// Exclusive scan of m counts in place (one block).
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t* v, int64_t m) {
+  __shared__ uint32_t part[kScanThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (m + kScanThreads - 1) / kScanThreads;
+  const int64_t b = t * per;
+  const int64_t e = b + per < m ? b + per : m;
+  uint32_t s = 0;
+  for (int64_t k = b; k < e; ++k) s += v[k];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {  // inclusive Hillis-Steele scan
+    const uint32_t x = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  uint32_t run = t > 0 ? part[t - 1] : 0u;
+  for (int64_t k = b; k < e; ++k) {
+    const uint32_t c = v[k];
+    v[k] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(kSortBlock)
+    digit_scatter_kernel(const uint32_t* key_in, const int32_t* val_in, uint32_t* key_out,
+                         int32_t* val_out, int64_t n, int shift, int nblocks,
+                         const uint32_t* offset) {
+  constexpr int kWarps = kSortBlock / 32;
+  __shared__ uint32_t wcnt[kWarps][kBins];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int k = t; k < kWarps * kBins; k += kSortBlock) (&wcnt[0][0])[k] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kSortBlock + t;
+  const bool live = i < n;
+  const uint32_t k = live ? key_in[i] : 0u;
+  // keys past the end get a digit of their own so that they match no live key
+  const int d = live ? (int)((k >> shift) & (kBins - 1)) : kBins;
+  const unsigned peers = __match_any_sync(0xffffffffu, d);
+  const int wrank = __popc(peers & ((1u << lane) - 1u));
+  if (live && wrank == 0) wcnt[warp][d] = __popc(peers);
+  __syncthreads();
+  if (!live) return;
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+  const uint32_t pos = offset[(int64_t)d * nblocks + blockIdx.x] + before + wrank;
+  key_out[pos] = k;
+  val_out[pos] = val_in ? val_in[i] : (int32_t)i;
+}
+
+// Sorted copy of the point arrays: slot s holds point perm[s].
+__global__ void gather_points_kernel(PointsDev p, const int32_t* perm, double* x, double* y,
+                                     double* z, float* hi, float* lo) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[s];
+    x[s] = p.x[i];
+    y[s] = p.y[i];
+    z[s] = p.z[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      hi[k * p.n + s] = p.hi[k * p.ld + i];
+      lo[k * p.n + s] = p.lo[k * p.ld + i];
+    }
+  }
+}
+
+unsigned grid_for(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+int sort_blocks(int64_t n) { return (int)((n + kSortBlock - 1) / kSortBlock); }
+
+}  // namespace
+
+size_t spatial_order_bytes(int64_t n) {
+  const auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  return al(sizeof(uint32_t) * (size_t)kBins * sort_blocks(n)) + 2 * al(sizeof(uint32_t) * n) +
+         2 * al(sizeof(int32_t) * n) + al(3 * sizeof(double) * n) + al(6 * sizeof(float) * n);
+}
+
+cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
+                                 const float box_hi[3], void* scratch, int32_t** perm_out,
+                                 PointsDev* sorted, cudaStream_t s) {
+  const auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const int64_t n = p.n;
+  const int nb = sort_blocks(n);
+  unsigned char* w = (unsigned char*)scratch;
+  uint32_t* hist = (uint32_t*)w;
+  w += al(sizeof(uint32_t) * (size_t)kBins * nb);
+  uint32_t* key[2] = {(uint32_t*)w, nullptr};
+  w += al(sizeof(uint32_t) * n);
+  key[1] = (uint32_t*)w;
+  w += al(sizeof(uint32_t) * n);
+  int32_t* val[2] = {(int32_t*)w, nullptr};
+  w += al(sizeof(int32_t) * n);
+  val[1] = (int32_t*)w;
+  w += al(sizeof(int32_t) * n);
+  double* x = (double*)w;
+  w += al(3 * sizeof(double) * n);
+  float* hi = (float*)w;
+  sorted->n = n;
+  sorted->x = x;
+  sorted->y = x + n;
+  sorted->z = x + 2 * n;
+  sorted->hi = hi;
+  sorted->lo = hi + 3 * n;
+  sorted->ld = n;
+  constexpr int kKeyBits = 3 * kCellBits;
+  constexpr int kPasses = (kKeyBits + kDigitBits - 1) / kDigitBits;
+  *perm_out = val[kPasses & 1];  // where the last pass leaves the values
+  if (n == 0) return cudaSuccess;
+  float3 lo, inv;
+  const float span = (float)(1 << kCellBits);
+  lo.x = box_lo[0];
+  lo.y = box_lo[1];
+  lo.z = box_lo[2];
+  inv.x = span / fmaxf(box_hi[0] - box_lo[0], 1e-3f);
+  inv.y = span / fmaxf(box_hi[1] - box_lo[1], 1e-3f);
+  inv.z = span / fmaxf(box_hi[2] - box_lo[2], 1e-3f);
+  cell_key_kernel<<<grid_for(n), 256, 0, s>>>(p, lo, inv, key[0]);
+  for (int pass = 0; pass < kPasses; ++pass) {
+    const int in = pass & 1, out = in ^ 1;
+    digit_count_kernel<<<nb, kSortBlock, 0, s>>>(key[in], n, kDigitBits * pass, nb, hist);
+    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(hist, (int64_t)kBins * nb);
+    digit_scatter_kernel<<<nb, kSortBlock, 0, s>>>(key[in], pass == 0 ? nullptr : val[in],
+                                                   key[out], val[out], n, kDigitBits * pass, nb,
+                                                   hist);
+  }
+  gather_points_kernel<<<grid_for(n), 256, 0, s>>>(p, *perm_out, x, x + n, x + 2 * n, hi,
+                                                   hi + 3 * n);
+  return cudaGetLastError();
+}
+
+}  // namespace qk

@@ -45,6 +45,7 @@ SIGNATURES = {
     "qk_set_cutoff": [_P, _D],
     "qk_set_compute_mode": [_P, _I32],
     "qk_set_fusion": [_P, _I32],
+    "qk_set_spatial_order": [_P, _I32],
     "qk_set_nucleus": [_P, _I64, _P, _P],
     "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
     "qk_set_mo_coefficient": [_P, _I64, _P],
@@ -190,6 +191,11 @@ class Context:
         """split-bf16: build AO blocks inside the contraction kernel (default
         off: ao_vgl and the contraction run as two kernels)."""
         self._check(self.lib.qk_set_fusion(self.h, 1 if enable else 0), "set_fusion")
+
+    def set_spatial_order(self, enable: bool):
+        """tensor-core modes: cut point tiles from a spatial order (default on)."""
+        self._check(self.lib.qk_set_spatial_order(self.h, 1 if enable else 0),
+                    "set_spatial_order")
 
     def set_compute_mode(self, mode: str):
         self._check(self.lib.qk_set_compute_mode(self.h, MODES[mode]), "set_compute_mode")

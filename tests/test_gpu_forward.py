@@ -253,3 +253,27 @@ def test_host_output_ranges_match_device(cfg, mode):
     np.testing.assert_array_equal(again, dev)
     pageable = c.mo_vgl()                     # plain numpy output buffer
     np.testing.assert_array_equal(pageable, dev)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_spatial_order_same_values_fewer_blocks(orc, cfg, mode):
+    """Tiles cut from the spatial order (default) and from the caller's order
+    give the same values; on points handed over in an order with no spatial
+    locality the spatial order multiplies far fewer blocks."""
+    m = cfg(2, walk_num=8)                       # 4 800 points
+    rng = np.random.default_rng(11)
+    mm = m.with_points(m.points[rng.permutation(m.point_num)])
+    outs, live = [], []
+    for spatial in (True, False):
+        c = _ctx(mm, mode)
+        c.set_spatial_order(spatial)
+        o = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        c.synchronize()
+        outs.append(o.double().cpu().numpy().reshape(-1, 5, mm.mo_num))
+        live.append(c.block_stats()[0])
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert live[0] < 0.6 * live[1], live
+    idx = np.sort(rng.choice(mm.point_num, 64, replace=False))
+    ref, size = orc.mo_vgl(mm, points=mm.points[idx])
+    assert_within(mode, outs[0][idx], ref, size, "spatial order")
