@@ -48,9 +48,14 @@ struct TcShape {
   static constexpr uint32_t A_BYTES = kBM * kRowBytes;
   static constexpr uint32_t B_BYTES = BN_MAX * kRowBytes;  // room for the widest B tile
   static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + B_BYTES);
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 4);
+  // accumulator buffers: as many BN_MAX-column regions (32-column aligned)
+  // as the 512 TMEM columns hold, at most 4, so that the epilogue may trail
+  // the MMAs by up to NBUF - 1 tiles
+  static constexpr uint32_t ACC = (BN_MAX + 31) / 32 * 32;
+  static constexpr int NBUF = 512 / ACC > 4 ? 4 : (int)(512 / ACC);
+  static constexpr uint32_t TMEM_ALLOC = tmem_cols<NBUF * ACC>();
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2 * NBUF);
   static_assert(SMEM + kEpiBytes + 64 <= kSmemLimit, "shared memory budget");
-  static constexpr uint32_t TMEM_COLS = tmem_cols<BN_MAX>();  // per accumulator buffer (two)
   static_assert(BN_MAX % 16 == 0 && BN_MAX >= 16 && BN_MAX <= 256, "MMA N: 16..256, step 16");
 };
 
@@ -141,8 +146,9 @@ struct BatchSched {
 
 // Persistent: CTA c walks tiles t = c, c + gridDim.x, ...  The shared-memory
 // ring runs on a k-block counter that continues across tiles; the
-// accumulator alternates between two TMEM buffers so that the epilogue of
-// tile i overlaps the MMAs of tile i + 1.
+// accumulator cycles through NBUF TMEM buffers so that the epilogue of tile
+// i overlaps the MMAs of the next tiles (tiles of few live K blocks take
+// less MMA time than their epilogue, so a lag of more than one tile pays).
 //   full[s]   TMA bytes of stage s landed        (producer -> MMA)
 //   empty[s]  MMAs reading stage s finished      (MMA -> producer, commit)
 //   tfull[b]  accumulator b complete             (MMA -> epilogue, commit)
@@ -152,7 +158,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mo_tc_kernel(const __grid_constant__ Sched sched, int* err_flag) {
   using S = TcShape<MODE, BN_MAX, STAGES>;
   using TR = TcTraits<MODE>;
-  constexpr uint32_t ACC = S::TMEM_COLS;  // columns of one accumulator buffer
+  constexpr uint32_t ACC = S::ACC;  // columns of one accumulator buffer
+  constexpr uint32_t NBUF = S::NBUF;
 
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + NBUF + b); };
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < (int)NBUF; ++b) {
       mbar_init(tfull_bar(b), 1);
       mbar_init(tempty_bar(b), 4);  // one arrival per epilogue warp
     }
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(2 * ACC)
+                 "r"(S::TMEM_ALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -239,8 +246,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
       const TileInfo x = sched.tile(t);
       const uint32_t idesc = make_idesc(TR::kFmt, kBM, x.bn);
-      const uint32_t b = i & 1u;
-      if (!mbar_wait(tempty_bar(b), ((i >> 1) & 1u) ^ 1u, abort_v)) {
+      const uint32_t b = i % NBUF;
+      if (!mbar_wait(tempty_bar(b), ((i / NBUF) & 1u) ^ 1u, abort_v)) {
         flag_error(err_flag, abort_v, 2);
         break;
       }
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         // aborted: wait for the MMAs in flight before TMEM can be freed
         const long long t0 = clock64();
-        while (!mbar_try_wait(tfull_bar(b), (i >> 1) & 1u) && clock64() - t0 < kWaitCycles) {
+        while (!mbar_try_wait(tfull_bar(b), (i / NBUF) & 1u) && clock64() - t0 < kWaitCycles) {
         }
       }
     }
@@ -290,10 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ epilogue
     uint32_t i = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-      const uint32_t b = i & 1u;
+      const uint32_t b = i % NBUF;
       const long long t0 = clock64();
       bool ok = true;
-      while (!mbar_try_wait(tfull_bar(b), (i >> 1) & 1u)) {
+      while (!mbar_try_wait(tfull_bar(b), (i / NBUF) & 1u)) {
         if (clock64() - t0 > kWaitCycles) {
           ok = false;
           break;
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 5) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * ACC)
+                 "r"(S::TMEM_ALLOC)
                  : "memory");
   }
 }
@@ -400,7 +407,7 @@ cudaError_t persistent_grid(Kern kern, size_t smem, uint32_t tmem_cols, int64_t 
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
-  if (occ < 1 || occ * 2 * (int)tmem_cols > 512) return cudaErrorInvalidConfiguration;
+  if (occ < 1 || occ * (int)tmem_cols > 512) return cudaErrorInvalidConfiguration;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -443,7 +450,7 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   sc.total = ((M + kBM - 1) / kBM) * sc.n_tiles;
   auto kern = mo_tc_kernel<MODE, BN, ST, SingleSched<BN>>;
   int64_t grid = 0;
-  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_COLS, sc.total, &grid);
+  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_ALLOC, sc.total, &grid);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
   return cudaGetLastError();
@@ -476,7 +483,7 @@ cudaError_t launch_batch_bn(const TcProblem* probs, const int4* items, int64_t n
   BatchSched sc{probs, items, n_items};
   auto kern = mo_tc_kernel<MODE, BN_MAX, ST, BatchSched>;
   int64_t grid = 0;
-  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_COLS, n_items, &grid);
+  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_ALLOC, n_items, &grid);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
   return cudaGetLastError();
