@@ -192,9 +192,22 @@ __global__ void __launch_bounds__(kThreads)
 // Pre-pass of the tiled layout: one warp per 25-point tile forms the tile's
 // bounding box (float hi parts of the coordinates) and, for every chunk,
 // the bit mask of the chunk's shells that may reach it (shell_reaches_box,
-// the test ao_vgl applies itself when no table is given).
-__global__ void __launch_bounds__(256)
-    tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles) {
+// the test ao_vgl applies itself when no table is given).  Each block first
+// copies the shells' centres and radii^2 into shared memory (when they fit).
+constexpr int kReachThreads = 256;
+constexpr int kReachSmemShells = 8192;  // 128 KB of float4
+
+__global__ void __launch_bounds__(kReachThreads)
+    tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles, int staged) {
+  extern __shared__ float4 shell_tab[];  // [shell] (X, Y, Z, r2max), float
+  if (staged) {
+    for (int s = threadIdx.x; s < b.shell_num; s += blockDim.x) {
+      const int A = b.shell_nuc[s];
+      shell_tab[s] = make_float4(b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1], b.nucl_hi[3 * A + 2],
+                                 b.shell_r2_f[s]);
+    }
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles;
@@ -214,14 +227,39 @@ __global__ void __launch_bounds__(256)
       const int s = ch.x + lane;
       bool keep = false;
       if (s < ch.y) {
-        const int A = b.shell_nuc[s];
-        keep = shell_reaches_box(lo, hi, b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1],
-                                 b.nucl_hi[3 * A + 2], b.shell_r2_f[s]);
+        float4 c;
+        if (staged) {
+          c = shell_tab[s];
+        } else {
+          const int A = b.shell_nuc[s];
+          c = make_float4(b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1], b.nucl_hi[3 * A + 2],
+                          b.shell_r2_f[s]);
+        }
+        keep = shell_reaches_box(lo, hi, c.x, c.y, c.z, c.w);
       }
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) reach[t * b.nchunk + q] = m;
     }
   }
+}
+
+cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* reach,
+                              int64_t tiles, cudaStream_t s) {
+  const int staged = b.shell_num <= kReachSmemShells ? 1 : 0;
+  const size_t smem = staged ? sizeof(float4) * (size_t)b.shell_num : 0;
+  cudaError_t e = cudaFuncSetAttribute(tile_reach_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float4) * kReachSmemShells));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // a few blocks per SM, each staging the table once and walking tiles
+  const int64_t want = (tiles + 7) / 8;
+  const int64_t blocks = want < 4 * (int64_t)sms ? want : 4 * (int64_t)sms;
+  tile_reach_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s>>>(
+      b, p, reach, tiles, staged);
+  return cudaGetLastError();
 }
 
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
@@ -236,10 +274,7 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   const int64_t n_ptiles = (p.n + TP - 1) / TP;
   if (n_ptiles == 0 || b.nchunk == 0) return cudaSuccess;
   if (kTiled && out.reach) {
-    const int64_t blocks = (n_ptiles + 7) / 8;
-    tile_reach_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(b, p, out.reach,
-                                                                                n_ptiles);
-    e = cudaGetLastError();
+    e = launch_tile_reach(b, p, out.reach, n_ptiles, s);
     if (e != cudaSuccess) return e;
   }
   int occ = 1, sms = 1, dev = 0;

@@ -44,23 +44,28 @@ __global__ void cell_key_kernel(PointsDev p, float3 lo, float3 inv, uint32_t* ke
 }
 
 // Stable LSD radix sort of the cell keys, 8-bit digits.  Block b owns keys
-// [b * kSortBlock, (b + 1) * kSortBlock).  A pass: per-block digit counts,
-// an exclusive scan of the counts in digit-major order (so the offset of
-// (digit d, block b) counts every key of a smaller digit and every key of
-// digit d in an earlier block), then a scatter in which a key's place among
-// the equal digits of its block follows warp order and lane order.  Equal
-// keys therefore keep their index order and the result is unique.
-constexpr int kSortBlock = 1024;
+// [b * kSortBlock, (b + 1) * kSortBlock), taken in kRounds rounds of
+// kSortThreads.  A pass: per-block digit counts, an exclusive scan of the
+// counts in digit-major order (so the offset of (digit d, block b) counts
+// every key of a smaller digit and every key of digit d in an earlier
+// block), then a scatter in which a key's place among the equal digits of
+// its block follows round, warp and lane order.  Equal keys therefore keep
+// their index order and the result is unique.
+constexpr int kSortThreads = 1024;
+constexpr int kRounds = 4;
+constexpr int kSortBlock = kSortThreads * kRounds;
 constexpr int kDigitBits = 8;
 constexpr int kBins = 1 << kDigitBits;
 
-__global__ void __launch_bounds__(kSortBlock)
+__global__ void __launch_bounds__(kSortThreads)
     digit_count_kernel(const uint32_t* key, int64_t n, int shift, int nblocks, uint32_t* hist) {
   __shared__ uint32_t cnt[kBins];
   for (int d = threadIdx.x; d < kBins; d += blockDim.x) cnt[d] = 0;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kSortBlock + threadIdx.x;
-  if (i < n) atomicAdd(&cnt[(key[i] >> shift) & (kBins - 1)], 1u);
+  for (int r = 0; r < kRounds; ++r) {
+    const int64_t i = (int64_t)blockIdx.x * kSortBlock + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & (kBins - 1)], 1u);
+  }
   __syncthreads();
   for (int d = threadIdx.x; d < kBins; d += blockDim.x)
     hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
@@ -92,30 +97,43 @@ __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t* 
   }
 }
 
-__global__ void __launch_bounds__(kSortBlock)
+__global__ void __launch_bounds__(kSortThreads)
     digit_scatter_kernel(const uint32_t* key_in, const int32_t* val_in, uint32_t* key_out,
                          int32_t* val_out, int64_t n, int shift, int nblocks,
                          const uint32_t* offset) {
-  constexpr int kWarps = kSortBlock / 32;
+  constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t wcnt[kWarps][kBins];
+  __shared__ uint32_t run[kBins];  // keys of each digit placed by earlier rounds
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int k = t; k < kWarps * kBins; k += kSortBlock) (&wcnt[0][0])[k] = 0;
-  __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kSortBlock + t;
-  const bool live = i < n;
-  const uint32_t k = live ? key_in[i] : 0u;
-  // keys past the end get a digit of their own so that they match no live key
-  const int d = live ? (int)((k >> shift) & (kBins - 1)) : kBins;
-  const unsigned peers = __match_any_sync(0xffffffffu, d);
-  const int wrank = __popc(peers & ((1u << lane) - 1u));
-  if (live && wrank == 0) wcnt[warp][d] = __popc(peers);
-  __syncthreads();
-  if (!live) return;
-  uint32_t before = 0;
-  for (int w = 0; w < warp; ++w) before += wcnt[w][d];
-  const uint32_t pos = offset[(int64_t)d * nblocks + blockIdx.x] + before + wrank;
-  key_out[pos] = k;
-  val_out[pos] = val_in ? val_in[i] : (int32_t)i;
+  for (int d = t; d < kBins; d += kSortThreads) run[d] = 0;
+  for (int r = 0; r < kRounds; ++r) {
+    for (int k = t; k < kWarps * kBins; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kSortBlock + r * kSortThreads + t;
+    const bool live = i < n;
+    const uint32_t k = live ? key_in[i] : 0u;
+    // keys past the end get a digit of their own so that they match no live key
+    const int d = live ? (int)((k >> shift) & (kBins - 1)) : kBins;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int wrank = __popc(peers & ((1u << lane) - 1u));
+    if (live && wrank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (live) {
+      uint32_t before = run[d];
+      for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+      const uint32_t pos = offset[(int64_t)d * nblocks + blockIdx.x] + before + wrank;
+      key_out[pos] = k;
+      val_out[pos] = val_in ? val_in[i] : (int32_t)i;
+    }
+    __syncthreads();
+    for (int dd = t; dd < kBins; dd += kSortThreads) {
+      uint32_t s = 0;
+      for (int w = 0; w < kWarps; ++w) s += wcnt[w][dd];
+      run[dd] += s;
+    }
+    // the next round's clearing of wcnt starts after this barrier
+    __syncthreads();
+  }
 }
 
 // Sorted copy of the point arrays: slot s holds point perm[s].
@@ -192,9 +210,9 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
   cell_key_kernel<<<grid_for(n), 256, 0, s>>>(p, lo, inv, key[0]);
   for (int pass = 0; pass < kPasses; ++pass) {
     const int in = pass & 1, out = in ^ 1;
-    digit_count_kernel<<<nb, kSortBlock, 0, s>>>(key[in], n, kDigitBits * pass, nb, hist);
+    digit_count_kernel<<<nb, kSortThreads, 0, s>>>(key[in], n, kDigitBits * pass, nb, hist);
     exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(hist, (int64_t)kBins * nb);
-    digit_scatter_kernel<<<nb, kSortBlock, 0, s>>>(key[in], pass == 0 ? nullptr : val[in],
+    digit_scatter_kernel<<<nb, kSortThreads, 0, s>>>(key[in], pass == 0 ? nullptr : val[in],
                                                    key[out], val[out], n, kDigitBits * pass, nb,
                                                    hist);
   }
