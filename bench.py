@@ -311,6 +311,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extra:
         res["large"] = measure_large(args, world)
         res["adjoint"] = measure_adjoint(args)
+        res["cusp"] = measure_cusp(args)
 
     # end to end through the host-memory C-ABI calls: H2D of the coordinates
     # and D2H of the whole MO vgl tensor inside the timed region
@@ -469,6 +470,44 @@ def measure_adjoint(args):
         ms = _time_steps(fwd_bwd, steps, warmup=1)
         res[mode] = {"ms_per_fwd_bwd": ms,
                      "evals_per_s": mol.elec_num * mol.walk_num * mol.mo_num / (ms * 1e-3)}
+    return res
+
+
+def measure_cusp(args):
+    """Organic chain step (bf16x3, 600 e- x 256 walkers) with the MO cusp
+    correction of Sec. 3.3 at radii 0.5/sqrt(Z) bohr, against the same step
+    without it; FP64 set-up of the coefficients timed once."""
+    import numpy as np
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+    mol = synth.make_config(2)
+    rc = synth.cusp_radii(mol)
+    coord = torch.from_numpy(mol.coord).cuda()
+    pts = mol.points
+    inside = 0
+    for A in range(mol.nucl_num):
+        d2 = ((pts - mol.nucl_coord[A]) ** 2).sum(1)
+        inside += int((d2 < rc[A] ** 2).sum())
+    res = {"workload": "organic150 step with the Sec. 3.3 cusp correction, radii 0.5/sqrt(Z) bohr",
+           "point_sphere_pairs": inside}
+    for on in (False, True):
+        ctx = qmckl.Context("bf16x3")
+        ctx.set_molecule(mol)
+        ctx.set_points_device(coord)
+        if on:
+            ctx.set_mo_cusp(rc)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.cusp_coefficients_device()   # FP64 set-up of the coefficients
+            torch.cuda.synchronize()
+            res["setup_ms"] = (time.perf_counter() - t0) * 1e3
+        o = ctx.mo_vgl_device()
+
+        def step():
+            ctx.set_points_device(coord)
+            ctx.mo_vgl_device(o)
+        res["ms_per_step_with" if on else "ms_per_step_without"] = _time_steps(step, 10, warmup=2)
+    res["overhead_ms"] = res["ms_per_step_with"] - res["ms_per_step_without"]
     return res
 
 

@@ -111,6 +111,31 @@ qk_status qk_set_fusion(qk_context ctx, int32_t enable);
    of the paper's method.  Other modes and the host-memory calls ignore it. */
 qk_status qk_set_spatial_order(qk_context ctx, int32_t enable);
 
+/* MO cusp correction (Sec. 3.3).  rc [nucl_num]: sphere radius in bohr
+   around each nucleus (>= 0, 0 = no correction there); NULL switches the
+   correction off.  Inside the sphere of A every MO output becomes
+   phi - phi^{s_A} + f_0 + f_1 rho + f_2 rho^2 + f_3 rho^3 (rho = |r - R_A|,
+   phi^{s_A} the part of the MO carried by the s AOs on A), with value
+   gradient and Laplacian of that expression.  The f_k (per nucleus and MO)
+   make value, first and second radial derivative continuous at rc and
+   satisfy Kato's cusp f_1 = -Z_A (phi(R_A) - phi^{s_A}(R_A) + f_0); the
+   paper names the first two conditions and the cusp, the second-derivative
+   one is this library's reading.  Z_A is the charge given to
+   qk_set_nucleus.  The coefficients are set up in FP64 on the device and
+   the correction is added in FP64 to the output of every MO call.  A point
+   exactly on a nucleus gets an infinite Laplacian.  Copies rc; changing the
+   number of nuclei switches the correction off.  Non-finite or negative
+   radii are QK_ERR_INVALID_ARG; more than 32 s shells on one nucleus gives
+   QK_ERR_NOT_IMPLEMENTED at the next evaluation, as do
+   qk_mo_vgl_backward_device and multi-molecule batches on a context with
+   the correction on. */
+qk_status qk_set_mo_cusp(qk_context ctx, const double* rc);
+
+/* The coefficients f [nucl_num][mo_num][4] (device memory, FP64) of the
+   current cusp correction; size >= 4 * nucl_num * mo_num.  QK_ERR_NOT_PROVIDED
+   without radii. */
+qk_status qk_get_mo_cusp_coefficients_device(qk_context ctx, double* df, int64_t size);
+
 /* ------------------------------------------------------------- system --- */
 
 /* Nuclei (Sec. 3.1): charge [nucl_num] (kept for reference only) and

@@ -184,8 +184,3 @@ def mo_vgl_cusp(mol, rc, points=None, C: Optional[np.ndarray] = None,
     base, size = oracle.mo_vgl(mol, points=pts, screened=screened, C=C)
     add, asize = correction(mol, rc, pts, C=C, screened=screened)
     return base + add, size + asize
-
-
-def default_radii(mol) -> np.ndarray:
-    """A cusp radius per nucleus for tests and measurement: 0.5 / sqrt(Z) bohr."""
-    return 0.5 / np.sqrt(np.asarray(mol.nucl_charge, dtype=np.float64))

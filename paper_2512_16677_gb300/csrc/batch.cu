@@ -68,6 +68,9 @@ qk_status build(qk_batch b, float* const* outs) {
   std::vector<double> ao_cost, tc_cost;
   for (int i = 0; i < n; ++i) {
     ForwardViews v;
+    if (context_cusp_on(b->ctxs[i]))
+      return bfail(b, QK_ERR_NOT_IMPLEMENTED,
+                   "context " + std::to_string(i) + " has the cusp correction on");
     qk_status st = context_forward_views(b->ctxs[i], &v);
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
     aop[i].b = v.b;
@@ -134,6 +137,9 @@ qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig)
   sig->push_back((uintptr_t)b->bn_max);
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     ForwardViews v;
+    if (context_cusp_on(b->ctxs[i]))
+      return bfail(b, QK_ERR_NOT_IMPLEMENTED,
+                   "context " + std::to_string(i) + " has the cusp correction on");
     qk_status st = context_forward_views(b->ctxs[i], &v);
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
     sig->push_back((uintptr_t)v.ao.a);
@@ -161,6 +167,9 @@ qk_status prepare(qk_batch b, float* const* outs, const int64_t* sizes) {
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     if (!outs[i]) return bfail(b, QK_ERR_NULL_POINTER, "output " + std::to_string(i) + " is NULL");
     ForwardViews v;
+    if (context_cusp_on(b->ctxs[i]))
+      return bfail(b, QK_ERR_NOT_IMPLEMENTED,
+                   "context " + std::to_string(i) + " has the cusp correction on");
     qk_status st = context_forward_views(b->ctxs[i], &v);
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
     if (v.mode != b->mode)

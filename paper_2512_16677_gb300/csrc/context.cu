@@ -108,6 +108,17 @@ struct qk_context_s {
   // host-output staging, device error word, backward scratch
   DevBuf d_out;
   cudaStream_t copy_stream = nullptr;   // device -> host copies of output ranges
+  // MO cusp correction (Sec. 3.3)
+  bool cusp_on = false;
+  bool cusp_dirty = true;
+  std::vector<double> cusp_rc;
+  uint64_t cusp_basis = 0, cusp_mo = 0;
+  DevBuf d_cusp;
+  DevBuf d_cusp_list;  // points inside a sphere, per MO call
+  CuspDev cudev{};
+  double* cusp_f64 = nullptr;
+  float* cusp_f32 = nullptr;
+  uint64_t mo_version = 0;  // bumped by every upload of C
   std::vector<cudaEvent_t> range_done;  // one per output range of a host call
   DevBuf d_flag;
   DevBuf bwd_own;
@@ -309,6 +320,89 @@ qk_status ensure_mo(qk_context c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "MO coefficient upload");
   c->mo_dirty = false;
+  c->mo_version++;
+  return QK_SUCCESS;
+}
+
+// The cusp coefficients of the current basis, C and radii (FP64 set-up on
+// the device, once per change).
+qk_status ensure_cusp(qk_context c) {
+  if (!c->cusp_on) return QK_SUCCESS;
+  qk_status st = ensure_tables(c);
+  if (st) return st;
+  st = ensure_mo(c);
+  if (st) return st;
+  if (!c->cusp_dirty && c->cusp_basis == c->basis_version && c->cusp_mo == c->mo_version)
+    return QK_SUCCESS;
+  const int64_t nn = c->nucl_num, nm = c->mo_num, na = c->ao_num;
+  std::vector<int> start(nn + 1, 0), list;
+  for (int64_t A = 0; A < nn; ++A) {
+    start[A] = (int)list.size();
+    for (int64_t s = 0; s < c->shell_num; ++s)
+      if (c->shell_nuc[s] == A && c->shell_l[s] == 0) list.push_back((int)s);
+    if ((int)list.size() - start[A] > 32)
+      return fail(c, QK_ERR_NOT_IMPLEMENTED, "cusp correction: more than 32 s shells on a nucleus");
+  }
+  start[nn] = (int)list.size();
+  if (list.empty()) list.push_back(0);
+  const size_t b_rc = align_up(sizeof(double) * nn, 256);
+  const size_t b_rf = align_up(sizeof(float) * nn, 256);
+  const size_t b_st = align_up(sizeof(int) * (nn + 1), 256);
+  const size_t b_ls = align_up(sizeof(int) * list.size(), 256);
+  const size_t b_x = align_up(sizeof(double) * nn * na, 256);
+  const size_t b_q = align_up(sizeof(double) * nn * nm, 256);
+  const size_t b_f = align_up(sizeof(double) * nn * nm * 4, 256);
+  const size_t b_g = align_up(sizeof(float) * nn * nm * 4, 256);
+  cudaError_t e = c->d_cusp.ensure(2 * b_rc + b_st + b_ls + b_x + b_q + b_f + b_g + b_rf);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cusp tables");
+  unsigned char* p = (unsigned char*)c->d_cusp.p;
+  double* rc = (double*)p;
+  double* charge = (double*)(p + b_rc);
+  int* dstart = (int*)(p + 2 * b_rc);
+  int* dlist = (int*)(p + 2 * b_rc + b_st);
+  double* X = (double*)(p + 2 * b_rc + b_st + b_ls);
+  double* Q = (double*)((unsigned char*)X + b_x);
+  c->cusp_f64 = (double*)((unsigned char*)Q + b_q);
+  c->cusp_f32 = (float*)((unsigned char*)c->cusp_f64 + b_f);
+  c->cudev.rc_f = (float*)((unsigned char*)c->cusp_f32 + b_g);
+  c->cudev.rc = rc;
+  c->cudev.charge = charge;
+  c->cudev.s_start = dstart;
+  c->cudev.s_shell = dlist;
+  e = cudaMemcpyAsync(rc, c->cusp_rc.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(charge, c->nucl_charge.data(), sizeof(double) * nn,
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dstart, start.data(), sizeof(int) * (nn + 1), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dlist, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = launch_cusp_setup(c->bdev, c->cudev, nm, c->c64, X, Q, c->cusp_f64, c->cusp_f32,
+                          c->stream);
+  // the host vectors above must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cusp set-up");
+  c->cusp_dirty = false;
+  c->cusp_basis = c->basis_version;
+  c->cusp_mo = c->mo_version;
+  return QK_SUCCESS;
+}
+
+// Adds the cusp correction to MO rows D of the points p (caller's order).
+qk_status apply_cusp(qk_context c, const PointsDev& p, void* D) {
+  if (!c->cusp_on) return QK_SUCCESS;
+  cudaError_t e = c->d_cusp_list.ensure(cusp_list_bytes(p.n));
+  if (e != cudaSuccess) return cuda_fail(c, e, "cusp point list");
+  {
+    TimedLaunch t(c, 2);
+    e = launch_cusp_apply(c->bdev, c->cudev, p, c->mo_num, c->c64, c->c32, c->ldc, c->cusp_f64,
+                          c->cusp_f32, c->mode == QK_FP64, D, c->d_cusp_list.p, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cusp correction");
   return QK_SUCCESS;
 }
 
@@ -628,7 +722,9 @@ qk_status qk_set_nucleus(qk_context c, int64_t nucl_num, const double* charge,
   if (nucl_num != c->nucl_num) {
     c->has_basis = false;
     c->has_mo = false;
+    c->cusp_on = false;  // radii were given per nucleus of the old system
   }
+  c->cusp_dirty = true;
   c->nucl_num = nucl_num;
   c->nucl_charge.assign(charge, charge + nucl_num);
   c->nucl_coord.assign(coord, coord + 3 * nucl_num);
@@ -846,6 +942,39 @@ qk_status qk_set_fusion(qk_context c, int32_t enable) {
   return QK_SUCCESS;
 }
 
+qk_status qk_set_mo_cusp(qk_context c, const double* rc) {
+  CHECK_CTX(c);
+  if (!rc) {
+    c->cusp_on = false;
+    return QK_SUCCESS;
+  }
+  if (c->nucl_num < 1) return fail(c, QK_ERR_NOT_PROVIDED, "set the nuclei before cusp radii");
+  for (int64_t A = 0; A < c->nucl_num; ++A)
+    if (!(std::isfinite(rc[A]) && rc[A] >= 0.0))
+      return fail(c, QK_ERR_INVALID_ARG, "cusp radii must be finite and >= 0");
+  c->cusp_rc.assign(rc, rc + c->nucl_num);
+  c->cusp_on = true;
+  c->cusp_dirty = true;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_mo_cusp_coefficients_device(qk_context c, double* df, int64_t size) {
+  CHECK_CTX(c);
+  if (!df) return fail(c, QK_ERR_NULL_POINTER, "df is NULL");
+  if (!c->cusp_on) return fail(c, QK_ERR_NOT_PROVIDED, "no cusp radii set");
+  qk_status st = require(c, true);
+  if (st) return st;
+  if (size < c->nucl_num * c->mo_num * 4)
+    return fail(c, QK_ERR_BAD_SIZE, "df holds %lld elements, %lld needed", (long long)size,
+                (long long)(c->nucl_num * c->mo_num * 4));
+  st = ensure_cusp(c);
+  if (st) return st;
+  cudaError_t e = cudaMemcpyAsync(df, c->cusp_f64, sizeof(double) * c->nucl_num * c->mo_num * 4,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cusp coefficients");
+  return QK_SUCCESS;
+}
+
 qk_status qk_set_spatial_order(qk_context c, int32_t enable) {
   CHECK_CTX(c);
   c->spatial = enable != 0;
@@ -934,6 +1063,8 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
                 (long long)(M * N));
   st = ensure_mo(c);
   if (st) return st;
+  st = ensure_cusp(c);
+  if (st) return st;
   if (use_fused(c)) {
     void* ws = nullptr;
     const size_t fb = fused_workspace_bytes(c->point_num, (int)c->chunks.size());
@@ -959,12 +1090,14 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
     c->fused_date = c->date;
     c->fused_lists = lp;
     c->ao_date = ~0ull;  // no AO tensor was written
-    return QK_SUCCESS;
+    return apply_cusp(c, c->pdev, dout);
   }
   AOTensor ao{};
   st = provide_ao(c, &ao);
   if (st) return st;
-  return contract(c, ao, M, dout);
+  st = contract(c, ao, M, dout);
+  if (st) return st;
+  return apply_cusp(c, c->pdev, dout);
 }
 
 qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
@@ -989,6 +1122,8 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
   // Point ranges in turn: range r's output goes to the host on a second
   // stream while range r + 1 is evaluated (the copy link is the slower part).
   st = ensure_mo(c);
+  if (st) return st;
+  st = ensure_cusp(c);
   if (st) return st;
   AOTensor ao{};
   bool have_ao = false;
@@ -1019,6 +1154,8 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
     }
     const size_t off = (size_t)5 * p0 * N * es;
     st = contract(c, av, 5 * (p1 - p0), dbase + off);
+    if (st) return st;
+    st = apply_cusp(c, points_range(c->pdev, p0, p1), dbase + off);
     if (st) return st;
     e = cudaEventRecord(c->range_done[r], c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->range_done[r], 0);
@@ -1169,6 +1306,8 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
   if (!dW) return fail(c, QK_ERR_NULL_POINTER, "dW is NULL");
   qk_status st = require(c, true);
   if (st) return st;
+  if (c->cusp_on)
+    return fail(c, QK_ERR_NOT_IMPLEMENTED, "the adjoint does not cover the cusp correction");
   const int64_t rows = 5 * c->point_num, N = c->mo_num, K = c->ao_num;
   if (size < rows * N)
     return fail(c, QK_ERR_BAD_SIZE, "dW holds %lld elements, %lld needed", (long long)size,
@@ -1268,6 +1407,8 @@ qk_status context_forward_views(qk_context c, ForwardViews* v) {
   v->mode = c->mode;
   return QK_SUCCESS;
 }
+
+bool context_cusp_on(qk_context c) { return c->cusp_on; }
 
 void context_mark_ao_valid(qk_context c) {
   c->ao_date = c->date;

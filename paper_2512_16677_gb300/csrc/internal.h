@@ -202,6 +202,28 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
                                  const float box_hi[3], void* scratch, int32_t** perm,
                                  PointsDev* sorted, cudaStream_t s);
 
+// MO cusp correction (cusp.cu, Sec. 3.3).
+struct CuspDev {
+  const double* rc;      // [nucl] sphere radius in bohr (0: no correction at A)
+  const float* rc_f;     // [nucl] float(rc)
+  const double* charge;  // [nucl] Z_A
+  const int* s_start;    // [nucl + 1] range of each nucleus in s_shell
+  const int* s_shell;    // the s shells of each nucleus
+};
+// Coefficients f [nucl][mo][4] (FP64 and FP32) of the current basis, C
+// ([mo][ao] FP64) and radii; X [nucl][ao] and Q [nucl][mo] are scratch.
+cudaError_t launch_cusp_setup(const BasisDev& b, const CuspDev& cu, int64_t mo_num,
+                              const double* C, double* X, double* Q, double* f64, float* f32,
+                              cudaStream_t s);
+// Adds the correction to D [points][5][mo] (FP64 or FP32) at the points.
+// FP64 output: C64 [mo][ao] and f64; FP32 output: C32 [mo][ldc32] and f32.
+// scratch: cusp_list_bytes(p.n) bytes of device memory.
+size_t cusp_list_bytes(int64_t n);
+cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const PointsDev& p,
+                              int64_t mo_num, const double* C64, const float* C32, int64_t ldc32,
+                              const double* f64, const float* f32, bool f64_out, void* D,
+                              void* scratch, cudaStream_t s);
+
 // Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
 // points, reduced into d_dR [nucl][3] (FP64).
 cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
@@ -233,6 +255,8 @@ struct ForwardViews {
   int mode;
 };
 qk_status context_forward_views(qk_context c, ForwardViews* v);
+// Whether the context applies the MO cusp correction.
+bool context_cusp_on(qk_context c);
 // Record that the AO tensor of the current time stamp is now in the workspace.
 void context_mark_ao_valid(qk_context c);
 qk_status context_fail(qk_context c, qk_status code, const char* msg);

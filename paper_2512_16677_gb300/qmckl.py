@@ -46,6 +46,8 @@ SIGNATURES = {
     "qk_set_compute_mode": [_P, _I32],
     "qk_set_fusion": [_P, _I32],
     "qk_set_spatial_order": [_P, _I32],
+    "qk_set_mo_cusp": [_P, _P],
+    "qk_get_mo_cusp_coefficients_device": [_P, _P, _I64],
     "qk_set_nucleus": [_P, _I64, _P, _P],
     "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
     "qk_set_mo_coefficient": [_P, _I64, _P],
@@ -191,6 +193,25 @@ class Context:
         """split-bf16: build AO blocks inside the contraction kernel (default
         off: ao_vgl and the contraction run as two kernels)."""
         self._check(self.lib.qk_set_fusion(self.h, 1 if enable else 0), "set_fusion")
+
+    def set_mo_cusp(self, rc):
+        """Cusp radii [nucl] in bohr (None switches the correction off)."""
+        if rc is None:
+            self._check(self.lib.qk_set_mo_cusp(self.h, None), "set_mo_cusp")
+            return
+        a = _f64(rc)
+        self._check(self.lib.qk_set_mo_cusp(self.h, _ptr(a)), "set_mo_cusp")
+
+    def cusp_coefficients_device(self):
+        """f [nucl][mo][4] (FP64 CUDA tensor) of the current cusp correction."""
+        import torch
+        self._bind_stream()
+        n = self.lib
+        nn, nm = self.nucl_num, self.mo_num
+        out = torch.empty((nn, nm, 4), dtype=torch.float64, device="cuda")
+        self._check(n.qk_get_mo_cusp_coefficients_device(self.h, out.data_ptr(), out.numel()),
+                    "get_mo_cusp_coefficients_device")
+        return out
 
     def set_spatial_order(self, enable: bool):
         """tensor-core modes: cut point tiles from a spatial order (default on)."""

@@ -346,6 +346,12 @@ def make_config(idx: int, walk_num: Optional[int] = None):
     return m
 
 
+def cusp_radii(mol: Molecule) -> np.ndarray:
+    """Cusp-correction radii for tests and measurement: 0.5 / sqrt(Z) bohr
+    per nucleus (0.5 for H, 0.20 for C, 0.18 for O)."""
+    return 0.5 / np.sqrt(np.asarray(mol.nucl_charge, dtype=np.float64))
+
+
 def random_weights(rng: np.random.Generator, point_num: int, mo_num: int) -> np.ndarray:
     """Loss weights W [point][5][mo] for the adjoint workload, U(-1, 1)."""
     return rng.uniform(-1.0, 1.0, size=(point_num, 5, mo_num))

@@ -87,7 +87,7 @@ def pin_kato(mol, rc, f):
 def water():
     orc.build()
     m = synth.make_config(1, walk_num=2)
-    rc = cusp.default_radii(m)
+    rc = synth.cusp_radii(m)
     return m, rc, cusp.coefficients(m, rc)
 
 
@@ -140,7 +140,7 @@ def test_chain_molecule_pins():
     """A molecule with several s shells per nucleus and other centres nearby."""
     orc.build()
     m = synth.make_config(3, walk_num=1)
-    rc = cusp.default_radii(m)
+    rc = synth.cusp_radii(m)
     f = cusp.coefficients(m, rc)
     rng = np.random.default_rng(4)
     pin_continuity(m, rc, f, rng, nuclei=[0, 1, 2])
