@@ -312,6 +312,7 @@ def run_ours(args, rank, world, local_rank):
         res["large"] = measure_large(args, world)
         res["adjoint"] = measure_adjoint(args)
         res["cusp"] = measure_cusp(args)
+        res["density"] = measure_density(args)
 
     # end to end through the host-memory C-ABI calls: H2D of the coordinates
     # and D2H of the whole MO vgl tensor inside the timed region
@@ -508,6 +509,38 @@ def measure_cusp(args):
             ctx.mo_vgl_device(o)
         res["ms_per_step_with" if on else "ms_per_step_without"] = _time_steps(step, 10, warmup=2)
     res["overhead_ms"] = res["ms_per_step_with"] - res["ms_per_step_without"]
+    return res
+
+
+def measure_density(args):
+    """Density on a 100^3 grid (Sec. 5.4) for the 104-nucleus stand-in with
+    1090 AOs and 218 doubly occupied MOs: one density evaluation per step,
+    the grid built on the device."""
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+    mol = synth.make_config(6)
+    o, h, n = synth.density_grid(mol, n=100)
+    ax = [torch.arange(n[k], dtype=torch.float64, device="cuda") * float(h[k]) + float(o[k])
+          for k in range(3)]
+    gx, gy, gz = torch.meshgrid(*ax, indexing="ij")
+    grid = torch.stack([gx, gy, gz], -1).reshape(-1, 3).contiguous()
+    w = synth.occupations(mol)
+    res = {"workload": "100^3 grid, 104 nuclei, 1090 AOs, 218 doubly occupied MOs, eps=1e-10",
+           "points": int(grid.shape[0])}
+    for mode, steps in (("bf16x3", 10), ("tf32", 10), ("fp32", 3), ("fp64", 1)):
+        ctx = qmckl.Context(mode)
+        ctx.set_molecule(mol)
+        ctx.set_points_device(grid)
+        rho = ctx.density_device(w)
+        ctx.set_timing(True)
+
+        def step():
+            ctx.density_device(w, rho)
+        ms = _time_steps(step, steps, warmup=1)
+        kms, kn = ctx.get_timing()
+        res[mode] = {"ms_per_grid": ms, "points_per_s": grid.shape[0] / (ms * 1e-3),
+                     "ao_values_ms": kms[0] / max(kn[0], 1), "contraction_ms": kms[1] / max(kn[1], 1)}
+        del ctx
     return res
 
 

@@ -131,6 +131,19 @@ qk_status qk_set_spatial_order(qk_context ctx, int32_t enable);
    the correction on. */
 qk_status qk_set_mo_cusp(qk_context ctx, const double* rc);
 
+/* Electron density on the current points (Sec. 5.4, e.g. a grid):
+   rho(p) = sum_i w[i] phi_i(p)^2 with the MO values of Eqs. 5-7 (no
+   derivatives are formed).  w [mo_num] (host, copied): occupation weights,
+   e.g. 2 for doubly occupied MOs; MOs with w = 0 cost nothing.  drho
+   [point_num] on the device, FP64 in QK_FP64 mode and FP32 otherwise;
+   size >= point_num.  The tensor-core modes contract values-only AO tiles
+   of 128 points and reduce sum w phi^2 in the contraction's epilogue; the
+   FP64 / FP32 modes go through the SIMT GEMM.  Runs on the context's stream
+   after a short synchronisation (the weights' upload); uses the AO
+   workspace, so the next MO call evaluates its AOs again.  The cusp
+   correction does not apply.  Non-finite weights are QK_ERR_INVALID_ARG. */
+qk_status qk_get_density_device(qk_context ctx, const double* w, void* drho, int64_t size);
+
 /* The coefficients f [nucl_num][mo_num][4] (device memory, FP64) of the
    current cusp correction; size >= 4 * nucl_num * mo_num.  QK_ERR_NOT_PROVIDED
    without radii. */

@@ -238,6 +238,8 @@ __host__ __device__ constexpr int cart_exp(int l, int j, int axis) {
 
 template <typename T, int kLanes>
 struct AOStageSmem {
+  using value_type = T;
+  static constexpr int kRows = 5 * kLanes;  // staging rows
   T nuc[kMaxShellsChunk][3];     // FP64: R_A; FP32: float(R_A)
   T nuc_lo[kMaxShellsChunk][3];  // FP32: residual R_A - float(R_A)
   T r2max[kMaxShellsChunk];
@@ -260,11 +262,13 @@ struct AOStageSmem {
 };
 
 // Chunk tables into shared memory and zeros into the staging columns past
-// the chunk's last AO (nothing else writes them).
-template <typename T, int kLanes>
-__device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q,
-                                                  AOStageSmem<T, kLanes>& sh,
-                                                  int tid, int nthreads) {
+// the chunk's last AO (nothing else writes them).  Smem: a shared-memory
+// layout with the table fields of AOStageSmem, a staging tile of
+// Smem::kRows rows and a dirty flag per shell.
+template <class Smem>
+__device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q, Smem& sh, int tid,
+                                                  int nthreads) {
+  using T = typename Smem::value_type;
   using A = Arith<T>;
   const int4 ch = b.chunk[q];
   const int ns = ch.y - ch.x;
@@ -311,7 +315,7 @@ __device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q,
   }
   for (int i = tid; i < na; i += nthreads) sh.M[i] = A::aofac(b, ch.z + i);
   const int npad = kChunkAO - na;
-  for (int i = tid; i < 5 * kLanes * npad; i += nthreads)
+  for (int i = tid; i < Smem::kRows * npad; i += nthreads)
     sh.stage[i / npad][na + i % npad] = T(0);
 }
 

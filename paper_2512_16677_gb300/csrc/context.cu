@@ -115,6 +115,7 @@ struct qk_context_s {
   uint64_t cusp_basis = 0, cusp_mo = 0;
   DevBuf d_cusp;
   DevBuf d_cusp_list;  // points inside a sphere, per MO call
+  DevBuf d_dens;       // density: occupied-MO tables, weights, partial sums
   CuspDev cudev{};
   double* cusp_f64 = nullptr;
   float* cusp_f32 = nullptr;
@@ -972,6 +973,125 @@ qk_status qk_get_mo_cusp_coefficients_device(qk_context c, double* df, int64_t s
   cudaError_t e = cudaMemcpyAsync(df, c->cusp_f64, sizeof(double) * c->nucl_num * c->mo_num * 4,
                                   cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cusp coefficients");
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_density_device(qk_context c, const double* w, void* drho, int64_t size) {
+  CHECK_CTX(c);
+  if (!w || !drho) return fail(c, QK_ERR_NULL_POINTER, "w/drho is NULL");
+  qk_status st = require(c, true);
+  if (st) return st;
+  const int64_t P = c->point_num;
+  if (size < P)
+    return fail(c, QK_ERR_BAD_SIZE, "drho holds %lld elements, %lld needed", (long long)size,
+                (long long)P);
+  std::vector<int> occ;
+  std::vector<double> w64;
+  std::vector<float> w32;
+  for (int64_t i = 0; i < c->mo_num; ++i) {
+    if (!std::isfinite(w[i])) return fail(c, QK_ERR_INVALID_ARG, "non-finite occupation");
+    if (w[i] != 0.0) {
+      occ.push_back((int)i);
+      w64.push_back(w[i]);
+      w32.push_back((float)w[i]);
+    }
+  }
+  st = ensure_tables(c);
+  if (st) return st;
+  st = ensure_mo(c);
+  if (st) return st;
+  const int mode = c->mode;
+  const bool f64 = mode == QK_FP64;
+  const bool tiled = tiled_mode(mode);
+  const bool split = mode == QK_BF16X3;
+  cudaError_t e;
+  const int64_t no = (int64_t)occ.size();
+  if (no == 0) {
+    e = cudaMemsetAsync(drho, 0, (f64 ? sizeof(double) : sizeof(float)) * P, c->stream);
+    return e == cudaSuccess ? QK_SUCCESS : cuda_fail(c, e, "density");
+  }
+  const int64_t kp = c->kpad;
+  const TcConfig cfg = tc_default_config(mode, no);
+  const int64_t n_tiles_n = (no + cfg.bn - 1) / cfg.bn;
+  const size_t ce = f64 ? sizeof(double) : (split ? sizeof(__nv_bfloat16) : sizeof(float));
+  const size_t b_idx = align_up(sizeof(int) * no, 256);
+  const size_t b_w64 = align_up(sizeof(double) * no, 256);
+  const size_t b_w32 = align_up(sizeof(float) * no, 256);
+  const size_t b_c = align_up(ce * no * kp, 256);
+  const size_t b_extra = tiled ? align_up(sizeof(float) * n_tiles_n * P, 256)
+                               : align_up((f64 ? sizeof(double) : sizeof(float)) * P * no, 256);
+  e = c->d_dens.ensure(b_idx + b_w64 + b_w32 + (split ? 2 : 1) * b_c + b_extra);
+  if (e != cudaSuccess) return cuda_fail(c, e, "density scratch");
+  unsigned char* q = (unsigned char*)c->d_dens.p;
+  int* didx = (int*)q;
+  double* dw64 = (double*)(q + b_idx);
+  float* dw32 = (float*)(q + b_idx + b_w64);
+  unsigned char* c0 = q + b_idx + b_w64 + b_w32;
+  unsigned char* c1 = c0 + b_c;
+  unsigned char* extra = c0 + (split ? 2 : 1) * b_c;
+  e = cudaMemcpyAsync(didx, occ.data(), sizeof(int) * no, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dw64, w64.data(), sizeof(double) * no, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dw32, w32.data(), sizeof(float) * no, cudaMemcpyHostToDevice, c->stream);
+  // the host vectors above must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  // the occupied MOs' rows of the chunked C planes
+  if (e == cudaSuccess) {
+    if (split) {
+      e = launch_gather_rows(c->c_hi, kp, ce, didx, no, c0, c->stream);
+      if (e == cudaSuccess) e = launch_gather_rows(c->c_lo, kp, ce, didx, no, c1, c->stream);
+    } else {
+      e = launch_gather_rows(f64 ? (const void*)c->c64p : (const void*)c->c32p, kp, ce, didx, no,
+                             c0, c->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "density tables");
+  // the values-only AO tensor, in the workspace (the vgl AO tensor's memo is lost)
+  const int64_t tp = ao_value_tile_points();
+  const int64_t tiles = (P + tp - 1) / tp;
+  AOTensor av{};
+  av.ld = kp;
+  av.chunked = true;
+  av.nchunk = (int)c->chunks.size();
+  av.comps = 1;
+  av.tiled = tiled;
+  av.rows = tiled ? tiles * kTileRows : P;
+  const size_t ae = f64 ? sizeof(double) : (split ? sizeof(__nv_bfloat16) : sizeof(float));
+  const size_t plane = align_up((size_t)av.rows * kp * ae, 256);
+  const size_t need = (split ? 2 : 1) * plane +
+                      (tiled ? align_up((size_t)tiles * c->chunks.size(), 256) : 0);
+  void* ws = nullptr;
+  st = workspace(c, need, &ws);
+  if (st) return st;
+  c->ao_date = ~0ull;
+  av.a = ws;
+  if (split) av.a_lo = (unsigned char*)ws + plane;
+  if (tiled) av.mask = (uint8_t*)ws + (split ? 2 : 1) * plane;
+  {
+    TimedLaunch t(c, 0);
+    e = launch_ao_value(c->bdev, c->pdev, mode, av, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "density ao values");
+  {
+    TimedLaunch t(c, 1);
+    if (tiled) {
+      float* part = (float*)extra;
+      e = launch_mo_tc(mode, av, kp, c0, split ? (const void*)c1 : nullptr, kp, no, nullptr, cfg,
+                       (int*)c->d_flag.p, c->stream, P, dw32, part);
+      if (e == cudaSuccess)
+        e = launch_density_reduce(part, (int)n_tiles_n, P, (float*)drho, c->stream);
+    } else if (f64) {
+      e = launch_gemm_f64(P, no, kp, (const double*)av.a, kp, 1, (const double*)c0, kp, 1,
+                          (double*)extra, no, 1, c->stream);
+      if (e == cudaSuccess) e = launch_density_from_mo(true, extra, P, no, dw64, drho, c->stream);
+    } else {
+      e = launch_gemm_f32(P, no, kp, (const float*)av.a, kp, 1, (const float*)c0, kp, 1,
+                          (float*)extra, no, 1, c->stream);
+      if (e == cudaSuccess) e = launch_density_from_mo(false, extra, P, no, dw64, drho, c->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "density contraction");
   return QK_SUCCESS;
 }
 

@@ -91,6 +91,9 @@ struct AOTensor {
   // perm[s] (spatial order); the contraction writes its rows there.  NULL:
   // slot s is point s.
   const int32_t* perm;
+  // tiled: 0 or 5 -> the vgl layout (25 points x 5 components per 128-row
+  // tile); 1 -> values only (128 points per tile, one row each)
+  int comps;
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
@@ -152,10 +155,14 @@ struct TcConfig {
   int stages;  // shared-memory pipeline depth
 };
 // out_rows: rows of D (5 * points); -1 = ao.rows (dense layout).
+// Density epilogue (wdens != NULL): instead of D, each output row r gets
+// sum_n wdens[n] D[r][n]^2 over the columns of its N tile, written to
+// rho_part[N tile][r]; out is then unused.
 cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
                          const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
                          const TcConfig& cfg, int* err_flag, cudaStream_t s,
-                         int64_t out_rows = -1);
+                         int64_t out_rows = -1, const float* wdens = nullptr,
+                         float* rho_part = nullptr);
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
 
@@ -193,6 +200,21 @@ struct AOProblem {
 // hi/lo planes, else FP32.
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s);
+
+// Values-only AO tensor (ao_value.cu): tiled (128 points per tile, bf16
+// hi/lo or FP32) for the tensor-core modes, dense rows = points (FP32 or
+// FP64) otherwise; chunked columns in both.
+int ao_value_tile_points();
+cudaError_t launch_ao_value(const BasisDev& b, const PointsDev& p, int out_mode,
+                            const AOTensor& out, cudaStream_t s);
+// Density helpers (density.cu).
+cudaError_t launch_gather_rows(const void* src, int64_t ld, size_t elem, const int* rows,
+                               int64_t nrows, void* dst, cudaStream_t s);
+cudaError_t launch_density_reduce(const float* part, int parts, int64_t n, float* rho,
+                                  cudaStream_t s);
+// rho[p] = sum_i w[i] D[p][i]^2 for D [n][m] (FP64 or FP32, rho of the same type).
+cudaError_t launch_density_from_mo(bool f64, const void* D, int64_t n, int64_t m,
+                                   const double* w, void* rho, cudaStream_t s);
 
 // Spatial order of the points (sort.cu): a permutation perm (slot -> point)
 // and the point arrays in that order, in `scratch` of spatial_order_bytes(n)

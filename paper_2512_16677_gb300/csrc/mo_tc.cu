@@ -72,7 +72,10 @@ struct TileInfo {
   int m0, n0;            // AO-tensor row and output column of the tile
   int num_kb;
   int bn;                // MMA N of this problem (multiple of 16, <= BN_MAX)
-  bool tiled;            // rows: 125 live of 128, output row = 125 (m0/128) + local
+  bool tiled;            // rows: rows_per_tile live of 128, output row = rpt (m0/128) + local
+  int rows_per_tile;     // tiled: 125 (vgl) or 128 (values only)
+  const float* wdens;    // density epilogue: column weights (NULL: store D)
+  float* rho;            // density epilogue: [N tiles][M] partial sums
 };
 
 template <int MODE>
@@ -90,8 +93,10 @@ struct SingleSched {
   float* D;
   const uint8_t* mask;  // [m tiles][nchunk] when tiled
   const int32_t* perm;
+  const float* wdens;
+  float* rho;
   int64_t M, N, total;
-  int num_kb, n_tiles, nchunk;
+  int num_kb, n_tiles, nchunk, rows_per_tile;
   bool tiled;
   __device__ __forceinline__ int64_t count() const { return total; }
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
@@ -111,6 +116,9 @@ struct SingleSched {
     x.num_kb = num_kb;
     x.bn = BN;
     x.tiled = tiled;
+    x.rows_per_tile = rows_per_tile;
+    x.wdens = wdens;
+    x.rho = rho;
     return x;
   }
 };
@@ -140,6 +148,9 @@ struct BatchSched {
     x.num_kb = p.num_kb;
     x.bn = p.bn;
     x.tiled = p.mask != nullptr;
+    x.rows_per_tile = 5 * kTilePoints;
+    x.wdens = nullptr;
+    x.rho = nullptr;
     return x;
   }
 };
@@ -321,8 +332,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int rq = lane >> 2;
       const int cq = (lane & 3) * 4;
       const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(x.D) & 15) == 0;
-      const int64_t row0 = x.tiled ? (int64_t)(x.m0 / kBM) * (5 * kTilePoints) : (int64_t)x.m0;
-      const int rows_here = x.tiled ? 5 * kTilePoints : kBM;  // tile rows that exist in D
+      const int64_t row0 = x.tiled ? (int64_t)(x.m0 / kBM) * x.rows_per_tile : (int64_t)x.m0;
+      const int rows_here = x.tiled ? x.rows_per_tile : kBM;  // tile rows that exist in D
+      if (x.rho) {
+        // density: this thread's TMEM lane is its row; sum w_n D_n^2 over the tile's columns
+        const int loc = warp * 32 + lane;
+        float acc = 0.0f;
+#pragma unroll 1
+        for (int c = 0; c < x.bn; c += 16) {
+          float v[16];
+          if (any_live) {
+            tmem_ld16(tbase + c, v);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int64_t col = x.n0 + c + q;
+            if (col < N) acc += x.wdens[col] * v[q] * v[q];
+          }
+        }
+        if (loc < rows_here && row0 + loc < x.M)
+          x.rho[(int64_t)(x.n0 / x.bn) * x.M + row0 + loc] = acc;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(b));
+        continue;
+      }
       // the four output rows this lane writes (slot rows mapped to the
       // caller's points when the tiles hold a spatial order); -1: none
       int64_t orow[4];
@@ -418,7 +455,7 @@ cudaError_t persistent_grid(Kern kern, size_t smem, uint32_t tmem_cols, int64_t 
 template <int MODE, int BN>
 cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
                           int64_t ldc, int64_t N, float* out, int64_t out_rows, int* err_flag,
-                          cudaStream_t s) {
+                          cudaStream_t s, const float* wdens, float* rho) {
   constexpr int ST = stages_for(MODE, BN);
   using S = TcShape<MODE, BN, ST>;
   using TR = TcTraits<MODE>;
@@ -441,6 +478,9 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   sc.D = out;
   sc.mask = ao.tiled ? ao.mask : nullptr;
   sc.perm = ao.tiled ? ao.perm : nullptr;
+  sc.rows_per_tile = ao.comps == 1 ? kBM : 5 * kTilePoints;
+  sc.wdens = wdens;
+  sc.rho = rho;
   sc.tiled = ao.tiled;
   sc.nchunk = ao.nchunk;
   sc.M = ao.tiled ? out_rows : M;
@@ -459,16 +499,16 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
 template <int MODE>
 cudaError_t launch_mode(const TcConfig& cfg, const AOTensor& ao, int64_t K, const void* c_hi,
                         const void* c_lo, int64_t ldc, int64_t N, float* out, int64_t out_rows,
-                        int* err_flag, cudaStream_t s) {
+                        int* err_flag, cudaStream_t s, const float* wdens, float* rho) {
   switch (cfg.bn) {
-    case 16: return launch_single<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 32: return launch_single<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 64: return launch_single<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 96: return launch_single<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 128: return launch_single<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 160: return launch_single<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 192: return launch_single<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
-    case 256: return launch_single<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s);
+    case 16: return launch_single<MODE, 16>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 32: return launch_single<MODE, 32>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 64: return launch_single<MODE, 64>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 96: return launch_single<MODE, 96>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 128: return launch_single<MODE, 128>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 160: return launch_single<MODE, 160>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 192: return launch_single<MODE, 192>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
+    case 256: return launch_single<MODE, 256>(ao, K, c_hi, c_lo, ldc, N, out, out_rows, err_flag, s, wdens, rho);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -559,14 +599,16 @@ cudaError_t launch_mo_tc_batch(int mode, int bn_max, const TcProblem* probs, con
 
 cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
                          const void* c_lo, int64_t ldc, int64_t mo_num, float* out,
-                         const TcConfig& cfg, int* err_flag, cudaStream_t s, int64_t out_rows) {
+                         const TcConfig& cfg, int* err_flag, cudaStream_t s, int64_t out_rows,
+                         const float* wdens, float* rho_part) {
   if (out_rows < 0) out_rows = ao.rows;
+  if ((wdens == nullptr) != (rho_part == nullptr)) return cudaErrorInvalidValue;
   if (mode == QK_BF16X3)
     return launch_mode<QK_BF16X3>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows,
-                                  err_flag, s);
+                                  err_flag, s, wdens, rho_part);
   if (mode == QK_TF32)
     return launch_mode<QK_TF32>(cfg, ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows,
-                                err_flag, s);
+                                err_flag, s, wdens, rho_part);
   return cudaErrorInvalidValue;
 }
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "qk_set_fusion": [_P, _I32],
     "qk_set_spatial_order": [_P, _I32],
     "qk_set_mo_cusp": [_P, _P],
+    "qk_get_density_device": [_P, _P, _P, _I64],
     "qk_get_mo_cusp_coefficients_device": [_P, _P, _I64],
     "qk_set_nucleus": [_P, _I64, _P, _P],
     "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
@@ -211,6 +212,22 @@ class Context:
         out = torch.empty((nn, nm, 4), dtype=torch.float64, device="cuda")
         self._check(n.qk_get_mo_cusp_coefficients_device(self.h, out.data_ptr(), out.numel()),
                     "get_mo_cusp_coefficients_device")
+        return out
+
+    def density_device(self, w, out=None):
+        """Electron density sum_i w_i phi_i^2 at the current points as a CUDA
+        tensor [point_num] (FP64 in fp64 mode, else FP32)."""
+        import torch
+        self._bind_stream()
+        wa = _f64(w)
+        if wa.shape != (self.mo_num,):
+            raise ValueError("one occupation weight per MO")
+        n = self.point_num
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64 if self.mode == "fp64" else torch.float32,
+                              device="cuda")
+        self._check(self.lib.qk_get_density_device(self.h, _ptr(wa), out.data_ptr(), out.numel()),
+                    "get_density_device")
         return out
 
     def set_spatial_order(self, enable: bool):

@@ -30,7 +30,7 @@ import numpy as np
 
 ANGSTROM = 1.8897261246  # bohr per angstrom
 SEED_BASE = 2512166770
-ELEMENT_Z = {"H": 1, "C": 6, "N": 7, "O": 8}
+ELEMENT_Z = {"H": 1, "C": 6, "N": 7, "O": 8, "Cu": 29}
 
 
 def cartesian_powers(l: int) -> List[Tuple[int, int, int]]:
@@ -135,6 +135,7 @@ RECIPE_SMALL: Dict[str, _Recipe] = {
     "C": [(0, *_GEN_S)] * 3 + [(1, *_GEN_S)] * 2 + [(2, *_GEN_S)],
     "N": [(0, *_GEN_S)] * 3 + [(1, *_GEN_S)] * 2 + [(2, *_GEN_S)],
     "H": [(0, *_GEN_S)] * 2 + [(1, *_GEN_S)],
+    "Cu": [(0, *_GEN_S)] * 4 + [(1, *_GEN_S)] * 3 + [(2, *_GEN_S)] * 2,
 }
 _S = (0, (1, 8), (0.1, 5000.0))
 _P = (1, (1, 4), (0.1, 500.0))
@@ -295,11 +296,14 @@ CONFIGS = {
        "4 e-/nucleus, 16-256 walkers, MOs = e-/2, eps = 1e-10",
     5: "large cluster: 1000 nuclei C:O:H 400:100:500 in 10^4 A^3, C/O 3s2p1d "
        "H 2s1p (10000 AOs), 2000 MOs, 4000 e- x 16 walkers, eps = 1e-10",
+    6: "density stand-in: 104 nuclei C:N:O:H:Cu 34:11:10:48:1 in a sphere of 1040 A^3, "
+       "C/N/O 3s2p1d, H 2s1p, Cu 4s3p2d (1090 AOs), 218 doubly occupied MOs, "
+       "100^3 grid over the nuclei +- 4 bohr, eps = 1e-10",
 }
 
 
 def make_config(idx: int, walk_num: Optional[int] = None):
-    """Draw workload ``idx`` (1..5).  Config 4 returns a list of molecules.
+    """Draw workload ``idx`` (1..6).  Config 4 returns a list of molecules.
 
     ``walk_num`` overrides the walker count (used for reduced test sizes);
     every other draw is unchanged, so the first walkers match the full case.
@@ -332,6 +336,14 @@ def make_config(idx: int, walk_num: Optional[int] = None):
         if walk_num is not None:
             mols = [mm.with_walkers(min(walk_num, mm.walk_num)) for mm in mols]
         return mols
+    elif idx == 6:
+        # stand-in for the density workload of Sec. 5.4 (a Cu(II)-peptide
+        # complex in a double-zeta basis: ~1100 AOs, 218 occupied MOs)
+        el = element_counts({"C": 34, "N": 11, "O": 10, "H": 48, "Cu": 1}, 104)
+        el = [el[i] for i in rng.permutation(len(el))]
+        radius = (3.0 * 10.0 * 104 / (4.0 * math.pi)) ** (1.0 / 3.0)
+        pos = packed_cluster(rng, 104, radius)
+        m = make_molecule("peptide104", rng, el, pos, RECIPE_SMALL, 218, 436, 1, eps=1e-10)
     elif idx == 5:
         el = element_counts({"C": 400, "O": 100, "H": 500}, 1000)
         el = [el[i] for i in rng.permutation(len(el))]
@@ -344,6 +356,19 @@ def make_config(idx: int, walk_num: Optional[int] = None):
     if walk_num is not None:
         m = m.with_walkers(walk_num)
     return m
+
+
+def density_grid(mol: Molecule, n: int = 100, margin: float = 4.0):
+    """(origin, spacing, counts) of an n^3 grid over the nuclei's bounding
+    box widened by ``margin`` bohr on every side (Sec. 5.4's 100^3 grid)."""
+    lo = mol.nucl_coord.min(axis=0) - margin
+    hi = mol.nucl_coord.max(axis=0) + margin
+    return lo, (hi - lo) / (n - 1), (n, n, n)
+
+
+def occupations(mol: Molecule) -> np.ndarray:
+    """Occupation weights of the density workloads: 2 for every MO."""
+    return np.full(mol.mo_coef.shape[0], 2.0)
 
 
 def cusp_radii(mol: Molecule) -> np.ndarray:
