@@ -313,6 +313,7 @@ def run_ours(args, rank, world, local_rank):
         res["adjoint"] = measure_adjoint(args)
         res["cusp"] = measure_cusp(args)
         res["density"] = measure_density(args)
+        res["single_move"] = measure_single(args)
 
     # end to end through the host-memory C-ABI calls: H2D of the coordinates
     # and D2H of the whole MO vgl tensor inside the timed region
@@ -509,6 +510,41 @@ def measure_cusp(args):
             ctx.mo_vgl_device(o)
         res["ms_per_step_with" if on else "ms_per_step_without"] = _time_steps(step, 10, warmup=2)
     res["overhead_ms"] = res["ms_per_step_with"] - res["ms_per_step_without"]
+    return res
+
+
+def measure_single(args):
+    """Single-electron moves on the organic chain (256 walkers): per move,
+    the proposed positions of one electron in every walker go in and the MO
+    vgl [256][5][300] at them comes out (device memory, one stream)."""
+    import torch
+    from paper_2512_16677_gb300 import qmckl, synth
+    mol = synth.make_config(2)
+    coord = torch.from_numpy(mol.coord).cuda()
+    g = torch.Generator(device="cpu").manual_seed(99)
+    moves = [(e, (coord[:, e, :] + 0.3 * torch.randn((mol.walk_num, 3), generator=g,
+                                                      dtype=torch.float64).cuda()).contiguous())
+             for e in range(0, mol.elec_num, 37)]
+    res = {"workload": "organic150, 256 walkers, one electron moved per call, 300 MOs",
+           "walkers": mol.walk_num}
+    for mode in ("bf16x3", "fp64"):
+        ctx = qmckl.Context(mode)
+        ctx.set_molecule(mol)
+        ctx.set_points_device(coord)
+        ctx.mo_vgl_device()
+        out = None
+        k = [0]
+
+        def move():
+            nonlocal out
+            e, p = moves[k[0] % len(moves)]
+            k[0] += 1
+            ctx.set_single_point_device(e, p)
+            out = ctx.mo_vgl_single_device(out)
+        ms = _time_steps(move, 200 if mode == "bf16x3" else 20, warmup=3)
+        res[mode] = {"us_per_move": ms * 1e3,
+                     "evals_per_s": mol.walk_num * mol.mo_num / (ms * 1e-3)}
+        del ctx
     return res
 
 

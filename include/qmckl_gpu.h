@@ -131,6 +131,23 @@ qk_status qk_set_spatial_order(qk_context ctx, int32_t enable);
    the correction on. */
 qk_status qk_set_mo_cusp(qk_context ctx, const double* rc);
 
+/* Single-electron moves (the usage of Sec. 4, CHAMP: one electron of every
+   walker moved, its MOs needed at the proposed position).
+   qk_set_single_point_device: dcoord [walk_num][3] (device, bohr) are the
+   proposed positions of electron `elec` (0 <= elec < elec_num, else
+   QK_ERR_INVALID_ARG) in each walker; copied.  The context's points are not
+   changed and its cached AO tensor stays valid.
+   qk_get_mo_vgl_single_device: MO vgl [walk_num][5][mo_num] at the proposed
+   positions (FP64 in QK_FP64 mode, else FP32), with the same arithmetic as
+   qk_get_mo_vgl_device (so each row equals the row the full evaluation gives
+   that point), cusp correction included; size >= 5 * walk_num * mo_num.
+   qk_accept_single_point: the proposed positions replace electron `elec`
+   of every walker in the context's points (a new time stamp).
+   QK_ERR_NOT_PROVIDED without a proposal. */
+qk_status qk_set_single_point_device(qk_context ctx, int64_t elec, const double* dcoord);
+qk_status qk_get_mo_vgl_single_device(qk_context ctx, void* dout, int64_t size);
+qk_status qk_accept_single_point(qk_context ctx);
+
 /* Electron density on the current points (Sec. 5.4, e.g. a grid):
    rho(p) = sum_i w[i] phi_i(p)^2 with the MO values of Eqs. 5-7 (no
    derivatives are formed).  w [mo_num] (host, copied): occupation weights,

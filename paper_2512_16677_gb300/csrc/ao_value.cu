@@ -292,16 +292,12 @@ cudaError_t launch_value(const BasisDev& b, const PointsDev& p, const AOTensor& 
                          cudaStream_t s) {
   constexpr size_t smem = sizeof(AOValueSmem<T>);
   auto kern = ao_value_kernel<T, kSplit, kTiled>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  KernelFacts f;
+  cudaError_t e = kernel_facts<ao_value_kernel<T, kSplit, kTiled>>(smem, kThreads, &f);
   if (e != cudaSuccess) return e;
   const int64_t n_tiles = (p.n + kTP - 1) / kTP;
   if (n_tiles == 0 || b.nchunk == 0) return cudaSuccess;
-  int occ = 1, sms = 1, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = f.occ < 1 ? 1 : f.occ, sms = f.sms;
   int64_t gy = ((int64_t)sms * occ * 4 + b.nchunk - 1) / b.nchunk;
   if (gy > n_tiles) gy = n_tiles;
   if (gy > 65535) gy = 65535;

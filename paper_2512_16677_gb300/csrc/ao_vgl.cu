@@ -247,16 +247,13 @@ cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* r
                               int64_t tiles, cudaStream_t s) {
   const int staged = b.shell_num <= kReachSmemShells ? 1 : 0;
   const size_t smem = staged ? sizeof(float4) * (size_t)b.shell_num : 0;
-  cudaError_t e = cudaFuncSetAttribute(tile_reach_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float4) * kReachSmemShells));
+  KernelFacts f;
+  cudaError_t e = kernel_facts<tile_reach_kernel>(sizeof(float4) * kReachSmemShells,
+                                                  kReachThreads, &f);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // a few blocks per SM, each staging the table once and walking tiles
   const int64_t want = (tiles + 7) / 8;
-  const int64_t blocks = want < 4 * (int64_t)sms ? want : 4 * (int64_t)sms;
+  const int64_t blocks = want < 4 * (int64_t)f.sms ? want : 4 * (int64_t)f.sms;
   tile_reach_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s>>>(
       b, p, reach, tiles, staged);
   return cudaGetLastError();
@@ -268,8 +265,8 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   constexpr size_t smem = sizeof(StageOf<T, kTiled>);
   constexpr int TP = kTiled ? kTilePoints : kPT;
   auto kern = ao_vgl_kernel<T, kSplit, kChunked, kTiled>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  KernelFacts f;
+  cudaError_t e = kernel_facts<ao_vgl_kernel<T, kSplit, kChunked, kTiled>>(smem, kThreads, &f);
   if (e != cudaSuccess) return e;
   const int64_t n_ptiles = (p.n + TP - 1) / TP;
   if (n_ptiles == 0 || b.nchunk == 0) return cudaSuccess;
@@ -277,11 +274,7 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
     e = launch_tile_reach(b, p, out.reach, n_ptiles, s);
     if (e != cudaSuccess) return e;
   }
-  int occ = 1, sms = 1, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = f.occ < 1 ? 1 : f.occ, sms = f.sms;
   // about four waves of resident CTAs, each CTA walking several point tiles
   int64_t gy = ((int64_t)sms * occ * 4 + b.nchunk - 1) / b.nchunk;
   if (gy > n_ptiles) gy = n_ptiles;
@@ -296,15 +289,11 @@ cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n
                             cudaStream_t s) {
   constexpr size_t smem = sizeof(StageOf<float, true>);
   auto kern = ao_vgl_batch_kernel<kSplit>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  KernelFacts f;
+  cudaError_t e = kernel_facts<ao_vgl_batch_kernel<kSplit>>(smem, kThreads, &f);
   if (e != cudaSuccess) return e;
   if (n_items == 0) return cudaSuccess;
-  int occ = 1, sms = 1, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = f.occ < 1 ? 1 : f.occ, sms = f.sms;
   const int64_t grid = n_items < (int64_t)sms * occ ? n_items : (int64_t)sms * occ;
   kern<<<(unsigned)grid, kThreads, smem, s>>>(probs, items, n_items);
   return cudaGetLastError();

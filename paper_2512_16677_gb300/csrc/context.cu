@@ -116,6 +116,11 @@ struct qk_context_s {
   DevBuf d_cusp;
   DevBuf d_cusp_list;  // points inside a sphere, per MO call
   DevBuf d_dens;       // density: occupied-MO tables, weights, partial sums
+  // single-electron moves: proposed positions of electron single_elec of
+  // every walker, and the AO tensor at them
+  DevBuf d_single, d_single_ws;
+  PointsDev psingle{};
+  int64_t single_elec = -1;
   CuspDev cudev{};
   double* cusp_f64 = nullptr;
   float* cusp_f32 = nullptr;
@@ -1092,6 +1097,110 @@ qk_status qk_get_density_device(qk_context c, const double* w, void* drho, int64
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "density contraction");
+  return QK_SUCCESS;
+}
+
+qk_status qk_set_single_point_device(qk_context c, int64_t elec, const double* dcoord) {
+  CHECK_CTX(c);
+  if (!dcoord) return fail(c, QK_ERR_NULL_POINTER, "dcoord is NULL");
+  if (!c->has_points) return fail(c, QK_ERR_NOT_PROVIDED, "set the points first");
+  if (elec < 0 || elec >= c->elec_num)
+    return fail(c, QK_ERR_INVALID_ARG, "electron index %lld outside [0, %lld)", (long long)elec,
+                (long long)c->elec_num);
+  qk_status st = ensure_device(c);
+  if (st) return st;
+  const int64_t W = c->walk_num;
+  cudaError_t e = c->d_single.ensure(align_up(sizeof(double) * 3 * W, 256) +
+                                     align_up(sizeof(float) * 6 * W, 256));
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-point buffers");
+  double* base = (double*)c->d_single.p;
+  float* fb = (float*)((unsigned char*)c->d_single.p + align_up(sizeof(double) * 3 * W, 256));
+  c->psingle.n = W;
+  c->psingle.x = base;
+  c->psingle.y = base + W;
+  c->psingle.z = base + 2 * W;
+  c->psingle.hi = fb;
+  c->psingle.lo = fb + 3 * W;
+  c->psingle.ld = W;
+  {
+    TimedLaunch t(c, 2);
+    e = launch_points_soa(dcoord, 'N', W, base, base + W, base + 2 * W, fb, fb + 3 * W,
+                          c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_single_point_device");
+  c->single_elec = elec;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_mo_vgl_single_device(qk_context c, void* dout, int64_t size) {
+  CHECK_CTX(c);
+  if (!dout) return fail(c, QK_ERR_NULL_POINTER, "dout is NULL");
+  qk_status st = require(c, true);
+  if (st) return st;
+  if (c->single_elec < 0) return fail(c, QK_ERR_NOT_PROVIDED, "no single-electron move set");
+  const int64_t W = c->psingle.n, N = c->mo_num;
+  if (size < 5 * W * N)
+    return fail(c, QK_ERR_BAD_SIZE, "output holds %lld elements, %lld needed", (long long)size,
+                (long long)(5 * W * N));
+  st = ensure_tables(c);
+  if (st) return st;
+  st = ensure_mo(c);
+  if (st) return st;
+  st = ensure_cusp(c);
+  if (st) return st;
+  // AO tensor of the W moved points in a workspace of its own, so that the
+  // cached AO tensor of the full configuration stays valid
+  AOTensor av{};
+  av.ld = c->kpad;
+  av.chunked = true;
+  av.nchunk = (int)c->chunks.size();
+  const bool tiled = tiled_mode(c->mode);
+  const size_t es = c->mode == QK_FP64 ? sizeof(double)
+                                       : (c->mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
+  size_t need = 0, plane = 0, mask = 0;
+  int64_t tiles = 0;
+  if (tiled) {
+    tiles = (W + kTilePoints - 1) / kTilePoints;
+    av.tiled = true;
+    av.rows = tiles * kTileRows;
+    plane = align_up((size_t)av.rows * av.ld * es, 256);
+    mask = align_up((size_t)tiles * av.nchunk, 256);
+    need = (c->mode == QK_BF16X3 ? 2 : 1) * plane + mask;
+  } else {
+    av.rows = 5 * W;
+    plane = align_up((size_t)av.rows * av.ld * es, 256);
+    need = plane;
+  }
+  cudaError_t e = c->d_single_ws.ensure(need);
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-move workspace");
+  unsigned char* p = (unsigned char*)c->d_single_ws.p;
+  av.a = p;
+  if (tiled) {
+    if (c->mode == QK_BF16X3) av.a_lo = p + plane;
+    // a few tiles only: each ao_vgl tile culls for itself (no pre-pass launch)
+    av.mask = p + (c->mode == QK_BF16X3 ? 2 : 1) * plane;
+  }
+  {
+    TimedLaunch t(c, 0);
+    e = launch_ao_vgl(c->bdev, c->psingle, c->mode, av, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-move ao_vgl");
+  st = contract(c, av, 5 * W, dout);
+  if (st) return st;
+  return apply_cusp(c, c->psingle, dout);
+}
+
+qk_status qk_accept_single_point(qk_context c) {
+  CHECK_CTX(c);
+  if (c->single_elec < 0) return fail(c, QK_ERR_NOT_PROVIDED, "no single-electron move set");
+  cudaError_t e;
+  {
+    TimedLaunch t(c, 2);
+    e = launch_scatter_points(c->psingle, c->pdev, c->elec_num, c->single_elec, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "accept_single_point");
+  c->single_elec = -1;
+  c->date++;  // new configuration: cached AOs and point order are stale
   return QK_SUCCESS;
 }
 

@@ -319,10 +319,7 @@ cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const Points
   if (e != cudaSuccess) return e;
   const int64_t blocks = (p.n + 255) / 256;  // one thread per point
   const unsigned g = (unsigned)(blocks < 4096 ? blocks : 4096);
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned g2 = (unsigned)(8 * sms);
+  const unsigned g2 = (unsigned)(8 * device_sms());
   if (f64_out) {
     cusp_find_kernel<<<g, 256, 0, s>>>(b, cu, p, list, count);
     cusp_apply_list_kernel<double><<<g2, 256, 0, s>>>(b, cu, p, mo_num, C64, b.ao_num, f64,

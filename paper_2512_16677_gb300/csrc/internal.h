@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -97,6 +98,56 @@ struct AOTensor {
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
+
+// Launch facts of a kernel on the current device, worked out once per
+// (kernel, device): its opt-in dynamic shared memory set, resident blocks
+// per SM at that size and the SM count.  Small calls (a single-electron
+// move) would otherwise spend more time in these queries than on the GPU.
+struct KernelFacts {
+  int occ;
+  int sms;
+};
+constexpr int kMaxDevices = 64;
+template <auto Kern>
+cudaError_t kernel_facts(size_t smem, int threads, KernelFacts* out) {
+  static std::atomic<int> ready[kMaxDevices];
+  static KernelFacts facts[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  if (cache && ready[dev].load(std::memory_order_acquire)) {
+    *out = facts[dev];
+    return cudaSuccess;
+  }
+  e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  KernelFacts f{0, 1};
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f.occ, Kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (cache) {
+    facts[dev] = f;
+    ready[dev].store(1, std::memory_order_release);
+  }
+  *out = f;
+  return cudaSuccess;
+}
+// The SM count of the current device (cached per device).
+inline int device_sms() {
+  static std::atomic<int> sms[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= kMaxDevices) return 1;
+  int v = sms[dev].load(std::memory_order_acquire);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+    sms[dev].store(v, std::memory_order_release);
+  }
+  return v;
+}
 
 // A device allocation owned by the library.
 struct DevBuf {
@@ -207,6 +258,9 @@ cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* 
 int ao_value_tile_points();
 cudaError_t launch_ao_value(const BasisDev& b, const PointsDev& p, int out_mode,
                             const AOTensor& out, cudaStream_t s);
+// Single-electron moves (single.cu): src point w -> dst point w * elec_num + elec.
+cudaError_t launch_scatter_points(const PointsDev& src, const PointsDev& dst, int64_t elec_num,
+                                  int64_t elec, cudaStream_t s);
 // Density helpers (density.cu).
 cudaError_t launch_gather_rows(const void* src, int64_t ld, size_t elem, const int* rows,
                                int64_t nrows, void* dst, cudaStream_t s);

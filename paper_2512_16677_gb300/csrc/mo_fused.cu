@@ -403,17 +403,12 @@ cudaError_t launch_fused_bn(const BasisDev& b, const PointsDev& p, const void* c
   const int64_t tiles = (p.n + kTilePoints - 1) / kTilePoints;
   prm.total = tiles * prm.n_tiles;
   auto kern = mo_fused_kernel<BN>;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+  KernelFacts f;
+  cudaError_t e = kernel_facts<mo_fused_kernel<BN>>(Sh::SMEM, kFThreads, &f);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kFThreads, Sh::SMEM);
-  if (e != cudaSuccess) return e;
+  const int occ = f.occ;
   if (occ < 1 || occ * 2 * (int)Sh::TMEM_COLS > 512) return cudaErrorInvalidConfiguration;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t grid = prm.total < (int64_t)sms * occ ? prm.total : (int64_t)sms * occ;
+  const int64_t grid = prm.total < (int64_t)f.sms * occ ? prm.total : (int64_t)f.sms * occ;
   if (grid == 0) return cudaSuccess;
   kern<<<(unsigned)grid, kFThreads, Sh::SMEM, s>>>(prm, err_flag);
   return cudaGetLastError();

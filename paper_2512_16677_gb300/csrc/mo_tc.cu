@@ -435,20 +435,14 @@ constexpr int stages_for(int mode, int bn) {
 }
 
 // Grid of resident CTAs for a kernel instance (TMEM never oversubscribed).
-template <class Kern>
-cudaError_t persistent_grid(Kern kern, size_t smem, uint32_t tmem_cols, int64_t work,
-                            int64_t* grid) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+template <auto Kern>
+cudaError_t persistent_grid(size_t smem, uint32_t tmem_cols, int64_t work, int64_t* grid) {
+  KernelFacts f;
+  cudaError_t e = kernel_facts<Kern>(smem, kThreads, &f);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-  if (e != cudaSuccess) return e;
+  const int occ = f.occ;
   if (occ < 1 || occ * (int)tmem_cols > 512) return cudaErrorInvalidConfiguration;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  *grid = work < (int64_t)sms * occ ? work : (int64_t)sms * occ;
+  *grid = work < (int64_t)f.sms * occ ? work : (int64_t)f.sms * occ;
   return cudaSuccess;
 }
 
@@ -490,7 +484,8 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   sc.total = ((M + kBM - 1) / kBM) * sc.n_tiles;
   auto kern = mo_tc_kernel<MODE, BN, ST, SingleSched<BN>>;
   int64_t grid = 0;
-  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_ALLOC, sc.total, &grid);
+  cudaError_t e = persistent_grid<mo_tc_kernel<MODE, BN, ST, SingleSched<BN>>>(
+      S::SMEM, S::TMEM_ALLOC, sc.total, &grid);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
   return cudaGetLastError();
@@ -523,7 +518,8 @@ cudaError_t launch_batch_bn(const TcProblem* probs, const int4* items, int64_t n
   BatchSched sc{probs, items, n_items};
   auto kern = mo_tc_kernel<MODE, BN_MAX, ST, BatchSched>;
   int64_t grid = 0;
-  cudaError_t e = persistent_grid(kern, S::SMEM, S::TMEM_ALLOC, n_items, &grid);
+  cudaError_t e = persistent_grid<mo_tc_kernel<MODE, BN_MAX, ST, BatchSched>>(
+      S::SMEM, S::TMEM_ALLOC, n_items, &grid);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
   return cudaGetLastError();

@@ -48,6 +48,9 @@ SIGNATURES = {
     "qk_set_spatial_order": [_P, _I32],
     "qk_set_mo_cusp": [_P, _P],
     "qk_get_density_device": [_P, _P, _P, _I64],
+    "qk_set_single_point_device": [_P, _I64, _P],
+    "qk_get_mo_vgl_single_device": [_P, _P, _I64],
+    "qk_accept_single_point": [_P],
     "qk_get_mo_cusp_coefficients_device": [_P, _P, _I64],
     "qk_set_nucleus": [_P, _I64, _P, _P],
     "qk_set_ao_basis": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P],
@@ -213,6 +216,29 @@ class Context:
         self._check(n.qk_get_mo_cusp_coefficients_device(self.h, out.data_ptr(), out.numel()),
                     "get_mo_cusp_coefficients_device")
         return out
+
+    def set_single_point_device(self, elec: int, coords):
+        """Proposed positions [walk][3] (CUDA float64) of electron `elec`."""
+        self._bind_stream()
+        assert coords.is_cuda and coords.dtype.is_floating_point and coords.is_contiguous()
+        self._single = coords  # kept alive until the copy has run
+        self._check(self.lib.qk_set_single_point_device(self.h, int(elec), coords.data_ptr()),
+                    "set_single_point_device")
+
+    def mo_vgl_single_device(self, out=None):
+        """MO vgl [walk][5][mo] at the proposed positions (CUDA tensor)."""
+        import torch
+        self._bind_stream()
+        w = self._walk_elec_shape[0]
+        if out is None:
+            out = torch.empty((w, 5, self.mo_num), dtype=self.dtype_torch, device="cuda")
+        self._check(self.lib.qk_get_mo_vgl_single_device(self.h, out.data_ptr(), out.numel()),
+                    "get_mo_vgl_single_device")
+        return out
+
+    def accept_single_point(self):
+        self._bind_stream()
+        self._check(self.lib.qk_accept_single_point(self.h), "accept_single_point")
 
     def density_device(self, w, out=None):
         """Electron density sum_i w_i phi_i^2 at the current points as a CUDA
