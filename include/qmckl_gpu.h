@@ -102,6 +102,20 @@ qk_status qk_set_compute_mode(qk_context ctx, int32_t mode);
    workspace.  Both give the same arithmetic.  Other modes ignore it. */
 qk_status qk_set_fusion(qk_context ctx, int32_t enable);
 
+/* Internal order of the shells (a layout choice of this library, not a
+   step of the paper's method).  AO chunks are cut from consecutive shells,
+   so a chunk whose nuclei are close in space is reached by few point tiles.
+   mode 0 (default): the nuclei in Morton (Z-curve) order when that shortens
+   the path through the nuclei in shell order below 0.7 of the caller's
+   order (bases listed in random atom order), else the caller's order;
+   1: always the caller's order; 2: always the Morton order.  Takes effect at
+   the next qk_set_ao_basis.  Every input and output keeps the caller's AO
+   order (C columns, AO tensors, dL/dC).  Other values: QK_ERR_INVALID_ARG.
+   qk_get_basis_order: *spatial = 1 when the current basis runs in the
+   Morton order. */
+qk_status qk_set_basis_order(qk_context ctx, int32_t mode);
+qk_status qk_get_basis_order(qk_context ctx, int32_t* spatial);
+
 /* QK_BF16X3 / QK_TF32, device-memory calls: 1 (default) cuts the point tiles
    of the block-sparse contraction from a spatial (Morton cell) order of the
    points, so that a tile's points share their nonzero AOs and fewer

@@ -151,14 +151,16 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
         ol[lane] = l.x;
         ol[lane + 32] = l.y;
       } else {
-        T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
         if constexpr (kChunked) {
           // chunk window: padding columns are written as zeros
+          T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
           o[lane] = v0;
           o[lane + 32] = v1;
         } else {
-          if (lane < na) o[lane] = v0;
-          if (lane + 32 < na) o[lane + 32] = v1;
+          T* o = static_cast<T*>(out.a) + grow * out.ld;
+          const int* cmap = out.caller_cols ? b.ao_caller : nullptr;
+          if (lane < na) o[cmap ? cmap[col0 + lane] : col0 + lane] = v0;
+          if (lane + 32 < na) o[cmap ? cmap[col0 + lane + 32] : col0 + lane + 32] = v1;
         }
       }
     }

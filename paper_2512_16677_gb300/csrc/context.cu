@@ -68,6 +68,11 @@ struct qk_context_s {
   std::vector<int> shell_nuc, shell_l, shell_prim0, shell_nprim, shell_ao0, ao_shell;
   std::vector<double> prim_g, prim_c, ao_fac, shell_gmin;
   std::vector<int4> chunks;
+  // internal shell order: 0 = chosen from the nuclei (default), 1 = the
+  // caller's, 2 = spatial; ao_caller[internal AO] = the caller's AO index
+  int order_mode = 0;
+  bool order_spatial = false;
+  std::vector<int> ao_caller;
   DevBuf d_tables;
   BasisDev bdev{};
   bool tables_dirty = true;
@@ -200,6 +205,62 @@ double threshold(const qk_context c) {
 }
 
 // Upload the basis tables (and the threshold-dependent shell radii).
+// Internal shell order.  AO chunks are cut from consecutive shells, so the
+// nuclei of a chunk should be close in space: a tile of points then reaches
+// few chunks.  Bases listed along a chain or molecule by molecule already are;
+// bases listed in random atom order are not.  Spatial order: nuclei ranked
+// by the Morton code of a 1024^3 grid over their box, a nucleus's shells
+// keep the caller's order.  The default takes it when the path through the
+// nuclei in shell order gets shorter than 0.7 of the caller's.
+std::vector<int64_t> shell_order(qk_context c, int64_t S, const int64_t* shell_nucleus) {
+  std::vector<int64_t> caller(S);
+  std::iota(caller.begin(), caller.end(), 0);
+  if (c->order_mode == 1 || S < 2) return caller;
+  const int64_t NN = c->nucl_num;
+  const double* R = c->nucl_coord.data();
+  double lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = hi[k] = R[k];
+    for (int64_t a = 1; a < NN; ++a) {
+      lo[k] = std::min(lo[k], R[3 * a + k]);
+      hi[k] = std::max(hi[k], R[3 * a + k]);
+    }
+  }
+  auto spread = [](uint64_t v) {
+    uint64_t r = 0;
+    for (int i = 0; i < 10; ++i) r |= ((v >> i) & 1ull) << (3 * i);
+    return r;
+  };
+  std::vector<uint64_t> key(NN);
+  for (int64_t a = 0; a < NN; ++a) {
+    uint64_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      const double span = hi[k] - lo[k];
+      const double f = span > 0 ? (R[3 * a + k] - lo[k]) / span * 1023.0 : 0.0;
+      q[k] = (uint64_t)std::min(1023.0, std::max(0.0, f));
+    }
+    key[a] = spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2);
+  }
+  std::vector<int64_t> spatial(caller);
+  std::stable_sort(spatial.begin(), spatial.end(), [&](int64_t x, int64_t y) {
+    const int64_t ax = shell_nucleus[x], ay = shell_nucleus[y];
+    return key[ax] != key[ay] ? key[ax] < key[ay] : ax < ay;
+  });
+  if (c->order_mode == 2) return spatial;
+  auto path = [&](const std::vector<int64_t>& o) {
+    double L = 0.0;
+    for (int64_t i = 1; i < S; ++i) {
+      const int64_t a = shell_nucleus[o[i - 1]], b = shell_nucleus[o[i]];
+      if (a == b) continue;
+      const double dx = R[3 * a] - R[3 * b], dy = R[3 * a + 1] - R[3 * b + 1],
+                   dz = R[3 * a + 2] - R[3 * b + 2];
+      L += std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    return L;
+  };
+  return path(spatial) < 0.7 * path(caller) ? spatial : caller;
+}
+
 qk_status ensure_tables(qk_context c) {
   if (!c->tables_dirty) return QK_SUCCESS;
   const double T = threshold(c);
@@ -250,6 +311,7 @@ qk_status ensure_tables(qk_context c) {
       {c->ao_shell.data(), sizeof(int) * NA, 0},
       {c->chunks.data(), sizeof(int4) * NC, 0},
       {sch.data(), sizeof(int) * S, 0},
+      {c->ao_caller.data(), sizeof(int) * NA, 0},
   };
   size_t total = 0;
   for (auto& p : pieces) {
@@ -289,6 +351,7 @@ qk_status ensure_tables(qk_context c) {
   b.ao_shell = (const int*)at(16);
   b.chunk = (const int4*)at(17);
   b.shell_chunk = (const int*)at(18);
+  b.ao_caller = c->order_spatial ? (const int*)at(19) : nullptr;
   b.T = T;
   b.T_f = std::isinf(T) ? INFINITY : (float)T;
   c->tables_dirty = false;
@@ -317,8 +380,17 @@ qk_status ensure_mo(qk_context c) {
   c->c_lo = (__nv_bfloat16*)(base + b64 + b32 + b64p + b32p + b16);
   c->ldc = ldc;
   c->kpad = kp;
-  e = cudaMemcpyAsync(c->c64, c->mo_coef.data(), sizeof(double) * nm * na,
-                      cudaMemcpyHostToDevice, c->stream);
+  // C in the internal AO order (columns follow ao_caller)
+  std::vector<double> cint;
+  const double* csrc = c->mo_coef.data();
+  if (c->order_spatial) {
+    cint.resize((size_t)nm * na);
+    for (int64_t i = 0; i < nm; ++i)
+      for (int64_t a = 0; a < na; ++a) cint[i * na + a] = c->mo_coef[i * na + c->ao_caller[a]];
+    csrc = cint.data();
+  }
+  e = cudaMemcpyAsync(c->c64, csrc, sizeof(double) * nm * na, cudaMemcpyHostToDevice,
+                      c->stream);
   if (e == cudaSuccess) e = launch_to_f32(c->c64, nm, na, ldc, c->c32, c->stream);
   if (e == cudaSuccess)
     e = launch_mo_chunked(c->c64, nm, na, c->bdev.chunk, c->bdev.nchunk, c->c64p, c->c32p,
@@ -789,6 +861,17 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
   for (int64_t k = 0; k < ao_num; ++k)
     if (!std::isfinite(ao_factor[k])) return fail(c, QK_ERR_INVALID_ARG, "non-finite M_n");
 
+  // internal shell order (see shell_order): caller's, or nuclei in Morton order
+  std::vector<int64_t> caller_p0(shell_num + 1, 0), caller_a0(shell_num + 1, 0);
+  for (int64_t s = 0; s < shell_num; ++s) {
+    caller_p0[s + 1] = caller_p0[s] + shell_prim_num[s];
+    caller_a0[s + 1] = caller_a0[s] + (shell_ang_mom[s] + 1) * (shell_ang_mom[s] + 2) / 2;
+  }
+  std::vector<int64_t> order = shell_order(c, shell_num, shell_nucleus);
+  c->order_spatial = false;
+  for (int64_t i = 0; i < shell_num; ++i)
+    if (order[i] != i) c->order_spatial = true;
+
   c->shell_num = shell_num;
   c->prim_num = prim_num;
   c->ao_num = ao_num;
@@ -800,26 +883,32 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
   c->shell_gmin.resize(shell_num);
   c->prim_g.resize(prim_num);
   c->prim_c.resize(prim_num);
-  c->ao_fac.assign(ao_factor, ao_factor + ao_num);
+  c->ao_fac.resize(ao_num);
+  c->ao_caller.resize(ao_num);
   c->ao_shell.resize(ao_num);
   c->chunks.clear();
   int64_t p0 = 0, a0 = 0, chunk_prims = 0;
   int4 cur = make_int4(0, 0, 0, 0);
   for (int64_t s = 0; s < shell_num; ++s) {
-    const int l = shell_ang_mom[s];
+    const int64_t cs = order[s];  // the caller's shell at internal position s
+    const int l = shell_ang_mom[cs];
     const int nc = (l + 1) * (l + 2) / 2;
-    const int64_t npr = shell_prim_num[s];
+    const int64_t npr = shell_prim_num[cs];
     std::vector<int64_t> idx(npr);
-    std::iota(idx.begin(), idx.end(), p0);
+    std::iota(idx.begin(), idx.end(), caller_p0[cs]);
     // Sec. 3.1: primitives sorted by ascending exponent, so the first one that
     // fails Eq. 3 ends the loop
     std::stable_sort(idx.begin(), idx.end(),
                      [&](int64_t x, int64_t y) { return exponent[x] < exponent[y]; });
     for (int64_t k = 0; k < npr; ++k) {
       c->prim_g[p0 + k] = exponent[idx[k]];
-      c->prim_c[p0 + k] = shell_factor[s] * coefficient[idx[k]] * prim_factor[idx[k]];
+      c->prim_c[p0 + k] = shell_factor[cs] * coefficient[idx[k]] * prim_factor[idx[k]];
     }
-    c->shell_nuc[s] = (int)shell_nucleus[s];
+    for (int j = 0; j < nc; ++j) {
+      c->ao_fac[a0 + j] = ao_factor[caller_a0[cs] + j];
+      c->ao_caller[a0 + j] = (int)(caller_a0[cs] + j);
+    }
+    c->shell_nuc[s] = (int)shell_nucleus[cs];
     c->shell_l[s] = l;
     c->shell_prim0[s] = (int)p0;
     c->shell_nprim[s] = (int)npr;
@@ -1204,6 +1293,21 @@ qk_status qk_accept_single_point(qk_context c) {
   return QK_SUCCESS;
 }
 
+qk_status qk_set_basis_order(qk_context c, int32_t mode) {
+  CHECK_CTX(c);
+  if (mode < 0 || mode > 2) return fail(c, QK_ERR_INVALID_ARG, "order mode must be 0, 1 or 2");
+  c->order_mode = mode;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_basis_order(qk_context c, int32_t* spatial) {
+  CHECK_CTX(c);
+  if (!spatial) return fail(c, QK_ERR_NULL_POINTER, "spatial is NULL");
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "AO basis not set");
+  *spatial = c->order_spatial ? 1 : 0;
+  return QK_SUCCESS;
+}
+
 qk_status qk_set_spatial_order(qk_context c, int32_t enable) {
   CHECK_CTX(c);
   c->spatial = enable != 0;
@@ -1257,6 +1361,7 @@ qk_status qk_get_ao_vgl_device(qk_context c, void* dout, int64_t size) {
   t.a = dout;
   t.rows = 5 * c->point_num;
   t.ld = c->ao_num;
+  t.caller_cols = true;  // the caller's AO order
   const int m = c->mode == QK_FP64 ? QK_FP64 : QK_FP32;
   cudaError_t e = launch_ao_vgl(c->bdev, c->pdev, m, t, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
@@ -1586,12 +1691,14 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
       e = launch_gemm_f64(N, K, rows, (const double*)dW, 1, N, (const double*)ao.a, 1, ld,
                           (double*)dcp, K, L.k_split, c->stream);
       if (e == cudaSuccess)
-        e = launch_reduce_partials_f64((const double*)dcp, L.k_split, N * K, d_dC, c->stream);
+        e = launch_reduce_partials_f64((const double*)dcp, L.k_split, N * K, d_dC, c->stream,
+                                       c->bdev.ao_caller, K);
     } else {
       e = launch_gemm_f32(N, K, rows, (const float*)dW, 1, N, (const float*)ao.a, 1, ld,
                           (float*)dcp, K, L.k_split, c->stream);
       if (e == cudaSuccess)
-        e = launch_reduce_partials_f32((const float*)dcp, L.k_split, N * K, d_dC, c->stream);
+        e = launch_reduce_partials_f32((const float*)dcp, L.k_split, N * K, d_dC, c->stream,
+                                       c->bdev.ao_caller, K);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "backward dL/dC");
   }

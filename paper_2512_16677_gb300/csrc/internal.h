@@ -48,6 +48,7 @@ struct BasisDev {
   const int* ao_shell;      // [ao] shell of each AO
   const int4* chunk;        // [nchunk] (shell_begin, shell_end, ao_begin, ao_end)
   const int* shell_chunk;   // [shell] chunk holding each shell
+  const int* ao_caller;     // [ao] the caller's index of each AO (NULL: the same order)
   double T;                 // Eq. 3 threshold on gamma r^2
   float T_f;
 };
@@ -95,6 +96,8 @@ struct AOTensor {
   // tiled: 0 or 5 -> the vgl layout (25 points x 5 components per 128-row
   // tile); 1 -> values only (128 points per tile, one row each)
   int comps;
+  // dense layout only: columns in the caller's AO order (BasisDev::ao_caller)
+  bool caller_cols;
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
@@ -193,11 +196,14 @@ cudaError_t launch_gemm_f32(int64_t M, int64_t N, int64_t K, const float* A, int
 cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t sam,
                             int64_t sak, const double* B, int64_t sbn, int64_t sbk, double* D,
                             int64_t ldd, int k_split, cudaStream_t s);
-// Sum k_split partials [k_split][n] into dst (FP64 out).
+// Sum k_split partials [k_split][n] into dst (FP64 out).  col_map (optional):
+// the partials are rows of ncol columns and column j lands in column col_map[j].
 cudaError_t launch_reduce_partials_f32(const float* part, int k_split, int64_t n, double* dst,
-                                       cudaStream_t s);
+                                       cudaStream_t s, const int* col_map = nullptr,
+                                       int64_t ncol = 0);
 cudaError_t launch_reduce_partials_f64(const double* part, int k_split, int64_t n, double* dst,
-                                       cudaStream_t s);
+                                       cudaStream_t s, const int* col_map = nullptr,
+                                       int64_t ncol = 0);
 
 // tcgen05 contraction (QK_BF16X3 / QK_TF32): D[rows][mo] float.
 struct TcConfig {

@@ -155,30 +155,32 @@ cudaError_t launch_gemm_f64(int64_t M, int64_t N, int64_t K, const double* A, in
 }
 
 template <typename T>
-__global__ void reduce_partials_kernel(const T* part, int k_split, int64_t n, double* dst) {
+__global__ void reduce_partials_kernel(const T* part, int k_split, int64_t n, double* dst,
+                                       const int* col_map, int64_t ncol) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int z = 0; z < k_split; ++z) s += (double)part[(int64_t)z * n + i];
-    dst[i] = s;
+    // col_map: column j of each row goes to column col_map[j]
+    dst[col_map ? (i / ncol) * ncol + col_map[i % ncol] : i] = s;
   }
 }
 
 cudaError_t launch_reduce_partials_f32(const float* part, int k_split, int64_t n, double* dst,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, const int* col_map, int64_t ncol) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
   reduce_partials_kernel<float><<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(
-      part, k_split, n, dst);
+      part, k_split, n, dst, col_map, ncol);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials_f64(const double* part, int k_split, int64_t n, double* dst,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, const int* col_map, int64_t ncol) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
   reduce_partials_kernel<double><<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(
-      part, k_split, n, dst);
+      part, k_split, n, dst, col_map, ncol);
   return cudaGetLastError();
 }
 

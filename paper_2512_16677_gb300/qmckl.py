@@ -46,6 +46,8 @@ SIGNATURES = {
     "qk_set_compute_mode": [_P, _I32],
     "qk_set_fusion": [_P, _I32],
     "qk_set_spatial_order": [_P, _I32],
+    "qk_set_basis_order": [_P, _I32],
+    "qk_get_basis_order": [_P, ctypes.POINTER(_I32)],
     "qk_set_mo_cusp": [_P, _P],
     "qk_get_density_device": [_P, _P, _P, _I64],
     "qk_set_single_point_device": [_P, _I64, _P],
@@ -255,6 +257,16 @@ class Context:
         self._check(self.lib.qk_get_density_device(self.h, _ptr(wa), out.data_ptr(), out.numel()),
                     "get_density_device")
         return out
+
+    def set_basis_order(self, mode: int):
+        """0: chosen from the nuclei (default), 1: caller's, 2: Morton order;
+        applies to the next set_molecule / basis."""
+        self._check(self.lib.qk_set_basis_order(self.h, int(mode)), "set_basis_order")
+
+    def basis_order_spatial(self) -> bool:
+        v = ctypes.c_int32()
+        self._check(self.lib.qk_get_basis_order(self.h, ctypes.byref(v)), "get_basis_order")
+        return bool(v.value)
 
     def set_spatial_order(self, enable: bool):
         """tensor-core modes: cut point tiles from a spatial order (default on)."""
