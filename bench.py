@@ -123,20 +123,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ roofline ---
-def roofline(mode, mol, ms_per_launch, peaks, stats=None):
+def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
     """Roofline entries for the two kernels, from algorithmic work per launch.
 
     Dense modes: every (point, AO) entry.  Tensor-core modes skip blocks of
-    screened AOs, so their algorithmic work is that of the live blocks only
-    (stats = (live blocks, all blocks, live (point, AO) entries)); the padded
-    work the kernels actually move or issue is reported beside it.
+    screened AOs: ao_vgl's algorithmic bytes are those of the live blocks'
+    (point, AO) entries (stats = (live blocks, all blocks, live entries)),
+    and the contraction's algorithmic flops are 2 * 5 * mo_num * nnz with
+    nnz the nonzero (point, AO) pairs (sparsity = (live 16-AO groups, nnz)).
+    The padded work the kernels actually move or issue is reported beside it.
     """
     P, na, nm = mol.point_num, mol.ao_num, mol.mo_num
     es = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode]
     entries = P * na if stats is None else stats[2]
+    nnz = P * na if sparsity is None else sparsity[1]
     ao_bytes = es * 5 * entries
     dense = 2.0 * 5 * P * nm * na
-    useful = 2.0 * 5 * entries * nm
+    useful = 2.0 * 5 * nnz * nm
     out = {}
     t_ao = ms_per_launch[0] * 1e-3
     if t_ao > 0:
@@ -175,11 +178,14 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None):
         out["mo_contraction"].update({"achieved": a, "frac": a / peak, "algorithmic_flops": fl,
                                       "dense_equivalent_flops": dense * (3 if mode == "bf16x3"
                                                                           else 1)})
-        if stats is not None:
+        if sparsity is not None:
+            # one 128 x 16 x N_pad k-step per live (tile, 16-AO group)
             n_pad = -(-nm // 160) * 160
-            issued = stats[0] * 128 * 64 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
+            issued = sparsity[0] * 128 * 16 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
+            out["mo_contraction"]["nnz_fraction"] = nnz / (P * na)
             out["mo_contraction"]["issued_flops"] = issued
             out["mo_contraction"]["issued_tflops"] = issued / t_mo / 1e12
+            out["mo_contraction"]["issued_frac"] = issued / t_mo / 1e12 / peak
     return out
 
 
@@ -264,7 +270,8 @@ def run_ours(args, rank, world, local_rank):
     value = world * evals_per_step / (ms_step * 1e-3)
     per_launch = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(3)]
     stats = ctx.block_stats() if args.mode in ("bf16x3", "tf32") else None
-    roof = roofline(args.mode, mol, per_launch, peaks, stats)
+    sparsity = ctx.sparsity_stats() if args.mode in ("bf16x3", "tf32") else None
+    roof = roofline(args.mode, mol, per_launch, peaks, stats, sparsity)
     dominant = max(roof, key=lambda k: per_launch[0 if k == "ao_vgl" else 1])
     dom = dict(roof[dominant])
     dom["kernel"] = dominant

@@ -103,18 +103,27 @@ qk_status qk_set_compute_mode(qk_context ctx, int32_t mode);
 qk_status qk_set_fusion(qk_context ctx, int32_t enable);
 
 /* Internal order of the shells (a layout choice of this library, not a
-   step of the paper's method).  AO chunks are cut from consecutive shells,
-   so a chunk whose nuclei are close in space is reached by few point tiles.
-   mode 0 (default): the nuclei in Morton (Z-curve) order when that shortens
+   step of the paper's method).  AO chunks and the contraction's 16-AO
+   column groups are cut from consecutive shells, and blocks and groups
+   that no point of a tile reaches are skipped, so the shells of a group
+   should be close in space and alike in screening radius.
+   Nuclei, mode 0 (default): in Morton (Z-curve) order when that shortens
    the path through the nuclei in shell order below 0.7 of the caller's
-   order (bases listed in random atom order), else the caller's order;
-   1: always the caller's order; 2: always the Morton order.  Takes effect at
-   the next qk_set_ao_basis.  Every input and output keeps the caller's AO
-   order (C columns, AO tensors, dL/dC).  Other values: QK_ERR_INVALID_ARG.
-   qk_get_basis_order: *spatial = 1 when the current basis runs in the
-   Morton order. */
+   order (bases listed in random atom order), else in the caller's order;
+   mode 2: always in Morton order.  In both modes the shells are then split
+   stably into a compact class (minimum exponent >= that of the shell
+   holding the AO-weighted median) followed by a diffuse class.
+   Mode 1: the caller's shell order as it is.  Takes effect at the next
+   qk_set_ao_basis.  Every input and output keeps the caller's AO order
+   (C columns, AO tensors, dL/dC).  Other values: QK_ERR_INVALID_ARG.
+   qk_get_basis_order: *spatial = 1 when the current basis takes its
+   nuclei in Morton order.
+   qk_get_shell_order: order[i] = the caller's shell at internal position
+   i (n >= shell_num, else QK_ERR_BAD_SIZE; QK_ERR_NOT_PROVIDED before a
+   basis). */
 qk_status qk_set_basis_order(qk_context ctx, int32_t mode);
 qk_status qk_get_basis_order(qk_context ctx, int32_t* spatial);
+qk_status qk_get_shell_order(qk_context ctx, int64_t* order, int64_t n);
 
 /* QK_BF16X3 / QK_TF32, device-memory calls: 1 (default) cuts the point tiles
    of the block-sparse contraction from a spatial (Morton cell) order of the
@@ -269,6 +278,16 @@ qk_status qk_get_timing(qk_context ctx, double* ms, int64_t* launches, int32_t n
    (point, AO) pairs the contraction multiplies.  Synchronises the stream. */
 qk_status qk_get_block_stats(qk_context ctx, int64_t* live_blocks, int64_t* total_blocks,
                              int64_t* live_entries);
+
+/* Finer sparsity of the same AO tensor (two-kernel tensor-core path, after
+   a get_mo_vgl at this time stamp; else QK_ERR_NOT_PROVIDED).
+   live_groups = (tile, 16-AO column group) pairs holding an entry that
+   survived Eq. 3 screening: the contraction issues its tensor-core
+   k-steps over these only.  nnz = sum over points p of nnz_AO(p), the
+   (point, AO) pairs with any nonzero component (Sec. 3.2's sparse MO
+   product needs 2 * 5 * mo_num * nnz flops).  Runs a counting kernel and
+   synchronises the stream. */
+qk_status qk_get_sparsity_stats(qk_context ctx, int64_t* live_groups, int64_t* nnz);
 
 /* ----------------------------------------------------------- evaluate --- */
 

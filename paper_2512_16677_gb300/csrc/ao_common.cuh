@@ -256,6 +256,7 @@ struct AOStageSmem {
   int work[kMaxShellsChunk];   // this tile's shells to visit, in `order` order
   unsigned char dirty[kMaxShellsChunk];  // staging columns of the shell may be nonzero
   unsigned reach;              // bit s: shell s may reach a point of the tile
+  unsigned gmask;              // bit g: 16-AO column group g holds a nonzero entry
   int nwork;
   int next;                    // next entry of `work` to hand out
   T stage[5 * kLanes][kStagePitch];
@@ -488,14 +489,24 @@ __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const Poi
   if (visit) sh.work[__popc(vm & ((1u << lane) - 1u))] = sl;
   if (lane == 0) {
     sh.reach = reach;
+    sh.gmask = 0;
     sh.nwork = __popc(vm);
     sh.next = 0;
   }
 }
 
+// The 16-AO column groups of a 64-column chunk (one tensor-core k-step
+// each) that the columns of a shell of angular momentum l starting at
+// column c0 fall in.
+__device__ __forceinline__ unsigned shell_group_bits(int c0, int l) {
+  const int nc = (l + 1) * (l + 2) / 2;
+  const int g0 = c0 >> 4, g1 = (c0 + nc - 1) >> 4;
+  return ((2u << g1) - 1u) & ~((1u << g0) - 1u);
+}
+
 // Radial sums and every component of shell `sl` at tile point `lane` (valid
-// lanes only; the others get zeros), written to the staging tile.  Returns
-// whether this lane's S were nonzero.
+// lanes only; the others get zeros), written to the staging tile.  Returns,
+// on every lane, whether the S of any lane were nonzero.
 template <typename T, int kLanes>
 __device__ __forceinline__ bool shell_at_point(AOStageSmem<T, kLanes>& sh, int sl, int lane,
                                                bool valid, T Tthr) {
@@ -529,7 +540,8 @@ __device__ __forceinline__ bool shell_at_point(AOStageSmem<T, kLanes>& sh, int s
     }
   }
   const bool nz = S0 != T(0) || S1 != T(0) || S2 != T(0);
-  if (__any_sync(0xffffffffu, nz)) {
+  const bool any = __any_sync(0xffffffffu, nz);
+  if (any) {
     const int c0 = sh.col[sl];
     T* st = &sh.stage[5 * (lane < kLanes ? lane : kLanes - 1)][c0];
     const T* M = &sh.M[c0];
@@ -543,7 +555,7 @@ __device__ __forceinline__ bool shell_at_point(AOStageSmem<T, kLanes>& sh, int s
   } else {
     shell_zero_columns(sh, sl, lane);
   }
-  return nz;
+  return any;
 }
 
 

@@ -52,6 +52,7 @@ struct AOValueSmem {
   // byte each: warps on different groups of a shell update them at once)
   unsigned char gdirty[kGroups][kMaxShellsChunk];
   unsigned reach[kGroups];
+  unsigned gmask;  // bit g: 16-AO column group g holds a nonzero entry
   int work[kMaxShellsChunk * kGroups];   // shell | group << 8
   int nwork;
   int next;
@@ -89,8 +90,8 @@ __device__ __forceinline__ void clear_columns(AOValueSmem<T>& sh, int sl, int gr
   if (lane == 0) sh.gdirty[grp][sl] = 0;
 }
 
-// Shell sl at point 32 grp + lane of the tile; returns whether its S_0 was
-// nonzero.
+// Shell sl at point 32 grp + lane of the tile; returns, on every lane,
+// whether the S_0 of any lane was nonzero.
 template <typename T>
 __device__ __forceinline__ bool shell_value_at_point(AOValueSmem<T>& sh, int sl, int grp,
                                                      int lane, bool valid, T Tthr) {
@@ -119,7 +120,8 @@ __device__ __forceinline__ bool shell_value_at_point(AOValueSmem<T>& sh, int sl,
     }
   }
   const bool nz = S0 != T(0);
-  if (__any_sync(0xffffffffu, nz)) {
+  const bool any = __any_sync(0xffffffffu, nz);
+  if (any) {
     const int c0 = sh.col[sl];
     T* st = &sh.stage[pl][c0];
     const T* M = &sh.M[c0];
@@ -133,7 +135,7 @@ __device__ __forceinline__ bool shell_value_at_point(AOValueSmem<T>& sh, int sl,
   } else {
     clear_columns(sh, sl, grp, lane);
   }
-  return nz;
+  return any;
 }
 
 template <typename T, bool kSplit, bool kTiled>
@@ -225,7 +227,10 @@ __global__ void __launch_bounds__(kThreads)
         if ((mine >> g) & 1u) sh.work[w++] = sl | (g << 8);
       if (lane == 31) sh.nwork = pos;
       if (lane < kGroups) sh.reach[lane] = rg[lane];
-      if (lane == 0) sh.next = 0;
+      if (lane == 0) {
+        sh.next = 0;
+        sh.gmask = 0;
+      }
     }
     __syncthreads();
     const bool reached = (sh.reach[0] | sh.reach[1] | sh.reach[2] | sh.reach[3]) != 0u;
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     // ---- phase 1
     const int nwork = sh.nwork;
-    int live = 0;
+    unsigned groups = 0;  // warp-uniform: column groups this warp made nonzero
     for (;;) {
       int k = 0;
       if (lane == 0) k = atomicAdd(&sh.next, 1);
@@ -246,15 +251,21 @@ __global__ void __launch_bounds__(kThreads)
       const int item = sh.work[k];
       const int sl = item & 0xff, grp = item >> 8;
       const bool valid = p0 + 32 * grp + lane < n;
-      if ((sh.reach[grp] >> sl) & 1u)
-        live |= shell_value_at_point(sh, sl, grp, lane, valid, Tthr);
-      else
+      if ((sh.reach[grp] >> sl) & 1u) {
+        if (shell_value_at_point(sh, sl, grp, lane, valid, Tthr))
+          groups |= shell_group_bits(sh.col[sl], sh.lsh[sl]);
+      } else {
         clear_columns(sh, sl, grp, lane);
+      }
     }
-    const int any_live = __syncthreads_or(live);
     if constexpr (kTiled) {
-      if (tid == 0) out.mask[tile * out.nchunk + q] = any_live ? 1 : 0;
-      if (!any_live) continue;
+      if (lane == 0 && groups) atomicOr(&sh.gmask, groups);
+    }
+    __syncthreads();
+    if constexpr (kTiled) {
+      const unsigned gm = sh.gmask;  // the vgl layout's mask byte: live column groups
+      if (tid == 0) out.mask[tile * out.nchunk + q] = (uint8_t)gm;
+      if (!gm) continue;
     }
     // ---- phase 2: copy-out, one warp per row, lanes over columns lane, lane + 32
     for (int r = warp; r < kTP; r += kWarps) {

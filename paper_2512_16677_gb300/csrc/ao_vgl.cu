@@ -106,24 +106,31 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
     // culled shells only get their staging columns cleared
     const bool valid = lane < TP && p0 + lane < n;
     const int nwork = sh.nwork;
-    int live = 0;
+    unsigned groups = 0;  // warp-uniform: column groups this warp made nonzero
     for (;;) {
       int k = 0;
       if (lane == 0) k = atomicAdd(&sh.next, 1);
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= nwork) break;
       const int sl = sh.work[k];
-      if ((reach >> sl) & 1u)
-        live |= shell_at_point(sh, sl, lane, valid, Tthr);
-      else
+      if ((reach >> sl) & 1u) {
+        if (shell_at_point(sh, sl, lane, valid, Tthr))
+          groups |= shell_group_bits(sh.col[sl], sh.lsh[sl]);
+      } else {
         shell_zero_columns(sh, sl, lane);
+      }
     }
-    // block barrier; in the tiled layout it also tells whether any entry of
-    // block (tile, chunk) survived screening
-    const int any_live = __syncthreads_or(live);
     if constexpr (kTiled) {
-      if (tid == 0) out.mask[ptile * out.nchunk + q] = any_live ? 1 : 0;
-      if (!any_live) continue;  // not written: the contraction skips this block
+      if (lane == 0 && groups) atomicOr(&sh.gmask, groups);
+    }
+    __syncthreads();
+    if constexpr (kTiled) {
+      // mask byte: bit g set when column group g of block (tile, chunk) holds
+      // an entry that survived screening; 0: block not written, the
+      // contraction skips it
+      const unsigned gm = sh.gmask;
+      if (tid == 0) out.mask[ptile * out.nchunk + q] = (uint8_t)gm;
+      if (!gm) continue;
     }
     // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
     // lane + 32.  Tiled: all 128 rows (stage rows 125..127 belong to the
@@ -347,6 +354,65 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 }
 
 // ------------------------------------------------------------ helpers ---
+
+// Nonzero (point, AO) pairs of a tiled vgl AO tensor: the AO of a point
+// counts when any of its five rows holds a nonzero entry at that column
+// (either bf16 plane when split; the sign bit ignored).  Blocks whose mask
+// byte is zero were not written and count nothing.  Statistics only.
+template <bool kSplit>
+__global__ void __launch_bounds__(256)
+    ao_nnz_kernel(AOTensor t, int64_t n, int64_t tiles, unsigned long long* out) {
+  __shared__ unsigned long long tot;
+  if (threadIdx.x == 0) tot = 0ull;
+  __syncthreads();
+  unsigned cnt = 0;
+  const int64_t blocks = tiles * t.nchunk;
+  for (int64_t bi = blockIdx.x; bi < blocks; bi += gridDim.x) {
+    if (t.mask[bi] == 0) continue;
+    const int64_t tile = bi / t.nchunk;
+    const int q = (int)(bi % t.nchunk);
+    const int64_t left = n - tile * kTilePoints;
+    const int pts = left < kTilePoints ? (int)left : kTilePoints;
+    for (int i = threadIdx.x; i < pts * kChunkAO; i += blockDim.x) {
+      const int j = i / kChunkAO, c = i % kChunkAO;
+      const int64_t e0 = (tile * kTileRows + 5 * j) * t.ld + (int64_t)q * kChunkAO + c;
+      bool nz = false;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const int64_t e = e0 + r * t.ld;
+        if constexpr (kSplit) {
+          nz |= (static_cast<const uint16_t*>(t.a)[e] & 0x7fffu) != 0u;
+          nz |= (static_cast<const uint16_t*>(t.a_lo)[e] & 0x7fffu) != 0u;
+        } else {
+          nz |= (static_cast<const uint32_t*>(t.a)[e] & 0x7fffffffu) != 0u;
+        }
+      }
+      cnt += nz ? 1u : 0u;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&tot, (unsigned long long)cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(out, tot);
+}
+
+cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned long long* out,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (n + kTilePoints - 1) / kTilePoints;
+  const int64_t blocks = tiles * t.nchunk;
+  if (blocks == 0) return cudaSuccess;
+  const unsigned g = (unsigned)(blocks < 8 * (int64_t)device_sms() ? blocks
+                                                                    : 8 * (int64_t)device_sms());
+  if (split)
+    ao_nnz_kernel<true><<<g, 256, 0, s>>>(t, n, tiles, out);
+  else
+    ao_nnz_kernel<false><<<g, 256, 0, s>>>(t, n, tiles, out);
+  return cudaGetLastError();
+}
+
 
 __global__ void points_soa_kernel(const double* raw, char transp, int64_t n, double* x,
                                   double* y, double* z, float* hi, float* lo) {

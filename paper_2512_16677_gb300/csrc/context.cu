@@ -71,7 +71,9 @@ struct qk_context_s {
   // internal shell order: 0 = chosen from the nuclei (default), 1 = the
   // caller's, 2 = spatial; ao_caller[internal AO] = the caller's AO index
   int order_mode = 0;
-  bool order_spatial = false;
+  std::vector<int64_t> shell_perm;  // caller's shell at each internal position
+  bool order_spatial = false;   // nuclei taken in Morton order
+  bool order_permuted = false;  // internal shell order differs from the caller's
   std::vector<int> ao_caller;
   DevBuf d_tables;
   BasisDev bdev{};
@@ -204,18 +206,28 @@ double threshold(const qk_context c) {
   return (double)(c->bits - 1) * std::log(2.0);
 }
 
-// Upload the basis tables (and the threshold-dependent shell radii).
-// Internal shell order.  AO chunks are cut from consecutive shells, so the
-// nuclei of a chunk should be close in space: a tile of points then reaches
-// few chunks.  Bases listed along a chain or molecule by molecule already are;
-// bases listed in random atom order are not.  Spatial order: nuclei ranked
-// by the Morton code of a 1024^3 grid over their box, a nucleus's shells
-// keep the caller's order.  The default takes it when the path through the
-// nuclei in shell order gets shorter than 0.7 of the caller's.
-std::vector<int64_t> shell_order(qk_context c, int64_t S, const int64_t* shell_nucleus) {
+// Internal shell order.  AO chunks are cut from consecutive shells, and
+// the contraction skips (tile, chunk) blocks and 16-AO column groups that
+// hold no entry surviving Eq. 3, so the shells that share a column group
+// should reach the same points: nearby nuclei, and similar screening radii
+// (r^2 < T / gamma_min).
+//  - Nuclei: bases listed along a chain or molecule by molecule already
+//    are in a spatial order; bases listed in random atom order are not.
+//    Spatial order: nuclei ranked by the Morton code of a 1024^3 grid over
+//    their box, a nucleus's shells keep the caller's order.  The default
+//    takes it when the path through the nuclei in shell order gets shorter
+//    than 0.7 of the caller's.
+//  - Radii: the shells are then split, stably, into a compact class
+//    (gamma_min at least that of the AO-weighted median shell) followed by
+//    a diffuse class.  A diffuse shell reaches far, so a column group that
+//    mixes one with compact shells is live wherever the diffuse one is;
+//    the split is threshold-free because r^2 scales with 1 / gamma_min for
+//    every shell alike.
+// Mode 1 keeps the caller's order as it is.
+std::vector<int64_t> nucleus_order(qk_context c, int64_t S, const int64_t* shell_nucleus) {
   std::vector<int64_t> caller(S);
   std::iota(caller.begin(), caller.end(), 0);
-  if (c->order_mode == 1 || S < 2) return caller;
+  if (S < 2) return caller;
   const int64_t NN = c->nucl_num;
   const double* R = c->nucl_coord.data();
   double lo[3], hi[3];
@@ -259,6 +271,43 @@ std::vector<int64_t> shell_order(qk_context c, int64_t S, const int64_t* shell_n
     return L;
   };
   return path(spatial) < 0.7 * path(caller) ? spatial : caller;
+}
+
+// *morton: the nuclei were taken in Morton order.
+std::vector<int64_t> shell_order(qk_context c, int64_t S, const int64_t* shell_nucleus,
+                                 const int32_t* shell_ang_mom, const int64_t* shell_prim_num,
+                                 const double* exponent, bool* morton) {
+  std::vector<int64_t> order(S);
+  std::iota(order.begin(), order.end(), 0);
+  *morton = false;
+  if (c->order_mode == 1 || S < 2) return order;
+  order = nucleus_order(c, S, shell_nucleus);
+  for (int64_t i = 0; i < S; ++i)
+    if (order[i] != i) *morton = true;
+  std::vector<double> gmin(S);
+  int64_t p = 0, na = 0;
+  for (int64_t s = 0; s < S; ++s) {
+    gmin[s] = exponent[p];
+    for (int64_t k = 1; k < shell_prim_num[s]; ++k) gmin[s] = std::min(gmin[s], exponent[p + k]);
+    p += shell_prim_num[s];
+    na += (shell_ang_mom[s] + 1) * (shell_ang_mom[s] + 2) / 2;
+  }
+  // gamma_min of the shell that holds the middle AO, shells by descending gamma_min
+  std::vector<int64_t> by_g(S);
+  std::iota(by_g.begin(), by_g.end(), 0);
+  std::stable_sort(by_g.begin(), by_g.end(),
+                   [&](int64_t x, int64_t y) { return gmin[x] > gmin[y]; });
+  double gmed = gmin[by_g[0]];
+  for (int64_t i = 0, a = 0; i < S; ++i) {
+    a += (shell_ang_mom[by_g[i]] + 1) * (shell_ang_mom[by_g[i]] + 2) / 2;
+    if (2 * a >= na) {
+      gmed = gmin[by_g[i]];
+      break;
+    }
+  }
+  std::stable_partition(order.begin(), order.end(),
+                        [&](int64_t s) { return gmin[s] >= gmed; });
+  return order;
 }
 
 qk_status ensure_tables(qk_context c) {
@@ -351,7 +400,7 @@ qk_status ensure_tables(qk_context c) {
   b.ao_shell = (const int*)at(16);
   b.chunk = (const int4*)at(17);
   b.shell_chunk = (const int*)at(18);
-  b.ao_caller = c->order_spatial ? (const int*)at(19) : nullptr;
+  b.ao_caller = c->order_permuted ? (const int*)at(19) : nullptr;
   b.T = T;
   b.T_f = std::isinf(T) ? INFINITY : (float)T;
   c->tables_dirty = false;
@@ -383,7 +432,7 @@ qk_status ensure_mo(qk_context c) {
   // C in the internal AO order (columns follow ao_caller)
   std::vector<double> cint;
   const double* csrc = c->mo_coef.data();
-  if (c->order_spatial) {
+  if (c->order_permuted) {
     cint.resize((size_t)nm * na);
     for (int64_t i = 0; i < nm; ++i)
       for (int64_t a = 0; a < na; ++a) cint[i * na + a] = c->mo_coef[i * na + c->ao_caller[a]];
@@ -861,16 +910,20 @@ qk_status qk_set_ao_basis(qk_context c, int64_t shell_num, int64_t prim_num,
   for (int64_t k = 0; k < ao_num; ++k)
     if (!std::isfinite(ao_factor[k])) return fail(c, QK_ERR_INVALID_ARG, "non-finite M_n");
 
-  // internal shell order (see shell_order): caller's, or nuclei in Morton order
+  // internal shell order (see shell_order)
   std::vector<int64_t> caller_p0(shell_num + 1, 0), caller_a0(shell_num + 1, 0);
   for (int64_t s = 0; s < shell_num; ++s) {
     caller_p0[s + 1] = caller_p0[s] + shell_prim_num[s];
     caller_a0[s + 1] = caller_a0[s] + (shell_ang_mom[s] + 1) * (shell_ang_mom[s] + 2) / 2;
   }
-  std::vector<int64_t> order = shell_order(c, shell_num, shell_nucleus);
-  c->order_spatial = false;
+  bool morton = false;
+  std::vector<int64_t> order =
+      shell_order(c, shell_num, shell_nucleus, shell_ang_mom, shell_prim_num, exponent, &morton);
+  c->order_spatial = morton;
+  c->order_permuted = false;
   for (int64_t i = 0; i < shell_num; ++i)
-    if (order[i] != i) c->order_spatial = true;
+    if (order[i] != i) c->order_permuted = true;
+  c->shell_perm = order;
 
   c->shell_num = shell_num;
   c->prim_num = prim_num;
@@ -1308,6 +1361,17 @@ qk_status qk_get_basis_order(qk_context c, int32_t* spatial) {
   return QK_SUCCESS;
 }
 
+qk_status qk_get_shell_order(qk_context c, int64_t* order, int64_t n) {
+  CHECK_CTX(c);
+  if (!order) return fail(c, QK_ERR_NULL_POINTER, "order is NULL");
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "AO basis not set");
+  if (n < c->shell_num)
+    return fail(c, QK_ERR_BAD_SIZE, "order holds %lld entries, %lld needed", (long long)n,
+                (long long)c->shell_num);
+  std::copy(c->shell_perm.begin(), c->shell_perm.end(), order);
+  return QK_SUCCESS;
+}
+
 qk_status qk_set_spatial_order(qk_context c, int32_t enable) {
   CHECK_CTX(c);
   c->spatial = enable != 0;
@@ -1620,6 +1684,32 @@ qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_
   *live_blocks = live;
   *total_blocks = tiles * nq;
   *live_entries = entries;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz) {
+  CHECK_CTX(c);
+  if (!live_groups || !nnz) return fail(c, QK_ERR_NULL_POINTER, "output pointer is NULL");
+  if (use_fused(c) || !tiled_mode(c->ao_mode) || c->ao_ws == nullptr ||
+      c->ao_date != c->date)
+    return fail(c, QK_ERR_NOT_PROVIDED,
+                "no AO tensor of the current points in a two-kernel tensor-core mode");
+  const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
+  const int64_t tiles = ao_tiles(c), nq = t.nchunk;
+  std::vector<uint8_t> mask((size_t)(tiles * nq));
+  // the counter lives in the second half of the 256-byte error-word buffer
+  auto* cnt = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_flag.p) + 128);
+  unsigned long long h = 0;
+  cudaError_t e = launch_ao_nnz(t, c->ao_mode == QK_BF16X3, c->point_num, cnt, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(mask.data(), t.mask, mask.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sparsity count");
+  int64_t g = 0;
+  for (uint8_t m : mask) g += __builtin_popcount(m & 0xFu);
+  *live_groups = g;
+  *nnz = (int64_t)h;
   return QK_SUCCESS;
 }
 

@@ -72,10 +72,11 @@ struct PointsDev {
 //
 // tiled (tensor-core modes): points go in tiles of kTilePoints; the 125
 // (point, component) rows of tile t are rows 128 t .. 128 t + 124, rows
-// 125..127 of each tile are zero, and mask[t * nchunk + q] says whether
-// block (t, q) holds any entry that survived screening.  Blocks with a zero
-// mask byte are not written and the contraction skips them (the sparse-AO
-// MO product of Sec. 3.2 at tile granularity).
+// 125..127 of each tile are zero, and bit g of mask[t * nchunk + q] says
+// whether columns 16 g .. 16 g + 15 of block (t, q) hold any entry that
+// survived screening.  Blocks with a zero mask byte are not written and the
+// contraction skips them, and its MMA k-steps over dead column groups (the
+// sparse-AO MO product of Sec. 3.2 at tile granularity).
 struct AOTensor {
   void* a;        // FP64 / FP32 values, or bf16 "hi" plane
   void* a_lo;     // bf16 "lo" plane (QK_BF16X3 only)
@@ -83,7 +84,7 @@ struct AOTensor {
   int64_t ld;     // row stride in elements
   bool chunked;
   bool tiled;
-  uint8_t* mask;  // [tiles][nchunk] when tiled
+  uint8_t* mask;  // [tiles][nchunk] live 16-column groups when tiled
   int nchunk;
   // tiled, optional: [tiles][nchunk] bit s set when shell s of the chunk may
   // reach a point of the tile (filled by a pre-pass in launch_ao_vgl; NULL:
@@ -168,6 +169,11 @@ struct DevBuf {
 // float, QK_BF16X3 -> bf16 hi/lo planes.
 cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s);
+
+// Nonzero (point, AO) pairs of the tiled vgl AO tensor t of n points
+// (split: bf16 hi/lo planes) summed into *out (device; zeroed first).
+cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned long long* out,
+                          cudaStream_t s);
 
 // Point coordinates [n][3] ('N') or [3][n] ('T') -> SoA + hi/lo floats.
 cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double* x,

@@ -66,7 +66,7 @@ struct TileInfo {
   const CUtensorMap* b;
   const CUtensorMap* b_lo;
   float* D;
-  const uint8_t* kmask;  // live 64-column chunks of this M tile (NULL: all live)
+  const uint8_t* kmask;  // live 16-column groups of this M tile's chunks (NULL: all)
   const int32_t* perm;   // tiled: point of each slot (NULL: slot = point)
   int64_t M, N;          // output rows and columns
   int m0, n0;            // AO-tensor row and output column of the tile
@@ -78,11 +78,25 @@ struct TileInfo {
   float* rho;            // density epilogue: [N tiles][M] partial sums
 };
 
+// The MMA k-steps of K block kb (bit kk: k-step kk) that meet a nonzero AO.
+// The mask byte of a 64-column chunk has a bit per 16-column group.  A K
+// block of 64 bf16 columns is one chunk, its four k-steps of 16 one group
+// each; a K block of 32 TF32 columns is half kb & 1 of chunk kb >> 1, and
+// its k-steps of 8 take two per group.
+template <int MODE>
+__device__ __forceinline__ uint32_t kb_steps(const TileInfo& x, int kb) {
+  if (x.kmask == nullptr) return 0xFu;
+  if constexpr (TcTraits<MODE>::kBK == 64) {
+    return x.kmask[kb] & 0xFu;
+  } else {
+    const uint32_t g = ((uint32_t)x.kmask[kb >> 1] >> (2 * (kb & 1))) & 3u;
+    return (g & 1u ? 0x3u : 0u) | (g & 2u ? 0xCu : 0u);
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ bool kb_live(const TileInfo& x, int kb) {
-  // K blocks of 64 bf16 or 32 TF32 elements; the mask is per 64-column chunk
-  constexpr int kShift = TcTraits<MODE>::kBK == 64 ? 0 : 1;
-  return x.kmask == nullptr || x.kmask[kb >> kShift] != 0;
+  return kb_steps<MODE>(x, kb) != 0u;
 }
 
 // One problem: tile t -> (m, n) = (t / n_tiles, t % n_tiles), N tile fastest
@@ -264,9 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const uint32_t dacc = tmem + b * ACC;
-      uint32_t issued = 0;
+      bool first = true;  // the tile's first MMA overwrites the accumulator
       for (int kb = 0; kb < x.num_kb; ++kb) {
-        if (!kb_live<MODE>(x, kb)) continue;
+        const uint32_t steps = kb_steps<MODE>(x, kb);
+        if (!steps) continue;
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         ++it;
@@ -283,8 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t b_lo = b_hi + S::B_BYTES;
 #pragma unroll
         for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
+          // k-steps over AO columns that are zero at every row of the tile
+          // would add exact zeros
+          if (!((steps >> kk) & 1u)) continue;
           const uint32_t koff = kk * kUmmaKBytes;
-          const uint32_t acc = (issued | (uint32_t)kk) != 0;  // first live block overwrites
+          const uint32_t acc = first ? 0u : 1u;
+          first = false;
           umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_hi + koff), idesc, acc);
           if constexpr (MODE == QK_BF16X3) {
             umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_lo + koff), idesc, 1u);
@@ -292,7 +311,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
-        ++issued;
       }
       // accumulator b complete (after an abort this still waits for the MMAs
       // already issued, so the epilogue never reads a buffer being written)

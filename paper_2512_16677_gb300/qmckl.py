@@ -48,6 +48,7 @@ SIGNATURES = {
     "qk_set_spatial_order": [_P, _I32],
     "qk_set_basis_order": [_P, _I32],
     "qk_get_basis_order": [_P, ctypes.POINTER(_I32)],
+    "qk_get_shell_order": [_P, _P, _I64],
     "qk_set_mo_cusp": [_P, _P],
     "qk_get_density_device": [_P, _P, _P, _I64],
     "qk_set_single_point_device": [_P, _I64, _P],
@@ -76,6 +77,7 @@ SIGNATURES = {
     "qk_set_timing": [_P, _I32],
     "qk_get_block_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                            ctypes.POINTER(_I64)],
+    "qk_get_sparsity_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "qk_batch_create": [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)],
     "qk_batch_destroy": [_P],
     "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
@@ -259,14 +261,24 @@ class Context:
         return out
 
     def set_basis_order(self, mode: int):
-        """0: chosen from the nuclei (default), 1: caller's, 2: Morton order;
-        applies to the next set_molecule / basis."""
+        """0: nuclei order chosen from the geometry (default), 1: caller's
+        shell order, 2: nuclei in Morton order; 0 and 2 then split the shells
+        into compact and diffuse classes.  Applies to the next set_molecule /
+        basis."""
         self._check(self.lib.qk_set_basis_order(self.h, int(mode)), "set_basis_order")
 
     def basis_order_spatial(self) -> bool:
+        """Whether the current basis takes its nuclei in Morton order."""
         v = ctypes.c_int32()
         self._check(self.lib.qk_get_basis_order(self.h, ctypes.byref(v)), "get_basis_order")
         return bool(v.value)
+
+    def shell_order(self, shell_num: int) -> np.ndarray:
+        """The caller's shell at each internal position."""
+        out = np.zeros(shell_num, dtype=np.int64)
+        self._check(self.lib.qk_get_shell_order(self.h, _ptr(out), shell_num),
+                    "get_shell_order")
+        return out
 
     def set_spatial_order(self, enable: bool):
         """tensor-core modes: cut point tiles from a spatial order (default on)."""
@@ -421,6 +433,14 @@ class Context:
         self._check(self.lib.qk_get_block_stats(self.h, ctypes.byref(a), ctypes.byref(b),
                                                 ctypes.byref(c)), "get_block_stats")
         return a.value, b.value, c.value
+
+    def sparsity_stats(self):
+        """(live (tile, 16-AO group) pairs, nonzero (point, AO) pairs) of the
+        current AO tensor on the two-kernel tensor-core path."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.qk_get_sparsity_stats(self.h, ctypes.byref(a), ctypes.byref(b)),
+                    "get_sparsity_stats")
+        return a.value, b.value
 
     # ------------------------------------------------------------ evaluate
     def mo_vgl_device(self, out=None):

@@ -277,3 +277,27 @@ def test_spatial_order_same_values_fewer_blocks(orc, cfg, mode):
     idx = np.sort(rng.choice(mm.point_num, 64, replace=False))
     ref, size = orc.mo_vgl(mm, points=mm.points[idx])
     assert_within(mode, outs[0][idx], ref, size, "spatial order")
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_sparsity_stats(orc, cfg, mode):
+    """The nonzero (point, AO) count of the AO tensor agrees with the
+    oracle's count of AOs that pass Eq. 3 (screening decided in FP32 on the
+    device: a few pairs at the threshold may differ), and the live 16-AO
+    groups the contraction's k-steps run over lie between the live blocks
+    and four times as many."""
+    m = cfg(2, walk_num=8)                       # 4 800 points
+    c = _ctx(m, mode)
+    o = c.mo_vgl_device()
+    torch.cuda.synchronize()
+    live, total, entries = c.block_stats()
+    groups, nnz = c.sparsity_stats()
+    ref = orc.screen_counts(m)[2]
+    assert abs(nnz - ref) <= max(8, 1e-4 * ref), (nnz, ref)
+    assert live <= groups <= 4 * live
+    assert nnz <= entries
+    assert nnz <= groups * 16 * 25               # 25 points per tile
+    got = o.double().cpu().numpy().reshape(-1, 5, m.mo_num)
+    idx = np.sort(np.random.default_rng(5).choice(m.point_num, 48, replace=False))
+    r, size = orc.mo_vgl(m, points=m.points[idx])
+    assert_within(mode, got[idx], r, size, "group-skipping contraction")
