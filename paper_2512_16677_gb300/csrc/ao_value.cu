@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads)
     const bool reached = (sh.reach[0] | sh.reach[1] | sh.reach[2] | sh.reach[3]) != 0u;
     if constexpr (kTiled) {
       if (!reached) {  // no shell reaches any point of the tile: block not written
-        if (tid == 0) out.mask[tile * out.nchunk + q] = 0;
+        if (tid == 0) out.mask[tile * mask_ld(out.nchunk) + q] = 0;
         continue;
       }
     }
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if constexpr (kTiled) {
       const unsigned gm = sh.gmask;  // the vgl layout's mask byte: live column groups
-      if (tid == 0) out.mask[tile * out.nchunk + q] = (uint8_t)gm;
+      if (tid == 0) out.mask[tile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
       if (!gm) continue;
     }
     // ---- phase 2: copy-out, one warp per row, lanes over columns lane, lane + 32

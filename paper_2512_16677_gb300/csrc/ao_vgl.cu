@@ -85,7 +85,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
       if (out.reach) {  // the pre-pass's culling: unreached blocks cost no barrier
         pre = out.reach[ptile * out.nchunk + q];
         if (pre == 0u) {
-          if (tid == 0) out.mask[ptile * out.nchunk + q] = 0;
+          if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = 0;
           continue;
         }
       }
@@ -98,7 +98,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
     const unsigned reach = sh.reach;
     if constexpr (kTiled) {
       if (reach == 0u) {  // no shell reaches the tile: block not written
-        if (tid == 0) out.mask[ptile * out.nchunk + q] = 0;
+        if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = 0;
         continue;
       }
     }
@@ -129,7 +129,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
       // an entry that survived screening; 0: block not written, the
       // contraction skips it
       const unsigned gm = sh.gmask;
-      if (tid == 0) out.mask[ptile * out.nchunk + q] = (uint8_t)gm;
+      if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
       if (!gm) continue;
     }
     // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
@@ -368,9 +368,9 @@ __global__ void __launch_bounds__(256)
   unsigned cnt = 0;
   const int64_t blocks = tiles * t.nchunk;
   for (int64_t bi = blockIdx.x; bi < blocks; bi += gridDim.x) {
-    if (t.mask[bi] == 0) continue;
     const int64_t tile = bi / t.nchunk;
     const int q = (int)(bi % t.nchunk);
+    if (t.mask[tile * mask_ld(t.nchunk) + q] == 0) continue;
     const int64_t left = n - tile * kTilePoints;
     const int pts = left < kTilePoints ? (int)left : kTilePoints;
     for (int i = threadIdx.x; i < pts * kChunkAO; i += blockDim.x) {

@@ -547,7 +547,7 @@ size_t ao_tensor_bytes(qk_context c, int mode) {
   const size_t ld = (size_t)kpad_of(c);
   if (tiled_mode(mode)) {
     const size_t rows = (size_t)ao_tiles(c) * kTileRows;
-    const size_t mask = align_up((size_t)ao_tiles(c) * c->chunks.size(), 256) +
+    const size_t mask = align_up((size_t)ao_tiles(c) * mask_ld((int)c->chunks.size()), 256) +
                         align_up((size_t)ao_tiles(c) * c->chunks.size() * sizeof(uint32_t), 256);
     if (mode == QK_BF16X3) return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256) + mask;
     return align_up(rows * ld * sizeof(float), 256) + mask;
@@ -610,7 +610,7 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
       p += plane;
     }
     t.mask = p;
-    t.reach = (uint32_t*)(p + align_up((size_t)ao_tiles(c) * c->chunks.size(), 256));
+    t.reach = (uint32_t*)(p + align_up((size_t)ao_tiles(c) * mask_ld(t.nchunk), 256));
   } else {
     t.rows = 5 * c->point_num;
   }
@@ -682,7 +682,7 @@ AOTensor ao_range(const AOTensor& t, int mode, int64_t p0, int64_t p1) {
     const int64_t t0 = p0 / kTilePoints;
     r0 = t0 * kTileRows;
     v.rows = (p1 - p0 + kTilePoints - 1) / kTilePoints * kTileRows;
-    v.mask = t.mask + t0 * t.nchunk;
+    v.mask = t.mask + t0 * mask_ld(t.nchunk);
     if (t.reach) v.reach = t.reach + t0 * t.nchunk;
   } else {
     r0 = 5 * p0;
@@ -1207,7 +1207,7 @@ qk_status qk_get_density_device(qk_context c, const double* w, void* drho, int64
   const size_t ae = f64 ? sizeof(double) : (split ? sizeof(__nv_bfloat16) : sizeof(float));
   const size_t plane = align_up((size_t)av.rows * kp * ae, 256);
   const size_t need = (split ? 2 : 1) * plane +
-                      (tiled ? align_up((size_t)tiles * c->chunks.size(), 256) : 0);
+                      (tiled ? align_up((size_t)tiles * mask_ld(av.nchunk), 256) : 0);
   void* ws = nullptr;
   st = workspace(c, need, &ws);
   if (st) return st;
@@ -1306,7 +1306,7 @@ qk_status qk_get_mo_vgl_single_device(qk_context c, void* dout, int64_t size) {
     av.tiled = true;
     av.rows = tiles * kTileRows;
     plane = align_up((size_t)av.rows * av.ld * es, 256);
-    mask = align_up((size_t)tiles * av.nchunk, 256);
+    mask = align_up((size_t)tiles * mask_ld(av.nchunk), 256);
     need = (c->mode == QK_BF16X3 ? 2 : 1) * plane + mask;
   } else {
     av.rows = 5 * W;
@@ -1666,8 +1666,8 @@ qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_
     return fail(c, QK_ERR_NOT_PROVIDED,
                 "no AO tensor of the current points in a tensor-core mode");
   const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
-  const int64_t tiles = ao_tiles(c), nq = t.nchunk;
-  std::vector<uint8_t> mask((size_t)(tiles * nq));
+  const int64_t tiles = ao_tiles(c), nq = t.nchunk, ld = mask_ld(t.nchunk);
+  std::vector<uint8_t> mask((size_t)(tiles * ld));
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpy(mask.data(), t.mask, mask.size(), cudaMemcpyDeviceToHost);
@@ -1676,7 +1676,7 @@ qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_
   for (int64_t ti = 0; ti < tiles; ++ti) {
     const int64_t pts = std::min<int64_t>(kTilePoints, c->point_num - ti * kTilePoints);
     for (int64_t q = 0; q < nq; ++q)
-      if (mask[ti * nq + q]) {
+      if (mask[ti * ld + q]) {
         ++live;
         entries += pts * (c->chunks[q].w - c->chunks[q].z);
       }
@@ -1695,8 +1695,8 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
     return fail(c, QK_ERR_NOT_PROVIDED,
                 "no AO tensor of the current points in a two-kernel tensor-core mode");
   const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
-  const int64_t tiles = ao_tiles(c), nq = t.nchunk;
-  std::vector<uint8_t> mask((size_t)(tiles * nq));
+  const int64_t tiles = ao_tiles(c), nq = t.nchunk, ld = mask_ld(t.nchunk);
+  std::vector<uint8_t> mask((size_t)(tiles * ld));
   // the counter lives in the second half of the 256-byte error-word buffer
   auto* cnt = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_flag.p) + 128);
   unsigned long long h = 0;
@@ -1707,7 +1707,8 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
   if (e == cudaSuccess) e = cudaMemcpy(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "sparsity count");
   int64_t g = 0;
-  for (uint8_t m : mask) g += __builtin_popcount(m & 0xFu);
+  for (int64_t ti = 0; ti < tiles; ++ti)
+    for (int64_t q = 0; q < nq; ++q) g += __builtin_popcount(mask[ti * ld + q] & 0xFu);
   *live_groups = g;
   *nnz = (int64_t)h;
   return QK_SUCCESS;

@@ -72,11 +72,15 @@ struct PointsDev {
 //
 // tiled (tensor-core modes): points go in tiles of kTilePoints; the 125
 // (point, component) rows of tile t are rows 128 t .. 128 t + 124, rows
-// 125..127 of each tile are zero, and bit g of mask[t * nchunk + q] says
-// whether columns 16 g .. 16 g + 15 of block (t, q) hold any entry that
-// survived screening.  Blocks with a zero mask byte are not written and the
+// 125..127 of each tile are zero, and bit g of mask[t * mask_ld(nchunk) + q]
+// says whether columns 16 g .. 16 g + 15 of block (t, q) hold any entry that
+// survived screening (rows padded to 16 bytes, so that a reader takes 16
+// chunks with one load; the padding bytes are never written).  Blocks with a zero mask byte are not written and the
 // contraction skips them, and its MMA k-steps over dead column groups (the
 // sparse-AO MO product of Sec. 3.2 at tile granularity).
+// Bytes per tile row of the live-group mask of a tiled AO tensor.
+__host__ __device__ inline int mask_ld(int nchunk) { return (nchunk + 15) & ~15; }
+
 struct AOTensor {
   void* a;        // FP64 / FP32 values, or bf16 "hi" plane
   void* a_lo;     // bf16 "lo" plane (QK_BF16X3 only)
@@ -84,7 +88,7 @@ struct AOTensor {
   int64_t ld;     // row stride in elements
   bool chunked;
   bool tiled;
-  uint8_t* mask;  // [tiles][nchunk] live 16-column groups when tiled
+  uint8_t* mask;  // [tiles][mask_ld(nchunk)] live 16-column groups when tiled
   int nchunk;
   // tiled, optional: [tiles][nchunk] bit s set when shell s of the chunk may
   // reach a point of the tile (filled by a pre-pass in launch_ao_vgl; NULL:
@@ -235,7 +239,7 @@ TcConfig tc_default_config(int mode, int64_t mo_num);
 struct TcProblem {
   CUtensorMap a, a_lo, b, b_lo;  // AO hi / lo, C hi / lo (lo = hi for TF32)
   float* D;                      // [M][N] output
-  const uint8_t* mask;           // tiled AO tensor: [tiles][nchunk] live blocks (else NULL)
+  const uint8_t* mask;           // tiled AO tensor: [tiles][mask_ld(nchunk)] (else NULL)
   const int32_t* perm;           // tiled AO tensor: point of each slot (NULL: identity)
   int64_t M, N;                  // output rows (5 * points) and columns
   int num_kb;                    // K blocks

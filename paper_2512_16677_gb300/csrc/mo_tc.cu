@@ -59,6 +59,13 @@ struct TcShape {
   static_assert(BN_MAX % 16 == 0 && BN_MAX >= 16 && BN_MAX <= 256, "MMA N: 16..256, step 16");
 };
 
+// Stage word from the TMA producer to the MMA thread: bits 0-3 the k-steps
+// to issue, kStageFirst / kStageLast on the first / last stage of a tile,
+// the tile's MMA N / 16 from bit kStageBnShift.
+constexpr uint32_t kStageFirst = 1u << 4;
+constexpr uint32_t kStageLast = 1u << 5;
+constexpr int kStageBnShift = 8;
+
 // One output tile as the three roles see it.
 struct TileInfo {
   const CUtensorMap* a;
@@ -78,25 +85,37 @@ struct TileInfo {
   float* rho;            // density epilogue: [N tiles][M] partial sums
 };
 
-// The MMA k-steps of K block kb (bit kk: k-step kk) that meet a nonzero AO.
-// The mask byte of a 64-column chunk has a bit per 16-column group.  A K
-// block of 64 bf16 columns is one chunk, its four k-steps of 16 one group
-// each; a K block of 32 TF32 columns is half kb & 1 of chunk kb >> 1, and
-// its k-steps of 8 take two per group.
+// The MMA k-steps of a K block: bit kk = k-step kk meets a nonzero AO.  The
+// mask byte of a 64-column chunk has a bit per 16-column group.  A K block
+// of 64 bf16 columns is one chunk, its four k-steps of 16 one group each; a
+// K block of 32 TF32 columns is half kb & 1 of chunk kb >> 1, and its
+// k-steps of 8 take two per group.
 template <int MODE>
-__device__ __forceinline__ uint32_t kb_steps(const TileInfo& x, int kb) {
-  if (x.kmask == nullptr) return 0xFu;
-  if constexpr (TcTraits<MODE>::kBK == 64) {
-    return x.kmask[kb] & 0xFu;
-  } else {
-    const uint32_t g = ((uint32_t)x.kmask[kb >> 1] >> (2 * (kb & 1))) & 3u;
-    return (g & 1u ? 0x3u : 0u) | (g & 2u ? 0xCu : 0u);
-  }
+constexpr int kb_per_chunk() {
+  return TcTraits<MODE>::kBK == 64 ? 1 : 2;
 }
 
+// Whether any chunk of the tile holds a live group (whole warp: lanes take
+// 16-chunk windows of the mask row; padding bytes past the last chunk are
+// never written and are ignored).
 template <int MODE>
-__device__ __forceinline__ bool kb_live(const TileInfo& x, int kb) {
-  return kb_steps<MODE>(x, kb) != 0u;
+__device__ __forceinline__ bool tile_live(const TileInfo& x, int lane) {
+  if (x.kmask == nullptr) return true;
+  const int nq = (x.num_kb + kb_per_chunk<MODE>() - 1) / kb_per_chunk<MODE>();
+  const uint4* row = reinterpret_cast<const uint4*>(x.kmask);
+  bool live = false;
+  for (int w = lane; 16 * w < nq; w += 32) {
+    const uint4 v = row[w];
+    const int valid = nq - 16 * w;  // bytes of this window that are chunks
+    const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int nb = valid - 4 * k;
+      const uint32_t keep = nb >= 4 ? 0x0F0F0F0Fu : (nb <= 0 ? 0u : (0x0F0F0F0Fu >> (8 * (4 - nb))));
+      live |= (wd[k] & keep) != 0u;
+    }
+  }
+  return __any_sync(0xffffffffu, live);
 }
 
 // One problem: tile t -> (m, n) = (t / n_tiles, t % n_tiles), N tile fastest
@@ -105,7 +124,7 @@ template <int BN>
 struct SingleSched {
   CUtensorMap a, a_lo, b, b_lo;
   float* D;
-  const uint8_t* mask;  // [m tiles][nchunk] when tiled
+  const uint8_t* mask;  // [m tiles][mask_ld(nchunk)] when tiled
   const int32_t* perm;
   const float* wdens;
   float* rho;
@@ -113,20 +132,28 @@ struct SingleSched {
   int num_kb, n_tiles, nchunk, rows_per_tile;
   bool tiled;
   __device__ __forceinline__ int64_t count() const { return total; }
+  // the tensor maps into the TMA unit's cache before the first copy
+  __device__ __forceinline__ void prefetch_maps() const {
+    tma_prefetch_map(&a);
+    tma_prefetch_map(&a_lo);
+    tma_prefetch_map(&b);
+    tma_prefetch_map(&b_lo);
+  }
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
     TileInfo x;
-    const int64_t mt = t / n_tiles;
+    const int64_t mt =
+        total <= 0x7fffffff ? (int64_t)((uint32_t)t / (uint32_t)n_tiles) : t / n_tiles;
     x.a = &a;
     x.a_lo = &a_lo;
     x.b = &b;
     x.b_lo = &b_lo;
     x.D = D;
-    x.kmask = tiled ? mask + mt * nchunk : nullptr;
+    x.kmask = tiled ? mask + mt * mask_ld(nchunk) : nullptr;
     x.perm = perm;
     x.M = M;
     x.N = N;
     x.m0 = (int)(mt * kBM);
-    x.n0 = (int)((t % n_tiles) * BN);
+    x.n0 = (int)((t - mt * n_tiles) * BN);
     x.num_kb = num_kb;
     x.bn = BN;
     x.tiled = tiled;
@@ -144,6 +171,7 @@ struct BatchSched {
   const int4* items;
   int64_t n_items;
   __device__ __forceinline__ int64_t count() const { return n_items; }
+  __device__ __forceinline__ void prefetch_maps() const {}  // maps differ per problem
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
     const int4 it = items[t];
     const TcProblem& p = probs[it.x];
@@ -153,7 +181,7 @@ struct BatchSched {
     x.b = &p.b;
     x.b_lo = &p.b_lo;
     x.D = p.D;
-    x.kmask = p.mask ? p.mask + (int64_t)it.y * p.nchunk : nullptr;
+    x.kmask = p.mask ? p.mask + (int64_t)it.y * mask_ld(p.nchunk) : nullptr;
     x.perm = p.perm;
     x.M = p.M;
     x.N = p.N;
@@ -189,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ uint32_t stage_info[STAGES];  // producer -> MMA, per stage (see kStageFirst)
   __shared__ __align__(16) float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
@@ -227,34 +256,96 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 4 && lane == 0) {
-    // ------------------------------------------------ TMA producer
+  if (warp == 4) {
+    // ------------------------------------------------ TMA producer (warp)
+    // Walks the tiles' live K blocks (blocks of screened AOs are never read)
+    // and tells the MMA thread, per stage, which k-steps to issue and where
+    // tiles begin and end; a tile with no live block still takes one stage
+    // (no copies, no MMAs) so that the MMA thread walks stages only.  The
+    // lanes read the mask bytes of 32 chunks at once; lane 0 takes the
+    // barriers and lanes 0..2 kPlanes - 1 issue the stage's copies together.
+    constexpr int kPer = kb_per_chunk<MODE>();  // K blocks per chunk
+    if (lane == 0) sched.prefetch_maps();
     uint32_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const TileInfo x = sched.tile(t);
       const uint32_t bytes = TR::kPlanes * (S::A_BYTES + (uint32_t)x.bn * kRowBytes);
-      for (int kb = 0; kb < x.num_kb; ++kb) {
-        if (!kb_live<MODE>(x, kb)) continue;  // block of screened AOs: never read
+      const int nq = (x.num_kb + kPer - 1) / kPer;  // chunks (the last may be half one)
+      auto groups_of = [&](int q) -> uint32_t {
+        if (q >= nq) return 0u;
+        return x.kmask ? (uint32_t)x.kmask[q] & 0xFu : 0xFu;
+      };
+      // the tile's last live K block (-1: none)
+      int lastkb = -1;
+      for (int q0 = 0; q0 < nq; q0 += 32) {
+        const uint32_t g = groups_of(q0 + lane);
+        const unsigned live = __ballot_sync(0xffffffffu, g != 0u);
+        if (live) {
+          const int j = 31 - __clz(live);
+          const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+          lastkb = (q0 + j) * kPer + ((kPer == 2 && (gj & 0xCu)) ? 1 : 0);
+        }
+      }
+      if (lastkb >= x.num_kb) lastkb = x.num_kb - 1;  // no mask, odd K block count
+      // this lane's copy of a stage: plane (lane % kPlanes) of A (lanes
+      // below kPlanes) or of B
+      const bool copier = lane < 2 * TR::kPlanes;
+      const bool of_b = lane >= TR::kPlanes;
+      const int plane = lane % TR::kPlanes;
+      const CUtensorMap* map = of_b ? (plane ? x.b_lo : x.b) : (plane ? x.a_lo : x.a);
+      const uint32_t dst_off = of_b ? TR::kPlanes * S::A_BYTES + plane * S::B_BYTES
+                                    : plane * S::A_BYTES;
+      const int row0 = of_b ? x.n0 : x.m0;
+      uint32_t flags = kStageFirst | ((uint32_t)(x.bn >> 4) << kStageBnShift);
+      // one stage: wait for the slot, post the stage word, issue the copies
+      auto stage = [&](int kb, uint32_t steps, bool last) -> bool {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         ++it;
-        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
-          flag_error(err_flag, abort_v, 1);
-          ok = false;
-          break;
+        bool got = true;
+        if (lane == 0) got = mbar_wait(empty_bar(s), ph ^ 1u, abort_v);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          if (lane == 0) flag_error(err_flag, abort_v, 1);
+          return false;
         }
-        const uint32_t st = base + s * S::STAGE_BYTES;
-        mbar_expect_tx(full_bar(s), bytes);
-        const int kc = kb * TR::kBK;
-        tma_load_2d(st, x.a, full_bar(s), kc, x.m0);
-        if constexpr (TR::kPlanes == 2) tma_load_2d(st + S::A_BYTES, x.a_lo, full_bar(s), kc, x.m0);
-        const uint32_t bst = st + TR::kPlanes * S::A_BYTES;
-        tma_load_2d(bst, x.b, full_bar(s), kc, x.n0);
-        if constexpr (TR::kPlanes == 2) tma_load_2d(bst + S::B_BYTES, x.b_lo, full_bar(s), kc, x.n0);
+        if (lane == 0) {
+          stage_info[s] = steps | flags | (last ? kStageLast : 0u);
+          mbar_expect_tx(full_bar(s), kb >= 0 ? bytes : 0u);
+        }
+        flags = 0;
+        __syncwarp();
+        if (kb >= 0 && copier)
+          tma_load_2d(base + s * S::STAGE_BYTES + dst_off, map, full_bar(s), kb * TR::kBK, row0);
+        return true;
+      };
+      if (lastkb < 0) {
+        ok = stage(-1, 0u, true);
+        continue;
+      }
+      for (int q0 = 0; q0 < nq && ok; q0 += 32) {
+        const uint32_t g = groups_of(q0 + lane);
+        unsigned live = __ballot_sync(0xffffffffu, g != 0u);
+        while (live && ok) {
+          const int j = __ffs(live) - 1;
+          live &= live - 1u;
+          const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+#pragma unroll
+          for (int h = 0; h < kPer; ++h) {
+            uint32_t steps = gj;
+            if constexpr (kPer == 2) {
+              const uint32_t hh = (gj >> (2 * h)) & 3u;
+              steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+            }
+            const int kb = (q0 + j) * kPer + h;
+            if (!steps || !ok || kb >= x.num_kb) continue;
+            ok = stage(kb, steps, kb == lastkb);
+          }
+        }
       }
     }
-    if (*abort_v) {
+    if (lane == 0 && *abort_v) {
       // drain: let the copies already issued land before the CTA leaves
       const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
       for (uint32_t k = first; k < it; ++k) {
@@ -266,60 +357,82 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 5 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    uint32_t it = 0, i = 0;
-    bool ok = true;
-    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
-      const TileInfo x = sched.tile(t);
-      const uint32_t idesc = make_idesc(TR::kFmt, kBM, x.bn);
-      const uint32_t b = i % NBUF;
-      if (!mbar_wait(tempty_bar(b), ((i / NBUF) & 1u) ^ 1u, abort_v)) {
+    // Stage by stage: the producer's stage word gives the k-steps to issue
+    // and marks the first and last stage of each tile.  Descriptors are
+    // those of stage 0 plus the byte offset / 16 (the start-address field
+    // cannot carry: shared addresses stay below 256 KB).
+    const int64_t my_tiles =
+        total > (int64_t)blockIdx.x ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint64_t d0 = sw128_desc(base);
+    uint32_t it = 0, i = 0, b = 0, dacc = tmem, idesc = 0;
+    bool first = true, in_tile = false, ok = true;
+    while ((int64_t)i < my_tiles) {
+      const int s = it % STAGES;
+      const uint32_t ph = (it / STAGES) & 1u;
+      ++it;
+      if (!mbar_wait(full_bar(s), ph, abort_v)) {
         flag_error(err_flag, abort_v, 2);
+        ok = false;
         break;
       }
-      tc_fence_after();
-      const uint32_t dacc = tmem + b * ACC;
-      bool first = true;  // the tile's first MMA overwrites the accumulator
-      for (int kb = 0; kb < x.num_kb; ++kb) {
-        const uint32_t steps = kb_steps<MODE>(x, kb);
-        if (!steps) continue;
-        const int s = it % STAGES;
-        const uint32_t ph = (it / STAGES) & 1u;
-        ++it;
-        if (!mbar_wait(full_bar(s), ph, abort_v)) {
+      const uint32_t info = stage_info[s];
+      if (info & kStageFirst) {
+        b = i % NBUF;
+        if (!mbar_wait(tempty_bar(b), ((i / NBUF) & 1u) ^ 1u, abort_v)) {
           flag_error(err_flag, abort_v, 2);
           ok = false;
           break;
         }
-        tc_fence_after();
-        const uint32_t st = base + s * S::STAGE_BYTES;
-        const uint32_t a_hi = st;
-        const uint32_t a_lo = st + S::A_BYTES;
-        const uint32_t b_hi = st + TR::kPlanes * S::A_BYTES;
-        const uint32_t b_lo = b_hi + S::B_BYTES;
-#pragma unroll
-        for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
-          // k-steps over AO columns that are zero at every row of the tile
-          // would add exact zeros
-          if (!((steps >> kk) & 1u)) continue;
-          const uint32_t koff = kk * kUmmaKBytes;
-          const uint32_t acc = first ? 0u : 1u;
-          first = false;
-          umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_hi + koff), idesc, acc);
-          if constexpr (MODE == QK_BF16X3) {
-            umma<MODE>(dacc, sw128_desc(a_hi + koff), sw128_desc(b_lo + koff), idesc, 1u);
-            umma<MODE>(dacc, sw128_desc(a_lo + koff), sw128_desc(b_hi + koff), idesc, 1u);
-          }
-        }
-        umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
+        in_tile = true;
+        dacc = tmem + b * ACC;
+        idesc = make_idesc(TR::kFmt, kBM, (int)((info >> kStageBnShift) << 4));
+        first = true;  // the tile's first MMA overwrites the accumulator
       }
-      // accumulator b complete (after an abort this still waits for the MMAs
-      // already issued, so the epilogue never reads a buffer being written)
-      umma_commit(tfull_bar(b));
-      if (!ok) {
-        // aborted: wait for the MMAs in flight before TMEM can be freed
-        const long long t0 = clock64();
-        while (!mbar_try_wait(tfull_bar(b), (i / NBUF) & 1u) && clock64() - t0 < kWaitCycles) {
+      tc_fence_after();
+      const uint64_t da = d0 + ((uint64_t)(s * S::STAGE_BYTES) >> 4);
+      const uint64_t da_lo = da + (S::A_BYTES >> 4);
+      const uint64_t db = da + ((TR::kPlanes * S::A_BYTES) >> 4);
+      const uint64_t db_lo = db + (S::B_BYTES >> 4);
+#pragma unroll
+      for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
+        // k-steps over AO columns that are zero at every row of the tile
+        // would add exact zeros
+        if (!((info >> kk) & 1u)) continue;
+        const uint64_t ko = (uint64_t)(kk * kUmmaKBytes) >> 4;
+        const uint32_t acc = first ? 0u : 1u;
+        first = false;
+        umma<MODE>(dacc, da + ko, db + ko, idesc, acc);
+        if constexpr (MODE == QK_BF16X3) {
+          umma<MODE>(dacc, da + ko, db_lo + ko, idesc, 1u);
+          umma<MODE>(dacc, da_lo + ko, db + ko, idesc, 1u);
         }
+      }
+      umma_commit(empty_bar(s));  // stage s is free once these MMAs finish
+      if (info & kStageLast) {
+        umma_commit(tfull_bar(b));  // accumulator b complete
+        in_tile = false;
+        ++i;
+      }
+    }
+    if (!ok) {
+      // aborted: the MMAs in flight must finish before TMEM can be freed;
+      // a tile cut short still gets its commit (the epilogue sees the abort
+      // flag and does not read it)
+      uint32_t wb = 0, wi = 0;
+      bool wait = false;
+      if (in_tile) {
+        umma_commit(tfull_bar(b));
+        wb = b;
+        wi = i;
+        wait = true;
+      } else if (i > 0) {
+        wb = (i - 1) % NBUF;
+        wi = i - 1;
+        wait = true;
+      }
+      const long long t0 = clock64();
+      while (wait && !mbar_try_wait(tfull_bar(wb), (wi / NBUF) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
       }
     }
   } else if (warp < 4) {
@@ -341,8 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       tc_fence_after();
       const TileInfo x = sched.tile(t);
-      bool any_live = x.kmask == nullptr;
-      for (int kb = 0; kb < x.num_kb && !any_live; ++kb) any_live = kb_live<MODE>(x, kb);
+      const bool any_live = tile_live<MODE>(x, lane);
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
       const int64_t N = x.N;
       // store phase: lane -> row 8 i + lane / 4 of the warp's 32, columns
