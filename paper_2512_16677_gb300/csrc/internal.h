@@ -237,7 +237,7 @@ TcConfig tc_default_config(int mode, int64_t mo_num);
 // tensor maps, 64-byte aligned by their type, are written by the host
 // before the launch).
 struct TcProblem {
-  CUtensorMap a, a_lo, b, b_lo;  // AO hi / lo, C hi / lo (lo = hi for TF32)
+  CUtensorMap a, b;  // AO and C; QK_BF16X3: 3-D maps over the hi and lo planes
   float* D;                      // [M][N] output
   const uint8_t* mask;           // tiled AO tensor: [tiles][mask_ld(nchunk)] (else NULL)
   const int32_t* perm;           // tiled AO tensor: point of each slot (NULL: identity)

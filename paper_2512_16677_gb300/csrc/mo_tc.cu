@@ -61,17 +61,16 @@ struct TcShape {
 
 // Stage word from the TMA producer to the MMA thread: bits 0-3 the k-steps
 // to issue, kStageFirst / kStageLast on the first / last stage of a tile,
-// the tile's MMA N / 16 from bit kStageBnShift.
+// the tile's MMA N / 16 from bit kStageBnShift (on every stage: the C lo
+// plane sits N rows after the hi plane).
 constexpr uint32_t kStageFirst = 1u << 4;
 constexpr uint32_t kStageLast = 1u << 5;
 constexpr int kStageBnShift = 8;
 
 // One output tile as the three roles see it.
 struct TileInfo {
-  const CUtensorMap* a;
-  const CUtensorMap* a_lo;
-  const CUtensorMap* b;
-  const CUtensorMap* b_lo;
+  const CUtensorMap* a;  // AO tiles (QK_BF16X3: hi and lo planes in one 3-D map)
+  const CUtensorMap* b;  // C tiles (likewise)
   float* D;
   const uint8_t* kmask;  // live 16-column groups of this M tile's chunks (NULL: all)
   const int32_t* perm;   // tiled: point of each slot (NULL: slot = point)
@@ -122,7 +121,7 @@ __device__ __forceinline__ bool tile_live(const TileInfo& x, int lane) {
 // so that the N tiles of one M tile run together and share A through L2.
 template <int BN>
 struct SingleSched {
-  CUtensorMap a, a_lo, b, b_lo;
+  CUtensorMap a, b;
   float* D;
   const uint8_t* mask;  // [m tiles][mask_ld(nchunk)] when tiled
   const int32_t* perm;
@@ -135,18 +134,14 @@ struct SingleSched {
   // the tensor maps into the TMA unit's cache before the first copy
   __device__ __forceinline__ void prefetch_maps() const {
     tma_prefetch_map(&a);
-    tma_prefetch_map(&a_lo);
     tma_prefetch_map(&b);
-    tma_prefetch_map(&b_lo);
   }
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
     TileInfo x;
     const int64_t mt =
         total <= 0x7fffffff ? (int64_t)((uint32_t)t / (uint32_t)n_tiles) : t / n_tiles;
     x.a = &a;
-    x.a_lo = &a_lo;
     x.b = &b;
-    x.b_lo = &b_lo;
     x.D = D;
     x.kmask = tiled ? mask + mt * mask_ld(nchunk) : nullptr;
     x.perm = perm;
@@ -177,9 +172,7 @@ struct BatchSched {
     const TcProblem& p = probs[it.x];
     TileInfo x;
     x.a = &p.a;
-    x.a_lo = &p.a_lo;
     x.b = &p.b;
-    x.b_lo = &p.b_lo;
     x.D = p.D;
     x.kmask = p.mask ? p.mask + (int64_t)it.y * mask_ld(p.nchunk) : nullptr;
     x.perm = p.perm;
@@ -263,7 +256,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // tiles begin and end; a tile with no live block still takes one stage
     // (no copies, no MMAs) so that the MMA thread walks stages only.  The
     // lanes read the mask bytes of 32 chunks at once; lane 0 takes the
-    // barriers and lanes 0..2 kPlanes - 1 issue the stage's copies together.
+    // barriers and lanes 0 and 1 issue the stage's two copies (AO, C; each
+    // both planes in QK_BF16X3) together.
     constexpr int kPer = kb_per_chunk<MODE>();  // K blocks per chunk
     if (lane == 0) sched.prefetch_maps();
     uint32_t it = 0;
@@ -288,16 +282,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (lastkb >= x.num_kb) lastkb = x.num_kb - 1;  // no mask, odd K block count
-      // this lane's copy of a stage: plane (lane % kPlanes) of A (lanes
-      // below kPlanes) or of B
-      const bool copier = lane < 2 * TR::kPlanes;
-      const bool of_b = lane >= TR::kPlanes;
-      const int plane = lane % TR::kPlanes;
-      const CUtensorMap* map = of_b ? (plane ? x.b_lo : x.b) : (plane ? x.a_lo : x.a);
-      const uint32_t dst_off = of_b ? TR::kPlanes * S::A_BYTES + plane * S::B_BYTES
-                                    : plane * S::A_BYTES;
-      const int row0 = of_b ? x.n0 : x.m0;
-      uint32_t flags = kStageFirst | ((uint32_t)(x.bn >> 4) << kStageBnShift);
+      // this lane's copy of a stage: lane 0 the AO tile, lane 1 the C tile
+      const bool copier = lane < 2;
+      const CUtensorMap* map = lane ? x.b : x.a;
+      const uint32_t dst_off = lane ? TR::kPlanes * S::A_BYTES : 0u;
+      const int row0 = lane ? x.n0 : x.m0;
+      const uint32_t bn_bits = (uint32_t)(x.bn >> 4) << kStageBnShift;  // on every stage
+      uint32_t flags = kStageFirst;
       // one stage: wait for the slot, post the stage word, issue the copies
       auto stage = [&](int kb, uint32_t steps, bool last) -> bool {
         const int s = it % STAGES;
@@ -311,13 +302,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           return false;
         }
         if (lane == 0) {
-          stage_info[s] = steps | flags | (last ? kStageLast : 0u);
+          stage_info[s] = steps | flags | bn_bits | (last ? kStageLast : 0u);
           mbar_expect_tx(full_bar(s), kb >= 0 ? bytes : 0u);
         }
         flags = 0;
         __syncwarp();
-        if (kb >= 0 && copier)
-          tma_load_2d(base + s * S::STAGE_BYTES + dst_off, map, full_bar(s), kb * TR::kBK, row0);
+        if (kb >= 0 && copier) {
+          const uint32_t dst = base + s * S::STAGE_BYTES + dst_off;
+          if constexpr (TR::kPlanes == 2)
+            tma_load_3d(dst, map, full_bar(s), kb * TR::kBK, row0, 0);
+          else
+            tma_load_2d(dst, map, full_bar(s), kb * TR::kBK, row0);
+        }
         return true;
       };
       if (lastkb < 0) {
@@ -392,7 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t da = d0 + ((uint64_t)(s * S::STAGE_BYTES) >> 4);
       const uint64_t da_lo = da + (S::A_BYTES >> 4);
       const uint64_t db = da + ((TR::kPlanes * S::A_BYTES) >> 4);
-      const uint64_t db_lo = db + (S::B_BYTES >> 4);
+      // the C lo plane follows the hi plane's bn rows (one 3-D box)
+      const uint64_t db_lo = db + ((((info >> kStageBnShift) << 4) * kRowBytes) >> 4);
 #pragma unroll
       for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
         // k-steps over AO columns that are zero at every row of the tile
@@ -590,14 +587,13 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
   if (ao.tiled && M % kBM != 0) return cudaErrorInvalidValue;
   SingleSched<BN> sc;
-  if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
   if (TR::kPlanes == 2) {
-    if (!make_map(&sc.a_lo, ao.a_lo, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
-    if (!make_map(&sc.b_lo, c_lo, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+    if (!make_map_planes(&sc.a, ao.a, ao.a_lo, K, M, ao.ld, TR::kBK, kBM))
+      return cudaErrorInvalidValue;
+    if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
   } else {
-    sc.a_lo = sc.a;
-    sc.b_lo = sc.b;
+    if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
   }
   sc.D = out;
   sc.mask = ao.tiled ? ao.mask : nullptr;
@@ -694,14 +690,12 @@ bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, 
   const int bk = f32 ? TcTraits<QK_TF32>::kBK : TcTraits<QK_BF16X3>::kBK;
   if (bn % 16 != 0 || bn < 16 || bn > 256) return false;
   if (ao.rows > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return false;
-  if (!make_map(&p->a, ao.a, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
-  if (!make_map(&p->b, c_hi, f32, K, N, ldc, bk, bn)) return false;
   if (!f32) {
-    if (!make_map(&p->a_lo, ao.a_lo, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
-    if (!make_map(&p->b_lo, c_lo, f32, K, N, ldc, bk, bn)) return false;
+    if (!make_map_planes(&p->a, ao.a, ao.a_lo, K, ao.rows, ao.ld, bk, kBM)) return false;
+    if (!make_map_planes(&p->b, c_hi, c_lo, K, N, ldc, bk, bn)) return false;
   } else {
-    p->a_lo = p->a;
-    p->b_lo = p->b;
+    if (!make_map(&p->a, ao.a, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
+    if (!make_map(&p->b, c_hi, f32, K, N, ldc, bk, bn)) return false;
   }
   p->D = out;
   p->mask = ao.tiled ? ao.mask : nullptr;

@@ -69,6 +69,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   return true;
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // Fetch a tensor map (kernel parameter or global memory) into the TMA
 // unit's descriptor cache.
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
@@ -190,6 +199,25 @@ inline bool make_map(CUtensorMap* m, const void* ptr, bool f32, int64_t inner, i
              const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The bf16 hi and lo planes of one matrix as a 3-D map (plane = third
+// dimension, stride lo - hi bytes), so that one copy brings a box of both
+// planes: plane 0 then plane 1, box_outer rows of 128 bytes each.  False if
+// lo does not follow hi at a positive multiple of 16 bytes.
+inline bool make_map_planes(CUtensorMap* m, const void* hi, const void* lo, int64_t inner,
+                            int64_t outer, int64_t ld, int box_inner, int box_outer) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const intptr_t gap = (const char*)lo - (const char*)hi;
+  if (gap <= 0 || gap % 16 != 0) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, 2};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)gap};
+  cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer, 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(hi), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace tc
