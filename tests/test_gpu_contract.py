@@ -13,8 +13,9 @@ pytestmark = pytest.mark.gpu
 
 # normwise bound |D - ref| / (|A| |B|^T) per mode (see tests/tolerances.py)
 TOL = {"fp64": 1e-14, "fp32": 2e-5, "bf16x3": 3e-5, "tf32": 3e-3}
+# MO counts on either side of the 160-column N tile and of two of them
 SHAPES = [(128, 16, 64), (200, 37, 70), (1000, 5, 25), (257, 256, 129), (300, 100, 500),
-          (513, 300, 1650)]
+          (513, 300, 1650), (390, 161, 200), (129, 304, 96), (200, 320, 300)]
 
 
 @pytest.fixture(scope="module", autouse=True)
