@@ -499,15 +499,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                       : -1;
       }
       float(*stg)[kEpiPitch] = epi[warp];
-#pragma unroll 1
-      for (int c = 0; c < x.bn; c += 16) {
-        float v[16];
-        if (any_live) {
-          tmem_ld16(tbase + c, v);
-        } else {  // every AO of the tile was screened: the MOs are exactly zero
+      float* rowp[4];  // start of each output row of this lane
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-        }
+      for (int i = 0; i < 4; ++i) rowp[i] = x.D + (orow[i] >= 0 ? orow[i] : 0) * N;
+      // one 16-column slice through the staging buffer to D
+      auto store_slice = [&](const float* v, int c) {
         float4* srow = reinterpret_cast<float4*>(&stg[lane][0]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -518,11 +514,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = 8 * i + rq;
-          const int64_t row = orow[i];
-          if (row >= 0) {
+          if (orow[i] >= 0) {
             const float4 w =
                 reinterpret_cast<const float4*>(&stg[r][0])[(lane & 3) ^ ((r >> 1) & 3)];
-            float* dst = x.D + row * N + col;
+            float* dst = rowp[i] + col;
             if (vec && col + 3 < N) {
               *reinterpret_cast<float4*>(dst) = w;
             } else {
@@ -534,6 +529,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         __syncwarp();
+      };
+      // 32 columns per TMEM round trip (two loads, one wait)
+#pragma unroll 1
+      for (int c = 0; c < x.bn; c += 32) {
+        const bool two = c + 16 < x.bn;
+        float v[32];
+        if (any_live) {
+          tmem_ld16x2(tbase + c, v, two);
+        } else {  // every AO of the tile was screened: the MOs are exactly zero
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+        }
+        store_slice(v, c);
+        if (two) store_slice(v + 16, c + 16);
       }
       tc_fence_before();
       __syncwarp();
