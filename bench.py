@@ -128,10 +128,14 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
 
     Dense modes: every (point, AO) entry.  Tensor-core modes skip blocks of
     screened AOs: ao_vgl's algorithmic bytes are those of the live blocks'
-    (point, AO) entries (stats = (live blocks, all blocks, live entries)),
-    and the contraction's algorithmic flops are 2 * 5 * mo_num * nnz with
-    nnz the nonzero (point, AO) pairs (sparsity = (live 16-AO groups, nnz)).
-    The padded work the kernels actually move or issue is reported beside it.
+    (point, AO) entries (stats = (live blocks, all blocks, live entries)).
+    The contraction's algorithmic work is the sparse product of Sec. 3.2:
+    2 * 5 * mo_num * nnz flops (x3 for the bf16 split) with nnz the nonzero
+    (point, AO) pairs (sparsity = (live 16-AO groups, nnz)), over the bytes
+    it must move (nonzero AO entries, C, the FP32 output).  Its bound is the
+    roofline whose floor is longer (arithmetic intensity against the ridge
+    point); both fractions are given.  The padded work the kernels actually
+    move or issue is reported beside it.
     """
     P, na, nm = mol.point_num, mol.ao_num, mol.mo_num
     es = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode]
@@ -153,39 +157,50 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
             out["ao_vgl"]["live_block_fraction"] = stats[0] / stats[1]
     t_mo = ms_per_launch[1] * 1e-3
     if t_mo > 0:
-        if mode == "bf16x3":
-            fl = 3 * useful
-            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-            out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                                     "peak_note": "measured bf16 sustained"}
-        elif mode == "tf32":
-            fl = useful
-            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 0.5
-            out["mo_contraction"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                                     "peak_note": "measured bf16 sustained x 1/2 (tf32/bf16 "
-                                                  "nominal ratio)"}
-        elif mode == "fp32":
-            fl = useful
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-                                     "peak_note": "152 SMs x 128 FP32 FMA/clk x max clock"}
+        hbm = peaks["hbm_gbs"]
+        if mode in ("bf16x3", "tf32"):
+            tensor = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            if mode == "bf16x3":
+                fl, tnote = 3 * useful, "measured bf16 sustained"
+            else:
+                fl, tensor = useful, tensor * 0.5
+                tnote = "measured bf16 sustained x 1/2 (tf32/bf16 nominal ratio)"
+            # what the sparse product must move: the nonzero AO entries (both
+            # bf16 planes, or FP32), C once, and the FP32 output
+            nbytes = 4.0 * 5 * nnz + 4.0 * nm * na + 4.0 * 5 * P * nm
+            t_hbm, t_tc = nbytes / (hbm * 1e9), fl / (tensor * 1e12)
+            ent = {"algorithmic_flops": fl, "algorithmic_bytes": nbytes,
+                   "arithmetic_intensity": fl / nbytes,
+                   "ridge_flop_per_byte": tensor * 1e12 / (hbm * 1e9),
+                   "dense_equivalent_flops": dense * (3 if mode == "bf16x3" else 1),
+                   "tensor": {"achieved": fl / t_mo / 1e12, "peak": tensor, "unit": "TFLOP/s",
+                              "frac": t_tc / t_mo, "peak_note": tnote},
+                   "hbm": {"achieved": nbytes / t_mo / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": t_hbm / t_mo, "peak_note": "measured copy"}}
+            # the roofline that binds is the one whose floor is the longer
+            bound = "hbm" if t_hbm >= t_tc else "tensor"
+            ent.update({"bound": bound, **{k: ent[bound][k] for k in
+                                           ("achieved", "peak", "unit", "frac", "peak_note")}})
+            if sparsity is not None:
+                # one 128 x 16 x N_pad k-step per live (tile, 16-AO group)
+                n_pad = -(-nm // 160) * 160
+                issued = sparsity[0] * 128 * 16 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
+                ent["nnz_fraction"] = nnz / (P * na)
+                ent["issued_flops"] = issued
+                ent["issued_tflops"] = issued / t_mo / 1e12
+                ent["issued_frac"] = issued / t_mo / 1e12 / tensor
+            out["mo_contraction"] = ent
         else:
-            fl = useful
-            peak = 1.25
+            if mode == "fp32":
+                peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                note = "152 SMs x 128 FP32 FMA/clk x max clock"
+            else:
+                peak, note = 1.25, "nominal GB300 FP64"
+            a = useful / t_mo / 1e12
             out["mo_contraction"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-                                     "peak_note": "nominal GB300 FP64"}
-        a = fl / t_mo / 1e12
-        out["mo_contraction"].update({"achieved": a, "frac": a / peak, "algorithmic_flops": fl,
-                                      "dense_equivalent_flops": dense * (3 if mode == "bf16x3"
-                                                                          else 1)})
-        if sparsity is not None:
-            # one 128 x 16 x N_pad k-step per live (tile, 16-AO group)
-            n_pad = -(-nm // 160) * 160
-            issued = sparsity[0] * 128 * 16 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
-            out["mo_contraction"]["nnz_fraction"] = nnz / (P * na)
-            out["mo_contraction"]["issued_flops"] = issued
-            out["mo_contraction"]["issued_tflops"] = issued / t_mo / 1e12
-            out["mo_contraction"]["issued_frac"] = issued / t_mo / 1e12 / peak
+                                     "peak_note": note, "achieved": a, "frac": a / peak,
+                                     "algorithmic_flops": useful,
+                                     "dense_equivalent_flops": dense}
     return out
 
 
