@@ -25,8 +25,11 @@
 //            screened one ends the loop) gives S_0..S_2, and every Cartesian
 //            component of the shell follows with compile-time exponents
 //            into a shared staging tile [5 points][64 AOs]
-//   phase 2  copy-out: one warp per (point, component) row, lanes over the
-//            64 columns, converted to the output type.
+//   phase 2  copy-out, converted to the output type: in the tiled layout a
+//            lane takes 8 (bf16 planes) or 4 (FP32) consecutive columns of a
+//            row and writes them with 16-byte stores, skipping dead 16-AO
+//            groups; otherwise one warp per (point, component) row, lanes
+//            over the 64 columns.
 // In the contraction layout (AOTensor::chunked) chunk q owns the 64 columns
 // [64q, 64q + 64) of the AO tensor, padding included, so each warp store is
 // an aligned row segment, and the contraction's K blocks coincide with the
@@ -131,19 +134,59 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
       const unsigned gm = sh.gmask;
       if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
       if (!gm) continue;
+      // ---- phase 2, tiled: all 128 rows (stage rows 125..127 belong to the
+      // lane past the tile and hold zeros) in 16-byte stores; the columns of
+      // dead 16-AO groups are not written (the contraction never reads them)
+      const int64_t row0 = ptile * kTileRows;
+      if constexpr (kSplit) {
+        // a lane splits 8 consecutive columns of one row into 16 bytes of each
+        // bf16 plane: hi = rn(v), lo = rn(v - hi); a warp covers 4 rows
+        const int rsub = lane >> 3, c8 = lane & 7;
+        const bool store = (gm >> (c8 >> 1)) & 1u;
+#pragma unroll
+        for (int it = 0; it < kTileRows / (4 * kWarps); ++it) {
+          const int r = 4 * (warp + kWarps * it) + rsub;
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float v0 = sh.stage[r][8 * c8 + 2 * j];
+            const float v1 = sh.stage[r][8 * c8 + 2 * j + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+            memcpy(&hw[j], &h, 4);
+            memcpy(&lw[j], &l, 4);
+          }
+          if (store) {
+            const int64_t e = (row0 + r) * out.ld + col0 + 8 * c8;
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a) + e) =
+                make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a_lo) + e) =
+                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+        }
+      } else {
+        // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
+        const int rsub = lane >> 4, c4 = lane & 15;
+        const bool store = (gm >> (c4 >> 2)) & 1u;
+#pragma unroll
+        for (int it = 0; it < kTileRows / (2 * kWarps); ++it) {
+          const int r = 2 * (warp + kWarps * it) + rsub;
+          const float4 w = make_float4(sh.stage[r][4 * c4], sh.stage[r][4 * c4 + 1],
+                                       sh.stage[r][4 * c4 + 2], sh.stage[r][4 * c4 + 3]);
+          if (store)
+            *reinterpret_cast<float4*>(static_cast<float*>(out.a) + (row0 + r) * out.ld + col0 +
+                                       4 * c4) = w;
+        }
+      }
+      continue;
     }
     // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
-    // lane + 32.  Tiled: all 128 rows (stage rows 125..127 belong to the
-    // lane past the tile and hold zeros).
-    constexpr int kRows = kTiled ? kTileRows : 5 * kPT;
+    // lane + 32.
+    constexpr int kRows = 5 * kPT;
     for (int r = warp; r < kRows; r += kWarps) {
-      int64_t grow;
-      if constexpr (kTiled) {
-        grow = ptile * kTileRows + r;
-      } else {
-        if (p0 + r / 5 >= n) break;
-        grow = 5 * p0 + r;
-      }
+      if (p0 + r / 5 >= n) break;
+      const int64_t grow = 5 * p0 + r;
       const T v0 = sh.stage[r][lane];
       const T v1 = sh.stage[r][lane + 32];
       if constexpr (kSplit) {
@@ -358,7 +401,8 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 // Nonzero (point, AO) pairs of a tiled vgl AO tensor: the AO of a point
 // counts when any of its five rows holds a nonzero entry at that column
 // (either bf16 plane when split; the sign bit ignored).  Blocks whose mask
-// byte is zero were not written and count nothing.  Statistics only.
+// byte is zero, and the dead 16-AO groups of live blocks, were not written
+// and count nothing.  Statistics only.
 template <bool kSplit>
 __global__ void __launch_bounds__(256)
     ao_nnz_kernel(AOTensor t, int64_t n, int64_t tiles, unsigned long long* out) {
@@ -370,11 +414,13 @@ __global__ void __launch_bounds__(256)
   for (int64_t bi = blockIdx.x; bi < blocks; bi += gridDim.x) {
     const int64_t tile = bi / t.nchunk;
     const int q = (int)(bi % t.nchunk);
-    if (t.mask[tile * mask_ld(t.nchunk) + q] == 0) continue;
+    const unsigned gm = t.mask[tile * mask_ld(t.nchunk) + q];
+    if (gm == 0) continue;
     const int64_t left = n - tile * kTilePoints;
     const int pts = left < kTilePoints ? (int)left : kTilePoints;
     for (int i = threadIdx.x; i < pts * kChunkAO; i += blockDim.x) {
       const int j = i / kChunkAO, c = i % kChunkAO;
+      if (!((gm >> (c >> 4)) & 1u)) continue;  // dead groups are not written
       const int64_t e0 = (tile * kTileRows + 5 * j) * t.ld + (int64_t)q * kChunkAO + c;
       bool nz = false;
 #pragma unroll

@@ -65,6 +65,9 @@ struct PointsDev {
   int64_t ld;       // distance between the coordinate planes of hi and lo
 };
 
+// Bytes per tile row of the live-group mask of a tiled AO tensor.
+__host__ __device__ inline int mask_ld(int nchunk) { return (nchunk + 15) & ~15; }
+
 // Layout of the AO tensor: rows are (point, component) pairs, row r = 5p + c,
 // ld elements apart.  chunked: AO n of chunk q sits in column
 // 64q + (n - first AO of q) and the padding columns hold zeros (the layout the
@@ -75,12 +78,10 @@ struct PointsDev {
 // 125..127 of each tile are zero, and bit g of mask[t * mask_ld(nchunk) + q]
 // says whether columns 16 g .. 16 g + 15 of block (t, q) hold any entry that
 // survived screening (rows padded to 16 bytes, so that a reader takes 16
-// chunks with one load; the padding bytes are never written).  Blocks with a zero mask byte are not written and the
-// contraction skips them, and its MMA k-steps over dead column groups (the
-// sparse-AO MO product of Sec. 3.2 at tile granularity).
-// Bytes per tile row of the live-group mask of a tiled AO tensor.
-__host__ __device__ inline int mask_ld(int nchunk) { return (nchunk + 15) & ~15; }
-
+// chunks with one load; the padding bytes are never written).  Blocks with a
+// zero mask byte are not written, nor are the dead column groups of live
+// blocks; the contraction skips both (K blocks, and MMA k-steps over dead
+// groups: the sparse-AO MO product of Sec. 3.2 at tile granularity).
 struct AOTensor {
   void* a;        // FP64 / FP32 values, or bf16 "hi" plane
   void* a_lo;     // bf16 "lo" plane (QK_BF16X3 only)
