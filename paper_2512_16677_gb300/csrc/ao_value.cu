@@ -16,7 +16,8 @@
 //            compile-time exponents, into a shared staging tile [128][65];
 //            unreached items only clear their columns, and only when an
 //            earlier tile left values there
-//   phase 2  copy-out of the 128 rows (bf16 hi/lo planes or FP32 / FP64).
+//   phase 2  copy-out of the 128 rows (bf16 hi/lo planes or FP32 / FP64;
+//            tiled: 16-byte stores per lane, dead 16-AO groups skipped).
 // Tiled output (tensor-core modes) writes live (tile, chunk) blocks only and
 // a mask byte per block; the dense output (FP64 / FP32 modes) writes every
 // row below the point count.
@@ -266,33 +267,58 @@ __global__ void __launch_bounds__(kThreads)
       const unsigned gm = sh.gmask;  // the vgl layout's mask byte: live column groups
       if (tid == 0) out.mask[tile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
       if (!gm) continue;
-    }
-    // ---- phase 2: copy-out, one warp per row, lanes over columns lane, lane + 32
-    for (int r = warp; r < kTP; r += kWarps) {
-      int64_t grow;
-      if constexpr (kTiled) {
-        grow = tile * kTileRows + r;
+      // ---- phase 2, tiled: 16-byte stores, dead 16-AO groups not written
+      // (the contraction never reads them), as in ao_vgl
+      const int64_t row0 = tile * kTileRows;
+      if constexpr (kSplit) {
+        const int rsub = lane >> 3, c8 = lane & 7;
+        const bool store = (gm >> (c8 >> 1)) & 1u;
+#pragma unroll
+        for (int it = 0; it < kTP / (4 * kWarps); ++it) {
+          const int r = 4 * (warp + kWarps * it) + rsub;
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float v0 = sh.stage[r][8 * c8 + 2 * j];
+            const float v1 = sh.stage[r][8 * c8 + 2 * j + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+            memcpy(&hw[j], &h, 4);
+            memcpy(&lw[j], &l, 4);
+          }
+          if (store) {
+            const int64_t e = (row0 + r) * out.ld + col0 + 8 * c8;
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a) + e) =
+                make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a_lo) + e) =
+                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+        }
       } else {
-        if (p0 + r >= n) break;
-        grow = p0 + r;
+        const int rsub = lane >> 4, c4 = lane & 15;
+        const bool store = (gm >> (c4 >> 2)) & 1u;
+#pragma unroll
+        for (int it = 0; it < kTP / (2 * kWarps); ++it) {
+          const int r = 2 * (warp + kWarps * it) + rsub;
+          const float4 w = make_float4(sh.stage[r][4 * c4], sh.stage[r][4 * c4 + 1],
+                                       sh.stage[r][4 * c4 + 2], sh.stage[r][4 * c4 + 3]);
+          if (store)
+            *reinterpret_cast<float4*>(static_cast<float*>(out.a) + (row0 + r) * out.ld + col0 +
+                                       4 * c4) = w;
+        }
       }
+      continue;
+    }
+    // ---- phase 2, dense: one warp per row, lanes over columns lane, lane + 32
+    for (int r = warp; r < kTP; r += kWarps) {
+      if (p0 + r >= n) break;
+      const int64_t grow = p0 + r;
       const T v0 = sh.stage[r][lane];
       const T v1 = sh.stage[r][lane + 32];
-      if constexpr (kSplit) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(out.a) + grow * out.ld + col0;
-        __nv_bfloat16* ol = static_cast<__nv_bfloat16*>(out.a_lo) + grow * out.ld + col0;
-        oh[lane] = h.x;
-        oh[lane + 32] = h.y;
-        ol[lane] = l.x;
-        ol[lane + 32] = l.y;
-      } else {
-        T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
-        o[lane] = v0;
-        o[lane + 32] = v1;
-      }
+      T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
+      o[lane] = v0;
+      o[lane + 32] = v1;
     }
   }
   (void)na;
