@@ -81,136 +81,143 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   const int64_t n = pts.n;
   const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
 
-  for (int64_t ptile = t_begin; ptile < t_end; ptile += t_step) {
-    const int64_t p0 = ptile * TP;
-    unsigned pre = ~0u;
-    if constexpr (kTiled) {
-      if (out.reach) {  // the pre-pass's culling: unreached blocks cost no barrier
-        pre = out.reach[ptile * out.nchunk + q];
-        if (pre == 0u) {
+  // Tiles go in batches of 32: lane i of every warp reads the pre-pass's
+  // reach word of tile base + i t_step, so that unreached blocks (most of
+  // them) cost neither a barrier nor a dependent load each; their mask bytes
+  // are written here.
+  const bool culled = kTiled && out.reach != nullptr;
+  for (int64_t base = t_begin; base < t_end; base += 32 * t_step) {
+    const int64_t mine = base + (int64_t)lane * t_step;
+    unsigned word = 0u;
+    if (mine < t_end) word = culled ? out.reach[mine * out.nchunk + q] : ~0u;
+    if (culled && warp == 0 && mine < t_end && word == 0u)
+      out.mask[mine * mask_ld(out.nchunk) + q] = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, word != 0u);
+    while (todo) {
+      const int i = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const int64_t ptile = base + (int64_t)i * t_step;
+      const int64_t p0 = ptile * TP;
+      const unsigned pre = culled ? __shfl_sync(0xffffffffu, word, i) : ~0u;
+      __syncthreads();  // tables ready / previous tile's copy-out done with the stage
+      // ---- phase 0 (warp 0): the tile's points, its bounding box and the
+      // shells that may reach it
+      if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0, pre);
+      __syncthreads();
+      const unsigned reach = sh.reach;
+      if constexpr (kTiled) {
+        if (reach == 0u) {  // no shell reaches the tile: block not written
           if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = 0;
           continue;
         }
       }
-    }
-    __syncthreads();  // tables ready / previous tile's copy-out done with the stage
-    // ---- phase 0 (warp 0): the tile's points, its bounding box and the
-    // shells that may reach it
-    if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0, pre);
-    __syncthreads();
-    const unsigned reach = sh.reach;
-    if constexpr (kTiled) {
-      if (reach == 0u) {  // no shell reaches the tile: block not written
-        if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = 0;
+      // ---- phase 1: warps take shells (costliest first), lanes are points;
+      // culled shells only get their staging columns cleared
+      const bool valid = lane < TP && p0 + lane < n;
+      const int nwork = sh.nwork;
+      unsigned groups = 0;  // warp-uniform: column groups this warp made nonzero
+      for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&sh.next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nwork) break;
+        const int sl = sh.work[k];
+        if ((reach >> sl) & 1u) {
+          if (shell_at_point(sh, sl, lane, valid, Tthr))
+            groups |= shell_group_bits(sh.col[sl], sh.lsh[sl]);
+        } else {
+          shell_zero_columns(sh, sl, lane);
+        }
+      }
+      if constexpr (kTiled) {
+        if (lane == 0 && groups) atomicOr(&sh.gmask, groups);
+      }
+      __syncthreads();
+      if constexpr (kTiled) {
+        // mask byte: bit g set when column group g of block (tile, chunk) holds
+        // an entry that survived screening; 0: block not written, the
+        // contraction skips it
+        const unsigned gm = sh.gmask;
+        if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
+        if (!gm) continue;
+        // ---- phase 2, tiled: all 128 rows (stage rows 125..127 belong to the
+        // lane past the tile and hold zeros) in 16-byte stores; the columns of
+        // dead 16-AO groups are not written (the contraction never reads them)
+        const int64_t row0 = ptile * kTileRows;
+        if constexpr (kSplit) {
+          // a lane splits 8 consecutive columns of one row into 16 bytes of each
+          // bf16 plane: hi = rn(v), lo = rn(v - hi); a warp covers 4 rows
+          const int rsub = lane >> 3, c8 = lane & 7;
+          const bool store = (gm >> (c8 >> 1)) & 1u;
+  #pragma unroll
+          for (int it = 0; it < kTileRows / (4 * kWarps); ++it) {
+            const int r = 4 * (warp + kWarps * it) + rsub;
+            uint32_t hw[4], lw[4];
+  #pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float v0 = sh.stage[r][8 * c8 + 2 * j];
+              const float v1 = sh.stage[r][8 * c8 + 2 * j + 1];
+              const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+              memcpy(&hw[j], &h, 4);
+              memcpy(&lw[j], &l, 4);
+            }
+            if (store) {
+              const int64_t e = (row0 + r) * out.ld + col0 + 8 * c8;
+              *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a) + e) =
+                  make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a_lo) + e) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+          }
+        } else {
+          // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
+          const int rsub = lane >> 4, c4 = lane & 15;
+          const bool store = (gm >> (c4 >> 2)) & 1u;
+  #pragma unroll
+          for (int it = 0; it < kTileRows / (2 * kWarps); ++it) {
+            const int r = 2 * (warp + kWarps * it) + rsub;
+            const float4 w = make_float4(sh.stage[r][4 * c4], sh.stage[r][4 * c4 + 1],
+                                         sh.stage[r][4 * c4 + 2], sh.stage[r][4 * c4 + 3]);
+            if (store)
+              *reinterpret_cast<float4*>(static_cast<float*>(out.a) + (row0 + r) * out.ld + col0 +
+                                         4 * c4) = w;
+          }
+        }
         continue;
       }
-    }
-    // ---- phase 1: warps take shells (costliest first), lanes are points;
-    // culled shells only get their staging columns cleared
-    const bool valid = lane < TP && p0 + lane < n;
-    const int nwork = sh.nwork;
-    unsigned groups = 0;  // warp-uniform: column groups this warp made nonzero
-    for (;;) {
-      int k = 0;
-      if (lane == 0) k = atomicAdd(&sh.next, 1);
-      k = __shfl_sync(0xffffffffu, k, 0);
-      if (k >= nwork) break;
-      const int sl = sh.work[k];
-      if ((reach >> sl) & 1u) {
-        if (shell_at_point(sh, sl, lane, valid, Tthr))
-          groups |= shell_group_bits(sh.col[sl], sh.lsh[sl]);
-      } else {
-        shell_zero_columns(sh, sl, lane);
-      }
-    }
-    if constexpr (kTiled) {
-      if (lane == 0 && groups) atomicOr(&sh.gmask, groups);
-    }
-    __syncthreads();
-    if constexpr (kTiled) {
-      // mask byte: bit g set when column group g of block (tile, chunk) holds
-      // an entry that survived screening; 0: block not written, the
-      // contraction skips it
-      const unsigned gm = sh.gmask;
-      if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
-      if (!gm) continue;
-      // ---- phase 2, tiled: all 128 rows (stage rows 125..127 belong to the
-      // lane past the tile and hold zeros) in 16-byte stores; the columns of
-      // dead 16-AO groups are not written (the contraction never reads them)
-      const int64_t row0 = ptile * kTileRows;
-      if constexpr (kSplit) {
-        // a lane splits 8 consecutive columns of one row into 16 bytes of each
-        // bf16 plane: hi = rn(v), lo = rn(v - hi); a warp covers 4 rows
-        const int rsub = lane >> 3, c8 = lane & 7;
-        const bool store = (gm >> (c8 >> 1)) & 1u;
-#pragma unroll
-        for (int it = 0; it < kTileRows / (4 * kWarps); ++it) {
-          const int r = 4 * (warp + kWarps * it) + rsub;
-          uint32_t hw[4], lw[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float v0 = sh.stage[r][8 * c8 + 2 * j];
-            const float v1 = sh.stage[r][8 * c8 + 2 * j + 1];
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-            memcpy(&hw[j], &h, 4);
-            memcpy(&lw[j], &l, 4);
-          }
-          if (store) {
-            const int64_t e = (row0 + r) * out.ld + col0 + 8 * c8;
-            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a) + e) =
-                make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a_lo) + e) =
-                make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          }
-        }
-      } else {
-        // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
-        const int rsub = lane >> 4, c4 = lane & 15;
-        const bool store = (gm >> (c4 >> 2)) & 1u;
-#pragma unroll
-        for (int it = 0; it < kTileRows / (2 * kWarps); ++it) {
-          const int r = 2 * (warp + kWarps * it) + rsub;
-          const float4 w = make_float4(sh.stage[r][4 * c4], sh.stage[r][4 * c4 + 1],
-                                       sh.stage[r][4 * c4 + 2], sh.stage[r][4 * c4 + 3]);
-          if (store)
-            *reinterpret_cast<float4*>(static_cast<float*>(out.a) + (row0 + r) * out.ld + col0 +
-                                       4 * c4) = w;
-        }
-      }
-      continue;
-    }
-    // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
-    // lane + 32.
-    constexpr int kRows = 5 * kPT;
-    for (int r = warp; r < kRows; r += kWarps) {
-      if (p0 + r / 5 >= n) break;
-      const int64_t grow = 5 * p0 + r;
-      const T v0 = sh.stage[r][lane];
-      const T v1 = sh.stage[r][lane + 32];
-      if constexpr (kSplit) {
-        // hi = rn(v), lo = rn(v - hi), both columns at once
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(out.a) + grow * out.ld + col0;
-        __nv_bfloat16* ol = static_cast<__nv_bfloat16*>(out.a_lo) + grow * out.ld + col0;
-        oh[lane] = h.x;
-        oh[lane + 32] = h.y;
-        ol[lane] = l.x;
-        ol[lane + 32] = l.y;
-      } else {
-        if constexpr (kChunked) {
-          // chunk window: padding columns are written as zeros
-          T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
-          o[lane] = v0;
-          o[lane + 32] = v1;
+      // ---- phase 2: copy-out, one warp per row, lanes over columns lane and
+      // lane + 32.
+      constexpr int kRows = 5 * kPT;
+      for (int r = warp; r < kRows; r += kWarps) {
+        if (p0 + r / 5 >= n) break;
+        const int64_t grow = 5 * p0 + r;
+        const T v0 = sh.stage[r][lane];
+        const T v1 = sh.stage[r][lane + 32];
+        if constexpr (kSplit) {
+          // hi = rn(v), lo = rn(v - hi), both columns at once
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+          __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(out.a) + grow * out.ld + col0;
+          __nv_bfloat16* ol = static_cast<__nv_bfloat16*>(out.a_lo) + grow * out.ld + col0;
+          oh[lane] = h.x;
+          oh[lane + 32] = h.y;
+          ol[lane] = l.x;
+          ol[lane + 32] = l.y;
         } else {
-          T* o = static_cast<T*>(out.a) + grow * out.ld;
-          const int* cmap = out.caller_cols ? b.ao_caller : nullptr;
-          if (lane < na) o[cmap ? cmap[col0 + lane] : col0 + lane] = v0;
-          if (lane + 32 < na) o[cmap ? cmap[col0 + lane + 32] : col0 + lane + 32] = v1;
+          if constexpr (kChunked) {
+            // chunk window: padding columns are written as zeros
+            T* o = static_cast<T*>(out.a) + grow * out.ld + col0;
+            o[lane] = v0;
+            o[lane + 32] = v1;
+          } else {
+            T* o = static_cast<T*>(out.a) + grow * out.ld;
+            const int* cmap = out.caller_cols ? b.ao_caller : nullptr;
+            if (lane < na) o[cmap ? cmap[col0 + lane] : col0 + lane] = v0;
+            if (lane + 32 < na) o[cmap ? cmap[col0 + lane + 32] : col0 + lane + 32] = v1;
+          }
         }
       }
     }
