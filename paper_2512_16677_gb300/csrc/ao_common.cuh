@@ -439,42 +439,63 @@ __device__ __forceinline__ void warp_box(bool pv, T x, T y, T z, T (&lo)[3], T (
   }
 }
 
-// Phase 0 of a tile, one warp: lane p < tp with p0 + p < n loads point p
-// into shared memory.  Shells that cannot reach the tile's bounding box
+// The coordinates of point p0 + lane of a tile (lane < tp, inside the point
+// set), held in registers: FP64 values, or the float hi/lo pairs.
+template <typename T>
+struct TilePoint {
+  T x, y, z;     // FP64: the coordinates; FP32: their float hi parts
+  T lx, ly, lz;  // FP32: the residuals
+  bool pv;
+};
+
+template <typename T>
+__device__ __forceinline__ TilePoint<T> tile_point(const PointsDev& pts, int lane, int tp,
+                                                   int64_t p0) {
+  TilePoint<T> r;
+  const int64_t ip = p0 + lane;
+  r.pv = lane < tp && ip < pts.n;
+  r.x = r.y = r.z = r.lx = r.ly = r.lz = T(0);
+  if (r.pv) {
+    if constexpr (sizeof(T) == 8) {
+      r.x = pts.x[ip];
+      r.y = pts.y[ip];
+      r.z = pts.z[ip];
+    } else {
+      const int64_t ld = pts.ld;
+      r.x = pts.hi[ip];
+      r.y = pts.hi[ld + ip];
+      r.z = pts.hi[2 * ld + ip];
+      r.lx = pts.lo[ip];
+      r.ly = pts.lo[ld + ip];
+      r.lz = pts.lo[2 * ld + ip];
+    }
+  }
+  return r;
+}
+
+// Phase 0 of a tile, one warp: each lane's point (P, from tile_point) into
+// shared memory.  Shells that cannot reach the tile's bounding box
 // (shell_reaches_box) are culled, from `pre` when a pre-pass worked that
 // out (pre != ~0u) or from the box here.  Writes sh.reach, the list of
 // shells to visit (kept ones, and culled ones whose staging columns are
-// dirty) in `order` order, and resets the work counter.
+// dirty) in `order` order, and resets the work counter and the group mask.
 template <typename T, int kLanes>
-__device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const PointsDev& pts,
-                                           int ns, int lane, int tp, int64_t p0,
-                                           unsigned pre = ~0u) {
-  const int64_t n = pts.n;
-  const int64_t ip = p0 + lane;
-  const bool pv = lane < tp && ip < n;
-  T x = T(0), y = T(0), z = T(0);
-  if (pv) {
-    if constexpr (sizeof(T) == 8) {
-      x = pts.x[ip];
-      y = pts.y[ip];
-      z = pts.z[ip];
-    } else {
-      const int64_t ld = pts.ld;
-      x = pts.hi[ip];
-      y = pts.hi[ld + ip];
-      z = pts.hi[2 * ld + ip];
-      sh.pt_lo[lane][0] = pts.lo[ip];
-      sh.pt_lo[lane][1] = pts.lo[ld + ip];
-      sh.pt_lo[lane][2] = pts.lo[2 * ld + ip];
+__device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const TilePoint<T>& P,
+                                           int ns, int lane, unsigned pre) {
+  if (P.pv) {
+    sh.pt[lane][0] = P.x;
+    sh.pt[lane][1] = P.y;
+    sh.pt[lane][2] = P.z;
+    if constexpr (sizeof(T) != 8) {
+      sh.pt_lo[lane][0] = P.lx;
+      sh.pt_lo[lane][1] = P.ly;
+      sh.pt_lo[lane][2] = P.lz;
     }
-    sh.pt[lane][0] = x;
-    sh.pt[lane][1] = y;
-    sh.pt[lane][2] = z;
   }
   unsigned reach = pre;
   if (pre == ~0u) {
     T lo[3], hi[3];
-    warp_box(pv, x, y, z, lo, hi);
+    warp_box(P.pv, P.x, P.y, P.z, lo, hi);
     const bool keep = lane < ns && shell_reaches_box(lo, hi, sh.nuc[lane][0], sh.nuc[lane][1],
                                                      sh.nuc[lane][2], sh.r2max[lane]);
     reach = __ballot_sync(0xffffffffu, keep);
@@ -493,6 +514,14 @@ __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const Poi
     sh.nwork = __popc(vm);
     sh.next = 0;
   }
+}
+
+// The same, loading point p0 + lane of the tile itself (lane < tp).
+template <typename T, int kLanes>
+__device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const PointsDev& pts,
+                                           int ns, int lane, int tp, int64_t p0,
+                                           unsigned pre = ~0u) {
+  tile_reach(sh, tile_point<T>(pts, lane, tp, p0), ns, lane, pre);
 }
 
 // The 16-AO column groups of a 64-column chunk (one tensor-core k-step

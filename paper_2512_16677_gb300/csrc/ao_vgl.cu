@@ -93,6 +93,11 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
     if (culled && warp == 0 && mine < t_end && word == 0u)
       out.mask[mine * mask_ld(out.nchunk) + q] = 0;
     unsigned todo = __ballot_sync(0xffffffffu, word != 0u);
+    // warp 0 holds the next tile's points in registers, loaded while the
+    // current tile is evaluated
+    TilePoint<T> next;
+    if (warp == 0 && todo)
+      next = tile_point<T>(pts, lane, TP, (base + (int64_t)(__ffs(todo) - 1) * t_step) * TP);
     while (todo) {
       const int i = __ffs(todo) - 1;
       todo &= todo - 1u;
@@ -102,7 +107,12 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
       __syncthreads();  // tables ready / previous tile's copy-out done with the stage
       // ---- phase 0 (warp 0): the tile's points, its bounding box and the
       // shells that may reach it
-      if (warp == 0) tile_reach(sh, pts, ns, lane, TP, p0, pre);
+      if (warp == 0) {
+        const TilePoint<T> cur = next;
+        if (todo)
+          next = tile_point<T>(pts, lane, TP, (base + (int64_t)(__ffs(todo) - 1) * t_step) * TP);
+        tile_reach(sh, cur, ns, lane, pre);
+      }
       __syncthreads();
       const unsigned reach = sh.reach;
       if constexpr (kTiled) {
