@@ -127,8 +127,9 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
     """Roofline entries for the two kernels, from algorithmic work per launch.
 
     Dense modes: every (point, AO) entry.  Tensor-core modes skip blocks of
-    screened AOs: ao_vgl's algorithmic bytes are those of the live blocks'
-    (point, AO) entries (stats = (live blocks, all blocks, live entries)).
+    screened AOs: ao_vgl's algorithmic bytes are those of the nonzero
+    (point, AO) entries (the live 16-AO groups it actually writes are given
+    beside them; stats = (live blocks, all blocks, live entries)).
     The contraction's algorithmic work is the sparse product of Sec. 3.2:
     2 * 5 * mo_num * nnz flops (x3 for the bf16 split) with nnz the nonzero
     (point, AO) pairs (sparsity = (live 16-AO groups, nnz)), over the bytes
@@ -139,9 +140,8 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
     """
     P, na, nm = mol.point_num, mol.ao_num, mol.mo_num
     es = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16x3": 4}[mode]
-    entries = P * na if stats is None else stats[2]
     nnz = P * na if sparsity is None else sparsity[1]
-    ao_bytes = es * 5 * entries
+    ao_bytes = es * 5 * nnz
     dense = 2.0 * 5 * P * nm * na
     useful = 2.0 * 5 * nnz * nm
     out = {}
@@ -152,8 +152,9 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
                          "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
                          "algorithmic_bytes": ao_bytes,
                          "dense_equivalent_bytes": es * 5 * P * na}
-        if stats is not None:
-            out["ao_vgl"]["written_bytes"] = stats[0] * 128 * 64 * es + stats[1]
+        if stats is not None and sparsity is not None:
+            # whole live 16-AO groups of 128 rows, plus the mask bytes
+            out["ao_vgl"]["written_bytes"] = sparsity[0] * 128 * 16 * es + stats[1]
             out["ao_vgl"]["live_block_fraction"] = stats[0] / stats[1]
     t_mo = ms_per_launch[1] * 1e-3
     if t_mo > 0:
