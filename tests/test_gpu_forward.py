@@ -301,3 +301,23 @@ def test_sparsity_stats(orc, cfg, mode):
     idx = np.sort(np.random.default_rng(5).choice(m.point_num, 48, replace=False))
     r, size = orc.mo_vgl(m, points=m.points[idx])
     assert_within(mode, got[idx], r, size, "group-skipping contraction")
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_reused_context_matches_fresh(cfg, mode):
+    """Blocks and 16-AO groups that no point of a tile reaches are neither
+    written nor read, so a context that evaluated other points before holds
+    stale values there: the MOs of a second point set must still equal, bit
+    for bit, those of a fresh context (different points light up different
+    groups)."""
+    m = cfg(2, walk_num=8)
+    rng = np.random.default_rng(21)
+    first = m.with_points(m.points + rng.normal(scale=2.0, size=m.points.shape))
+    second = m.with_points(m.points[rng.permutation(m.point_num)])
+    c = _ctx(first, mode)
+    c.mo_vgl_device()
+    c.set_points_device(torch.from_numpy(second.coord).cuda())
+    reused = c.mo_vgl_device()
+    torch.cuda.synchronize()
+    _, fresh = _run(second, mode)
+    np.testing.assert_array_equal(reused.double().cpu().numpy().reshape(fresh.shape), fresh)
