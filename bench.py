@@ -258,7 +258,11 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        ctx.set_timing(timing)
+        # the step is timed without the library's per-kernel events (they
+        # cost about 2% of the step); the kernel times come from a second
+        # pass of the same steps with the events on
+        ctx.set_timing(False)
+        ctx.kernel_count()
         stream = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -270,6 +274,7 @@ def run_ours(args, rank, world, local_rank):
             e1.record(stream)
             torch.cuda.synchronize()
         ctx.synchronize()
+        launches = ctx.kernel_count()
         if dist:
             dist.barrier()
         ms = e0.elapsed_time(e1)
@@ -277,11 +282,20 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        kms, kn = ctx.get_timing() if timing else ([0.0] * 3, [0] * 3)
-        return ctx, out, ms, kms, kn, clk.summary()
+        kms, kn = [0.0] * 3, [0] * 3
+        if timing:
+            ctx.set_timing(True)
+            for i in range(steps):
+                ctx.set_points_device(coord_set[i % 2])
+                ctx.mo_vgl_device(out)
+            torch.cuda.synchronize()
+            ctx.synchronize()
+            kms, kn = ctx.get_timing()
+            ctx.set_timing(False)
+        return ctx, out, ms, kms, kn, clk.summary(), launches
 
     evals_per_step = mol.elec_num * mol.walk_num * mol.mo_num
-    ctx, out, ms, kms, kn, clocks = measure(args.mode, args.steps, args.warmup)
+    ctx, out, ms, kms, kn, clocks, launches = measure(args.mode, args.steps, args.warmup)
     ms_step = ms / args.steps
     value = world * evals_per_step / (ms_step * 1e-3)
     per_launch = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(3)]
@@ -312,14 +326,14 @@ def run_ours(args, rank, world, local_rank):
         "roofline": dom,
         "kernels": {"ao_vgl_ms": per_launch[0], "contraction_ms": per_launch[1],
                     "points_ms": per_launch[2], "all": roof},
-        "gpu_launches": int(sum(kn)),
+        "gpu_launches": int(launches),
         "clocks": clocks,
     }
 
     # same workload through the plain FP32 path (SIMT ao_vgl + SIMT GEMM)
     if not args.no_fp32_line and args.mode != "fp32":
         del ctx
-        c32, _, ms32, k32, n32, clk32 = measure("fp32", max(3, args.steps // 4), 2)
+        c32, _, ms32, k32, n32, clk32, _ = measure("fp32", max(3, args.steps // 4), 2)
         ms32_step = ms32 / max(3, args.steps // 4)
         res["fp32_path"] = {"value": world * evals_per_step / (ms32_step * 1e-3),
                             "ms_per_step": ms32_step,

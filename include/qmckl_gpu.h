@@ -270,6 +270,10 @@ qk_status qk_set_timing(qk_context ctx, int32_t enable);
    reset.  1 <= n <= 3, else QK_ERR_BAD_SIZE. */
 qk_status qk_get_timing(qk_context ctx, double* ms, int64_t* launches, int32_t n);
 
+/* Kernel launches the context made in the timed classes above (whether or
+   not timing is enabled) since the last call; then reset. */
+qk_status qk_get_kernel_count(qk_context ctx, int64_t* count);
+
 /* Block sparsity of the AO tensor of the current points (tensor-core modes,
    after a get_mo_vgl at this time stamp; else QK_ERR_NOT_PROVIDED).  Points
    are grouped in tiles of 25 and AOs in chunks of <= 64; a block is live

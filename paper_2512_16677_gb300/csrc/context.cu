@@ -137,6 +137,7 @@ struct qk_context_s {
   DevBuf bwd_own;
   // optional per-kernel-class timing with events on the context's stream
   bool timing = false;
+  int64_t kernels = 0;  // kernel launches of the timed classes since the last read
   std::vector<cudaEvent_t> ev_start[kTimerClasses], ev_stop[kTimerClasses];
   size_t ev_used[kTimerClasses] = {0, 0, 0};
   ~qk_context_s() {
@@ -180,7 +181,9 @@ struct TimedLaunch {
   qk_context c;
   int k;
   bool on;
-  TimedLaunch(qk_context c_, int k_) : c(c_), k(k_), on(c_->timing) {
+  // nk: kernels the wrapped call launches (counted whether or not timing is on)
+  TimedLaunch(qk_context c_, int k_, int nk = 1) : c(c_), k(k_), on(c_->timing) {
+    c->kernels += nk;
     if (!on) return;
     size_t i = c->ev_used[k];
     if (i == c->ev_start[k].size()) {
@@ -651,7 +654,7 @@ qk_status ensure_spatial(qk_context c) {
   cudaError_t e = c->d_sort.ensure(spatial_order_bytes(c->point_num));
   if (e != cudaSuccess) return cuda_fail(c, e, "spatial order scratch");
   {
-    TimedLaunch t(c, 2);
+    TimedLaunch t(c, 2, spatial_order_kernels(c->point_num));
     e = launch_spatial_order(c->pdev, c->nbox_lo, c->nbox_hi, c->d_sort.p, &c->perm, &c->psort,
                              c->stream);
   }
@@ -705,7 +708,7 @@ qk_status provide_ao(qk_context c, AOTensor* out) {
   if (st || valid) return st;
   cudaError_t e;
   {
-    TimedLaunch t(c, 0);
+    TimedLaunch t(c, 0, out->tiled && out->reach ? 2 : 1);  // reach pre-pass + ao_vgl
     e = launch_ao_vgl(c->bdev, sorted ? c->psort : c->pdev, c->mode, *out, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
@@ -1546,7 +1549,7 @@ qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {
     const int64_t p1 = p0 + per < c->point_num ? p0 + per : c->point_num;
     const AOTensor av = ao_range(ao, c->mode, p0, p1);
     if (!have_ao) {
-      TimedLaunch t(c, 0);
+      TimedLaunch t(c, 0, av.tiled && av.reach ? 2 : 1);
       e = launch_ao_vgl(c->bdev, points_range(c->pdev, p0, p1), c->mode, av, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "ao_vgl launch");
     }
@@ -1572,6 +1575,14 @@ qk_status qk_set_timing(qk_context c, int32_t enable) {
   CHECK_CTX(c);
   c->timing = enable != 0;
   for (int k = 0; k < kTimerClasses; ++k) c->ev_used[k] = 0;
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_kernel_count(qk_context c, int64_t* count) {
+  CHECK_CTX(c);
+  if (!count) return fail(c, QK_ERR_NULL_POINTER, "count is NULL");
+  *count = c->kernels;
+  c->kernels = 0;
   return QK_SUCCESS;
 }
 

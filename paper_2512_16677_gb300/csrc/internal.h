@@ -294,6 +294,8 @@ size_t spatial_order_bytes(int64_t n);
 cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
                                  const float box_hi[3], void* scratch, int32_t** perm,
                                  PointsDev* sorted, cudaStream_t s);
+// Kernel launches launch_spatial_order makes for n points.
+int spatial_order_kernels(int64_t n);
 
 // MO cusp correction (cusp.cu, Sec. 3.3).
 struct CuspDev {

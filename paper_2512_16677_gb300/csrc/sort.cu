@@ -168,6 +168,11 @@ size_t spatial_order_bytes(int64_t n) {
          2 * al(sizeof(int32_t) * n) + al(3 * sizeof(double) * n) + al(6 * sizeof(float) * n);
 }
 
+int spatial_order_kernels(int64_t n) {
+  constexpr int kPasses = (3 * kCellBits + kDigitBits - 1) / kDigitBits;
+  return n == 0 ? 0 : 2 + 3 * kPasses;
+}
+
 cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
                                  const float box_hi[3], void* scratch, int32_t** perm_out,
                                  PointsDev* sorted, cudaStream_t s) {

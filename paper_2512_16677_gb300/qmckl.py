@@ -75,6 +75,7 @@ SIGNATURES = {
     "qk_mo_vgl_backward_device": [_P, _P, _I64, _P, _P],
     "qk_backward_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "qk_set_timing": [_P, _I32],
+    "qk_get_kernel_count": [_P, ctypes.POINTER(_I64)],
     "qk_get_block_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                            ctypes.POINTER(_I64)],
     "qk_get_sparsity_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
@@ -433,6 +434,12 @@ class Context:
         self._check(self.lib.qk_get_block_stats(self.h, ctypes.byref(a), ctypes.byref(b),
                                                 ctypes.byref(c)), "get_block_stats")
         return a.value, b.value, c.value
+
+    def kernel_count(self) -> int:
+        """Kernel launches of the timed classes since the last call (then reset)."""
+        v = ctypes.c_int64()
+        self._check(self.lib.qk_get_kernel_count(self.h, ctypes.byref(v)), "get_kernel_count")
+        return v.value
 
     def sparsity_stats(self):
         """(live (tile, 16-AO group) pairs, nonzero (point, AO) pairs) of the
