@@ -75,8 +75,10 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   const int lane = tid & 31;
   const int warp = tid >> 5;
 
-  // ---- chunk tables, once per call
+  // ---- chunk tables, once per call (static: they may load while the
+  // previous kernel in the stream finishes)
   load_stage_tables(b, q, sh, tid, kThreads);
+  griddep_wait();
   const T Tthr = A::thr(b);
   const int64_t n = pts.n;
   const int64_t col0 = kChunked ? (int64_t)q * kChunkAO : ch.z;
@@ -269,6 +271,7 @@ constexpr int kReachSmemShells = 8192;  // 128 KB of float4
 __global__ void __launch_bounds__(kReachThreads)
     tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles, int staged) {
   extern __shared__ float4 shell_tab[];  // [shell] (X, Y, Z, r2max), float
+  griddep_wait();
   if (staged) {
     for (int s = threadIdx.x; s < b.shell_num; s += blockDim.x) {
       const int A = b.shell_nuc[s];
@@ -323,9 +326,8 @@ cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* r
   // a few blocks per SM, each staging the table once and walking tiles
   const int64_t want = (tiles + 7) / 8;
   const int64_t blocks = want < 4 * (int64_t)f.sms ? want : 4 * (int64_t)f.sms;
-  tile_reach_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s>>>(
-      b, p, reach, tiles, staged);
-  return cudaGetLastError();
+  return launch_pdl(tile_reach_kernel, (unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s,
+                    b, p, reach, tiles, staged);
 }
 
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
@@ -349,8 +351,7 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   if (gy > n_ptiles) gy = n_ptiles;
   if (gy > 65535) gy = 65535;
   dim3 grid((unsigned)b.nchunk, (unsigned)gy);
-  kern<<<grid, kThreads, smem, s>>>(b, p, out, n_ptiles);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, kThreads, smem, s, b, p, out, n_ptiles);
 }
 
 template <bool kSplit>

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -156,6 +157,31 @@ inline int device_sms() {
     sms[dev].store(v, std::memory_order_release);
   }
   return v;
+}
+
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel in the stream finishes (its set-up overlapping that
+// kernel's tail); it must call griddep_wait() before it reads anything the
+// previous kernel wrote or writes anything it reads.  In a launch without
+// the attribute griddep_wait() returns at once.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // A device allocation owned by the library.

@@ -248,6 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // set-up done: from here on the previous kernel's results are read
+  griddep_wait();
 
   if (warp == 4) {
     // ------------------------------------------------ TMA producer (warp)
@@ -622,8 +624,7 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   cudaError_t e = persistent_grid<mo_tc_kernel<MODE, BN, ST, SingleSched<BN>>>(
       S::SMEM, S::TMEM_ALLOC, sc.total, &grid);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
-  return cudaGetLastError();
+  return launch_pdl(kern, (unsigned)grid, kThreads, S::SMEM, s, sc, err_flag);
 }
 
 template <int MODE>

@@ -34,6 +34,7 @@ __device__ __forceinline__ uint32_t cell_of(float x, float lo, float inv) {
 }
 
 __global__ void cell_key_kernel(PointsDev p, float3 lo, float3 inv, uint32_t* key) {
+  griddep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t cx = cell_of(p.hi[i], lo.x, inv.x);
@@ -59,6 +60,7 @@ constexpr int kBins = 1 << kDigitBits;
 
 __global__ void __launch_bounds__(kSortThreads)
     digit_count_kernel(const uint32_t* key, int64_t n, int shift, int nblocks, uint32_t* hist) {
+  griddep_wait();
   __shared__ uint32_t cnt[kBins];
   for (int d = threadIdx.x; d < kBins; d += blockDim.x) cnt[d] = 0;
   __syncthreads();
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // Exclusive scan of m counts in place (one block).
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) exclusive_scan_kernel(uint32_t* v, int64_t m) {
+  griddep_wait();
   __shared__ uint32_t part[kScanThreads];
   const int t = threadIdx.x;
   const int64_t per = (m + kScanThreads - 1) / kScanThreads;
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(kSortThreads)
     digit_scatter_kernel(const uint32_t* key_in, const int32_t* val_in, uint32_t* key_out,
                          int32_t* val_out, int64_t n, int shift, int nblocks,
                          const uint32_t* offset) {
+  griddep_wait();
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t wcnt[kWarps][kBins];
   __shared__ uint32_t run[kBins];  // keys of each digit placed by earlier rounds
@@ -139,6 +143,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // Sorted copy of the point arrays: slot s holds point perm[s].
 __global__ void gather_points_kernel(PointsDev p, const int32_t* perm, double* x, double* y,
                                      double* z, float* hi, float* lo) {
+  griddep_wait();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = perm[s];
@@ -212,18 +217,25 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
   inv.x = span / fmaxf(box_hi[0] - box_lo[0], 1e-3f);
   inv.y = span / fmaxf(box_hi[1] - box_lo[1], 1e-3f);
   inv.z = span / fmaxf(box_hi[2] - box_lo[2], 1e-3f);
-  cell_key_kernel<<<grid_for(n), 256, 0, s>>>(p, lo, inv, key[0]);
-  for (int pass = 0; pass < kPasses; ++pass) {
+  // each kernel waits for its predecessor's results first thing
+  // (programmatic dependent launches: only the launch latency overlaps)
+  cudaError_t e = launch_pdl(cell_key_kernel, grid_for(n), 256, 0, s, p, lo, inv, key[0]);
+  for (int pass = 0; pass < kPasses && e == cudaSuccess; ++pass) {
     const int in = pass & 1, out = in ^ 1;
-    digit_count_kernel<<<nb, kSortThreads, 0, s>>>(key[in], n, kDigitBits * pass, nb, hist);
-    exclusive_scan_kernel<<<1, kScanThreads, 0, s>>>(hist, (int64_t)kBins * nb);
-    digit_scatter_kernel<<<nb, kSortThreads, 0, s>>>(key[in], pass == 0 ? nullptr : val[in],
-                                                   key[out], val[out], n, kDigitBits * pass, nb,
-                                                   hist);
+    e = launch_pdl(digit_count_kernel, nb, kSortThreads, 0, s, (const uint32_t*)key[in], n,
+                   kDigitBits * pass, nb, hist);
+    if (e == cudaSuccess)
+      e = launch_pdl(exclusive_scan_kernel, 1, kScanThreads, 0, s, hist,
+                     (int64_t)kBins * nb);
+    if (e == cudaSuccess)
+      e = launch_pdl(digit_scatter_kernel, nb, kSortThreads, 0, s, (const uint32_t*)key[in],
+                     (const int32_t*)(pass == 0 ? nullptr : val[in]), key[out], val[out], n,
+                     kDigitBits * pass, nb, (const uint32_t*)hist);
   }
-  gather_points_kernel<<<grid_for(n), 256, 0, s>>>(p, *perm_out, x, x + n, x + 2 * n, hi,
-                                                   hi + 3 * n);
-  return cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_pdl(gather_points_kernel, grid_for(n), 256, 0, s, p, (const int32_t*)*perm_out, x,
+                   x + n, x + 2 * n, hi, hi + 3 * n);
+  return e;
 }
 
 }  // namespace qk
