@@ -480,6 +480,7 @@ cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned lon
 
 __global__ void points_soa_kernel(const double* raw, char transp, int64_t n, double* x,
                                   double* y, double* z, float* hi, float* lo) {
+  griddep_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double c[3];
@@ -508,9 +509,8 @@ cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double*
                               double* z, float* hi, float* lo, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
-  points_soa_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(raw, transp, n, x,
-                                                                              y, z, hi, lo);
-  return cudaGetLastError();
+  return launch_pdl(points_soa_kernel, (unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s, raw,
+                    transp, n, x, y, z, hi, lo);
 }
 
 // C [rows][cols] (FP64) -> the contraction's chunked column layout
