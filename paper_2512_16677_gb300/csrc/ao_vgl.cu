@@ -241,8 +241,11 @@ __global__ void __launch_bounds__(kThreads)
     ao_vgl_kernel(BasisDev b, PointsDev pts, AOTensor out, int64_t n_ptiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sh = *reinterpret_cast<StageOf<T, kTiled>*>(smem_raw);
-  ao_chunk_tiles<T, kSplit, kChunked, kTiled>(b, pts, out, blockIdx.x, blockIdx.y, n_ptiles,
-                                              gridDim.y, sh);
+  // CTAs start in grid order with the last chunk first: the internal shell
+  // order puts the diffuse shells, whose chunks reach the most tiles, at the
+  // end, so the longest CTAs start early and the tail is made of short ones
+  ao_chunk_tiles<T, kSplit, kChunked, kTiled>(b, pts, out, b.nchunk - 1 - (int)blockIdx.y,
+                                              blockIdx.x, n_ptiles, gridDim.x, sh);
 }
 
 // Several problems in one persistent launch: CTAs stride over a work list of
@@ -349,8 +352,8 @@ cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out
   // about four waves of resident CTAs, each CTA walking several point tiles
   int64_t gy = ((int64_t)sms * occ * 4 + b.nchunk - 1) / b.nchunk;
   if (gy > n_ptiles) gy = n_ptiles;
-  if (gy > 65535) gy = 65535;
-  dim3 grid((unsigned)b.nchunk, (unsigned)gy);
+  if (b.nchunk > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gy, (unsigned)b.nchunk);
   return launch_pdl(kern, grid, kThreads, smem, s, b, p, out, n_ptiles);
 }
 
