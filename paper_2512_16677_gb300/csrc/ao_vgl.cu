@@ -318,6 +318,20 @@ __global__ void __launch_bounds__(kReachThreads)
   }
 }
 
+cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* reach,
+                              int64_t tiles, cudaStream_t s) {
+  const int staged = b.shell_num <= kReachSmemShells ? 1 : 0;
+  const size_t smem = staged ? sizeof(float4) * (size_t)b.shell_num : 0;
+  KernelFacts f;
+  cudaError_t e = kernel_facts<tile_reach_kernel>(sizeof(float4) * kReachSmemShells,
+                                                  kReachThreads, &f);
+  if (e != cudaSuccess) return e;
+  // a few blocks per SM, each staging the table once and walking tiles
+  const int64_t want = (tiles + 7) / 8;
+  const int64_t blocks = want < 4 * (int64_t)f.sms ? want : 4 * (int64_t)f.sms;
+  return launch_pdl(tile_reach_kernel, (unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s,
+                    b, p, reach, tiles, staged);
+}
 
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
 cudaError_t launch_ao(const BasisDev& b, const PointsDev& p, const AOTensor& out,
@@ -359,21 +373,6 @@ cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n
 }
 
 }  // namespace
-
-cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* reach,
-                              int64_t tiles, cudaStream_t s) {
-  const int staged = b.shell_num <= kReachSmemShells ? 1 : 0;
-  const size_t smem = staged ? sizeof(float4) * (size_t)b.shell_num : 0;
-  KernelFacts f;
-  cudaError_t e = kernel_facts<tile_reach_kernel>(sizeof(float4) * kReachSmemShells,
-                                                  kReachThreads, &f);
-  if (e != cudaSuccess) return e;
-  // a few blocks per SM, each staging the table once and walking tiles
-  const int64_t want = (tiles + 7) / 8;
-  const int64_t blocks = want < 4 * (int64_t)f.sms ? want : 4 * (int64_t)f.sms;
-  return launch_pdl(tile_reach_kernel, (unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s,
-                    b, p, reach, tiles, staged);
-}
 
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s) {

@@ -206,12 +206,6 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned long long* out,
                           cudaStream_t s);
 
-// The reach pre-pass of the tiled layout: for each tile of kTilePoints
-// points and each chunk, the bit mask of the chunk's shells whose screening
-// sphere may reach the tile's bounding box ([tiles][nchunk] words).
-cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* reach,
-                              int64_t tiles, cudaStream_t s);
-
 // Point coordinates [n][3] ('N') or [3][n] ('T') -> SoA + hi/lo floats.
 cudaError_t launch_points_soa(const double* raw, char transp, int64_t n, double* x,
                               double* y, double* z, float* hi, float* lo, cudaStream_t s);
