@@ -145,20 +145,22 @@ __global__ void __launch_bounds__(kThreads)
   using A = Arith<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AOValueSmem<T>& sh = *reinterpret_cast<AOValueSmem<T>*>(smem_raw);
-  const int q = blockIdx.x;
+  // the last chunks (diffuse shells: the longest CTAs) start first
+  const int q = b.nchunk - 1 - (int)blockIdx.y;
   const int4 ch = b.chunk[q];
   const int ns = ch.y - ch.x;
   const int na = ch.w - ch.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kWarps = kThreads / 32;
   load_stage_tables(b, q, sh, tid, kThreads);
+  griddep_wait();  // the points are the previous kernel's output
   for (int i = tid; i < ns; i += kThreads)
     for (int g = 0; g < kGroups; ++g) sh.gdirty[g][i] = 1;  // the stage holds anything
   const T Tthr = A::thr(b);
   const int64_t n = pts.n;
   const int64_t col0 = (int64_t)q * kChunkAO;
 
-  for (int64_t tile = blockIdx.y; tile < n_tiles; tile += gridDim.y) {
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTP;
     __syncthreads();  // tables ready / previous tile's copy-out done
     // ---- phase 0: points and group boxes
@@ -337,9 +339,9 @@ cudaError_t launch_value(const BasisDev& b, const PointsDev& p, const AOTensor& 
   const int occ = f.occ < 1 ? 1 : f.occ, sms = f.sms;
   int64_t gy = ((int64_t)sms * occ * 4 + b.nchunk - 1) / b.nchunk;
   if (gy > n_tiles) gy = n_tiles;
-  if (gy > 65535) gy = 65535;
-  kern<<<dim3((unsigned)b.nchunk, (unsigned)gy), kThreads, smem, s>>>(b, p, out, n_tiles);
-  return cudaGetLastError();
+  if (b.nchunk > 65535) return cudaErrorInvalidValue;
+  return launch_pdl(kern, dim3((unsigned)gy, (unsigned)b.nchunk), kThreads, smem, s, b, p, out,
+                    n_tiles);
 }
 
 }  // namespace
