@@ -160,27 +160,27 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t n = pts.n;
   const int64_t col0 = (int64_t)q * kChunkAO;
 
+  // warps 0..3 hold their group's points of the next tile in registers,
+  // loaded while the current tile is evaluated
+  TilePoint<T> next;
+  if (warp < kGroups && (int64_t)blockIdx.x < n_tiles)
+    next = tile_point<T>(pts, lane, 32, (int64_t)blockIdx.x * kTP + 32 * warp);
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTP;
     __syncthreads();  // tables ready / previous tile's copy-out done
     // ---- phase 0: points and group boxes
     if (warp < kGroups) {
       const int pl = 32 * warp + lane;
-      const int64_t ip = p0 + pl;
-      const bool pv = ip < n;
-      T x = T(0), y = T(0), z = T(0);
+      const TilePoint<T> P = next;
+      if (tile + gridDim.x < n_tiles)
+        next = tile_point<T>(pts, lane, 32, (tile + gridDim.x) * kTP + 32 * warp);
+      const bool pv = P.pv;
+      const T x = P.x, y = P.y, z = P.z;
       if (pv) {
-        if constexpr (sizeof(T) == 8) {
-          x = pts.x[ip];
-          y = pts.y[ip];
-          z = pts.z[ip];
-        } else {
-          x = pts.hi[ip];
-          y = pts.hi[pts.ld + ip];
-          z = pts.hi[2 * pts.ld + ip];
-          sh.pt_lo[pl][0] = pts.lo[ip];
-          sh.pt_lo[pl][1] = pts.lo[pts.ld + ip];
-          sh.pt_lo[pl][2] = pts.lo[2 * pts.ld + ip];
+        if constexpr (sizeof(T) != 8) {
+          sh.pt_lo[pl][0] = P.lx;
+          sh.pt_lo[pl][1] = P.ly;
+          sh.pt_lo[pl][2] = P.lz;
         }
         sh.pt[pl][0] = x;
         sh.pt[pl][1] = y;
