@@ -516,14 +516,6 @@ __device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const Til
   }
 }
 
-// The same, loading point p0 + lane of the tile itself (lane < tp).
-template <typename T, int kLanes>
-__device__ __forceinline__ void tile_reach(AOStageSmem<T, kLanes>& sh, const PointsDev& pts,
-                                           int ns, int lane, int tp, int64_t p0,
-                                           unsigned pre = ~0u) {
-  tile_reach(sh, tile_point<T>(pts, lane, tp, p0), ns, lane, pre);
-}
-
 // The 16-AO column groups of a 64-column chunk (one tensor-core k-step
 // each) that the columns of a shell of angular momentum l starting at
 // column c0 fall in.
