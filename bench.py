@@ -183,8 +183,10 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
             ent.update({"bound": bound, **{k: ent[bound][k] for k in
                                            ("achieved", "peak", "unit", "frac", "peak_note")}})
             if sparsity is not None:
-                # one 128 x 16 x N_pad k-step per live (tile, 16-AO group)
-                n_pad = -(-nm // 160) * 160
+                # one 128 x 16 x N_pad k-step per live (tile, 16-AO group);
+                # N tiles of 160, the last one rounded up to 16
+                nt = -(-nm // 160)
+                n_pad = (nt - 1) * 160 + -(-(nm - (nt - 1) * 160) // 16) * 16
                 issued = sparsity[0] * 128 * 16 * n_pad * 2.0 * (3 if mode == "bf16x3" else 1)
                 ent["nnz_fraction"] = nnz / (P * na)
                 ent["issued_flops"] = issued

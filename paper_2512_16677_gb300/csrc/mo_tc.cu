@@ -77,7 +77,8 @@ struct TileInfo {
   int64_t M, N;          // output rows and columns
   int m0, n0;            // AO-tensor row and output column of the tile
   int num_kb;
-  int bn;                // MMA N of this problem (multiple of 16, <= BN_MAX)
+  int bn;                // MMA N of this tile (multiple of 16, <= BN_MAX)
+  int ntile;             // index of the tile's N range (density partials)
   bool tiled;            // rows: rows_per_tile live of 128, output row = rpt (m0/128) + local
   int rows_per_tile;     // tiled: 125 (vgl) or 128 (values only)
   const float* wdens;    // density epilogue: column weights (NULL: store D)
@@ -122,6 +123,8 @@ __device__ __forceinline__ bool tile_live(const TileInfo& x, int lane) {
 template <int BN>
 struct SingleSched {
   CUtensorMap a, b;
+  CUtensorMap b_last;  // the last N tile's C rows (box last_bn), when last_bn < BN
+  int last_bn;         // MMA N of the last N tile: the MOs left, rounded up to 16
   float* D;
   const uint8_t* mask;  // [m tiles][mask_ld(nchunk)] when tiled
   const int32_t* perm;
@@ -135,22 +138,26 @@ struct SingleSched {
   __device__ __forceinline__ void prefetch_maps() const {
     tma_prefetch_map(&a);
     tma_prefetch_map(&b);
+    if (last_bn != BN) tma_prefetch_map(&b_last);
   }
   __device__ __forceinline__ TileInfo tile(int64_t t) const {
     TileInfo x;
     const int64_t mt =
         total <= 0x7fffffff ? (int64_t)((uint32_t)t / (uint32_t)n_tiles) : t / n_tiles;
+    const int nt = (int)(t - mt * n_tiles);
+    const bool last = nt == n_tiles - 1 && last_bn != BN;
     x.a = &a;
-    x.b = &b;
+    x.b = last ? &b_last : &b;
     x.D = D;
     x.kmask = tiled ? mask + mt * mask_ld(nchunk) : nullptr;
     x.perm = perm;
     x.M = M;
     x.N = N;
     x.m0 = (int)(mt * kBM);
-    x.n0 = (int)((t - mt * n_tiles) * BN);
+    x.n0 = nt * BN;
     x.num_kb = num_kb;
-    x.bn = BN;
+    x.bn = last ? last_bn : BN;
+    x.ntile = nt;
     x.tiled = tiled;
     x.rows_per_tile = rows_per_tile;
     x.wdens = wdens;
@@ -182,6 +189,7 @@ struct BatchSched {
     x.n0 = it.z * p.bn;
     x.num_kb = p.num_kb;
     x.bn = p.bn;
+    x.ntile = it.z;
     x.tiled = p.mask != nullptr;
     x.rows_per_tile = 5 * kTilePoints;
     x.wdens = nullptr;
@@ -483,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (loc < rows_here && row0 + loc < x.M)
-          x.rho[(int64_t)(x.n0 / x.bn) * x.M + row0 + loc] = acc;
+          x.rho[(int64_t)x.ntile * x.M + row0 + loc] = acc;
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty_bar(b));
@@ -598,13 +606,21 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
   if (ao.tiled && M % kBM != 0) return cudaErrorInvalidValue;
   SingleSched<BN> sc;
+  // the last N tile multiplies only the MOs it has, rounded up to 16
+  const int64_t n_tiles = (N + BN - 1) / BN;
+  const int last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
+  sc.last_bn = last_bn;
   if (TR::kPlanes == 2) {
     if (!make_map_planes(&sc.a, ao.a, ao.a_lo, K, M, ao.ld, TR::kBK, kBM))
       return cudaErrorInvalidValue;
     if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+    if (last_bn != BN && !make_map_planes(&sc.b_last, c_hi, c_lo, K, N, ldc, TR::kBK, last_bn))
+      return cudaErrorInvalidValue;
   } else {
     if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
     if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
+    if (last_bn != BN && !make_map(&sc.b_last, c_hi, f32, K, N, ldc, TR::kBK, last_bn))
+      return cudaErrorInvalidValue;
   }
   sc.D = out;
   sc.mask = ao.tiled ? ao.mask : nullptr;
