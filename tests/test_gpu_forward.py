@@ -321,3 +321,20 @@ def test_reused_context_matches_fresh(cfg, mode):
     torch.cuda.synchronize()
     _, fresh = _run(second, mode)
     np.testing.assert_array_equal(reused.double().cpu().numpy().reshape(fresh.shape), fresh)
+
+
+def test_kernel_count(cfg):
+    """The library counts the kernels it launches for a step (point
+    conversion, spatial order, reach pre-pass, ao_vgl, contraction) and
+    resets the count when it is read."""
+    m = cfg(2, walk_num=8)
+    c = _ctx(m, "bf16x3")
+    c.mo_vgl_device()
+    torch.cuda.synchronize()
+    c.kernel_count()
+    c.set_points_device(torch.from_numpy(m.coord).cuda())
+    c.mo_vgl_device()
+    torch.cuda.synchronize()
+    n = c.kernel_count()
+    assert n == 1 + 8 + 2 + 1, n      # conversion, sort, pre-pass + ao_vgl, contraction
+    assert c.kernel_count() == 0
