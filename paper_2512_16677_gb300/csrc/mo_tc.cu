@@ -337,6 +337,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int j = __ffs(live) - 1;
           live &= live - 1u;
           const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+          // the AO block of the next live chunk into L2 now, so that its copy
+          // into the ring (a stage later) does not wait on HBM
+          if constexpr (kPer == 1) {
+            if (live && lane == 2)
+              tma_prefetch_l2_3d(x.a, (q0 + __ffs(live) - 1) * TR::kBK, x.m0, 0);
+          }
 #pragma unroll
           for (int h = 0; h < kPer; ++h) {
             uint32_t steps = gj;

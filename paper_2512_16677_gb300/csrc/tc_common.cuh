@@ -78,6 +78,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Bring the box at (c0, c1, c2) of a 3-D map into L2 (no shared memory).
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap* map, int c0, int c1,
+                                                   int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   (uint64_t)map),
+               "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
 // Fetch a tensor map (kernel parameter or global memory) into the TMA
 // unit's descriptor cache.
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
