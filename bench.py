@@ -37,7 +37,7 @@ CPU_SAMPLE_POINTS = 2400     # 4 walkers: about 10 s of oracle work on one core
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["bf16x3", "tf32", "fp32", "fp64"], default="bf16x3")
@@ -85,8 +85,13 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once the sampler is running
+            t0 = time.monotonic()
+            while not self.lines and self.proc.poll() is None and time.monotonic() - t0 < 5.0:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
+        self.first = len(self.lines)
         return self
 
     def _read(self):
@@ -102,9 +107,13 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Samples taken inside the timed region; when the region is shorter
+        than the sampling interval, the last sample before it (said so)."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = self.lines[self.first:]
+        lines = inside or self.lines[max(self.first - 1, 0):self.first]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -118,8 +127,11 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+               "reasons": sorted(reasons), "samples": len(inside)}
+        if not inside:
+            out["note"] = "timed region shorter than the 100 ms sampling interval: sample taken just before it"
+        return out
 
 
 # ------------------------------------------------------------ roofline ---
