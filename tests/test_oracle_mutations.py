@@ -25,6 +25,7 @@ MUTANTS = {
     "threshold_bits": ("return (double)(bits - 1) * log(2.0);", "return (double)(bits) * log(2.0);"),
     "radial_power": ("const double e = exp(-g * r2);", "const double e = exp(-g * sqrt(r2));"),
     "dot2_error_term": ("acc->s += q + r;", "acc->s += q;"),
+    "two_product_dropped": ("double r = fma(x, y, -h);", "double r = 0.0;"),
     "mo_transpose": ("dot2_add(&acc, ci[k], a[k]);",
                      "dot2_add(&acc, C[(size_t)k * mo_num + i], a[k]);"),
     "adjoint_sign": ("dot2_add(&accR[3 * A + j], -abar[(size_t)c * na + k], g[c]);",

@@ -275,6 +275,63 @@ def test_mo_brute_force_water(orc, cfg):
                 assert abs(mo[p, c, n] - ex) <= 2 * np.spacing(abs(ex)) + 1e-300
 
 
+_SPLIT = 134217729.0  # 2^27 + 1: Dekker's splitting constant for FP64
+
+
+def _two_product(x, y):
+    """x * y = p + e exactly (Dekker 1971, Veltkamp splitting), elementwise;
+    exact unless a product under- or overflows."""
+    p = x * y
+    cx = _SPLIT * x
+    xh = cx - (cx - x)
+    xl = x - xh
+    cy = _SPLIT * y
+    yh = cy - (cy - y)
+    yl = y - yh
+    e = ((xh * yh - p) + xh * yl + xl * yh) + xl * yl
+    return p, e
+
+
+def _exact_mo(C, ao):
+    """Correctly rounded sum_k C[n,k] ao[c,k] for every (c, n) of one point:
+    the products split exactly into p + e, then math.fsum (Shewchuk), which
+    rounds the exact sum of its arguments once."""
+    p, e = _two_product(C[None, :, :], ao[:, None, :])        # [5][mo][ao]
+    terms = np.concatenate([p, e], axis=-1).reshape(-1, 2 * C.shape[1]).tolist()
+    return np.array([math.fsum(t) for t in terms]).reshape(5, C.shape[0])
+
+
+@pytest.mark.parametrize("which, walk_num, npts, nmo", [
+    (1, None, None, None),   # water, every point
+    (3, 1, 48, None),        # 50-nucleus chain, 500 AOs
+    (2, 1, 12, None),        # organic chain, 1650 AOs, 300 MOs
+    (5, 1, 2, 48),           # 1000-nucleus cluster, 10 000 AOs (48 of the MOs)
+])
+def test_mo_brute_force_sums(orc, cfg, which, walk_num, npts, nmo):
+    """The oracle's MO sums (Eqs. 5-7, compensated Dot2) against correctly
+    rounded exact sums of the same AO values, on whole small workloads and
+    sampled points of large ones: within the Ogita-Rump-Oishi bound
+    eps|s| + 2 (K eps)^2 sum|C chi| (K AOs per sum)."""
+    m = cfg(which, walk_num=walk_num)
+    pts = m.points
+    if npts is not None:
+        idx = np.random.default_rng(11).choice(m.point_num, npts, replace=False)
+        pts = m.points[np.sort(idx)]
+    C = m.mo_coef if nmo is None else m.mo_coef[:nmo]
+    ao, _ = orc.ao_vgl(m, points=pts)
+    mo, _ = orc.mo_from_ao(ao, C)
+    eps = 2.0 ** -53
+    K = C.shape[1]
+    live = 0
+    for q in range(len(pts)):
+        ex = _exact_mo(C, ao[q])
+        size = np.abs(ao[q])[:, None, :] * np.abs(C)[None, :, :]
+        bound = eps * np.abs(ex) + 2 * (K * eps) ** 2 * size.sum(-1)
+        assert np.all(np.abs(mo[q] - ex) <= bound), (which, q)
+        live += int(np.count_nonzero(ex))
+    assert live > 0
+
+
 def test_mo_layout_and_transpose(orc, cfg):
     """Non-square C: output [point][component][mo] = C @ ao (not C^T)."""
     m = cfg(3, walk_num=1)
