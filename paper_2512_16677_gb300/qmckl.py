@@ -341,8 +341,7 @@ class Context:
         """Host coordinates [walk][elec][3] ('N') or [3][walk*elec] ('T')."""
         c = _f64(coord)
         if transp == "N":
-            c3 = c.reshape(-1, c.shape[-2], 3) if c.ndim == 3 else c.reshape(1, -1, 3)
-            w, e = c3.shape[0], c3.shape[1]
+            w, e = (c.shape[0], c.shape[1]) if c.ndim == 3 else (1, c.size // 3)
         else:
             w, e = 1, c.size // 3
         self._check(self.lib.qk_set_points(self.h, transp.encode(), w, e, _ptr(c)), "set_points")

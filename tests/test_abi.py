@@ -104,6 +104,14 @@ def test_setter_order_and_validation():
     with pytest.raises(qmckl.QmcklError) as e:      # nothing evaluated without points
         c.workspace_size()
     assert e.value.status == -4
+    # empty point sets and unknown layouts are refused before any device call
+    for pts, transp, code in ((np.zeros((0, 3)), "N", -3), (np.zeros((2, 0, 3)), "N", -3),
+                              (np.zeros(0), "T", -3), (m.points[:4], "X", -1)):
+        with pytest.raises(qmckl.QmcklError) as e:
+            c.set_points(pts, transp=transp)
+        assert e.value.status == code, (pts.shape, transp, e.value)
+    assert c.lib.qk_set_points(c.h, b"N", 1, 4, None) == -2
+    assert c.lib.qk_set_points_device(c.h, b"N", 1, 4, None) == -2
     c.close()
 
 

@@ -131,6 +131,37 @@ def test_edge_single_point_and_far_points(orc, cfg):
         assert np.all(got == 0.0)
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("l, nmo", [(0, 1), (3, 1), (2, 7)])
+def test_degenerate_one_shell(orc, mode, l, nmo):
+    """One nucleus carrying one shell (1, 10 or 6 AOs: K far below one 64-AO
+    chunk) and 1 or 7 MOs (N below one 16-wide MMA step); 37 points, so the
+    second 25-point tile is ragged, one of them on the nucleus (d = 0)."""
+    centre = np.array([0.3, -0.2, 0.1])
+    rng = np.random.default_rng(30 + l)
+    pts = centre + rng.normal(scale=1.2, size=(37, 3))
+    pts[7] = centre
+    nao = (l + 1) * (l + 2) // 2
+    C = rng.normal(size=(nmo, nao))
+    m = synth.tiny_shell(l, [0.4, 2.5, 30.0], [0.5, 0.3, 0.2], centre=tuple(centre),
+                         points=pts, mo_coef=C)
+    ref, size = orc.mo_vgl(m)
+    _, got = _run(m, mode)
+    assert got.shape == ref.shape == (37, 5, nmo)
+    assert_within(mode, got, ref, size, f"one l={l} shell, {nmo} MOs")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_points_on_nuclei(orc, cfg, mode):
+    """Electrons exactly at every nucleus of the organic chain (d = 0 for that
+    nucleus's shells) followed by ordinary points: 211 points, a ragged tail."""
+    m = cfg(2, walk_num=1)
+    mm = m.with_points(np.concatenate([m.nucl_coord, m.points[:61]]))
+    ref, size = orc.mo_vgl(mm)
+    _, got = _run(mm, mode)
+    assert_within(mode, got, ref, size, "points on nuclei")
+
+
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
 def test_sparse_tiles_mixed(orc, cfg, mode):
     """Tensor-core modes skip blocks of screened AOs: a point set where whole
