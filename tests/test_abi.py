@@ -126,3 +126,16 @@ def test_last_error_truncates(lib):
     assert lib.qk_last_error(c.h, buf, 8) == 0
     assert len(buf.value) == 7
     assert lib.qk_last_error(c.h, buf, 0) == -3
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises; nothing falls back to
+    a CPU implementation."""
+    import subprocess
+    import sys
+    code = ("from paper_2512_16677_gb300 import qmckl\n"
+            f"qmckl.load({str(tmp_path / 'libqmckl_gpu.so')!r})\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode != 0
+    assert "no CPU fallback" in r.stderr
