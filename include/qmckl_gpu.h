@@ -53,7 +53,7 @@ typedef int32_t qk_status;
 #define QK_ERR_NULL_POINTER -2     /* a required pointer is NULL */
 #define QK_ERR_BAD_SIZE -3         /* a size argument is too small or inconsistent */
 #define QK_ERR_NOT_PROVIDED -4     /* a required setter has not been called */
-#define QK_ERR_NOT_IMPLEMENTED -5  /* valid input outside what this build supports */
+#define QK_ERR_NOT_IMPLEMENTED -5  /* valid input outside what the library implements */
 #define QK_ERR_CUDA -6             /* a CUDA runtime/driver call failed */
 #define QK_ERR_DEVICE_TIMEOUT -7   /* a bounded device-side wait gave up */
 #define QK_ERR_OUT_OF_MEMORY -8    /* device or host allocation failed */

@@ -169,7 +169,7 @@ qk_status cuda_fail(qk_context c, cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation)
     return fail(c, QK_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
   if (e == cudaErrorNotSupported)
-    return fail(c, QK_ERR_NOT_IMPLEMENTED, "%s: not supported by this build", what);
+    return fail(c, QK_ERR_NOT_IMPLEMENTED, "%s: not supported on this device", what);
   return fail(c, QK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
