@@ -135,7 +135,43 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ roofline ---
-def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
+def screen_work(mol, points, block=2048):
+    """Algorithmic work of ao_vgl (Eqs. 1-4 under the Eq. 3 test), counted on
+    the host for the roofline: the (point, shell) pairs with at least one
+    primitive below the threshold, the primitives evaluated, and the
+    Cartesian AOs of those pairs.  FP64, r^2 = dx dx + dy dy + dz dz."""
+    import numpy as np
+    T = (mol.bits - 1) * math.log(2.0) if mol.eps is None else -math.log(mol.eps)
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    nprim = np.asarray(mol.shell_prim_num, dtype=np.int64)
+    prim_nuc = np.repeat(np.asarray(mol.shell_nucleus, dtype=np.int64), nprim)
+    first = np.concatenate([[0], np.cumsum(nprim)[:-1]])
+    lq = np.asarray(mol.shell_ang_mom, dtype=np.int64)
+    ncart = (lq + 1) * (lq + 2) // 2
+    gam = np.asarray(mol.exponent, dtype=np.float64)
+    R = np.asarray(mol.nucl_coord, dtype=np.float64)
+    pairs = prims = aos = 0
+    for b in range(0, pts.shape[0], block):
+        d = pts[b:b + block, None, :] - R[None, :, :]
+        r2 = d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1] + d[..., 2] * d[..., 2]
+        ev = (gam[None, :] * r2[:, prim_nuc]) < T
+        per_shell = np.add.reduceat(ev.astype(np.int32), first, axis=1)
+        live = per_shell > 0
+        pairs += int(live.sum())
+        prims += int(per_shell.sum())
+        aos += int((live * ncart[None, :]).sum())
+    return pairs, prims, aos
+
+
+def alu_peaks(peaks):
+    """FP32 FMA and MUFU (ex2) rates from unit counts and the maximum SM
+    clock: 152 SMs x 128 FP32 lanes x 2 flop, and 16 MUFU results per SM per
+    clock (4 per sub-partition)."""
+    hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return 152 * 128 * 2 * hz / 1e12, 152 * 16 * hz / 1e12
+
+
+def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None, work=None):
     """Roofline entries for the two kernels, from algorithmic work per launch.
 
     Dense modes: every (point, AO) entry.  Tensor-core modes skip blocks of
@@ -168,6 +204,28 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None):
             # whole live 16-AO groups of 128 rows, plus the mask bytes
             out["ao_vgl"]["written_bytes"] = sparsity[0] * 128 * 16 * es + stats[1]
             out["ao_vgl"]["live_block_fraction"] = stats[0] / stats[1]
+        if work is not None and mode != "fp64":
+            # per evaluated primitive one exp and ~5 FMA; per Cartesian AO of
+            # a surviving pair ~14 flop (value, gradient, Laplacian assembly)
+            fp32, mufu = alu_peaks(peaks)
+            flops = 10.0 * work[1] + 14.0 * work[2]
+            t_fma, t_xu = flops / (fp32 * 1e12), work[1] / (mufu * 1e12)
+            t_alu = max(t_fma, t_xu)
+            out["ao_vgl"]["alu"] = {
+                "pairs": work[0], "prims_evaluated": work[1], "cartesian_aos": work[2],
+                "fp32_flops": flops, "mufu_ops": work[1],
+                "fp32": {"achieved": flops / t_ao / 1e12, "peak": fp32, "unit": "TFLOP/s",
+                         "frac": t_fma / t_ao},
+                "mufu": {"achieved": work[1] / t_ao / 1e12, "peak": mufu, "unit": "Tops/s",
+                         "frac": t_xu / t_ao},
+                "frac": t_alu / t_ao,
+                "peak_note": "152 SMs x (128 FP32 FMA, 16 MUFU) per clock x max clock"}
+            # the roofline that binds is the one whose floor is the longer
+            if t_alu > ao_bytes / (peaks["hbm_gbs"] * 1e9):
+                unit = "fp32" if t_fma >= t_xu else "mufu"
+                e = out["ao_vgl"]["alu"][unit]
+                out["ao_vgl"].update({"bound": "alu", "achieved": e["achieved"],
+                                      "peak": e["peak"], "unit": e["unit"], "frac": e["frac"]})
     t_mo = ms_per_launch[1] * 1e-3
     if t_mo > 0:
         hbm = peaks["hbm_gbs"]
@@ -315,7 +373,9 @@ def run_ours(args, rank, world, local_rank):
     per_launch = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(3)]
     stats = ctx.block_stats() if args.mode in ("bf16x3", "tf32") else None
     sparsity = ctx.sparsity_stats() if args.mode in ("bf16x3", "tf32") else None
-    roof = roofline(args.mode, mol, per_launch, peaks, stats, sparsity)
+    # the library's last evaluation was of this point set
+    work = screen_work(mol, coord_set[(args.steps - 1) % 2].cpu().numpy())
+    roof = roofline(args.mode, mol, per_launch, peaks, stats, sparsity, work)
     dominant = max(roof, key=lambda k: per_launch[0 if k == "ao_vgl" else 1])
     dom = dict(roof[dominant])
     dom["kernel"] = dominant

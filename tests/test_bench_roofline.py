@@ -1,0 +1,46 @@
+"""The benchmark's roofline inputs: the host count of ao_vgl's algorithmic
+work (Eq. 3 screening) equals the oracle's own count exactly, and the
+roofline entries follow from the counts, the times and the peaks."""
+import numpy as np
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("which, walk_num, npts", [(1, None, None), (2, 1, 400), (5, 1, 150)])
+def test_screen_work_matches_oracle(orc, cfg, which, walk_num, npts):
+    m = cfg(which, walk_num=walk_num)
+    pts = m.points if npts is None else m.points[:npts]
+    assert bench.screen_work(m, pts, block=97) == orc.screen_counts(m, points=pts)
+
+
+def test_alu_entry_and_bound():
+    class Mol:
+        point_num, ao_num, mo_num = 1000, 100, 10
+    peaks = {"hbm_gbs": 1000.0, "bf16_tflops": 100.0, "sm_max_mhz": 2000.0}
+    fp32, mufu = bench.alu_peaks(peaks)
+    assert fp32 == pytest.approx(152 * 128 * 2 * 2e9 / 1e12)
+    assert mufu == pytest.approx(152 * 16 * 2e9 / 1e12)
+    work = (300, 2000, 900)
+    sparsity = (10, 5000)                     # live groups, nnz
+    stats = (5, 40, 0)
+    r = bench.roofline("bf16x3", Mol, [1.0, 1.0], peaks, stats, sparsity, work)["ao_vgl"]
+    alu = r["alu"]
+    assert alu["fp32_flops"] == 10 * 2000 + 14 * 900
+    assert alu["mufu_ops"] == 2000
+    t = 1e-3
+    assert alu["fp32"]["frac"] == pytest.approx(alu["fp32_flops"] / (fp32 * 1e12) / t)
+    assert alu["mufu"]["frac"] == pytest.approx(2000 / (mufu * 1e12) / t)
+    # 5 * nnz * 4 bytes over 1000 GB/s: a longer floor than the ALU's here
+    assert r["bound"] == "hbm"
+    assert r["frac"] == pytest.approx(5 * 5000 * 4 / 1e12 / t)
+    # make the arithmetic the longer floor: exps, then Cartesian assembly
+    r = bench.roofline("bf16x3", Mol, [1.0, 1.0], peaks, stats, (10, 1), (1, 10**9, 1))["ao_vgl"]
+    assert r["bound"] == "alu"
+    assert r["unit"] == "Tops/s" and r["frac"] == r["alu"]["mufu"]["frac"]
+    r = bench.roofline("bf16x3", Mol, [1.0, 1.0], peaks, stats, (10, 1), (1, 1, 10**9))["ao_vgl"]
+    assert r["bound"] == "alu"
+    assert r["unit"] == "TFLOP/s" and r["frac"] == r["alu"]["fp32"]["frac"]
+    # no ALU entry for the FP64 path
+    r = bench.roofline("fp64", Mol, [1.0, 1.0], peaks, None, None, work)["ao_vgl"]
+    assert "alu" not in r and r["bound"] == "hbm"
