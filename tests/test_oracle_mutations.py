@@ -46,9 +46,11 @@ def test_pins_fail_on_mutant(name, tmp_path):
     msrc.write_text(src.replace(old, new))
     lib = orc_mod.build(force=True, src=str(msrc), out=str(tmp_path / "liboracle_mutant.so"))
     env = dict(os.environ, ORACLE_LIB=lib)
+    suites = [os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+              os.path.join(ROOT, "tests", "test_oracle_adjoint.py")]
+    if name.startswith("adjoint"):
+        suites.reverse()          # the same suites; the adjoint pins first (-x stops early)
     r = subprocess.run(
-        [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-         os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
+        [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *suites],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
