@@ -132,6 +132,23 @@ def _tptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _device_tensor(t, what, dtype=None, numel=None, min_numel=None):
+    """Check a tensor handed to the library by pointer: on the GPU,
+    contiguous, of the element type the library reads or writes, and (where
+    the C call takes no size) of the element count it touches."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: a CUDA tensor is required")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: the tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what}: {t.numel()} elements, expected {numel}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{what}: {t.numel()} elements, at least {min_numel} needed")
+    return t
+
+
 def contract_device(A, B, mode: str = "fp32", out=None):
     """D = A @ B.T on the GPU with the kernel of `mode` (CUDA tensors)."""
     import torch
@@ -139,9 +156,11 @@ def contract_device(A, B, mode: str = "fp32", out=None):
     M, K = A.shape
     N = B.shape[0]
     dt = torch.float64 if mode == "fp64" else torch.float32
-    assert A.dtype == dt and B.dtype == dt and A.is_contiguous() and B.is_contiguous()
+    _device_tensor(A, "A", dt)
+    _device_tensor(B, "B", dt, numel=N * K)
     if out is None:
         out = torch.empty((M, N), dtype=dt, device=A.device)
+    _device_tensor(out, "out", dt, numel=M * N)
     st = lib.qk_contract_device(MODES[mode], M, N, K, _tptr(A), _tptr(B), _tptr(out),
                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if st != QK_SUCCESS:
@@ -224,8 +243,9 @@ class Context:
 
     def set_single_point_device(self, elec: int, coords):
         """Proposed positions [walk][3] (CUDA float64) of electron `elec`."""
+        import torch
+        _device_tensor(coords, "coords", torch.float64, numel=3 * self._walk_elec()[0])
         self._bind_stream()
-        assert coords.is_cuda and coords.dtype.is_floating_point and coords.is_contiguous()
         self._single = coords  # kept alive until the copy has run
         self._check(self.lib.qk_set_single_point_device(self.h, int(elec), coords.data_ptr()),
                     "set_single_point_device")
@@ -233,10 +253,11 @@ class Context:
     def mo_vgl_single_device(self, out=None):
         """MO vgl [walk][5][mo] at the proposed positions (CUDA tensor)."""
         import torch
-        self._bind_stream()
-        w = self._walk_elec_shape[0]
+        w = self._walk_elec()[0]
         if out is None:
             out = torch.empty((w, 5, self.mo_num), dtype=self.dtype_torch, device="cuda")
+        _device_tensor(out, "out", self.dtype_torch)
+        self._bind_stream()
         self._check(self.lib.qk_get_mo_vgl_single_device(self.h, out.data_ptr(), out.numel()),
                     "get_mo_vgl_single_device")
         return out
@@ -249,14 +270,15 @@ class Context:
         """Electron density sum_i w_i phi_i^2 at the current points as a CUDA
         tensor [point_num] (FP64 in fp64 mode, else FP32)."""
         import torch
-        self._bind_stream()
         wa = _f64(w)
         if wa.shape != (self.mo_num,):
             raise ValueError("one occupation weight per MO")
         n = self.point_num
+        dt = torch.float64 if self.mode == "fp64" else torch.float32
         if out is None:
-            out = torch.empty(n, dtype=torch.float64 if self.mode == "fp64" else torch.float32,
-                              device="cuda")
+            out = torch.empty(n, dtype=dt, device="cuda")
+        _device_tensor(out, "out", dt)
+        self._bind_stream()
         self._check(self.lib.qk_get_density_device(self.h, _ptr(wa), out.data_ptr(), out.numel()),
                     "get_density_device")
         return out
@@ -349,14 +371,15 @@ class Context:
 
     def set_points_device(self, coord, transp: str = "N", walk_num=None, elec_num=None):
         """CUDA float64 tensor [walk][elec][3] (or [3][n] with transp='T')."""
-        self._bind_stream()
         if walk_num is None:
             if transp == "N":
                 walk_num, elec_num = (coord.shape[0], coord.shape[1]) if coord.dim() == 3 \
                     else (1, coord.shape[0])
             else:
                 walk_num, elec_num = 1, coord.numel() // 3
-        assert coord.is_cuda and coord.is_contiguous() and str(coord.dtype) == "torch.float64"
+        import torch
+        _device_tensor(coord, "coord", torch.float64, min_numel=3 * walk_num * elec_num)
+        self._bind_stream()
         self._keep = [coord]
         self._check(self.lib.qk_set_points_device(self.h, transp.encode(), walk_num, elec_num,
                                                   _tptr(coord)), "set_points_device")
@@ -452,11 +475,12 @@ class Context:
     def mo_vgl_device(self, out=None):
         """MO vgl [walk][elec][5][mo] as a CUDA tensor (async on torch's stream)."""
         import torch
-        self._bind_stream()
-        self.ensure_workspace()
         w, e = self._walk_elec()
         if out is None:
             out = torch.empty((w, e, 5, self.mo_num), dtype=self.dtype_torch, device="cuda")
+        _device_tensor(out, "out", self.dtype_torch)
+        self._bind_stream()
+        self.ensure_workspace()
         self._check(self.lib.qk_get_mo_vgl_device(self.h, _tptr(out), out.numel()),
                     "get_mo_vgl_device")
         return out
@@ -465,9 +489,9 @@ class Context:
         """(dL/dC [mo][ao], dL/dR [nucl][3]) as CUDA float64 tensors for
         L = sum(dW * mo_vgl) at the current points (async on torch's stream)."""
         import torch
+        _device_tensor(dW, "dW", self.dtype_torch)
         self._bind_stream()
         self.ensure_workspace(extra=self.backward_workspace_size())
-        assert dW.is_cuda and dW.is_contiguous() and dW.dtype == self.dtype_torch
         dC = torch.empty((self.mo_num, self.ao_num), dtype=torch.float64, device="cuda") \
             if need_dC else None
         dR = torch.empty((self.nucl_num, 3), dtype=torch.float64, device="cuda") \
@@ -479,10 +503,11 @@ class Context:
 
     def ao_vgl_device(self, out=None):
         import torch
-        self._bind_stream()
         w, e = self._walk_elec()
         if out is None:
             out = torch.empty((w, e, 5, self.ao_num), dtype=self.dtype_torch, device="cuda")
+        _device_tensor(out, "out", self.dtype_torch)
+        self._bind_stream()
         self._check(self.lib.qk_get_ao_vgl_device(self.h, _tptr(out), out.numel()),
                     "get_ao_vgl_device")
         return out
@@ -570,8 +595,11 @@ class Batch:
         return (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
 
     def run(self, outs=None):
-        self._bind_stream()
+        import torch
         outs = self.outputs() if outs is None else outs
+        for o in outs:
+            _device_tensor(o, "batch output", torch.float32)
+        self._bind_stream()
         sizes = (ctypes.c_int64 * len(outs))(*[o.numel() for o in outs])
         self._check(self.lib.qk_batch_run(self.h, self._ptrs(outs), sizes), "batch_run")
         return outs

@@ -139,3 +139,54 @@ def test_missing_library_fails_loudly(tmp_path):
                        timeout=120)
     assert r.returncode != 0
     assert "no CPU fallback" in r.stderr
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor in the binding's checks (no GPU here)."""
+
+    def __init__(self, dtype, n, contiguous=True):
+        self.is_cuda, self.dtype, self._n, self._c = True, dtype, n, contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+
+def test_device_tensor_checks():
+    """Tensors passed by pointer are checked before any CUDA call: device,
+    layout, element type and, where the C call takes no size, the count."""
+    torch = pytest.importorskip("torch")
+    from paper_2512_16677_gb300 import qmckl
+    chk = qmckl._device_tensor
+    t = _FakeCuda(torch.float64, 12)
+    assert chk(t, "x", torch.float64, numel=12, min_numel=12) is t
+    bad = [(torch.zeros(4, 3, dtype=torch.float64), {}, "CUDA"),
+           (_FakeCuda(torch.float64, 12, contiguous=False), {}, "contiguous"),
+           (_FakeCuda(torch.float32, 12), {"dtype": torch.float64}, "dtype"),
+           (_FakeCuda(torch.float64, 11), {"numel": 12}, "expected 12"),
+           (_FakeCuda(torch.float64, 11), {"min_numel": 12}, "at least 12")]
+    for x, kw, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            chk(x, "x", **kw)
+
+
+def test_host_tensors_refused_before_any_device_call():
+    torch = pytest.importorskip("torch")
+    from paper_2512_16677_gb300 import qmckl
+    m = synth.make_config(1, walk_num=1)
+    c = _ctx()
+    c.set_nucleus(m.nucl_charge, m.nucl_coord)
+    c.set_ao_basis(m.shell_nucleus, m.shell_ang_mom, m.shell_prim_num, m.shell_factor,
+                   m.exponent, m.coefficient, m.prim_factor, m.ao_factor)
+    c.set_mo_coefficient(m.mo_coef)
+    with pytest.raises(ValueError, match="CUDA"):
+        c.set_points_device(torch.from_numpy(m.coord))
+    with pytest.raises(ValueError, match="CUDA"):
+        c.set_single_point_device(0, torch.zeros(1, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        c.backward_device(torch.zeros(1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        qmckl.contract_device(torch.zeros(2, 3), torch.zeros(4, 3))
+    c.close()
