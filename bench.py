@@ -37,7 +37,7 @@ CPU_SAMPLE_POINTS = 2400     # 4 walkers: about 10 s of oracle work on one core
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["bf16x3", "tf32", "fp32", "fp64"], default="bf16x3")
