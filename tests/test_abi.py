@@ -190,3 +190,24 @@ def test_host_tensors_refused_before_any_device_call():
     with pytest.raises(ValueError, match="CUDA"):
         qmckl.contract_device(torch.zeros(2, 3), torch.zeros(4, 3))
     c.close()
+
+
+def test_plain_c_consumer(lib, tmp_path):
+    """The header compiles as C99 with warnings as errors, a C program links
+    against the library and gets the documented status codes."""
+    import shutil
+    import subprocess
+    from paper_2512_16677_gb300 import qmckl
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(qmckl.LIB_PATH)
+    exe = tmp_path / "abi_consumer"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        f"-I{os.path.join(ROOT, 'include')}",
+                        os.path.join(ROOT, "tests", "c", "abi_consumer.c"), "-o", str(exe),
+                        f"-L{libdir}", "-lqmckl_gpu", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
