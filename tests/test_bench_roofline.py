@@ -44,3 +44,21 @@ def test_alu_entry_and_bound():
     # no ALU entry for the FP64 path
     r = bench.roofline("fp64", Mol, [1.0, 1.0], peaks, None, None, work)["ao_vgl"]
     assert "alu" not in r and r["bound"] == "hbm"
+
+
+def test_traffic_only_while_sources_match(tmp_path, monkeypatch):
+    """A kernel's ncu traffic is reported only while its source files hash
+    to what was captured; any edit turns it into null."""
+    import hashlib
+    import json
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"k:bf16x3": {"bytes_per_launch": 1234, "source": ["k.cu"], "source_sha": sha}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("k", "bf16x3") == 1234
+    assert bench.traffic_for("k", "tf32") is None
+    src.write_text("kernel v2\n")
+    assert bench.traffic_for("k", "bf16x3") is None
