@@ -34,6 +34,13 @@ MUTANTS = {
                               "g[1] = DV(e[0], 1 + e[1], e[2], k);"),
     "shell_factor": ("const double cf = b->shell_factor[s] * b->coefficient[k] * b->prim_factor[k];",
                      "const double cf = b->coefficient[k] * b->prim_factor[k];"),
+    "screen_count_radius": ("if (b->exponent[k] * r2 < T) ++np;",
+                            "if (b->exponent[k] * sqrt(r2) < T) ++np;"),
+    "screen_count_cartesians": ("counts[2] += (l + 1) * (l + 2) / 2;",
+                                "counts[2] += 2 * l + 1;"),
+    "screen_count_nucleus": ("const double* R = b->nucl_coord + 3 * b->shell_nucleus[s];\n"
+                             "      const double dx",
+                             "const double* R = b->nucl_coord;\n      const double dx"),
 }
 
 

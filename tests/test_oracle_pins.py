@@ -451,3 +451,44 @@ def test_screen_counts_match_tables(orc, cfg):
     assert aos >= int(nz.sum())
     assert 0 < pairs <= m.point_num * m.shell_num
     assert pairs <= prims <= m.point_num * m.prim_num
+
+
+def _screen_pin_molecule(bits, eps):
+    """Two nuclei 10 bohr apart on x: an s shell (gamma 0.1, 1, 10) and a p
+    shell (0.5, 4) on A at the origin, a d shell (2) on B; seven points whose
+    squared distances to A and B are whole numbers (or 18.9^2)."""
+    g = np.array([0.1, 1.0, 10.0, 0.5, 4.0, 2.0])
+    pts = np.array([[1, 0, 0], [3, 0, 0], [5, 0, 0], [8, 0, 0], [10, 0, 0], [30, 0, 0],
+                    [0, 18.9, 0]], dtype=float)
+    return synth.Molecule(
+        "screen-pin", np.array([1.0, 1.0]), np.array([[0, 0, 0], [10, 0, 0]], dtype=float),
+        np.array([0, 0, 1], dtype=np.int64), np.array([0, 1, 2], dtype=np.int32),
+        np.array([3, 2, 1], dtype=np.int64), np.ones(3), g, np.ones(6), np.ones(6),
+        np.ones(10), np.eye(10), pts.reshape(1, -1, 3), bits=bits, eps=eps)
+
+
+# (surviving point-shell pairs, evaluated primitives, point-AO pairs) per
+# point, counted by hand from gamma r^2 < T (Eq. 3):
+#   B = 53 -> T = 36.04; r^2_A = 1, 9, 25, 64, 100, 900, 357.21 and
+#   r^2_B = 81, 49, 25, 4, 0, 400, 457.21.  E.g. at x = 8: s passes 0.1*64,
+#   p passes 0.5*64, d passes 2*4 -> 3 shells, 3 primitives, 1 + 3 + 6 AOs;
+#   at (0, 18.9, 0) only 0.1 * 357.21 = 35.72 passes.
+#   eps = 1e-10 -> T = 23.03: the same points lose 1*25, 0.5*64, 4*9 and
+#   0.1*357.21.
+_SCREEN_PIN = {
+    (53, None): [(2, 5, 4), (2, 4, 4), (2, 3, 4), (3, 3, 10), (2, 2, 7), (0, 0, 0),
+                 (1, 1, 1)],
+    (None, 1e-10): [(2, 5, 4), (2, 3, 4), (2, 2, 4), (2, 2, 7), (2, 2, 7), (0, 0, 0),
+                    (0, 0, 0)],
+}
+
+
+@pytest.mark.parametrize("bits,eps", list(_SCREEN_PIN))
+def test_screen_counts_hand_counted(orc, bits, eps):
+    """screen_counts equals hand counts of Eq. 3 on a two-nucleus case, point
+    by point and in total (the roofline's denominator rests on it)."""
+    m = _screen_pin_molecule(bits, eps)
+    want = _SCREEN_PIN[(bits, eps)]
+    for p, w in zip(m.points, want):
+        assert orc.screen_counts(m, points=p[None, :]) == w, p
+    assert orc.screen_counts(m) == tuple(int(sum(c)) for c in zip(*want))
