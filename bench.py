@@ -179,7 +179,8 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None, work=No
     (point, AO) entries (the live 16-AO groups it actually writes are given
     beside them; stats = (live blocks, all blocks, live entries)).
     The contraction's algorithmic work is the sparse product of Sec. 3.2:
-    2 * 5 * mo_num * nnz flops (x3 for the bf16 split) with nnz the nonzero
+    2 * 5 * mo_num * nnz flops (one product; the bf16 split issues three,
+    counted under issued_*) with nnz the nonzero
     (point, AO) pairs (sparsity = (live 16-AO groups, nnz)), over the bytes
     it must move (nonzero AO entries, C, the FP32 output).  Its bound is the
     roofline whose floor is longer (arithmetic intensity against the ridge
@@ -231,10 +232,13 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None, work=No
         hbm = peaks["hbm_gbs"]
         if mode in ("bf16x3", "tf32"):
             tensor = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            # the method's own count is one product; the bf16 split issues
+            # three (hi*hi + hi*lo + lo*hi), reported under issued_* only
+            fl = useful
             if mode == "bf16x3":
-                fl, tnote = 3 * useful, "measured bf16 sustained"
+                tnote = "measured bf16 sustained"
             else:
-                fl, tensor = useful, tensor * 0.5
+                tensor = tensor * 0.5
                 tnote = "measured bf16 sustained x 1/2 (tf32/bf16 nominal ratio)"
             # what the sparse product must move: the nonzero AO entries (both
             # bf16 planes, or FP32), C once, and the FP32 output
@@ -243,7 +247,8 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None, work=No
             ent = {"algorithmic_flops": fl, "algorithmic_bytes": nbytes,
                    "arithmetic_intensity": fl / nbytes,
                    "ridge_flop_per_byte": tensor * 1e12 / (hbm * 1e9),
-                   "dense_equivalent_flops": dense * (3 if mode == "bf16x3" else 1),
+                   "dense_equivalent_flops": dense,
+                   "split_products": 3 if mode == "bf16x3" else 1,
                    "tensor": {"achieved": fl / t_mo / 1e12, "peak": tensor, "unit": "TFLOP/s",
                               "frac": t_tc / t_mo, "peak_note": tnote},
                    "hbm": {"achieved": nbytes / t_mo / 1e9, "peak": hbm, "unit": "GB/s",
@@ -275,6 +280,29 @@ def roofline(mode, mol, ms_per_launch, peaks, stats=None, sparsity=None, work=No
                                      "algorithmic_flops": useful,
                                      "dense_equivalent_flops": dense}
     return out
+
+
+def speedup_decomposition(res, roof, mol):
+    """The split-bf16 contraction's speedup over the plain FP32 SIMT GEMM,
+    split into the work the block-sparse product skips and the rate at which
+    the tensor cores do the rest (per product: the split issues three)."""
+    mo = roof.get("mo_contraction", {})
+    if "issued_flops" not in mo or not res.get("fp32_path"):
+        return None
+    dense = mo["dense_equivalent_flops"]
+    per_product = mo["issued_flops"] / mo["split_products"]
+    t32 = res["fp32_path"]["contraction_ms"] * 1e-3
+    t16 = res["kernels"]["contraction_ms"] * 1e-3
+    rate32 = dense / t32
+    rate16 = per_product / t16
+    return {"contraction_speedup": t32 / t16,
+            "skipped_work_factor": dense / per_product,
+            "rate_factor_per_product": rate16 / rate32,
+            "fp32_simt_tflops": rate32 / 1e12,
+            "split_bf16_tflops_per_product": rate16 / 1e12,
+            "ao_vgl_speedup": (res["fp32_path"]["ao_vgl_ms"] / res["kernels"]["ao_vgl_ms"]
+                               if res["kernels"]["ao_vgl_ms"] else None),
+            "note": "contraction_speedup = skipped_work_factor x rate_factor_per_product"}
 
 
 def traffic_for(kernel, mode):
@@ -404,18 +432,38 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
 
-    # same workload through the plain FP32 path (SIMT ao_vgl + SIMT GEMM)
-    if not args.no_fp32_line and args.mode != "fp32":
+    # the main mode's first rows, kept for the accuracy comparison below
+    samples = {}
+    if rank == 0 and not args.no_cpu_baseline:
+        samples[args.mode] = out[:CPU_SAMPLE_POINTS * 5 * mol.mo_num].double().cpu().numpy()
+
+    # same workload through the other compute paths: the plain FP32 path
+    # (SIMT ao_vgl + SIMT GEMM), TF32 tensor cores and FP64 (a few steps)
+    if not args.no_fp32_line:
         del ctx
-        c32, _, ms32, k32, n32, clk32, _ = measure("fp32", max(3, args.steps // 4), 2)
-        ms32_step = ms32 / max(3, args.steps // 4)
-        res["fp32_path"] = {"value": world * evals_per_step / (ms32_step * 1e-3),
-                            "ms_per_step": ms32_step,
-                            "contraction_ms": k32[1] / max(n32[1], 1),
-                            "ao_vgl_ms": k32[0] / max(n32[0], 1), "clocks": clk32}
-        res["speedup_vs_fp32_path"] = res["fp32_path"]["ms_per_step"] / ms_step
-        del c32
         ctx = None
+        for mode, steps in (("fp32", max(3, args.steps // 4)), ("tf32", max(3, args.steps // 4)),
+                            ("fp64", 3)):
+            if mode == args.mode:
+                continue
+            co, oo, mso, ko, no, clko, _ = measure(mode, steps, 2)
+            ms_o = mso / steps
+            ent = {"value": world * evals_per_step / (ms_o * 1e-3), "ms_per_step": ms_o,
+                   "steps": steps, "contraction_ms": ko[1] / max(no[1], 1),
+                   "ao_vgl_ms": ko[0] / max(no[0], 1), "clocks": clko}
+            if mode in ("bf16x3", "tf32"):
+                lt = [ko[i] / no[i] if no[i] else 0.0 for i in range(3)]
+                r = roofline(mode, mol, lt, peaks, co.block_stats(), co.sparsity_stats(), None)
+                ent["roofline"] = {k: r["mo_contraction"][k] for k in
+                                   ("bound", "achieved", "peak", "unit", "frac")}
+            res[f"{mode}_path"] = ent
+            if rank == 0 and not args.no_cpu_baseline:
+                samples[mode] = oo[:CPU_SAMPLE_POINTS * 5 * mol.mo_num].double().cpu().numpy()
+            del co, oo
+        res["speedup_vs_fp32_path"] = res["fp32_path"]["ms_per_step"] / ms_step
+        if args.mode == "bf16x3":
+            res["speedup_decomposition"] = speedup_decomposition(res, roof, mol)
+    res["_accuracy_samples"] = samples
 
     if not args.no_batch:
         res["batch"] = measure_batch(args, world)
@@ -692,24 +740,79 @@ def measure_density(args):
 
 
 # -------------------------------------------------------- cpu baseline ---
-def oracle_sample(mol, n_points):
-    """Time the FP64 oracle on the first n_points of walker 0."""
+_ORACLE_MEMO = {}
+
+
+def oracle_sample(mol, n_points, memo=False):
+    """Time the FP64 oracle on the first n_points of walker 0 (one thread);
+    memo=True returns an earlier result for the same molecule and size."""
+    key = (id(mol), n_points)
+    if memo and key in _ORACLE_MEMO:
+        return _ORACLE_MEMO[key]
     from oracle import oracle
     oracle.build()
     pts = mol.points[:n_points]
     t0 = time.perf_counter()
     ref, size = oracle.mo_vgl(mol, points=pts)
     dt = time.perf_counter() - t0
+    _ORACLE_MEMO[key] = (ref, size, dt)
     return ref, size, dt
 
 
+def host_cores():
+    """Threads to run the oracle on: the cores this process may use."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU's model string (lscpu), e.g. for placing the baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_parallel(mol, pts, threads):
+    """Time the unchanged FP64 oracle over `threads` disjoint ranges of pts,
+    one thread each (the oracle is C called through ctypes, which releases
+    the GIL, so the threads run on separate cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    parts = [p for p in np.array_split(pts, threads) if p.shape[0]]
+    with ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda p: oracle.mo_vgl(mol, points=p), parts))
+        dt = time.perf_counter() - t0
+    return dt, len(parts)
+
+
 def cpu_baseline(mol, gpu_w0):
+    """The FP64 oracle on the host cores: all of them (the line's value) and
+    one (single_core), on bounded samples of the workload's points."""
     n = CPU_SAMPLE_POINTS
     ref, size, dt = oracle_sample(mol, n)
-    out = {"value": n * mol.mo_num / dt, "unit": UNIT, "cores": 1,
-           "kind": "oracle",
-           "sample": f"walkers 0-{n // mol.elec_num - 1} ({n} points) of the 256-walker "
-                     f"workload, screened FP64 oracle with compensated sums, {dt:.1f} s"}
+    cores = host_cores()
+    npar = min(mol.point_num, cores * (n // 4))
+    dtp, used = oracle_parallel(mol, mol.points[:npar], cores)
+    model = cpu_model()
+    out = {"value": npar * mol.mo_num / dtp, "unit": UNIT, "cores": used,
+           "kind": "oracle", "cpu_model": model,
+           "sample": f"points 0-{npar - 1} of the 256-walker workload split over {used} "
+                     f"threads ({n // 4} points each), screened FP64 oracle with compensated "
+                     f"sums, {dtp:.1f} s wall",
+           "single_core": {"value": n * mol.mo_num / dt, "unit": UNIT, "cores": 1,
+                           "sample": f"walkers 0-{n // mol.elec_num - 1} ({n} points), "
+                                     f"{dt:.1f} s"}}
     if gpu_w0 is not None:
         import numpy as np
         e = np.abs(gpu_w0.reshape(ref.shape) - ref) / (size + 1e-300)
@@ -721,19 +824,55 @@ def cpu_baseline(mol, gpu_w0):
     return out
 
 
+def accuracy(mol, samples, main_mode):
+    """Max normwise error against the FP64 oracle per compute path, on the
+    first rows of each path's output (the CPU baseline's sample)."""
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from tolerances import TOL
+    if not samples:
+        return None
+    n = CPU_SAMPLE_POINTS
+    ref, size, _ = oracle_sample(mol, n, memo=True)
+    out = {}
+    for mode, got in samples.items():
+        e = np.abs(got.reshape(ref.shape) - ref) / (size + 1e-300)
+        out[mode] = {"value": float(e[:, 0].max()), "gradient": float(e[:, 1:4].max()),
+                     "laplacian": float(e[:, 4].max()), "stated_bar": TOL[mode][0]}
+    out["metric"] = "normwise |gpu-oracle|/sum|C||chi| on the first %d points" % n
+    return out
+
+
+def common_bar(res, main_mode):
+    """The main path's speedup over the plain FP32 path at one stated bar
+    both meet: the looser of the two stated bars, when both measured errors
+    are within it."""
+    acc = res["accuracy"]
+    if main_mode not in acc or "fp32" not in acc:
+        return None
+    bar = max(acc[main_mode]["stated_bar"], acc["fp32"]["stated_bar"])
+    worst = {m: max(acc[m]["value"], acc[m]["gradient"], acc[m]["laplacian"])
+             for m in (main_mode, "fp32")}
+    return {"bar": bar, "measured_max": worst, "both_meet": all(v <= bar for v in worst.values()),
+            "speedup": res["fp32_path"]["ms_per_step"] / res["ms_per_step"]}
+
+
 def run_reference(args, rank, world):
     from paper_2512_16677_gb300 import synth
     if rank != 0:
         return None
     mol = synth.make_config(2)
-    n = 48
+    cores = host_cores()
+    n = 48 * cores          # per step: 48 points on each host core
     for _ in range(args.warmup):
-        oracle_sample(mol, n)
+        oracle_parallel(mol, mol.points[:n], cores)
     times = []
+    used = cores
     for i in range(args.steps):
         # each step: a bounded sample of the workload's points
-        sub = mol.with_points(mol.points[(i * n) % mol.point_num:][:n])
-        _, _, dt = oracle_sample(sub, n)
+        start = (i * n) % mol.point_num
+        pts = mol.points[start:start + n]
+        dt, used = oracle_parallel(mol, pts, cores)
         times.append(dt)
     tot = sum(times)
     value = n * mol.mo_num * args.steps / tot
@@ -742,8 +881,10 @@ def run_reference(args, rank, world):
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": "oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} points per step of the workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"{n} points per step of the workload, "
+                                       f"48 per thread on {used} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -770,9 +911,13 @@ def main():
         import torch.distributed as dist
         dist.barrier()
     res, mol, gpu_w0 = run_ours(args, rank, world, local_rank)
+    samples = res.pop("_accuracy_samples", {})
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(mol, gpu_w0)
+            res["accuracy"] = accuracy(mol, samples, args.mode)
+            if res.get("fp32_path") and res["accuracy"]:
+                res["speedup_at_common_bar"] = common_bar(res, args.mode)
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

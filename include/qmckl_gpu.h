@@ -293,6 +293,17 @@ qk_status qk_get_block_stats(qk_context ctx, int64_t* live_blocks, int64_t* tota
    synchronises the stream. */
 qk_status qk_get_sparsity_stats(qk_context ctx, int64_t* live_groups, int64_t* nnz);
 
+/* Tile layout of the same AO tensor (tensor-core path, after a get_mo_vgl at
+   this time stamp; else QK_ERR_NOT_PROVIDED), for tests and profiling:
+   perm[s] (host int32, n >= point_num) = the caller's point held by point
+   slot s (slots 25 t .. 25 t + 24 make contraction tile t: the spatial
+   order of the points, or the identity when it is off); live[t] (host
+   int32, ntiles >= ceil(point_num / 25)) = the (tile, AO chunk) blocks of
+   tile t holding an entry that survived Eq. 3.  Either may be NULL.
+   Synchronises the context's stream. */
+qk_status qk_get_tile_layout(qk_context ctx, int32_t* perm, int64_t n, int32_t* live,
+                             int64_t ntiles);
+
 /* ----------------------------------------------------------- evaluate --- */
 
 /* AO vgl [walk][elec][5][ao_num] into host memory; size = number of elements
@@ -338,13 +349,28 @@ qk_status qk_contract_device(int32_t mode, int64_t M, int64_t N, int64_t K, cons
    planes 1, es 4; so about (M + N) * ld <= 8.38e6.  Larger problems are
    refused with QK_ERR_BAD_SIZE before any work is queued.
    The first call on a device looks up the array's device address (once per
-   device, with that device current); make that first call before any stream
-   capture.  All calls share the one array and it keeps the previous call's
+   device and CUDA context, with that device current: again after a device
+   reset); make that first call before any stream capture.  All calls share the one array and it keeps the previous call's
    contents (the error word is cleared on every call): calls that overlap on
    the GPU race, so serialise them (one stream, or events).  Synchronises
    `stream` to read the error word.  Allocates no device or host memory. */
 qk_status qk_contract_device_noalloc(int32_t mode, int64_t M, int64_t N, int64_t K,
                                      const float* A, const float* B, float* D, void* stream);
+
+/* Self-test of the bounded device-side waits (the paper has no counterpart:
+   every tcgen05 kernel here waits on mbarriers with a clock limit, and a
+   wait that gives up records a code in the caller's error word, which the
+   host reports as QK_ERR_DEVICE_TIMEOUT).  One small kernel waits on an
+   mbarrier that nothing arrives at: one thread with limit_cycles (1 ..
+   1e8 SM clock cycles, else QK_ERR_BAD_SIZE), which gives up and raises the
+   CTA's abort flag, and one with the library's normal limit (about 2 s),
+   which must leave through that flag.  Returns QK_ERR_DEVICE_TIMEOUT when
+   the short wait gave up as it should (QK_SUCCESS would mean it did not).
+   info (host, 4 int32, may be NULL): [0] the error word, [1] 1 if the
+   second waiter left through the abort flag (2: by its own limit),
+   [2], [3] the cycles each waiter spent.  Allocates 16 bytes of device
+   memory; synchronises the device. */
+qk_status qk_selftest_wait_timeout(int64_t limit_cycles, int32_t* info);
 
 /* ------------------------------------------------------------ adjoint --- */
 

@@ -61,6 +61,20 @@ int pick_bn(int64_t n, int bn_max) {
 
 // Build descriptors and work lists for the current contexts and outputs.
 qk_status build(qk_batch b, float* const* outs) {
+  // the descriptors, work lists and error word are rewritten below with
+  // blocking copies on the legacy stream: first let every earlier launch on
+  // the batch stream finish, and report a wait of one of them that gave up
+  // before its error word is cleared
+  if (b->d_flag.p) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, b->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "batch rebuild");
+    if (flag != 0) {
+      cudaMemset(b->d_flag.p, 0, sizeof(int));
+      return bfail(b, QK_ERR_DEVICE_TIMEOUT, "a device-side wait of an earlier run gave up");
+    }
+  }
   const int n = (int)b->ctxs.size();
   std::vector<AOProblem> aop(n);
   std::vector<TcProblem> tcp(n);
@@ -142,6 +156,14 @@ qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig)
                    "context " + std::to_string(i) + " has the cusp correction on");
     qk_status st = context_forward_views(b->ctxs[i], &v);
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
+    // tables re-uploaded in place (same sizes) keep their addresses: the
+    // basis version, the Eq. 3 threshold and the chunking say whether the
+    // AO problem copied into the descriptors is still the context's
+    sig->push_back((uintptr_t)v.basis_version);
+    uint64_t tbits = 0;
+    std::memcpy(&tbits, &v.b.T, sizeof tbits);
+    sig->push_back((uintptr_t)tbits);
+    sig->push_back((uintptr_t)v.b.nchunk);
     sig->push_back((uintptr_t)v.ao.a);
     sig->push_back((uintptr_t)v.ao.a_lo);
     sig->push_back((uintptr_t)v.ao.mask);

@@ -1725,6 +1725,42 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
   return QK_SUCCESS;
 }
 
+qk_status qk_get_tile_layout(qk_context c, int32_t* perm, int64_t n, int32_t* live,
+                             int64_t ntiles) {
+  CHECK_CTX(c);
+  if (use_fused(c) || !tiled_mode(c->ao_mode) || c->ao_ws == nullptr ||
+      c->ao_date != c->date)
+    return fail(c, QK_ERR_NOT_PROVIDED,
+                "no AO tensor of the current points in a two-kernel tensor-core mode");
+  const int64_t tiles = ao_tiles(c);
+  if ((perm && n < c->point_num) || (live && ntiles < tiles))
+    return fail(c, QK_ERR_BAD_SIZE, "perm needs %lld and live %lld elements",
+                (long long)c->point_num, (long long)tiles);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tile layout");
+  if (perm) {
+    if (c->ao_sorted && c->perm) {
+      e = cudaMemcpy(perm, c->perm, sizeof(int32_t) * c->point_num, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(c, e, "point order read");
+    } else {
+      for (int64_t s = 0; s < c->point_num; ++s) perm[s] = (int32_t)s;
+    }
+  }
+  if (live) {
+    const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
+    const int64_t nq = t.nchunk, ld = mask_ld(t.nchunk);
+    std::vector<uint8_t> mask((size_t)(tiles * ld));
+    e = cudaMemcpy(mask.data(), t.mask, mask.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "block mask read");
+    for (int64_t ti = 0; ti < tiles; ++ti) {
+      int32_t k = 0;
+      for (int64_t q = 0; q < nq; ++q) k += mask[ti * ld + q] != 0;
+      live[ti] = k;
+    }
+  }
+  return QK_SUCCESS;
+}
+
 qk_status qk_backward_workspace_size(qk_context c, size_t* bytes) {
   CHECK_CTX(c);
   if (!bytes) return QK_ERR_NULL_POINTER;
@@ -1843,6 +1879,7 @@ qk_status context_forward_views(qk_context c, ForwardViews* v) {
   v->walk_num = c->walk_num;
   v->elec_num = c->elec_num;
   v->mode = c->mode;
+  v->basis_version = c->basis_version;
   return QK_SUCCESS;
 }
 

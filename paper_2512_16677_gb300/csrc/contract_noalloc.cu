@@ -12,10 +12,12 @@
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes; every
 // GPU that loads the library holds it until the process exits.  Host code
 // cannot use the array's name as a device address (on the host it names a
-// stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made on
-// that device.
-#include <atomic>
+// stand-in), so the device address is looked up with cudaGetSymbolAddress,
+// with that device current, on the first call made on that device (and
+// again after a reset of the device gave it a new context).
+#include <cuda.h>
+
+#include <mutex>
 
 #include "internal.h"
 
@@ -28,22 +30,56 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::atomic<void*> g_scratch_addr[kMaxDevices];
+// Device address of the array, cached per device together with the CUDA
+// context it was looked up in: a reset of the device (cudaDeviceReset)
+// gives the next call a new primary context, in which the module and the
+// array are loaded afresh, so a cached address counts only while the
+// current context is the one it came from.
+struct ScratchAddr {
+  void* ctx = nullptr;
+  void* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current_fn() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  return fn;
+}
+
+// Device address of the scratch array in the current device's context (set-up
+// on the first call per device and context, with that device current).
 cudaError_t scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  void* p = g_scratch_addr[dev].load();
-  if (!p) {
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  CtxGetCurrentFn get = ctx_get_current_fn();
+  if (!get) return cudaErrorInitializationError;
+  CUcontext ctx = nullptr;  // NULL until the runtime first touches the device
+  if (get(&ctx) != CUDA_SUCCESS) return cudaErrorInitializationError;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  ScratchAddr& slot = g_scratch_addr[dev];
+  if (!ctx || slot.ctx != (void*)ctx || !slot.addr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the context current if need be
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev].store(p);
+    if (get(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorInitializationError;
+    slot.ctx = (void*)ctx;
+    slot.addr = p;
   }
-  *out = p;
+  *out = slot.addr;
   return cudaSuccess;
 }
 

@@ -374,6 +374,7 @@ struct ForwardViews {
   const void* c_lo;
   int64_t kpad, mo_num, walk_num, elec_num;
   int mode;
+  uint64_t basis_version;  // bumped by every change of nuclei, basis, cutoff or order
 };
 qk_status context_forward_views(qk_context c, ForwardViews* v);
 // Whether the context applies the MO cusp correction.

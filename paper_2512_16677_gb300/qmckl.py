@@ -79,6 +79,7 @@ SIGNATURES = {
     "qk_get_block_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                            ctypes.POINTER(_I64)],
     "qk_get_sparsity_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "qk_get_tile_layout": [_P, _P, _I64, _P, _I64],
     "qk_batch_create": [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)],
     "qk_batch_destroy": [_P],
     "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
@@ -91,6 +92,7 @@ SIGNATURES = {
     "qk_batch_autotune": [_P, ctypes.POINTER(_P), _I32, ctypes.POINTER(_D)],
     "qk_contract_device": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
     "qk_contract_device_noalloc": [_I32, _I64, _I64, _I64, _P, _P, _P, _P],
+    "qk_selftest_wait_timeout": [_I64, _P],
     "qk_get_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32],
 }
 
@@ -470,6 +472,18 @@ class Context:
         self._check(self.lib.qk_get_sparsity_stats(self.h, ctypes.byref(a), ctypes.byref(b)),
                     "get_sparsity_stats")
         return a.value, b.value
+
+    def tile_layout(self):
+        """(perm, live): the caller's point at each slot of the contraction
+        tiles (25 slots per tile) and the live AO blocks of each tile, for the
+        AO tensor of the current points (tensor-core path)."""
+        n = self.point_num
+        tiles = (n + 24) // 25
+        perm = np.zeros(n, dtype=np.int32)
+        live = np.zeros(tiles, dtype=np.int32)
+        self._check(self.lib.qk_get_tile_layout(self.h, perm.ctypes.data, n, live.ctypes.data,
+                                                tiles), "get_tile_layout")
+        return perm, live
 
     # ------------------------------------------------------------ evaluate
     def mo_vgl_device(self, out=None):

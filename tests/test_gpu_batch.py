@@ -92,3 +92,30 @@ def test_batch_rejects_mixed_or_unset(cfg):
     d.set_molecule(mols[1])                           # no points
     with pytest.raises(qmckl.QmcklError):
         qmckl.Batch([a, d])
+
+
+def test_batch_follows_a_cutoff_change(orc, cfg):
+    """A context's Eq. 3 threshold changed after a batch run (tables
+    re-uploaded in place, same sizes) must reach the next batch run: each
+    molecule's batch output equals its own single-context evaluation, and
+    the changed one matches the oracle at its new cutoff."""
+    import dataclasses
+
+    from paper_2512_16677_gb300 import qmckl
+    mols = cfg(4, walk_num=4)[:3]
+    coords = [torch.from_numpy(m.coord).cuda() for m in mols]
+    ctxs = _contexts(mols, coords)
+    b = qmckl.Batch(ctxs)
+    b.run()
+    b.synchronize()
+    ctxs[1].set_cutoff(1e-4)                          # T from 23.0 down to 9.2
+    outs = b.run()
+    b.synchronize()
+    m1 = dataclasses.replace(mols[1], bits=None, eps=1e-4)
+    _check_all(orc, [mols[0], m1, mols[2]], outs, n=32, seed=3)
+    for c, m, o in zip(ctxs, mols, outs):
+        single = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        ref = single.double().cpu().numpy().reshape(-1, 5, m.mo_num)
+        got = o.double().cpu().numpy().reshape(-1, 5, m.mo_num)
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.abs(ref).max()

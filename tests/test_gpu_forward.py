@@ -104,14 +104,35 @@ def test_organic_one_walker(orc, cfg, mode):
     _report("organic150_1w", mode, assert_within(mode, got, ref, size, "organic"))
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32", "fp32", "fp64"])
-def test_organic_full_size_sampled(orc, cfg, mode):
-    """Full benchmark workload (153 600 points), sampled outputs."""
+FULL_SAMPLE = 1024     # sampled points of the full organic workload
+
+
+@pytest.fixture(scope="module")
+def organic_full_sample(orc, cfg):
+    """The sampled points of the full organic workload (stratified over the
+    tiles of the split-bf16 launch) and the oracle's MO vgl at them."""
+    from sampling import mo_vgl_threaded, slot_offsets_covered, stratified_points
     m = cfg(2)
-    rng = np.random.default_rng(7)
-    idx = np.sort(rng.choice(m.point_num, 96, replace=False))
-    idx[0], idx[-1] = 0, m.point_num - 1          # first and last rows of the launch
-    ref, size = orc.mo_vgl(m, points=m.points[idx])
+    c = _ctx(m, "bf16x3")
+    c.mo_vgl_device()
+    torch.cuda.synchronize()
+    perm, live = c.tile_layout()
+    c.close()
+    idx = stratified_points(perm, live, FULL_SAMPLE, seed=7)
+    assert idx.shape[0] >= FULL_SAMPLE
+    assert slot_offsets_covered(perm, idx) == set(range(25))
+    ref, size = mo_vgl_threaded(orc, m, m.points[idx])
+    return idx, ref, size
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32", "fp32", "fp64"])
+def test_organic_full_size_sampled(cfg, organic_full_sample, mode):
+    """Full benchmark workload (153 600 points) in the benchmark's launch
+    configuration, checked on >= 1024 points stratified over tile classes
+    (sparsest to densest live-block counts), slot offsets and both ends of
+    the permutation."""
+    m = cfg(2)
+    idx, ref, size = organic_full_sample
     c, got = _run(m, mode)
     errs = assert_within(mode, got[idx], ref, size, "organic full")
     _report("organic150_full_sampled", mode, errs)

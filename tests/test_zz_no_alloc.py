@@ -3,9 +3,10 @@ cannot call cudaMalloc (a framework or pool owns the device memory, a
 latency-critical loop cannot take the synchronisation of cudaMalloc/
 cudaFree, or the caller must not fail for lack of memory once started).
 
-Its result must match the allocating entry point qk_contract_device within
-the contraction tolerances used elsewhere in the tests, on two calls in a
-row (the shared scratch array keeps the previous call's contents).  This
+Its result must match the FP64 product of its inputs, and the allocating
+entry point qk_contract_device, within the contraction tolerances used
+elsewhere in the tests, on two calls in a row (the shared scratch array
+keeps the previous call's contents).  This
 file is collected last so that a failure here comes after every other test.
 """
 import ctypes
@@ -46,7 +47,9 @@ def _inputs(seed, M, N, K):
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
 def test_noalloc_matches_allocating_entry(lib, mode):
     # two calls in a row with different shapes and data: the second must not
-    # see anything of the first
+    # see anything of the first.  Each result is held against the FP64
+    # product of its own inputs (normwise, the bar of the contraction tests)
+    # and against the allocating entry point on the same inputs.
     for seed, (M, N, K) in ((1, (700, 300, 1650)), (2, (333, 37, 70))):
         a, b = _inputs(seed, M, N, K)
         ref = torch.empty(M, N, dtype=torch.float32, device="cuda")
@@ -54,9 +57,14 @@ def test_noalloc_matches_allocating_entry(lib, mode):
         out = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
         assert _call(lib, "qk_contract_device_noalloc", mode, a, b, out) == 0
         torch.cuda.synchronize()
-        size = (a.double().abs() @ b.double().abs().T)
-        err = float(((out.double() - ref.double()).abs() / size).max())
-        assert err <= TOL[mode], f"{mode} {(M, N, K)}: {err:.3e}"
+        a64, b64 = a.double().cpu(), b.double().cpu()
+        exact = a64 @ b64.T
+        size = a64.abs() @ b64.abs().T
+        got = out.double().cpu()
+        err64 = float(((got - exact).abs() / size).max())
+        assert err64 <= TOL[mode], f"{mode} {(M, N, K)} vs FP64: {err64:.3e}"
+        err = float(((got - ref.double().cpu()).abs() / size).max())
+        assert err <= TOL[mode], f"{mode} {(M, N, K)} vs qk_contract_device: {err:.3e}"
 
 
 def test_noalloc_rejects_oversize_and_bad_mode(lib):
