@@ -134,6 +134,15 @@ qk_status qk_get_shell_order(qk_context ctx, int64_t* order, int64_t n);
    of the paper's method.  Other modes and the host-memory calls ignore it. */
 qk_status qk_set_spatial_order(qk_context ctx, int32_t enable);
 
+/* Tensor-core modes, two-kernel path: 1 (default) runs the contraction of
+   Eqs. 5-7 on pairs of SMs (one tcgen05 MMA with M = 256 over two
+   consecutive point tiles, each SM holding half of the C tile), 0 on single
+   SMs.  Both multiply the same live blocks; a pair multiplies the union of
+   its two tiles' live column groups, whose extra terms are exact zeros, so
+   the results are the same.  A layout choice of this library, not a step
+   of the paper's method. */
+qk_status qk_set_sm_pairs(qk_context ctx, int32_t enable);
+
 /* MO cusp correction (Sec. 3.3).  rc [nucl_num]: sphere radius in bohr
    around each nucleus (>= 0, 0 = no correction there); NULL switches the
    correction off.  Inside the sphere of A every MO output becomes
@@ -299,10 +308,17 @@ qk_status qk_get_sparsity_stats(qk_context ctx, int64_t* live_groups, int64_t* n
    slot s (slots 25 t .. 25 t + 24 make contraction tile t: the spatial
    order of the points, or the identity when it is off); live[t] (host
    int32, ntiles >= ceil(point_num / 25)) = the (tile, AO chunk) blocks of
-   tile t holding an entry that survived Eq. 3.  Either may be NULL.
-   Synchronises the context's stream. */
+   tile t holding an entry that survived Eq. 3; groups (host uint8,
+   gsize >= ntiles * nchunk, nchunk = ceil(padded AO columns / 64)) =
+   [tile][chunk] bit g set when 16-AO column group g of the block holds
+   such an entry.  Any of the three may be NULL.  Synchronises the
+   context's stream. */
 qk_status qk_get_tile_layout(qk_context ctx, int32_t* perm, int64_t n, int32_t* live,
-                             int64_t ntiles);
+                             int64_t ntiles, uint8_t* groups, int64_t gsize);
+
+/* Number of 64-column AO chunks of the current basis (the contraction's K
+   blocks; chunks end on shell boundaries, so it may exceed ao_num / 64). */
+qk_status qk_get_ao_chunk_num(qk_context ctx, int64_t* nchunk);
 
 /* ----------------------------------------------------------- evaluate --- */
 

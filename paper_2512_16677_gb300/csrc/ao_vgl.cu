@@ -90,8 +90,12 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
   const bool culled = kTiled && out.reach != nullptr;
   for (int64_t base = t_begin; base < t_end; base += 32 * t_step) {
     const int64_t mine = base + (int64_t)lane * t_step;
-    unsigned word = 0u;
+    unsigned word = 0u, pword = 0u;
     if (mine < t_end) word = culled ? out.reach[mine * out.nchunk + q] : ~0u;
+    // the partner tile's reach word (the contraction multiplies tiles 2i and
+    // 2i + 1 together over the union of their live column groups)
+    if (kTiled && culled && out.pair_zero && mine < t_end && (mine ^ 1) < t_end)
+      pword = out.reach[(mine ^ 1) * out.nchunk + q];
     if (culled && warp == 0 && mine < t_end && word == 0u)
       out.mask[mine * mask_ld(out.nchunk) + q] = 0;
     unsigned todo = __ballot_sync(0xffffffffu, word != 0u);
@@ -106,6 +110,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
       const int64_t ptile = base + (int64_t)i * t_step;
       const int64_t p0 = ptile * TP;
       const unsigned pre = culled ? __shfl_sync(0xffffffffu, word, i) : ~0u;
+      const unsigned ppre = __shfl_sync(0xffffffffu, pword, i);
       __syncthreads();  // tables ready / previous tile's copy-out done with the stage
       // ---- phase 0 (warp 0): the tile's points, its bounding box and the
       // shells that may reach it
@@ -152,6 +157,15 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
         const unsigned gm = sh.gmask;
         if (tid == 0) out.mask[ptile * mask_ld(out.nchunk) + q] = (uint8_t)gm;
         if (!gm) continue;
+        // groups written: the live ones, plus (pairs) those the partner tile
+        // may make live, which hold zeros here (their staging columns are
+        // zero: no shell of theirs had a nonzero value at this tile)
+        unsigned wm = gm;
+        if (out.pair_zero) {
+          const bool on = lane < ns && ((ppre >> lane) & 1u);
+          const unsigned gb = on ? shell_group_bits(sh.col[lane], sh.lsh[lane]) : 0u;
+          wm |= __reduce_or_sync(0xffffffffu, gb) & 0xFu;
+        }
         // ---- phase 2, tiled: all 128 rows (stage rows 125..127 belong to the
         // lane past the tile and hold zeros) in 16-byte stores; the columns of
         // dead 16-AO groups are not written (the contraction never reads them)
@@ -160,7 +174,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
           // a lane splits 8 consecutive columns of one row into 16 bytes of each
           // bf16 plane: hi = rn(v), lo = rn(v - hi); a warp covers 4 rows
           const int rsub = lane >> 3, c8 = lane & 7;
-          const bool store = (gm >> (c8 >> 1)) & 1u;
+          const bool store = (wm >> (c8 >> 1)) & 1u;
   #pragma unroll
           for (int it = 0; it < kTileRows / (4 * kWarps); ++it) {
             const int r = 4 * (warp + kWarps * it) + rsub;
@@ -186,7 +200,7 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
         } else {
           // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
           const int rsub = lane >> 4, c4 = lane & 15;
-          const bool store = (gm >> (c4 >> 2)) & 1u;
+          const bool store = (wm >> (c4 >> 2)) & 1u;
   #pragma unroll
           for (int it = 0; it < kTileRows / (2 * kWarps); ++it) {
             const int r = 2 * (warp + kWarps * it) + rsub;

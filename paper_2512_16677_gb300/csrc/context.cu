@@ -57,6 +57,7 @@ struct qk_context_s {
   int mode = QK_FP64;
   bool fused = false;  // split-bf16: AO blocks built inside the contraction kernel
   bool spatial = true;  // tensor-core modes: tiles cut from a spatial point order
+  bool sm_pairs = true;  // tensor-core modes: contraction on pairs of SMs (cta_group::2)
   uint64_t basis_version = 1;
   // nuclei
   int64_t nucl_num = 0;
@@ -112,6 +113,7 @@ struct qk_context_s {
   int ao_mode = -1;
   void* ao_ws = nullptr;
   bool ao_sorted = false;
+  bool ao_pairs = false;  // the AO tensor holds the zeros a pair contraction reads
   // host-output staging, device error word, backward scratch
   DevBuf d_out;
   cudaStream_t copy_stream = nullptr;   // device -> host copies of output ranges
@@ -630,8 +632,10 @@ qk_status ao_workspace(qk_context c, AOTensor* out, bool* valid, bool sorted) {
   if (st) return st;
   *out = ao_view(c, ws, c->mode);
   if (sorted) out->perm = c->perm;
+  out->pair_zero = out->tiled && out->reach != nullptr && c->sm_pairs;
   *valid = c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
-           c->ao_version == c->basis_version && c->ao_sorted == sorted;
+           c->ao_version == c->basis_version && c->ao_sorted == sorted &&
+           c->ao_pairs == out->pair_zero;
   return QK_SUCCESS;
 }
 
@@ -641,6 +645,7 @@ void mark_ao(qk_context c, const AOTensor& ao, bool sorted) {
   c->ao_ws = ao.a;
   c->ao_version = c->basis_version;
   c->ao_sorted = sorted;
+  c->ao_pairs = ao.pair_zero;
 }
 
 // Whether the device path cuts its tiles from a spatial point order.
@@ -733,9 +738,15 @@ qk_status contract(qk_context c, const AOTensor& ao, int64_t M, void* dout) {
       break;
     default: {
       const bool split = c->mode == QK_BF16X3;
-      e = launch_mo_tc(c->mode, ao, KP, split ? (const void*)c->c_hi : (const void*)c->c32p,
-                       split ? (const void*)c->c_lo : nullptr, KP, N, (float*)dout,
-                       tc_default_config(c->mode, N), (int*)c->d_flag.p, c->stream, M);
+      const void* b_hi = split ? (const void*)c->c_hi : (const void*)c->c32p;
+      const void* b_lo = split ? (const void*)c->c_lo : nullptr;
+      const TcConfig cfg = tc_default_config(c->mode, N);
+      if (ao.pair_zero && cfg.bn >= 64 && cfg.bn % 32 == 0)
+        e = launch_mo_tc_pair(c->mode, ao, KP, b_hi, b_lo, KP, N, (float*)dout, cfg.bn,
+                              (int*)c->d_flag.p, c->stream, M);
+      else
+        e = launch_mo_tc(c->mode, ao, KP, b_hi, b_lo, KP, N, (float*)dout, cfg,
+                         (int*)c->d_flag.p, c->stream, M);
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "mo_vgl contraction");
@@ -1381,6 +1392,12 @@ qk_status qk_set_spatial_order(qk_context c, int32_t enable) {
   return QK_SUCCESS;
 }
 
+qk_status qk_set_sm_pairs(qk_context c, int32_t enable) {
+  CHECK_CTX(c);
+  c->sm_pairs = enable != 0;
+  return QK_SUCCESS;
+}
+
 qk_status qk_set_workspace(qk_context c, void* dev, size_t bytes) {
   CHECK_CTX(c);
   if (dev && ((uintptr_t)dev % 256 != 0))
@@ -1726,16 +1743,18 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
 }
 
 qk_status qk_get_tile_layout(qk_context c, int32_t* perm, int64_t n, int32_t* live,
-                             int64_t ntiles) {
+                             int64_t ntiles, uint8_t* groups, int64_t gsize) {
   CHECK_CTX(c);
   if (use_fused(c) || !tiled_mode(c->ao_mode) || c->ao_ws == nullptr ||
       c->ao_date != c->date)
     return fail(c, QK_ERR_NOT_PROVIDED,
                 "no AO tensor of the current points in a two-kernel tensor-core mode");
   const int64_t tiles = ao_tiles(c);
-  if ((perm && n < c->point_num) || (live && ntiles < tiles))
-    return fail(c, QK_ERR_BAD_SIZE, "perm needs %lld and live %lld elements",
-                (long long)c->point_num, (long long)tiles);
+  const int64_t nchunk = (int64_t)c->chunks.size();
+  if ((perm && n < c->point_num) || (live && ntiles < tiles) ||
+      (groups && gsize < tiles * nchunk))
+    return fail(c, QK_ERR_BAD_SIZE, "perm needs %lld, live %lld and groups %lld elements",
+                (long long)c->point_num, (long long)tiles, (long long)(tiles * nchunk));
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "tile layout");
   if (perm) {
@@ -1746,7 +1765,7 @@ qk_status qk_get_tile_layout(qk_context c, int32_t* perm, int64_t n, int32_t* li
       for (int64_t s = 0; s < c->point_num; ++s) perm[s] = (int32_t)s;
     }
   }
-  if (live) {
+  if (live || groups) {
     const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
     const int64_t nq = t.nchunk, ld = mask_ld(t.nchunk);
     std::vector<uint8_t> mask((size_t)(tiles * ld));
@@ -1754,10 +1773,21 @@ qk_status qk_get_tile_layout(qk_context c, int32_t* perm, int64_t n, int32_t* li
     if (e != cudaSuccess) return cuda_fail(c, e, "block mask read");
     for (int64_t ti = 0; ti < tiles; ++ti) {
       int32_t k = 0;
-      for (int64_t q = 0; q < nq; ++q) k += mask[ti * ld + q] != 0;
-      live[ti] = k;
+      for (int64_t q = 0; q < nq; ++q) {
+        k += mask[ti * ld + q] != 0;
+        if (groups) groups[ti * nq + q] = mask[ti * ld + q] & 0xFu;
+      }
+      if (live) live[ti] = k;
     }
   }
+  return QK_SUCCESS;
+}
+
+qk_status qk_get_ao_chunk_num(qk_context c, int64_t* nchunk) {
+  CHECK_CTX(c);
+  if (!nchunk) return fail(c, QK_ERR_NULL_POINTER, "output pointer is NULL");
+  if (!c->has_basis) return fail(c, QK_ERR_NOT_PROVIDED, "AO basis not set");
+  *nchunk = (int64_t)c->chunks.size();
   return QK_SUCCESS;
 }
 
@@ -1891,6 +1921,7 @@ void context_mark_ao_valid(qk_context c) {
   c->ao_ws = c->ws_user ? c->ws_user : c->ws_own.p;
   c->ao_version = c->basis_version;
   c->ao_sorted = false;  // multi-molecule launches keep the caller's order
+  c->ao_pairs = false;   // and write no zeros for a pair contraction
 }
 
 }  // namespace qk

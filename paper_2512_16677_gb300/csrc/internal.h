@@ -105,6 +105,11 @@ struct AOTensor {
   int comps;
   // dense layout only: columns in the caller's AO order (BasisDev::ao_caller)
   bool caller_cols;
+  // tiled, with reach: the contraction multiplies tiles in pairs (2i, 2i+1)
+  // over the union of their live column groups, so ao_vgl also writes zeros
+  // into the groups of a live block that the partner tile's reach word says
+  // may be live there
+  bool pair_zero;
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
@@ -259,6 +264,12 @@ cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const voi
                          float* rho_part = nullptr);
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
+// The same contraction on pairs of SMs (mo_tc_pair.cu): tiled vgl AO tensors
+// only (25 points per tile, written with pair_zero), MMA N = bn (64, 128,
+// 160, 192 or 256) per pair of tiles; D[out_rows][mo] float.
+cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
+                              const void* c_lo, int64_t ldc, int64_t mo_num, float* out, int bn,
+                              int* err_flag, cudaStream_t s, int64_t out_rows);
 
 // One contraction problem of a multi-problem launch (device-resident; the
 // tensor maps, 64-byte aligned by their type, are written by the host

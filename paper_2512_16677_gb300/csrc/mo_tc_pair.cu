@@ -1,0 +1,672 @@
+// mo_tc_pair.cu -- the MO contraction of Eqs. 5-7 on pairs of SMs.
+//
+// Same product as mo_tc.cu, D[5P x N_mo] = AO[5P x N_ao] . C^T over the
+// tiled block-sparse AO tensor (Sec. 3.2's sparse-AO MO product at tile
+// granularity), with split-bf16 (hi*hi + hi*lo + lo*hi, FP32 accumulation
+// in TMEM) or TF32 operands.  The difference is the tensor-core issue: the
+// two CTAs of a cluster run one tcgen05.mma.cta_group::2 with M = 256 (two
+// consecutive 25-point tiles, one per CTA), and each CTA stages only half of
+// the C tile (N / 2 rows).  Per SM a pipeline stage then carries the AO
+// block (32 KB) and half the C block (20 KB at N = 160) instead of the whole
+// C block (40 KB), so four stages fit where three did, and every C byte
+// fetched from L2 serves twice the MMA work.
+//
+// The two tiles of a pair share one K sequence: the union of their live AO
+// blocks and 16-AO column groups.  A block dead in this CTA's own tile is
+// loaded from outside the tensor (TMA zero fill, no memory traffic); a
+// column group live in the partner only holds zeros in this tile's block,
+// because ao_vgl writes zeros there (it reads the partner's reach word).
+//
+// Roles (224 threads per CTA):
+//   warps 4, 6 TMA producers in both CTAs: warp 4 the own AO block, warp 6
+//              the own half of the C block (a thread's copies complete one
+//              after another, so each operand gets its own issuing warp); the
+//              copies of both CTAs complete on the leader CTA's full barrier.
+//   warp 5     TMEM allocation (cta_group::2, both CTAs); lane 0 of the
+//              leader issues the MMAs and commits them to both CTAs'
+//              barriers (multicast).
+//   warps 0-3  epilogue in both CTAs: own 128 TMEM lanes = own tile's rows,
+//              written through the point permutation; each warp then
+//              arrives on the leader's accumulator-free barrier.
+// Every wait is bounded (clock64); a wait that gives up records a code in
+// the caller's error word and raises the CTA's abort flag.
+#include <cuda.h>
+
+#include "tc_common.cuh"
+
+namespace qk {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 224;  // 4 epilogue warps, AO producer, MMA, C producer
+constexpr size_t kEpiBytes = 4 * 32 * 32 * sizeof(float);  // epilogue staging
+constexpr size_t kSmemLimit = 232448;
+
+constexpr uint32_t kStageFirst = 1u << 4;
+constexpr uint32_t kStageLast = 1u << 5;
+constexpr int kStageBnShift = 8;
+
+template <int MODE, int BN, int STAGES>
+struct PairShape {
+  using TR = TcTraits<MODE>;
+  static constexpr uint32_t A_BYTES = kBM * kRowBytes;            // own 128 rows
+  static constexpr uint32_t BH_BYTES = (BN / 2) * kRowBytes;      // own half of C
+  static constexpr uint32_t STAGE_BYTES = TR::kPlanes * (A_BYTES + BH_BYTES);
+  static constexpr uint32_t ACC = (BN + 31) / 32 * 32;
+  static constexpr int NBUF = 512 / ACC > 4 ? 4 : (int)(512 / ACC);
+  static constexpr uint32_t TMEM_ALLOC = tmem_cols<NBUF * ACC>();
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2 * NBUF);
+  static_assert(SMEM + kEpiBytes + 64 <= kSmemLimit, "shared memory budget");
+  static_assert(BN % 16 == 0, "MMA N: multiple of 16 (halves of whole 8-row groups)");
+  static_assert(BN >= 32 && BN <= 256, "MMA N of a pair: 32..256");
+};
+
+constexpr int stages_for_pair(int mode, int bn) {
+  return (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+               ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn / 2) * kRowBytes)) > 8
+             ? 8
+             : (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+                     ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn / 2) * kRowBytes));
+}
+
+// One launch over the tiled AO tensor: pair-tile p -> (M tile pair p / n_tiles,
+// N tile p % n_tiles); CTA rank r of the cluster owns M tile 2 (p / n_tiles) + r.
+template <int BN>
+struct PairSched {
+  CUtensorMap a;       // AO hi/lo planes (3-D) or FP32 (2-D), box 128 rows
+  CUtensorMap b;       // C, box BN / 2 rows
+  CUtensorMap b_last;  // C, box last_bn / 2 rows (last N tile, when last_bn < BN)
+  int last_bn;
+  float* D;
+  const uint8_t* mask;  // [m tiles][mask_ld(nchunk)]
+  const int32_t* perm;  // slot -> point (NULL: identity)
+  int64_t M, N;         // output rows (5 points) and columns
+  int a_rows;           // rows of the AO tensor (128 per tile): a row past them reads zeros
+  int m_tiles, n_tiles, num_kb, nchunk;
+  int64_t total;        // pair-tiles
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Shared-memory address `addr` of this CTA as seen in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Arrive on an mbarrier of a CTA of the cluster (cluster address), without
+// ordering this thread's earlier memory operations before the arrival.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+// TMA tile loads whose completion may be counted on the peer CTA's barrier.
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+template <int MODE>
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                          uint32_t idesc, uint32_t accumulate) {
+  if constexpr (MODE == QK_BF16X3) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+
+// Commit the leader's MMAs issued so far to the barrier at the same offset in
+// both CTAs of the pair.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b16 m;\n\tmov.b16 m, 3;\n\t"
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], m;\n\t}\n" ::"r"(bar)
+      : "memory");
+}
+
+// Mask windows of 32 chunks a lane holds for one pair-tile (chunks <= 256).
+constexpr int kMaxWin = 8;
+
+__device__ __forceinline__ uint32_t pick_window(const uint32_t (&g)[kMaxWin], int w) {
+  uint32_t v = g[0];
+#pragma unroll
+  for (int k = 1; k < kMaxWin; ++k) v = w == k ? g[k] : v;
+  return v;
+}
+
+template <int MODE>
+constexpr int kb_per_chunk() {
+  return TcTraits<MODE>::kBK == 64 ? 1 : 2;
+}
+
+// Whether the tile's mask row holds a live group (whole warp).
+__device__ __forceinline__ bool row_live(const uint8_t* row, int nq, int lane) {
+  bool live = false;
+  for (int q = lane; q < nq; q += 32) live |= (row[q] & 0xFu) != 0u;
+  return __any_sync(0xffffffffu, live);
+}
+
+template <int MODE, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    mo_tc_pair_kernel(const __grid_constant__ PairSched<BN> sc, int* err_flag) {
+  using S = PairShape<MODE, BN, STAGES>;
+  using TR = TcTraits<MODE>;
+  constexpr uint32_t ACC = S::ACC;
+  constexpr uint32_t NBUF = S::NBUF;
+  constexpr int kPer = kb_per_chunk<MODE>();
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ uint32_t stage_info[STAGES];
+  __shared__ __align__(16) float epi[4][32][32];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t bar0 = base + STAGES * S::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + NBUF + b); };
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t cluster = blockIdx.x >> 1;
+  const int64_t nclusters = gridDim.x >> 1;
+  volatile int* abort_v = &abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < (int)NBUF; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 8);  // four epilogue warps in each CTA
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(S::TMEM_ALLOC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised before either signals the other
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  griddep_wait();
+
+  const int64_t total = sc.total;
+  const int mld = mask_ld(sc.nchunk);
+
+  const int nq = (sc.num_kb + kPer - 1) / kPer;  // chunks (the last may be half one)
+  const int nwin = (nq + 31) / 32;                 // 32-chunk windows of a mask row
+
+  if (warp == 4 || warp == 6) {
+    // ------------------------------------------------ TMA producers (both CTAs)
+    // Warp 4 copies the AO blocks (and, in the leader, posts the stage word
+    // and the stage's byte count), warp 6 the C blocks: the copies one thread
+    // issues complete one after another, so the two operands of a stage come
+    // from two warps.  All four producers of a pair walk the same stage
+    // sequence: the union of the pair's live K blocks.  The two mask rows of a pair-tile are read one
+    // pair-tile ahead, a byte per lane and 32-chunk window, and kept in
+    // registers: per chunk the union groups (bits 0-3) and this CTA's own
+    // groups (bits 4-7).
+    const bool a_warp = warp == 4;
+    if (lane == 0) {
+      if (a_warp) {
+        tma_prefetch_map(&sc.a);
+      } else {
+        tma_prefetch_map(&sc.b);
+        if (sc.last_bn != BN) tma_prefetch_map(&sc.b_last);
+      }
+    }
+    auto load_groups = [&](int64_t p, uint32_t (&g)[kMaxWin]) {
+      const int mp = (int)(p / sc.n_tiles);
+      const int mo = 2 * mp + (int)rank, mr = 2 * mp + 1 - (int)rank;
+      const uint8_t* own_row = mo < sc.m_tiles ? sc.mask + (int64_t)mo * mld : nullptr;
+      const uint8_t* par_row = mr < sc.m_tiles ? sc.mask + (int64_t)mr * mld : nullptr;
+#pragma unroll
+      for (int w = 0; w < kMaxWin; ++w) {
+        const int q = 32 * w + lane;
+        uint32_t o = 0u, r = 0u;
+        if (w < nwin && q < nq) {
+          if (own_row) o = (uint32_t)own_row[q] & 0xFu;
+          if (par_row) r = (uint32_t)par_row[q] & 0xFu;
+        }
+        g[w] = (o | r) | (o << 4);
+      }
+    };
+    uint32_t gnext[kMaxWin];
+    if (cluster < total) load_groups(cluster, gnext);
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t p = cluster; p < total && ok; p += nclusters) {
+      uint32_t gcur[kMaxWin];
+#pragma unroll
+      for (int w = 0; w < kMaxWin; ++w) gcur[w] = gnext[w];
+      if (p + nclusters < total) load_groups(p + nclusters, gnext);
+      const int mp = (int)(p / sc.n_tiles);
+      const int nt = (int)(p - (int64_t)mp * sc.n_tiles);
+      const int mt_own = 2 * mp + (int)rank;
+      const bool last_n = nt == sc.n_tiles - 1 && sc.last_bn != BN;
+      const int bn = last_n ? sc.last_bn : BN;
+      const CUtensorMap* bmap = last_n ? &sc.b_last : &sc.b;
+      // the pair-tile's last live K block (-1: none)
+      int lastkb = -1;
+#pragma unroll
+      for (int w = 0; w < kMaxWin; ++w) {
+        const unsigned live = __ballot_sync(0xffffffffu, (gcur[w] & 0xFu) != 0u);
+        if (live) {
+          const int j = 31 - __clz(live);
+          const uint32_t gj = __shfl_sync(0xffffffffu, gcur[w], j);
+          lastkb = (32 * w + j) * kPer + ((kPer == 2 && (gj & 0xCu)) ? 1 : 0);
+        }
+      }
+      if (lastkb >= sc.num_kb) lastkb = sc.num_kb - 1;
+      const uint32_t cta_bytes = TR::kPlanes * (S::A_BYTES + (uint32_t)(bn / 2) * kRowBytes);
+      const uint32_t bn_bits = (uint32_t)(bn >> 4) << kStageBnShift;
+      uint32_t flags = kStageFirst;
+      auto stage = [&](int kb, uint32_t steps, bool own_live, bool last) -> bool {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
+        ++it;
+        bool got = true;
+        if (lane == 0) got = mbar_wait(empty_bar(s), ph ^ 1u, abort_v);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          if (lane == 0) flag_error(err_flag, abort_v, 1);
+          return false;
+        }
+        if (a_warp && leader && lane == 0) {
+          stage_info[s] = steps | flags | bn_bits | (last ? kStageLast : 0u);
+          mbar_expect_tx(full_bar(s), kb >= 0 ? 2u * cta_bytes : 0u);
+        }
+        flags = 0;
+        __syncwarp();
+        if (kb >= 0 && lane == 0) {
+          const uint32_t bar = map_to_rank(full_bar(s), 0);  // the leader's full[s]
+          const uint32_t dst = base + s * S::STAGE_BYTES + (a_warp ? 0u : TR::kPlanes * S::A_BYTES);
+          // own AO block, or zeros from past the tensor's last row when the
+          // block is dead in this CTA's tile; own half of the C block
+          const int row = a_warp ? (own_live ? mt_own * kBM : sc.a_rows)
+                                 : (int)(nt * BN + (int)rank * (bn / 2));
+          const CUtensorMap* map = a_warp ? &sc.a : bmap;
+          if constexpr (TR::kPlanes == 2)
+            tma_load_3d_pair(dst, map, bar, kb * TR::kBK, row, 0);
+          else
+            tma_load_2d_pair(dst, map, bar, kb * TR::kBK, row);
+        }
+        return true;
+      };
+      if (lastkb < 0) {
+        ok = stage(-1, 0u, false, true);
+        continue;
+      }
+#pragma unroll 1
+      for (int w = 0; w < nwin && ok; ++w) {
+        const uint32_t g = pick_window(gcur, w);
+        unsigned live = __ballot_sync(0xffffffffu, (g & 0xFu) != 0u);
+        while (live && ok) {
+          const int j = __ffs(live) - 1;
+          live &= live - 1u;
+          const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+          const bool own_live = (gj >> 4) != 0u;
+          if constexpr (kPer == 1) {
+            // the next live chunk's AO block of this tile into L2 now, so
+            // that its copy into the ring (a stage later) does not wait on HBM
+            const int jn = live ? __ffs(live) - 1 : 0;
+            const uint32_t gn = __shfl_sync(0xffffffffu, g, jn);
+            if (a_warp && live && lane == 2 && (gn >> 4) != 0u)
+              tma_prefetch_l2_3d(&sc.a, (32 * w + jn) * TR::kBK, mt_own * kBM, 0);
+          }
+#pragma unroll
+          for (int h = 0; h < kPer; ++h) {
+            uint32_t steps = gj & 0xFu;
+            if constexpr (kPer == 2) {
+              const uint32_t hh = (gj >> (2 * h)) & 3u;
+              steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+            }
+            const int kb = (32 * w + j) * kPer + h;
+            if (!steps || !ok || kb >= sc.num_kb) continue;
+            ok = stage(kb, steps, own_live, kb == lastkb);
+          }
+        }
+      }
+    }
+    if (a_warp && leader && lane == 0 && *abort_v) {
+      // drain: the copies of both CTAs complete on the leader's barriers
+      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      for (uint32_t k = first; k < it; ++k) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full_bar(k % STAGES), (k / STAGES) & 1u) &&
+               clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 5 && lane == 0 && leader) {
+    // ------------------------------------------------ MMA issuer (leader)
+    const int64_t my_tiles =
+        total > cluster ? (total - 1 - cluster) / nclusters + 1 : 0;
+    const uint64_t d0 = sw128_desc(base);
+    uint32_t it = 0, i = 0, b = 0, dacc = tmem, idesc = 0, bhalf = 0;
+    bool first = true, in_tile = false, ok = true;
+    while ((int64_t)i < my_tiles) {
+      const int s = it % STAGES;
+      const uint32_t ph = (it / STAGES) & 1u;
+      ++it;
+      if (!mbar_wait(full_bar(s), ph, abort_v)) {
+        flag_error(err_flag, abort_v, 2);
+        ok = false;
+        break;
+      }
+      const uint32_t info = stage_info[s];
+      if (info & kStageFirst) {
+        b = i % NBUF;
+        if (!mbar_wait(tempty_bar(b), ((i / NBUF) & 1u) ^ 1u, abort_v)) {
+          flag_error(err_flag, abort_v, 2);
+          ok = false;
+          break;
+        }
+        in_tile = true;
+        dacc = tmem + b * ACC;
+        const int bn = (int)((info >> kStageBnShift) << 4);
+        idesc = make_idesc(TR::kFmt, 2 * kBM, bn);
+        bhalf = (uint32_t)(bn / 2);
+        first = true;
+      }
+      tc_fence_after();
+      const uint64_t da = d0 + ((uint64_t)(s * S::STAGE_BYTES) >> 4);
+      const uint64_t da_lo = da + (S::A_BYTES >> 4);
+      const uint64_t db = da + ((TR::kPlanes * S::A_BYTES) >> 4);
+      const uint64_t db_lo = db + ((bhalf * kRowBytes) >> 4);
+#pragma unroll
+      for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
+        if (!((info >> kk) & 1u)) continue;
+        const uint64_t ko = (uint64_t)(kk * kUmmaKBytes) >> 4;
+        const uint32_t acc = first ? 0u : 1u;
+        first = false;
+        umma_pair<MODE>(dacc, da + ko, db + ko, idesc, acc);
+        if constexpr (MODE == QK_BF16X3) {
+          umma_pair<MODE>(dacc, da + ko, db_lo + ko, idesc, 1u);
+          umma_pair<MODE>(dacc, da_lo + ko, db + ko, idesc, 1u);
+        }
+      }
+      umma_commit_pair(empty_bar(s));
+      if (info & kStageLast) {
+        umma_commit_pair(tfull_bar(b));
+        in_tile = false;
+        ++i;
+      }
+    }
+    if (!ok) {
+      uint32_t wb = 0, wi = 0;
+      bool wait = false;
+      if (in_tile) {
+        umma_commit_pair(tfull_bar(b));
+        wb = b;
+        wi = i;
+        wait = true;
+      } else if (i > 0) {
+        wb = (i - 1) % NBUF;
+        wi = i - 1;
+        wait = true;
+      }
+      const long long t0 = clock64();
+      while (wait && !mbar_try_wait(tfull_bar(wb), (wi / NBUF) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------ epilogue (both CTAs)
+    // Warp w drains TMEM lanes 32 w .. 32 w + 31 (its rows of this CTA's
+    // tile), 32 columns per round trip: each lane's row goes into a staging
+    // tile [32 rows][32 floats] (16-byte chunk q of row r at q ^ (r % 8), free
+    // of bank conflicts both ways), then each store instruction writes 4 rows
+    // x 128 contiguous bytes.  The output rows (through the point
+    // permutation) and the tile's live flag are read one pair-tile ahead.
+    // The leader's accumulator-free barrier gets this warp's arrival as soon
+    // as its last TMEM load of the tile has completed.
+    auto load_setup = [&](int64_t p, int64_t (&orow)[8], uint32_t& livebits) {
+      const int mp = (int)(p / sc.n_tiles);
+      const int mt = 2 * mp + (int)rank;
+      const int64_t row0 = (int64_t)mt * (5 * kTilePoints);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int loc = warp * 32 + 4 * k + (lane >> 3);
+        const int64_t lin = row0 + loc;
+        orow[k] = (mt < sc.m_tiles && loc < 5 * kTilePoints && lin < sc.M)
+                      ? (sc.perm ? 5 * (int64_t)sc.perm[lin / 5] + lin % 5 : lin)
+                      : -1;
+      }
+      livebits = 0u;
+      if (mt < sc.m_tiles) {
+        const uint8_t* row = sc.mask + (int64_t)mt * mld;
+        for (int q = lane; q < nq; q += 32) livebits |= (uint32_t)row[q] & 0xFu;
+      }
+    };
+    int64_t onext[8];
+    uint32_t lnext = 0u;
+    if (cluster < total) load_setup(cluster, onext, lnext);
+    float(*stg)[32] = epi[warp];
+    const int64_t N = sc.N;
+    const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(sc.D) & 15) == 0;
+    uint32_t i = 0;
+    for (int64_t p = cluster; p < total; p += nclusters, ++i) {
+      int64_t orow[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) orow[k] = onext[k];
+      const uint32_t lcur = lnext;
+      if (p + nclusters < total) load_setup(p + nclusters, onext, lnext);
+      const uint32_t b = i % NBUF;
+      const long long t0 = clock64();
+      bool ok = true;
+      while (!mbar_try_wait(tfull_bar(b), (i / NBUF) & 1u)) {
+        if (*abort_v || clock64() - t0 > kWaitCycles) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) flag_error(err_flag, abort_v, 3);
+      ok = __all_sync(0xffffffffu, ok) && !*abort_v;
+      __syncwarp();
+      if (!ok) break;
+      tc_fence_after();
+      const int nt = (int)(p % sc.n_tiles);
+      const bool last_n = nt == sc.n_tiles - 1 && sc.last_bn != BN;
+      const int bn = last_n ? sc.last_bn : BN;
+      const int n0 = nt * BN;
+      const bool any_live = __any_sync(0xffffffffu, lcur != 0u);
+      const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
+      const int cq = lane & 7;
+      float* rowp[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) rowp[k] = sc.D + (orow[k] >= 0 ? orow[k] : 0) * N;
+#pragma unroll 1
+      for (int c = 0; c < bn; c += 32) {
+        const bool two = c + 16 < bn;
+        float v[32];
+        if (any_live) {
+          tmem_ld16x2(tbase + c, v, two);
+        } else {  // every AO of this tile was screened: the MOs are exactly zero
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+        }
+        if (c + 32 >= bn) {
+          // the tile's TMEM reads are complete: the buffer may be refilled
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster_relaxed(map_to_rank(tempty_bar(b), 0));
+        }
+        float4* srow = reinterpret_cast<float4*>(&stg[lane][0]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          srow[q ^ (lane & 7)] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+        const int64_t col = n0 + c + 4 * cq;
+        const bool in_tile = cq < (two ? 8 : 4);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = 4 * k + (lane >> 3);
+          if (orow[k] >= 0 && in_tile) {
+            const float4 w = reinterpret_cast<const float4*>(&stg[r][0])[cq ^ (r & 7)];
+            float* dst = rowp[k] + col;
+            if (vec && col + 3 < N) {
+              *reinterpret_cast<float4*>(dst) = w;
+            } else {
+              if (col < N) dst[0] = w.x;
+              if (col + 1 < N) dst[1] = w.y;
+              if (col + 2 < N) dst[2] = w.z;
+              if (col + 3 < N) dst[3] = w.w;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // no role of either CTA touches the other's barriers or TMEM after this
+  if (warp == 5) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(S::TMEM_ALLOC)
+                 : "memory");
+  }
+}
+
+template <int MODE, int BN>
+cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
+                           int64_t ldc, int64_t N, float* out, int64_t out_rows, int* err_flag,
+                           cudaStream_t s) {
+  constexpr int ST = stages_for_pair(MODE, BN);
+  using S = PairShape<MODE, BN, ST>;
+  using TR = TcTraits<MODE>;
+  const bool f32 = MODE == QK_TF32;
+  const int64_t M = ao.rows;
+  if (M == 0 || N == 0) return cudaSuccess;
+  if (M > INT32_MAX / 2 || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
+  if (!ao.tiled || M % kBM != 0 || ao.comps == 1) return cudaErrorInvalidValue;
+  PairSched<BN> sc;
+  const int64_t n_tiles = (N + BN - 1) / BN;
+  // the last N tile multiplies only the MOs it has, rounded up to 16 (halves
+  // of whole 8-row groups)
+  sc.last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
+  if (TR::kPlanes == 2) {
+    if (!make_map_planes(&sc.a, ao.a, ao.a_lo, K, M, ao.ld, TR::kBK, kBM))
+      return cudaErrorInvalidValue;
+    if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN / 2))
+      return cudaErrorInvalidValue;
+    if (sc.last_bn != BN &&
+        !make_map_planes(&sc.b_last, c_hi, c_lo, K, N, ldc, TR::kBK, sc.last_bn / 2))
+      return cudaErrorInvalidValue;
+  } else {
+    if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+    if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN / 2)) return cudaErrorInvalidValue;
+    if (sc.last_bn != BN && !make_map(&sc.b_last, c_hi, f32, K, N, ldc, TR::kBK, sc.last_bn / 2))
+      return cudaErrorInvalidValue;
+  }
+  sc.D = out;
+  sc.mask = ao.mask;
+  sc.perm = ao.perm;
+  sc.M = out_rows;
+  sc.N = N;
+  sc.a_rows = (int)M;
+  sc.m_tiles = (int)(M / kBM);
+  sc.n_tiles = (int)n_tiles;
+  sc.num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
+  sc.nchunk = ao.nchunk;
+  sc.total = ((sc.m_tiles + 1) / 2) * n_tiles;
+  auto kern = mo_tc_pair_kernel<MODE, BN, ST>;
+  KernelFacts f;
+  cudaError_t e = kernel_facts<mo_tc_pair_kernel<MODE, BN, ST>>(S::SMEM, kThreads, &f);
+  if (e != cudaSuccess) return e;
+  if (f.occ < 1) return cudaErrorInvalidConfiguration;
+  // one CTA per SM (TMEM is taken whole), pairs of SMs, persistent
+  int64_t clusters = f.sms / 2;
+  if (clusters > sc.total) clusters = sc.total;
+  if (clusters < 1) clusters = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * clusters));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = S::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kern, sc, err_flag);
+}
+
+}  // namespace
+
+cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
+                              const void* c_lo, int64_t ldc, int64_t mo_num, float* out, int bn,
+                              int* err_flag, cudaStream_t s, int64_t out_rows) {
+  if (mode == QK_BF16X3) {
+    switch (bn) {
+      case 64: return launch_pair_bn<QK_BF16X3, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 128: return launch_pair_bn<QK_BF16X3, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 160: return launch_pair_bn<QK_BF16X3, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 192: return launch_pair_bn<QK_BF16X3, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 256: return launch_pair_bn<QK_BF16X3, 256>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (mode == QK_TF32) {
+    switch (bn) {
+      case 64: return launch_pair_bn<QK_TF32, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 128: return launch_pair_bn<QK_TF32, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 160: return launch_pair_bn<QK_TF32, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 192: return launch_pair_bn<QK_TF32, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 256: return launch_pair_bn<QK_TF32, 256>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qk

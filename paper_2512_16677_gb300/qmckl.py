@@ -79,7 +79,9 @@ SIGNATURES = {
     "qk_get_block_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                            ctypes.POINTER(_I64)],
     "qk_get_sparsity_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
-    "qk_get_tile_layout": [_P, _P, _I64, _P, _I64],
+    "qk_get_tile_layout": [_P, _P, _I64, _P, _I64, _P, _I64],
+    "qk_get_ao_chunk_num": [_P, ctypes.POINTER(_I64)],
+    "qk_set_sm_pairs": [_P, _I32],
     "qk_batch_create": [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)],
     "qk_batch_destroy": [_P],
     "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
@@ -305,6 +307,10 @@ class Context:
                     "get_shell_order")
         return out
 
+    def set_sm_pairs(self, enable: bool):
+        """Contraction on pairs of SMs (default) or on single SMs."""
+        self._check(self.lib.qk_set_sm_pairs(self.h, 1 if enable else 0), "set_sm_pairs")
+
     def set_spatial_order(self, enable: bool):
         """tensor-core modes: cut point tiles from a spatial order (default on)."""
         self._check(self.lib.qk_set_spatial_order(self.h, 1 if enable else 0),
@@ -473,17 +479,26 @@ class Context:
                     "get_sparsity_stats")
         return a.value, b.value
 
-    def tile_layout(self):
-        """(perm, live): the caller's point at each slot of the contraction
-        tiles (25 slots per tile) and the live AO blocks of each tile, for the
-        AO tensor of the current points (tensor-core path)."""
+    def tile_layout(self, groups: bool = False):
+        """(perm, live[, groups]): the caller's point at each slot of the
+        contraction tiles (25 slots per tile), the live AO blocks of each
+        tile and, with groups=True, the [tile][chunk] bit masks of live
+        16-AO column groups, for the AO tensor of the current points
+        (tensor-core path)."""
         n = self.point_num
         tiles = (n + 24) // 25
         perm = np.zeros(n, dtype=np.int32)
         live = np.zeros(tiles, dtype=np.int32)
-        self._check(self.lib.qk_get_tile_layout(self.h, perm.ctypes.data, n, live.ctypes.data,
-                                                tiles), "get_tile_layout")
-        return perm, live
+        nchunk = 0
+        g = None
+        if groups:
+            nchunk = self._get_i64(self.lib.qk_get_ao_chunk_num, "get_ao_chunk_num")
+            g = np.zeros((tiles, nchunk), dtype=np.uint8)
+        self._check(self.lib.qk_get_tile_layout(
+            self.h, perm.ctypes.data, n, live.ctypes.data, tiles,
+            None if g is None else g.ctypes.data, 0 if g is None else g.size),
+            "get_tile_layout")
+        return (perm, live, g) if groups else (perm, live)
 
     # ------------------------------------------------------------ evaluate
     def mo_vgl_device(self, out=None):

@@ -390,3 +390,30 @@ def test_kernel_count(cfg):
     n = c.kernel_count()
     assert n == 1 + 8 + 2 + 1, n      # conversion, sort, pre-pass + ao_vgl, contraction
     assert c.kernel_count() == 0
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_sm_pairs_same_values_as_single_sm(orc, cfg, mode):
+    """The contraction on pairs of SMs (cta_group::2, the default) and on
+    single SMs multiply the same live blocks; the pair's extra k-steps over
+    its partner's live groups add exact zeros.  47 tiles (an odd count: the
+    last pair has one tile) of the organic chain, against the oracle and
+    against each other."""
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(2, walk_num=2)
+    mm = m.with_points(m.points[:47 * 25 - 3])
+    outs = {}
+    for pairs in (True, False):
+        c = qmckl.Context(mode)
+        c.set_molecule(mm)
+        c.set_sm_pairs(pairs)
+        c.set_points_device(torch.from_numpy(mm.coord).cuda())
+        out = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        c.synchronize()
+        outs[pairs] = out.double().cpu().numpy().reshape(-1, 5, mm.mo_num)
+        c.close()
+    ref, size = orc.mo_vgl(mm)
+    assert_within(mode, outs[True], ref, size, "organic pairs")
+    diff = np.abs(outs[True] - outs[False]) / (size + 1e-300)
+    assert float(diff.max()) <= 1e-6, float(diff.max())
