@@ -610,14 +610,18 @@ def measure_large(args, world):
 
 def measure_adjoint(args):
     """C/H chain, 50 nuclei, 500 AOs, 100 MOs, 200 e- x 128 walkers: forward
-    plus backward (dL/dC and dL/dR_nuc) per step, FP64 and split-bf16 forward
-    with the FP32 adjoint."""
+    plus backward (dL/dC and dL/dR_nuc) per step, and the backward alone, in
+    FP64, FP32 (SIMT products) and split bf16 (tensor-core products)."""
     import torch
     from paper_2512_16677_gb300 import qmckl, synth
     mol = synth.make_config(3)
+    peaks, _ = load_peaks()
     coord = torch.from_numpy(mol.coord).cuda()
     res = {"workload": "chain50: 50 nuclei, 500 AO, 100 MO, 200 e- x 128 walkers"}
-    for mode, steps in (("fp64", 3), ("bf16x3", 10)):
+    rows = 5 * mol.point_num
+    # the two products of the backward, one product each (the method's count)
+    flops = 2.0 * 2 * rows * mol.mo_num * mol.ao_num
+    for mode, steps in (("fp64", 3), ("fp32", 10), ("bf16x3", 10)):
         ctx = qmckl.Context(mode)
         ctx.set_molecule(mol)
         ctx.set_points_device(coord)
@@ -628,9 +632,30 @@ def measure_adjoint(args):
             ctx.set_points_device(coord)
             ctx.mo_vgl_device(o)
             ctx.backward_device(W)
+
+        def bwd():
+            ctx.backward_device(W)
         ms = _time_steps(fwd_bwd, steps, warmup=1)
-        res[mode] = {"ms_per_fwd_bwd": ms,
-                     "evals_per_s": mol.elec_num * mol.walk_num * mol.mo_num / (ms * 1e-3)}
+        mb = _time_steps(bwd, steps, warmup=1)
+        ent = {"ms_per_fwd_bwd": ms, "ms_backward": mb,
+               "evals_per_s": mol.elec_num * mol.walk_num * mol.mo_num / (ms * 1e-3),
+               "products_flops": flops, "products_tflops": flops / (mb * 1e-3) / 1e12}
+        if mode == "bf16x3":
+            tensor = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            # what the backward must move at least: W in, the recomputed AO
+            # tensor out and back (FP32), Abar out and back (FP32), dL/dC
+            nbytes = 4.0 * rows * mol.mo_num + 2 * 4.0 * rows * mol.ao_num * 2 + \
+                8.0 * mol.mo_num * mol.ao_num
+            ent["roofline"] = {
+                "bound": "hbm", "achieved": nbytes / (mb * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": nbytes / (mb * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "algorithmic_bytes": nbytes,
+                "tensor": {"achieved": flops / (mb * 1e-3) / 1e12, "peak": tensor,
+                           "unit": "TFLOP/s", "frac": flops / (mb * 1e-3) / 1e12 / tensor},
+                "note": "whole backward (AO recompute, operand splits, both products, dR kernel) "
+                        "against the bytes its FP32 AO and Abar tensors must move"}
+        res[mode] = ent
+        ctx.close()
     return res
 
 

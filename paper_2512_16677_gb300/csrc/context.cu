@@ -134,6 +134,8 @@ struct qk_context_s {
   double* cusp_f64 = nullptr;
   float* cusp_f32 = nullptr;
   uint64_t mo_version = 0;  // bumped by every upload of C
+  DevBuf d_ct;              // C^T bf16 hi/lo planes for the split-bf16 adjoint
+  uint64_t ct_version = ~0ull;
   std::vector<cudaEvent_t> range_done;  // one per output range of a host call
   DevBuf d_flag;
   DevBuf bwd_own;
@@ -1632,6 +1634,7 @@ namespace {
 struct BwdLayout {
   size_t ao, abar, dc, dr, total;
   int k_split;
+  bool tc;  // split-bf16 products on the tensor cores (dc: their scratch)
 };
 
 BwdLayout bwd_layout(qk_context c) {
@@ -1648,10 +1651,12 @@ BwdLayout bwd_layout(qk_context c) {
   if (ks > kmax) ks = kmax;
   if (ks < 1) ks = 1;
   L.k_split = (int)ks;
+  L.tc = c->mode == QK_BF16X3;
   L.ao = 0;
   L.abar = align_up(rows * ld * es, 256);
   L.dc = L.abar + align_up(rows * ld * es, 256);
-  L.dr = L.dc + align_up((size_t)ks * c->mo_num * c->ao_num * es, 256);
+  L.dr = L.dc + (L.tc ? align_up(adjoint_tc_scratch_bytes(rows, c->mo_num, c->ao_num), 256)
+                      : align_up((size_t)ks * c->mo_num * c->ao_num * es, 256));
   L.total = L.dr + align_up(adjoint_dR_partial_bytes(c->bdev, c->point_num), 256);
   return L;
 }
@@ -1845,6 +1850,24 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
   // 1. AO values recomputed, not kept from the forward pass
   e = launch_ao_vgl(c->bdev, c->pdev, f64 ? QK_FP64 : QK_FP32, ao, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "backward ao_vgl");
+  if (L.tc) {
+    // 2-3. split bf16 on the tensor cores: Abar = W . C and dL/dC = W^T . AO
+    if (c->ct_version != c->mo_version || !c->d_ct.p) {
+      e = c->d_ct.ensure(adjoint_tc_ct_bytes(N, K));
+      if (e == cudaSuccess) e = launch_adjoint_ct_split(c->c64, N, K, c->d_ct.p, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "backward C^T planes");
+      c->ct_version = c->mo_version;
+    }
+    e = launch_adjoint_tc((const float*)dW, rows, N, (const float*)ao.a, ld, K, c->d_ct.p,
+                          (float*)abar, d_dC, c->bdev.ao_caller, dcp, (int*)c->d_flag.p,
+                          c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "backward tensor-core products");
+    if (d_dR) {
+      e = launch_adjoint_dR(c->bdev, c->pdev, QK_FP32, abar, K, drp, d_dR, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "backward dL/dR");
+    }
+    return QK_SUCCESS;
+  }
   // 2. Abar[row][k] = sum_i W[row][i] C[i][k]
   if (f64)
     e = launch_gemm_f64(rows, K, N, (const double*)dW, N, 1, c->c64, 1, K, (double*)abar, ld, 1,
