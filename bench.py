@@ -451,11 +451,14 @@ def run_ours(args, rank, world, local_rank):
             ent = {"value": world * evals_per_step / (ms_o * 1e-3), "ms_per_step": ms_o,
                    "steps": steps, "contraction_ms": ko[1] / max(no[1], 1),
                    "ao_vgl_ms": ko[0] / max(no[0], 1), "clocks": clko}
-            if mode in ("bf16x3", "tf32"):
+            if mode in ("bf16x3", "tf32", "fp64"):
+                # block-sparse paths: the contraction against its roofline, from
+                # the method's sparse count
                 lt = [ko[i] / no[i] if no[i] else 0.0 for i in range(3)]
                 r = roofline(mode, mol, lt, peaks, co.block_stats(), co.sparsity_stats(), None)
                 ent["roofline"] = {k: r["mo_contraction"][k] for k in
-                                   ("bound", "achieved", "peak", "unit", "frac")}
+                                   ("bound", "achieved", "peak", "unit", "frac")
+                                   if k in r["mo_contraction"]}
             res[f"{mode}_path"] = ent
             if rank == 0 and not args.no_cpu_baseline:
                 samples[mode] = oo[:CPU_SAMPLE_POINTS * 5 * mol.mo_num].double().cpu().numpy()

@@ -197,6 +197,18 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
                   make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
           }
+        } else if constexpr (sizeof(T) == 8) {
+          // a lane stores 2 consecutive columns (16 bytes) of one row; a warp
+          // covers a row
+          const bool store = (wm >> (lane >> 3)) & 1u;
+  #pragma unroll 4
+          for (int it = 0; it < kTileRows / kWarps; ++it) {
+            const int r = warp + kWarps * it;
+            const double2 w = make_double2(sh.stage[r][2 * lane], sh.stage[r][2 * lane + 1]);
+            if (store)
+              *reinterpret_cast<double2*>(static_cast<double*>(out.a) + (row0 + r) * out.ld +
+                                          col0 + 2 * lane) = w;
+          }
         } else {
           // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
           const int rsub = lane >> 4, c4 = lane & 15;
@@ -398,6 +410,8 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s) {
   if (out.tiled) {
     switch (out_mode) {
+      case QK_FP64:
+        return launch_ao<double, false, true, true>(b, p, out, s);
       case QK_FP32:
       case QK_TF32:
         return launch_ao<float, false, true, true>(b, p, out, s);
@@ -435,10 +449,10 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 
 // Nonzero (point, AO) pairs of a tiled vgl AO tensor: the AO of a point
 // counts when any of its five rows holds a nonzero entry at that column
-// (either bf16 plane when split; the sign bit ignored).  Blocks whose mask
+// (either bf16 plane when split; the sign bit ignored; kEs bytes per entry).  Blocks whose mask
 // byte is zero, and the dead 16-AO groups of live blocks, were not written
 // and count nothing.  Statistics only.
-template <bool kSplit>
+template <int kEs>
 __global__ void __launch_bounds__(256)
     ao_nnz_kernel(AOTensor t, int64_t n, int64_t tiles, unsigned long long* out) {
   __shared__ unsigned long long tot;
@@ -461,11 +475,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int r = 0; r < 5; ++r) {
         const int64_t e = e0 + r * t.ld;
-        if constexpr (kSplit) {
+        if constexpr (kEs == 2) {
           nz |= (static_cast<const uint16_t*>(t.a)[e] & 0x7fffu) != 0u;
           nz |= (static_cast<const uint16_t*>(t.a_lo)[e] & 0x7fffu) != 0u;
-        } else {
+        } else if constexpr (kEs == 4) {
           nz |= (static_cast<const uint32_t*>(t.a)[e] & 0x7fffffffu) != 0u;
+        } else {
+          nz |= (static_cast<const uint64_t*>(t.a)[e] & 0x7fffffffffffffffull) != 0ull;
         }
       }
       cnt += nz ? 1u : 0u;
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) atomicAdd(out, tot);
 }
 
-cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned long long* out,
+cudaError_t launch_ao_nnz(const AOTensor& t, int es, int64_t n, unsigned long long* out,
                           cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -487,10 +503,12 @@ cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned lon
   if (blocks == 0) return cudaSuccess;
   const unsigned g = (unsigned)(blocks < 8 * (int64_t)device_sms() ? blocks
                                                                     : 8 * (int64_t)device_sms());
-  if (split)
-    ao_nnz_kernel<true><<<g, 256, 0, s>>>(t, n, tiles, out);
+  if (es == 2)
+    ao_nnz_kernel<2><<<g, 256, 0, s>>>(t, n, tiles, out);
+  else if (es == 4)
+    ao_nnz_kernel<4><<<g, 256, 0, s>>>(t, n, tiles, out);
   else
-    ao_nnz_kernel<false><<<g, 256, 0, s>>>(t, n, tiles, out);
+    ao_nnz_kernel<8><<<g, 256, 0, s>>>(t, n, tiles, out);
   return cudaGetLastError();
 }
 

@@ -546,18 +546,26 @@ int64_t kpad_of(qk_context c) { return (int64_t)c->chunks.size() * kChunkAO; }
 // Tensor-core modes use the tiled layout: kTilePoints points per 128-row
 // tile, plus one live-block byte per (tile, chunk).
 bool tiled_mode(int mode) { return mode == QK_BF16X3 || mode == QK_TF32; }
+// The MO vgl AO tensor is tiled and block-sparse in the tensor-core modes and
+// in FP64 (whose contraction multiplies live column groups only); the plain
+// FP32 path keeps the dense layout.
+bool vgl_tiled(int mode) { return tiled_mode(mode) || mode == QK_FP64; }
+size_t ao_elem_bytes(int mode) {
+  return mode == QK_FP64 ? sizeof(double)
+                         : (mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
+}
 int64_t ao_tiles(qk_context c) { return (c->point_num + kTilePoints - 1) / kTilePoints; }
 
 bool use_fused(qk_context c) { return c->mode == QK_BF16X3 && c->fused; }
 
 size_t ao_tensor_bytes(qk_context c, int mode) {
   const size_t ld = (size_t)kpad_of(c);
-  if (tiled_mode(mode)) {
+  if (vgl_tiled(mode)) {
     const size_t rows = (size_t)ao_tiles(c) * kTileRows;
     const size_t mask = align_up((size_t)ao_tiles(c) * mask_ld((int)c->chunks.size()), 256) +
                         align_up((size_t)ao_tiles(c) * c->chunks.size() * sizeof(uint32_t), 256);
-    if (mode == QK_BF16X3) return 2 * align_up(rows * ld * sizeof(__nv_bfloat16), 256) + mask;
-    return align_up(rows * ld * sizeof(float), 256) + mask;
+    const size_t planes = mode == QK_BF16X3 ? 2 : 1;
+    return planes * align_up(rows * ld * ao_elem_bytes(mode), 256) + mask;
   }
   const size_t rows = (size_t)5 * c->point_num;
   if (mode == QK_FP64) return align_up(rows * ld * sizeof(double), 256);
@@ -606,10 +614,10 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
   t.chunked = true;
   t.nchunk = (int)c->chunks.size();
   t.a = ws;
-  if (tiled_mode(mode)) {
+  if (vgl_tiled(mode)) {
     t.tiled = true;
     t.rows = ao_tiles(c) * kTileRows;
-    const size_t es = mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float);
+    const size_t es = ao_elem_bytes(mode);
     const size_t plane = align_up((size_t)t.rows * t.ld * es, 256);
     unsigned char* p = (unsigned char*)ws + plane;
     if (mode == QK_BF16X3) {
@@ -634,7 +642,7 @@ qk_status ao_workspace(qk_context c, AOTensor* out, bool* valid, bool sorted) {
   if (st) return st;
   *out = ao_view(c, ws, c->mode);
   if (sorted) out->perm = c->perm;
-  out->pair_zero = out->tiled && out->reach != nullptr && c->sm_pairs;
+  out->pair_zero = tiled_mode(c->mode) && out->tiled && out->reach != nullptr && c->sm_pairs;
   *valid = c->ao_date == c->date && c->ao_mode == c->mode && c->ao_ws == ws &&
            c->ao_version == c->basis_version && c->ao_sorted == sorted &&
            c->ao_pairs == out->pair_zero;
@@ -652,7 +660,7 @@ void mark_ao(qk_context c, const AOTensor& ao, bool sorted) {
 
 // Whether the device path cuts its tiles from a spatial point order.
 bool use_spatial(qk_context c) {
-  return tiled_mode(c->mode) && c->spatial && c->point_num >= 2 * kTilePoints;
+  return vgl_tiled(c->mode) && c->spatial && c->point_num >= 2 * kTilePoints;
 }
 
 // The spatial order of the current points (once per time stamp).
@@ -731,8 +739,11 @@ qk_status contract(qk_context c, const AOTensor& ao, int64_t M, void* dout) {
   TimedLaunch timer(c, 1);
   switch (c->mode) {
     case QK_FP64:
-      e = launch_gemm_f64(M, N, KP, (const double*)ao.a, ao.ld, 1, c->c64p, KP, 1, (double*)dout,
-                          N, 1, c->stream);
+      if (ao.tiled)  // live 16-AO column groups only (Sec. 3.2's sparse product)
+        e = launch_mo_sparse64(ao, c->c64p, KP, N, (double*)dout, M, c->stream);
+      else
+        e = launch_gemm_f64(M, N, KP, (const double*)ao.a, ao.ld, 1, c->c64p, KP, 1,
+                            (double*)dout, N, 1, c->stream);
       break;
     case QK_FP32:
       e = launch_gemm_f32(M, N, KP, (const float*)ao.a, ao.ld, 1, c->c32p, KP, 1, (float*)dout,
@@ -1312,7 +1323,7 @@ qk_status qk_get_mo_vgl_single_device(qk_context c, void* dout, int64_t size) {
   av.ld = c->kpad;
   av.chunked = true;
   av.nchunk = (int)c->chunks.size();
-  const bool tiled = tiled_mode(c->mode);
+  const bool tiled = vgl_tiled(c->mode);
   const size_t es = c->mode == QK_FP64 ? sizeof(double)
                                        : (c->mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
   size_t need = 0, plane = 0, mask = 0;
@@ -1695,9 +1706,9 @@ qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_
     *live_entries = entries;
     return QK_SUCCESS;
   }
-  if (!tiled_mode(c->ao_mode) || c->ao_ws == nullptr || c->ao_date != c->date)
+  if (!vgl_tiled(c->ao_mode) || c->ao_ws == nullptr || c->ao_date != c->date)
     return fail(c, QK_ERR_NOT_PROVIDED,
-                "no AO tensor of the current points in a tensor-core mode");
+                "no AO tensor of the current points in a block-sparse mode");
   const AOTensor t = ao_view(c, c->ao_ws, c->ao_mode);
   const int64_t tiles = ao_tiles(c), nq = t.nchunk, ld = mask_ld(t.nchunk);
   std::vector<uint8_t> mask((size_t)(tiles * ld));
@@ -1723,7 +1734,7 @@ qk_status qk_get_block_stats(qk_context c, int64_t* live_blocks, int64_t* total_
 qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz) {
   CHECK_CTX(c);
   if (!live_groups || !nnz) return fail(c, QK_ERR_NULL_POINTER, "output pointer is NULL");
-  if (use_fused(c) || !tiled_mode(c->ao_mode) || c->ao_ws == nullptr ||
+  if (use_fused(c) || !vgl_tiled(c->ao_mode) || c->ao_ws == nullptr ||
       c->ao_date != c->date)
     return fail(c, QK_ERR_NOT_PROVIDED,
                 "no AO tensor of the current points in a two-kernel tensor-core mode");
@@ -1733,7 +1744,7 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
   // the counter lives in the second half of the 256-byte error-word buffer
   auto* cnt = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->d_flag.p) + 128);
   unsigned long long h = 0;
-  cudaError_t e = launch_ao_nnz(t, c->ao_mode == QK_BF16X3, c->point_num, cnt, c->stream);
+  cudaError_t e = launch_ao_nnz(t, (int)ao_elem_bytes(c->ao_mode), c->point_num, cnt, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpy(mask.data(), t.mask, mask.size(), cudaMemcpyDeviceToHost);
@@ -1750,7 +1761,7 @@ qk_status qk_get_sparsity_stats(qk_context c, int64_t* live_groups, int64_t* nnz
 qk_status qk_get_tile_layout(qk_context c, int32_t* perm, int64_t n, int32_t* live,
                              int64_t ntiles, uint8_t* groups, int64_t gsize) {
   CHECK_CTX(c);
-  if (use_fused(c) || !tiled_mode(c->ao_mode) || c->ao_ws == nullptr ||
+  if (use_fused(c) || !vgl_tiled(c->ao_mode) || c->ao_ws == nullptr ||
       c->ao_date != c->date)
     return fail(c, QK_ERR_NOT_PROVIDED,
                 "no AO tensor of the current points in a two-kernel tensor-core mode");

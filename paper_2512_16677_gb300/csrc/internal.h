@@ -207,8 +207,9 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s);
 
 // Nonzero (point, AO) pairs of the tiled vgl AO tensor t of n points
-// (split: bf16 hi/lo planes) summed into *out (device; zeroed first).
-cudaError_t launch_ao_nnz(const AOTensor& t, bool split, int64_t n, unsigned long long* out,
+// (es = 2: bf16 hi/lo planes; 4: FP32; 8: FP64) summed into *out (device;
+// zeroed first).
+cudaError_t launch_ao_nnz(const AOTensor& t, int es, int64_t n, unsigned long long* out,
                           cudaStream_t s);
 
 // Point coordinates [n][3] ('N') or [3][n] ('T') -> SoA + hi/lo floats.
@@ -262,6 +263,11 @@ cudaError_t launch_mo_tc(int mode, const AOTensor& ao, int64_t ao_num, const voi
                          const TcConfig& cfg, int* err_flag, cudaStream_t s,
                          int64_t out_rows = -1, const float* wdens = nullptr,
                          float* rho_part = nullptr);
+// FP64 contraction over a tiled vgl AO tensor (mo_sparse64.cu): only the
+// live 16-AO column groups of live blocks are multiplied; C [N][ldc] in the
+// chunked column layout; D [out_rows][N] double, rows through ao.perm.
+cudaError_t launch_mo_sparse64(const AOTensor& ao, const double* C, int64_t ldc, int64_t N,
+                               double* D, int64_t out_rows, cudaStream_t s);
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
 // The same contraction on pairs of SMs (mo_tc_pair.cu): tiled vgl AO tensors
