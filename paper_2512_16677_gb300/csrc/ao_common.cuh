@@ -324,7 +324,7 @@ __device__ __forceinline__ void load_stage_tables(const BasisDev& b, int q, Smem
 //   chi = M S0 P,  d_i chi = M (S0 d_iP - 2 S1 d_i P),
 //   lap chi = M (S0 lapP + (4 r^2 S2 - 2 (2L+3) S1) P),
 // with u_i = 2 S1 d_i and Lr = 4 r^2 S2 - 2 (2L+3) S1 formed once per shell.
-template <typename T, int L, int J>
+template <typename T, int L, int J, int kPitch = kStagePitch>
 __device__ __forceinline__ void cart_component(const T (&px)[4], const T (&py)[4],
                                                const T (&pz)[4], const T* M, T S0, T ux, T uy,
                                                T uz, T Lr, T* st) {
@@ -335,17 +335,17 @@ __device__ __forceinline__ void cart_component(const T (&px)[4], const T (&py)[4
     const T mP = M[J] * P;
     st[J] = mS0 * P;
     if constexpr (a > 0)
-      st[kStagePitch + J] = mS0 * (T(a) * px[a > 0 ? a - 1 : 0] * py[b] * pz[c]) - ux * mP;
+      st[kPitch + J] = mS0 * (T(a) * px[a > 0 ? a - 1 : 0] * py[b] * pz[c]) - ux * mP;
     else
-      st[kStagePitch + J] = -(ux * mP);
+      st[kPitch + J] = -(ux * mP);
     if constexpr (b > 0)
-      st[2 * kStagePitch + J] = mS0 * (T(b) * px[a] * py[b > 0 ? b - 1 : 0] * pz[c]) - uy * mP;
+      st[2 * kPitch + J] = mS0 * (T(b) * px[a] * py[b > 0 ? b - 1 : 0] * pz[c]) - uy * mP;
     else
-      st[2 * kStagePitch + J] = -(uy * mP);
+      st[2 * kPitch + J] = -(uy * mP);
     if constexpr (c > 0)
-      st[3 * kStagePitch + J] = mS0 * (T(c) * px[a] * py[b] * pz[c > 0 ? c - 1 : 0]) - uz * mP;
+      st[3 * kPitch + J] = mS0 * (T(c) * px[a] * py[b] * pz[c > 0 ? c - 1 : 0]) - uz * mP;
     else
-      st[3 * kStagePitch + J] = -(uz * mP);
+      st[3 * kPitch + J] = -(uz * mP);
     if constexpr (a > 1 || b > 1 || c > 1) {
       T lapP = T(0);
       bool first = true;
@@ -362,17 +362,17 @@ __device__ __forceinline__ void cart_component(const T (&px)[4], const T (&py)[4
         const T t = T(c * (c - 1)) * px[a] * py[b] * pz[c > 1 ? c - 2 : 0];
         lapP = first ? t : lapP + t;
       }
-      st[4 * kStagePitch + J] = mS0 * lapP + Lr * mP;
+      st[4 * kPitch + J] = mS0 * lapP + Lr * mP;
     } else {
-      st[4 * kStagePitch + J] = Lr * mP;
+      st[4 * kPitch + J] = Lr * mP;
     }
-    cart_component<T, L, J + 1>(px, py, pz, M, S0, ux, uy, uz, Lr, st);
+    cart_component<T, L, J + 1, kPitch>(px, py, pz, M, S0, ux, uy, uz, Lr, st);
   }
 }
 
 // All components of a momentum-L shell at one point into the staging rows
-// st[c * kStagePitch + j] (c = value, d/dx, d/dy, d/dz, Laplacian).
-template <typename T, int L>
+// st[c * kPitch + j] (c = value, d/dx, d/dy, d/dz, Laplacian).
+template <typename T, int L, int kPitch = kStagePitch>
 __device__ __forceinline__ void shell_components(T dx, T dy, T dz, T S0, T S1, T S2, const T* M,
                                                  T* st) {
   const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void shell_components(T dx, T dy, T dz, T S0, T S1, T
   const T r2 = x2 + y2 + z2;
   const T S1x2 = T(2) * S1;
   const T Lr = T(4) * r2 * S2 - T(2 * (2 * L + 3)) * S1;
-  cart_component<T, L, 0>(px, py, pz, M, S0, S1x2 * dx, S1x2 * dy, S1x2 * dz, Lr, st);
+  cart_component<T, L, 0, kPitch>(px, py, pz, M, S0, S1x2 * dx, S1x2 * dy, S1x2 * dz, Lr, st);
 }
 
 // Zeros into the staging columns of shell `sl` if they may hold values of

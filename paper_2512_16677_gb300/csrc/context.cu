@@ -127,7 +127,9 @@ struct qk_context_s {
   DevBuf d_dens;       // density: occupied-MO tables, weights, partial sums
   // single-electron moves: proposed positions of electron single_elec of
   // every walker, and the AO tensor at them
-  DevBuf d_single, d_single_ws;
+  DevBuf d_single, d_single_ws, d_single_ct;
+  uint64_t single_ct_version = ~0ull;  // C^T for single moves, per upload of C
+  bool single_ct_f64 = false;
   PointsDev psingle{};
   int64_t single_elec = -1;
   CuspDev cudev{};
@@ -1269,6 +1271,57 @@ qk_status qk_get_density_device(qk_context c, const double* w, void* drho, int64
   return QK_SUCCESS;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Single-electron moves for a basis whose tables do not fit the one-launch
+// kernel's shared memory: the W moved points through the full path's
+// kernels (ao_vgl in a workspace of its own, then the contraction), so that
+// the cached AO tensor of the full configuration stays valid.
+qk_status single_move_tiled(qk_context c, int64_t W, void* dout) {
+  AOTensor av{};
+  av.ld = c->kpad;
+  av.chunked = true;
+  av.nchunk = (int)c->chunks.size();
+  const bool tiled = vgl_tiled(c->mode);
+  const size_t es = ao_elem_bytes(c->mode);
+  size_t need = 0, plane = 0, mask = 0;
+  if (tiled) {
+    const int64_t tiles = (W + kTilePoints - 1) / kTilePoints;
+    av.tiled = true;
+    av.rows = tiles * kTileRows;
+    plane = align_up((size_t)av.rows * av.ld * es, 256);
+    mask = align_up((size_t)tiles * mask_ld(av.nchunk), 256);
+    need = (c->mode == QK_BF16X3 ? 2 : 1) * plane + mask;
+  } else {
+    av.rows = 5 * W;
+    plane = align_up((size_t)av.rows * av.ld * es, 256);
+    need = plane;
+  }
+  cudaError_t e = c->d_single_ws.ensure(need);
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-move workspace");
+  unsigned char* p = (unsigned char*)c->d_single_ws.p;
+  av.a = p;
+  if (tiled) {
+    if (c->mode == QK_BF16X3) av.a_lo = p + plane;
+    // a few tiles only: each ao_vgl tile culls for itself (no pre-pass launch)
+    av.mask = p + (c->mode == QK_BF16X3 ? 2 : 1) * plane;
+  }
+  {
+    TimedLaunch t(c, 0);
+    e = launch_ao_vgl(c->bdev, c->psingle, c->mode, av, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-move ao_vgl");
+  qk_status st = contract(c, av, 5 * W, dout);
+  if (st) return st;
+  return apply_cusp(c, c->psingle, dout);
+}
+
+}  // namespace
+
+extern "C" {
+
 qk_status qk_set_single_point_device(qk_context c, int64_t elec, const double* dcoord) {
   CHECK_CTX(c);
   if (!dcoord) return fail(c, QK_ERR_NULL_POINTER, "dcoord is NULL");
@@ -1317,45 +1370,28 @@ qk_status qk_get_mo_vgl_single_device(qk_context c, void* dout, int64_t size) {
   if (st) return st;
   st = ensure_cusp(c);
   if (st) return st;
-  // AO tensor of the W moved points in a workspace of its own, so that the
-  // cached AO tensor of the full configuration stays valid
-  AOTensor av{};
-  av.ld = c->kpad;
-  av.chunked = true;
-  av.nchunk = (int)c->chunks.size();
-  const bool tiled = vgl_tiled(c->mode);
-  const size_t es = c->mode == QK_FP64 ? sizeof(double)
-                                       : (c->mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
-  size_t need = 0, plane = 0, mask = 0;
-  int64_t tiles = 0;
-  if (tiled) {
-    tiles = (W + kTilePoints - 1) / kTilePoints;
-    av.tiled = true;
-    av.rows = tiles * kTileRows;
-    plane = align_up((size_t)av.rows * av.ld * es, 256);
-    mask = align_up((size_t)tiles * mask_ld(av.nchunk), 256);
-    need = (c->mode == QK_BF16X3 ? 2 : 1) * plane + mask;
-  } else {
-    av.rows = 5 * W;
-    plane = align_up((size_t)av.rows * av.ld * es, 256);
-    need = plane;
+  // FP64: one launch, each moved point's AO row and its product with C^T
+  // (kept per upload of C), when the basis tables fit the kernel's shared
+  // memory; the reduced modes (and larger bases) run the moved points through
+  // the tile kernels, whose shared C blocks move far fewer bytes than a
+  // product per point.  The cached AO tensor of the full configuration stays
+  // valid either way.
+  const bool f64 = c->mode == QK_FP64;
+  if (!f64 || !single_mo_fits(f64, c->bdev)) return single_move_tiled(c, W, dout);
+  if (c->single_ct_version != c->mo_version || c->single_ct_f64 != f64 || !c->d_single_ct.p) {
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = c->d_single_ct.ensure(es * (size_t)c->ao_num * single_ct_ld(f64, N));
+    if (e == cudaSuccess) e = launch_single_ct(f64, c->c64, N, c->ao_num, c->d_single_ct.p, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "single-move C^T");
+    c->single_ct_version = c->mo_version;
+    c->single_ct_f64 = f64;
   }
-  cudaError_t e = c->d_single_ws.ensure(need);
-  if (e != cudaSuccess) return cuda_fail(c, e, "single-move workspace");
-  unsigned char* p = (unsigned char*)c->d_single_ws.p;
-  av.a = p;
-  if (tiled) {
-    if (c->mode == QK_BF16X3) av.a_lo = p + plane;
-    // a few tiles only: each ao_vgl tile culls for itself (no pre-pass launch)
-    av.mask = p + (c->mode == QK_BF16X3 ? 2 : 1) * plane;
-  }
+  cudaError_t e;
   {
-    TimedLaunch t(c, 0);
-    e = launch_ao_vgl(c->bdev, c->psingle, c->mode, av, c->stream);
+    TimedLaunch t(c, 1);
+    e = launch_single_mo(f64, c->bdev, c->psingle, c->d_single_ct.p, N, dout, c->stream);
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "single-move ao_vgl");
-  st = contract(c, av, 5 * W, dout);
-  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "single-move MO vgl");
   return apply_cusp(c, c->psingle, dout);
 }
 

@@ -318,6 +318,17 @@ cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* 
 int ao_value_tile_points();
 cudaError_t launch_ao_value(const BasisDev& b, const PointsDev& p, int out_mode,
                             const AOTensor& out, cudaStream_t s);
+// Single-electron moves in FP64 (single_mo.cu): C^T [ao][single_ct_ld] from
+// C [mo][ao], then the MO vgl of the W moved points p into out [W][5][mo] in
+// one launch (f64 must be true).
+int64_t single_ct_ld(bool f64, int64_t mo_num);
+cudaError_t launch_single_ct(bool f64, const double* C, int64_t mo_num, int64_t ao_num, void* ct,
+                             cudaStream_t s);
+cudaError_t launch_single_mo(bool f64, const BasisDev& b, const PointsDev& p, const void* ct,
+                             int64_t mo_num, void* out, cudaStream_t s);
+// Whether the one-launch kernel applies (FP64, and the basis tables fit its
+// shared memory).
+bool single_mo_fits(bool f64, const BasisDev& b);
 // Single-electron moves (single.cu): src point w -> dst point w * elec_num + elec.
 cudaError_t launch_scatter_points(const PointsDev& src, const PointsDev& dst, int64_t elec_num,
                                   int64_t elec, cudaStream_t s);
