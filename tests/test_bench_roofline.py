@@ -62,3 +62,20 @@ def test_traffic_only_while_sources_match(tmp_path, monkeypatch):
     assert bench.traffic_for("k", "tf32") is None
     src.write_text("kernel v2\n")
     assert bench.traffic_for("k", "bf16x3") is None
+
+
+def test_accuracy_and_common_bar(orc, cfg, monkeypatch):
+    """The per-path accuracy entry compares each path's first rows with the
+    oracle, and the speedup is stated at a bar both paths meet."""
+    m = cfg(1)
+    monkeypatch.setattr(bench, "CPU_SAMPLE_POINTS", 40)
+    ref, size = orc.mo_vgl(m, points=m.points[:40])
+    rng = np.random.default_rng(0)
+    samples = {"bf16x3": (ref + 1e-6 * size * rng.uniform(-1, 1, ref.shape)).reshape(-1),
+               "fp32": (ref + 1e-7 * size * rng.uniform(-1, 1, ref.shape)).reshape(-1)}
+    acc = bench.accuracy(m, samples, "bf16x3")
+    assert 5e-7 < acc["bf16x3"]["value"] <= 1e-6 and acc["fp32"]["value"] <= 1e-7
+    assert acc["bf16x3"]["stated_bar"] == 5e-5 and acc["fp32"]["stated_bar"] == 3e-5
+    res = {"accuracy": acc, "fp32_path": {"ms_per_step": 30.0}, "ms_per_step": 1.0}
+    cb = bench.common_bar(res, "bf16x3")
+    assert cb["bar"] == 5e-5 and cb["both_meet"] and cb["speedup"] == 30.0
