@@ -167,9 +167,9 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
           wm |= __reduce_or_sync(0xffffffffu, gb) & 0xFu;
         }
         // ---- phase 2, tiled: all 128 rows (stage rows 125..127 belong to the
-        // lane past the tile and hold zeros) in 16-byte stores; the columns of
-        // dead 16-AO groups are not written (the contraction never reads them)
-        const int64_t row0 = ptile * kTileRows;
+        // lane past the tile and hold zeros) in 16-byte stores into the
+        // block's 128-byte column slices; the columns of dead 16-AO groups
+        // are not written (the contraction never reads them)
         if constexpr (kSplit) {
           // a lane splits 8 consecutive columns of one row into 16 bytes of each
           // bf16 plane: hi = rn(v), lo = rn(v - hi); a warp covers 4 rows
@@ -190,11 +190,10 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
               memcpy(&lw[j], &l, 4);
             }
             if (store) {
-              const int64_t e = (row0 + r) * out.ld + col0 + 8 * c8;
-              *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a) + e) =
-                  make_uint4(hw[0], hw[1], hw[2], hw[3]);
-              *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out.a_lo) + e) =
-                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
+              __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out.a) +
+                                 blocked_offset(ptile, q, out.nchunk, 2, 0, r, 8 * c8, 2);
+              *reinterpret_cast<uint4*>(o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(o + kBlockElems) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
           }
         } else if constexpr (sizeof(T) == 8) {
@@ -206,8 +205,9 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
             const int r = warp + kWarps * it;
             const double2 w = make_double2(sh.stage[r][2 * lane], sh.stage[r][2 * lane + 1]);
             if (store)
-              *reinterpret_cast<double2*>(static_cast<double*>(out.a) + (row0 + r) * out.ld +
-                                          col0 + 2 * lane) = w;
+              *reinterpret_cast<double2*>(
+                  static_cast<double*>(out.a) +
+                  blocked_offset(ptile, q, out.nchunk, 1, 0, r, 2 * lane, 8)) = w;
           }
         } else {
           // a lane stores 4 consecutive columns of one row; a warp covers 2 rows
@@ -219,8 +219,9 @@ __device__ __forceinline__ void ao_chunk_tiles(const BasisDev& b, const PointsDe
             const float4 w = make_float4(sh.stage[r][4 * c4], sh.stage[r][4 * c4 + 1],
                                          sh.stage[r][4 * c4 + 2], sh.stage[r][4 * c4 + 3]);
             if (store)
-              *reinterpret_cast<float4*>(static_cast<float*>(out.a) + (row0 + r) * out.ld + col0 +
-                                         4 * c4) = w;
+              *reinterpret_cast<float4*>(
+                  static_cast<float*>(out.a) +
+                  blocked_offset(ptile, q, out.nchunk, 1, 0, r, 4 * c4, 4)) = w;
           }
         }
         continue;
@@ -409,6 +410,7 @@ cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* 
 cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
                           const AOTensor& out, cudaStream_t s) {
   if (out.tiled) {
+    if (!out.blocked || !out.chunked) return cudaErrorInvalidValue;  // the one tiled vgl layout
     switch (out_mode) {
       case QK_FP64:
         return launch_ao<double, false, true, true>(b, p, out, s);
@@ -447,7 +449,7 @@ cudaError_t launch_ao_vgl(const BasisDev& b, const PointsDev& p, int out_mode,
 
 // ------------------------------------------------------------ helpers ---
 
-// Nonzero (point, AO) pairs of a tiled vgl AO tensor: the AO of a point
+// Nonzero (point, AO) pairs of a tiled (blocked) vgl AO tensor: the AO of a point
 // counts when any of its five rows holds a nonzero entry at that column
 // (either bf16 plane when split; the sign bit ignored; kEs bytes per entry).  Blocks whose mask
 // byte is zero, and the dead 16-AO groups of live blocks, were not written
@@ -470,14 +472,14 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < pts * kChunkAO; i += blockDim.x) {
       const int j = i / kChunkAO, c = i % kChunkAO;
       if (!((gm >> (c >> 4)) & 1u)) continue;  // dead groups are not written
-      const int64_t e0 = (tile * kTileRows + 5 * j) * t.ld + (int64_t)q * kChunkAO + c;
       bool nz = false;
 #pragma unroll
       for (int r = 0; r < 5; ++r) {
-        const int64_t e = e0 + r * t.ld;
+        const int64_t e =
+            blocked_offset(tile, q, t.nchunk, kEs == 2 ? 2 : 1, 0, 5 * j + r, c, kEs);
         if constexpr (kEs == 2) {
           nz |= (static_cast<const uint16_t*>(t.a)[e] & 0x7fffu) != 0u;
-          nz |= (static_cast<const uint16_t*>(t.a_lo)[e] & 0x7fffu) != 0u;
+          nz |= (static_cast<const uint16_t*>(t.a)[e + kBlockElems] & 0x7fffu) != 0u;
         } else if constexpr (kEs == 4) {
           nz |= (static_cast<const uint32_t*>(t.a)[e] & 0x7fffffffu) != 0u;
         } else {
@@ -496,6 +498,7 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_ao_nnz(const AOTensor& t, int es, int64_t n, unsigned long long* out,
                           cudaStream_t s) {
+  if (!t.tiled || !t.blocked) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (n + kTilePoints - 1) / kTilePoints;

@@ -618,12 +618,13 @@ AOTensor ao_view(qk_context c, void* ws, int mode) {
   t.a = ws;
   if (vgl_tiled(mode)) {
     t.tiled = true;
+    t.blocked = true;
     t.rows = ao_tiles(c) * kTileRows;
     const size_t es = ao_elem_bytes(mode);
     const size_t plane = align_up((size_t)t.rows * t.ld * es, 256);
     unsigned char* p = (unsigned char*)ws + plane;
     if (mode == QK_BF16X3) {
-      t.a_lo = p;
+      t.a_lo = (unsigned char*)ws + kBlockElems * es;  // planes interleave by block
       p += plane;
     }
     t.mask = p;
@@ -695,19 +696,20 @@ PointsDev points_range(const PointsDev& p, int64_t p0, int64_t p1) {
 
 AOTensor ao_range(const AOTensor& t, int mode, int64_t p0, int64_t p1) {
   AOTensor v = t;
-  const size_t es = mode == QK_FP64 ? sizeof(double)
-                                    : (mode == QK_BF16X3 ? sizeof(__nv_bfloat16) : sizeof(float));
-  int64_t r0;
+  const size_t es = ao_elem_bytes(mode);
   if (t.tiled) {
     const int64_t t0 = p0 / kTilePoints;
-    r0 = t0 * kTileRows;
     v.rows = (p1 - p0 + kTilePoints - 1) / kTilePoints * kTileRows;
     v.mask = t.mask + t0 * mask_ld(t.nchunk);
     if (t.reach) v.reach = t.reach + t0 * t.nchunk;
-  } else {
-    r0 = 5 * p0;
-    v.rows = 5 * (p1 - p0);
+    // the blocks of tile t0 onwards (both planes in each block)
+    const size_t off = (size_t)blocked_offset(t0, 0, t.nchunk, t.a_lo ? 2 : 1, 0, 0, 0, (int)es);
+    v.a = (unsigned char*)t.a + off * es;
+    if (t.a_lo) v.a_lo = (unsigned char*)v.a + kBlockElems * es;
+    return v;
   }
+  const int64_t r0 = 5 * p0;
+  v.rows = 5 * (p1 - p0);
   v.a = (unsigned char*)t.a + (size_t)r0 * t.ld * es;
   if (t.a_lo) v.a_lo = (unsigned char*)t.a_lo + (size_t)r0 * t.ld * es;
   return v;
@@ -1290,6 +1292,7 @@ qk_status single_move_tiled(qk_context c, int64_t W, void* dout) {
   if (tiled) {
     const int64_t tiles = (W + kTilePoints - 1) / kTilePoints;
     av.tiled = true;
+    av.blocked = true;
     av.rows = tiles * kTileRows;
     plane = align_up((size_t)av.rows * av.ld * es, 256);
     mask = align_up((size_t)tiles * mask_ld(av.nchunk), 256);
@@ -1304,7 +1307,7 @@ qk_status single_move_tiled(qk_context c, int64_t W, void* dout) {
   unsigned char* p = (unsigned char*)c->d_single_ws.p;
   av.a = p;
   if (tiled) {
-    if (c->mode == QK_BF16X3) av.a_lo = p + plane;
+    if (c->mode == QK_BF16X3) av.a_lo = p + kBlockElems * es;  // planes interleave by block
     // a few tiles only: each ao_vgl tile culls for itself (no pre-pass launch)
     av.mask = p + (c->mode == QK_BF16X3 ? 2 : 1) * plane;
   }

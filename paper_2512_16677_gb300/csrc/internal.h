@@ -105,6 +105,14 @@ struct AOTensor {
   int comps;
   // dense layout only: columns in the caller's AO order (BasisDev::ao_caller)
   bool caller_cols;
+  // tiled vgl layout, blocked: block b = tile * nchunk + chunk holds its
+  // planes (bf16 hi then lo; one otherwise) one after the other, each plane
+  // as 128-byte-wide column slices ([64 / w][128 rows][w columns], w = 128
+  // bytes / element size), blocks in b order: a live block is one contiguous
+  // read and a slice one TMA box (element offset: blocked_offset below).
+  // a_lo then points at the lo plane of block 0.  Otherwise rows of ld
+  // elements.
+  bool blocked;
   // tiled, with reach: the contraction multiplies tiles in pairs (2i, 2i+1)
   // over the union of their live column groups, so ao_vgl also writes zeros
   // into the groups of a live block that the partner tile's reach word says
@@ -113,6 +121,17 @@ struct AOTensor {
 };
 constexpr int kTilePoints = 25;   // 125 rows of a 128-row contraction tile
 constexpr int kTileRows = 128;
+constexpr int64_t kBlockElems = (int64_t)kTileRows * 64;  // one plane of one block
+
+// Element offset of (tile row r, chunk column c, plane p) of block
+// (tile, chunk) in the blocked layout, for elements of `es` bytes.
+__host__ __device__ __forceinline__ int64_t blocked_offset(int64_t tile, int chunk, int nchunk,
+                                                           int planes, int plane, int r, int c,
+                                                           int es) {
+  const int w = 128 / es;  // columns of one slice
+  return ((tile * nchunk + chunk) * planes + plane) * kBlockElems +
+         (int64_t)(c / w) * (kTileRows * w) + (int64_t)r * w + c % w;
+}
 
 // Launch facts of a kernel on the current device, worked out once per
 // (kernel, device): its opt-in dynamic shared memory set, resident blocks
@@ -289,6 +308,7 @@ struct TcProblem {
   int num_kb;                    // K blocks
   int bn;                        // MMA N (multiple of 16, <= the launch's bn_max)
   int nchunk;
+  int blocked;                   // AO tensor in the blocked layout (map over its slices)
 };
 // BN_MAX values instantiated for multi-problem launches.
 extern const int kBatchBnMax[6];

@@ -7,7 +7,8 @@
 // sparse-AO MO product of Sec. 3.2 does; skipped terms are exact zeros.
 //
 // A CTA computes a 128-row x 64-column tile of D.  Per live column group it
-// stages the 128 x 16 AO block (k-major) and the 64 x 16 block of C in shared
+// stages the 128 x 16 AO block (one contiguous 16 KB slice of the blocked
+// layout; k-major in shared memory) and the 64 x 16 block of C in shared
 // memory, double buffered so that the next group loads while this one is
 // multiplied; each thread accumulates an 8-row x 4-column block in FP64
 // registers.  The output rows go to the caller's points through the tile
@@ -23,8 +24,7 @@ constexpr int kBN = 64;    // output columns per CTA
 constexpr int kBK = 16;    // one column group
 
 struct Sparse64Args {
-  const double* A;        // tiled AO tensor [tiles * 128][lda]
-  int64_t lda;
+  const double* A;        // tiled AO tensor, blocked: a 16-column group is one 16 KB slice
   const uint8_t* mask;    // [tiles][mask_ld(nchunk)] live column groups
   int nchunk;
   const double* C;        // [N][ldc] chunked columns (padding zero)
@@ -75,10 +75,11 @@ __global__ void __launch_bounds__(kThreads)
     auto stage = [&](int b, int qq, int gg) {
       const int64_t col = (int64_t)qq * kChunkAO + 16 * gg;
       {
-        // 128 rows x 16 columns: thread -> row tid / 2, columns 8 (tid & 1) .. + 7
+        // 128 rows x 16 columns (one contiguous slice): thread -> row tid / 2,
+        // columns 8 (tid & 1) .. + 7
         const int r = tid >> 1, k0 = (tid & 1) * 8;
         const double2* src = reinterpret_cast<const double2*>(
-            a.A + (mt * kTileRows + r) * a.lda + col + k0);
+            a.A + blocked_offset(mt, qq, a.nchunk, 1, 0, r, 16 * gg + k0, 8));
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const double2 v = src[k];
@@ -160,13 +161,12 @@ __global__ void __launch_bounds__(kThreads)
 
 cudaError_t launch_mo_sparse64(const AOTensor& ao, const double* C, int64_t ldc, int64_t N,
                                double* D, int64_t out_rows, cudaStream_t s) {
-  if (!ao.tiled || ao.comps == 1) return cudaErrorInvalidValue;
+  if (!ao.tiled || !ao.blocked || ao.comps == 1) return cudaErrorInvalidValue;
   if (ao.nchunk > 256) return cudaErrorInvalidValue;
   const int64_t m_tiles = ao.rows / kTileRows;
   if (m_tiles == 0 || N == 0) return cudaSuccess;
   Sparse64Args a;
   a.A = static_cast<const double*>(ao.a);
-  a.lda = ao.ld;
   a.mask = ao.mask;
   a.nchunk = ao.nchunk;
   a.C = C;

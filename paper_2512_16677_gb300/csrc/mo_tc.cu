@@ -69,7 +69,8 @@ constexpr int kStageBnShift = 8;
 
 // One output tile as the three roles see it.
 struct TileInfo {
-  const CUtensorMap* a;  // AO tiles (QK_BF16X3: hi and lo planes in one 3-D map)
+  const CUtensorMap* a;  // AO tiles (QK_BF16X3: hi and lo planes in one 3-D map;
+                         // blocked: a 3-D map over the tensor's column slices)
   const CUtensorMap* b;  // C tiles (likewise)
   float* D;
   const uint8_t* kmask;  // live 16-column groups of this M tile's chunks (NULL: all)
@@ -81,6 +82,8 @@ struct TileInfo {
   int ntile;             // index of the tile's N range (density partials)
   bool tiled;            // rows: rows_per_tile live of 128, output row = rpt (m0/128) + local
   int rows_per_tile;     // tiled: 125 (vgl) or 128 (values only)
+  int nchunk;
+  bool ablocked;         // AO tensor in the blocked layout (coordinates: blocked_slice)
   const float* wdens;    // density epilogue: column weights (NULL: store D)
   float* rho;            // density epilogue: [N tiles][M] partial sums
 };
@@ -132,7 +135,7 @@ struct SingleSched {
   float* rho;
   int64_t M, N, total;
   int num_kb, n_tiles, nchunk, rows_per_tile;
-  bool tiled;
+  bool tiled, blocked;
   __device__ __forceinline__ int64_t count() const { return total; }
   // the tensor maps into the TMA unit's cache before the first copy
   __device__ __forceinline__ void prefetch_maps() const {
@@ -160,6 +163,8 @@ struct SingleSched {
     x.ntile = nt;
     x.tiled = tiled;
     x.rows_per_tile = rows_per_tile;
+    x.nchunk = nchunk;
+    x.ablocked = blocked;
     x.wdens = wdens;
     x.rho = rho;
     return x;
@@ -192,6 +197,8 @@ struct BatchSched {
     x.ntile = it.z;
     x.tiled = p.mask != nullptr;
     x.rows_per_tile = 5 * kTilePoints;
+    x.nchunk = p.nchunk;
+    x.ablocked = p.blocked != 0;
     x.wdens = nullptr;
     x.rho = nullptr;
     return x;
@@ -319,7 +326,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (kb >= 0 && copier) {
           const uint32_t dst = base + s * S::STAGE_BYTES + dst_off;
-          if constexpr (TR::kPlanes == 2)
+          if (lane == 0 && x.ablocked)
+            tma_load_3d(dst, map, full_bar(s), 0, 0,
+                        blocked_slice<MODE>(x.m0 / kBM, kb, x.nchunk));
+          else if constexpr (TR::kPlanes == 2)
             tma_load_3d(dst, map, full_bar(s), kb * TR::kBK, row0, 0);
           else
             tma_load_2d(dst, map, full_bar(s), kb * TR::kBK, row0);
@@ -340,8 +350,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the AO block of the next live chunk into L2 now, so that its copy
           // into the ring (a stage later) does not wait on HBM
           if constexpr (kPer == 1) {
-            if (live && lane == 2)
-              tma_prefetch_l2_3d(x.a, (q0 + __ffs(live) - 1) * TR::kBK, x.m0, 0);
+            if (live && lane == 2) {
+              const int kn = q0 + __ffs(live) - 1;
+              if (x.ablocked)
+                tma_prefetch_l2_3d(x.a, 0, 0, blocked_slice<MODE>(x.m0 / kBM, kn, x.nchunk));
+              else
+                tma_prefetch_l2_3d(x.a, kn * TR::kBK, x.m0, 0);
+            }
           }
 #pragma unroll
           for (int h = 0; h < kPer; ++h) {
@@ -611,19 +626,26 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   if (M == 0 || N == 0) return cudaSuccess;
   if (M > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
   if (ao.tiled && M % kBM != 0) return cudaErrorInvalidValue;
+  if (ao.blocked && (!ao.tiled || K > (int64_t)ao.nchunk * kChunkAO)) return cudaErrorInvalidValue;
   SingleSched<BN> sc;
   // the last N tile multiplies only the MOs it has, rounded up to 16
   const int64_t n_tiles = (N + BN - 1) / BN;
   const int last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
   sc.last_bn = last_bn;
-  if (TR::kPlanes == 2) {
+  if (ao.blocked) {
+    if (!make_map_blocked(&sc.a, ao.a, TR::kPlanes == 2, M / kBM * ao.nchunk))
+      return cudaErrorInvalidValue;
+  } else if (TR::kPlanes == 2) {
     if (!make_map_planes(&sc.a, ao.a, ao.a_lo, K, M, ao.ld, TR::kBK, kBM))
       return cudaErrorInvalidValue;
+  } else {
+    if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
+  }
+  if (TR::kPlanes == 2) {
     if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
     if (last_bn != BN && !make_map_planes(&sc.b_last, c_hi, c_lo, K, N, ldc, TR::kBK, last_bn))
       return cudaErrorInvalidValue;
   } else {
-    if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
     if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN)) return cudaErrorInvalidValue;
     if (last_bn != BN && !make_map(&sc.b_last, c_hi, f32, K, N, ldc, TR::kBK, last_bn))
       return cudaErrorInvalidValue;
@@ -635,6 +657,7 @@ cudaError_t launch_single(const AOTensor& ao, int64_t K, const void* c_hi, const
   sc.wdens = wdens;
   sc.rho = rho;
   sc.tiled = ao.tiled;
+  sc.blocked = ao.blocked;
   sc.nchunk = ao.nchunk;
   sc.M = ao.tiled ? out_rows : M;
   sc.N = N;
@@ -722,17 +745,24 @@ bool tc_make_problem(int mode, const AOTensor& ao, int64_t K, const void* c_hi, 
   const int bk = f32 ? TcTraits<QK_TF32>::kBK : TcTraits<QK_BF16X3>::kBK;
   if (bn % 16 != 0 || bn < 16 || bn > 256) return false;
   if (ao.rows > INT32_MAX || K > INT32_MAX || N > INT32_MAX) return false;
-  if (!f32) {
+  if (ao.blocked) {
+    if (!ao.tiled || ao.rows % kBM != 0 || K > (int64_t)ao.nchunk * kChunkAO) return false;
+    if (!make_map_blocked(&p->a, ao.a, !f32, ao.rows / kBM * ao.nchunk)) return false;
+  } else if (!f32) {
     if (!make_map_planes(&p->a, ao.a, ao.a_lo, K, ao.rows, ao.ld, bk, kBM)) return false;
-    if (!make_map_planes(&p->b, c_hi, c_lo, K, N, ldc, bk, bn)) return false;
   } else {
     if (!make_map(&p->a, ao.a, f32, K, ao.rows, ao.ld, bk, kBM)) return false;
+  }
+  if (!f32) {
+    if (!make_map_planes(&p->b, c_hi, c_lo, K, N, ldc, bk, bn)) return false;
+  } else {
     if (!make_map(&p->b, c_hi, f32, K, N, ldc, bk, bn)) return false;
   }
   p->D = out;
   p->mask = ao.tiled ? ao.mask : nullptr;
   p->perm = ao.tiled ? ao.perm : nullptr;
   p->nchunk = ao.nchunk;
+  p->blocked = ao.blocked ? 1 : 0;
   p->M = out_rows;
   p->N = N;
   p->num_kb = (int)((K + bk - 1) / bk);

@@ -7,9 +7,10 @@
 // two CTAs of a cluster run one tcgen05.mma.cta_group::2 with M = 256 (two
 // consecutive 25-point tiles, one per CTA), and each CTA stages only half of
 // the C tile (N / 2 rows).  Per SM a pipeline stage then carries the AO
-// block (32 KB) and half the C block (20 KB at N = 160) instead of the whole
-// C block (40 KB), so four stages fit where three did, and every C byte
-// fetched from L2 serves twice the MMA work.
+// block (32 KB, one contiguous box of the blocked layout) and half the C
+// block (20 KB at N = 160) instead of the whole C block (40 KB), so four
+// stages fit where three did, and every C byte fetched from L2 serves twice
+// the MMA work.
 //
 // The two tiles of a pair share one K sequence: the union of their live AO
 // blocks and 16-AO column groups.  A block dead in this CTA's own tile is
@@ -74,7 +75,7 @@ constexpr int stages_for_pair(int mode, int bn) {
 // N tile p % n_tiles); CTA rank r of the cluster owns M tile 2 (p / n_tiles) + r.
 template <int BN>
 struct PairSched {
-  CUtensorMap a;       // AO hi/lo planes (3-D) or FP32 (2-D), box 128 rows
+  CUtensorMap a;       // blocked AO tensor: 3-D map over its column slices (one box = one K block)
   CUtensorMap b;       // C, box BN / 2 rows
   CUtensorMap b_last;  // C, box last_bn / 2 rows (last N tile, when last_bn < BN)
   int last_bn;
@@ -82,7 +83,7 @@ struct PairSched {
   const uint8_t* mask;  // [m tiles][mask_ld(nchunk)]
   const int32_t* perm;  // slot -> point (NULL: identity)
   int64_t M, N;         // output rows (5 points) and columns
-  int a_rows;           // rows of the AO tensor (128 per tile): a row past them reads zeros
+  int zero_slice;       // a slice past the tensor's end: its box reads zeros
   int m_tiles, n_tiles, num_kb, nchunk;
   int64_t total;        // pair-tiles
 };
@@ -324,15 +325,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (kb >= 0 && lane == 0) {
           const uint32_t bar = map_to_rank(full_bar(s), 0);  // the leader's full[s]
           const uint32_t dst = base + s * S::STAGE_BYTES + (a_warp ? 0u : TR::kPlanes * S::A_BYTES);
-          // own AO block, or zeros from past the tensor's last row when the
-          // block is dead in this CTA's tile; own half of the C block
-          const int row = a_warp ? (own_live ? mt_own * kBM : sc.a_rows)
-                                 : (int)(nt * BN + (int)rank * (bn / 2));
-          const CUtensorMap* map = a_warp ? &sc.a : bmap;
-          if constexpr (TR::kPlanes == 2)
-            tma_load_3d_pair(dst, map, bar, kb * TR::kBK, row, 0);
-          else
-            tma_load_2d_pair(dst, map, bar, kb * TR::kBK, row);
+          // own AO block (one contiguous box), or zeros from past the
+          // tensor's end when the block is dead in this CTA's tile; own half
+          // of the C block
+          if (a_warp) {
+            const int z = own_live ? blocked_slice<MODE>(mt_own, kb, sc.nchunk) : sc.zero_slice;
+            tma_load_3d_pair(dst, &sc.a, bar, 0, 0, z);
+          } else {
+            const int row = (int)(nt * BN + (int)rank * (bn / 2));
+            if constexpr (TR::kPlanes == 2)
+              tma_load_3d_pair(dst, bmap, bar, kb * TR::kBK, row, 0);
+            else
+              tma_load_2d_pair(dst, bmap, bar, kb * TR::kBK, row);
+          }
         }
         return true;
       };
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int jn = live ? __ffs(live) - 1 : 0;
             const uint32_t gn = __shfl_sync(0xffffffffu, g, jn);
             if (a_warp && live && lane == 2 && (gn >> 4) != 0u)
-              tma_prefetch_l2_3d(&sc.a, (32 * w + jn) * TR::kBK, mt_own * kBM, 0);
+              tma_prefetch_l2_3d(&sc.a, 0, 0, blocked_slice<MODE>(mt_own, 32 * w + jn, sc.nchunk));
           }
 #pragma unroll
           for (int h = 0; h < kPer; ++h) {
@@ -584,22 +589,23 @@ cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, cons
   const int64_t M = ao.rows;
   if (M == 0 || N == 0) return cudaSuccess;
   if (M > INT32_MAX / 2 || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
-  if (!ao.tiled || M % kBM != 0 || ao.comps == 1) return cudaErrorInvalidValue;
+  if (!ao.tiled || !ao.blocked || M % kBM != 0 || ao.comps == 1) return cudaErrorInvalidValue;
+  if (K > (int64_t)ao.nchunk * kChunkAO) return cudaErrorInvalidValue;
   PairSched<BN> sc;
   const int64_t n_tiles = (N + BN - 1) / BN;
   // the last N tile multiplies only the MOs it has, rounded up to 16 (halves
   // of whole 8-row groups)
   sc.last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
+  const int64_t nblocks = M / kBM * ao.nchunk;
+  if (2 * nblocks + 2 > INT32_MAX) return cudaErrorInvalidValue;
+  if (!make_map_blocked(&sc.a, ao.a, TR::kPlanes == 2, nblocks)) return cudaErrorInvalidValue;
   if (TR::kPlanes == 2) {
-    if (!make_map_planes(&sc.a, ao.a, ao.a_lo, K, M, ao.ld, TR::kBK, kBM))
-      return cudaErrorInvalidValue;
     if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN / 2))
       return cudaErrorInvalidValue;
     if (sc.last_bn != BN &&
         !make_map_planes(&sc.b_last, c_hi, c_lo, K, N, ldc, TR::kBK, sc.last_bn / 2))
       return cudaErrorInvalidValue;
   } else {
-    if (!make_map(&sc.a, ao.a, f32, K, M, ao.ld, TR::kBK, kBM)) return cudaErrorInvalidValue;
     if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN / 2)) return cudaErrorInvalidValue;
     if (sc.last_bn != BN && !make_map(&sc.b_last, c_hi, f32, K, N, ldc, TR::kBK, sc.last_bn / 2))
       return cudaErrorInvalidValue;
@@ -609,7 +615,7 @@ cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, cons
   sc.perm = ao.perm;
   sc.M = out_rows;
   sc.N = N;
-  sc.a_rows = (int)M;
+  sc.zero_slice = (int)(2 * nblocks);
   sc.m_tiles = (int)(M / kBM);
   sc.n_tiles = (int)n_tiles;
   sc.num_kb = (int)((K + TR::kBK - 1) / TR::kBK);

@@ -258,5 +258,35 @@ inline bool make_map_planes(CUtensorMap* m, const void* hi, const void* lo, int6
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The blocked AO tensor (AOTensor::blocked) as a 3-D map over its 128-byte
+// column slices: (w columns, 128 rows, slice), slice z = block * 2 + j with
+// j the plane (split bf16: hi, lo; box of 2 slices = the whole 32 KB block,
+// the same shared-memory image as the row layout's 3-D box of both planes)
+// or the 32-column half (TF32: box of 1 slice = one K block).  A box at
+// slice 2 * nblocks (past the end) reads zeros.
+inline bool make_map_blocked(CUtensorMap* m, const void* base, bool split, int64_t nblocks) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t w = split ? 64 : 32;
+  cuuint64_t dims[3] = {w, 128, (cuuint64_t)(2 * nblocks)};
+  cuuint64_t strides[2] = {128, 128 * 128};
+  cuuint32_t box[3] = {(cuuint32_t)w, 128, split ? 2u : 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, split ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Slice coordinate of K block kb of M tile mt in the blocked map: a split
+// K block is one chunk (both planes), a TF32 K block half a chunk.
+template <int MODE>
+__device__ __forceinline__ int blocked_slice(int mt, int kb, int nchunk) {
+  if constexpr (TcTraits<MODE>::kBK == 64)
+    return 2 * (mt * nchunk + kb);
+  else
+    return 2 * (mt * nchunk + (kb >> 1)) + (kb & 1);
+}
+
 }  // namespace tc
 }  // namespace qk
