@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int4 w = items[i];
     const AOProblem& P = probs[w.x];
-    ao_chunk_tiles<float, kSplit, true, true>(P.b, P.p, P.out, w.y, w.z, w.w, 1, sh);
+    const int64_t tiles = (P.p.n + kTilePoints - 1) / kTilePoints;
+    ao_chunk_tiles<float, kSplit, true, true>(P.b, P.p, P.out, w.y, w.z, tiles, w.w, sh);
   }
 }
 
@@ -298,22 +299,13 @@ __global__ void __launch_bounds__(kThreads)
 constexpr int kReachThreads = 256;
 constexpr int kReachSmemShells = 8192;  // 128 KB of float4
 
-__global__ void __launch_bounds__(kReachThreads)
-    tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles, int staged) {
-  extern __shared__ float4 shell_tab[];  // [shell] (X, Y, Z, r2max), float
-  griddep_wait();
-  if (staged) {
-    for (int s = threadIdx.x; s < b.shell_num; s += blockDim.x) {
-      const int A = b.shell_nuc[s];
-      shell_tab[s] = make_float4(b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1], b.nucl_hi[3 * A + 2],
-                                 b.shell_r2_f[s]);
-    }
-    __syncthreads();
-  }
+// Tiles first, first + step, ... of one problem, one warp each.
+__device__ __forceinline__ void reach_tiles(const BasisDev& b, const PointsDev& pts,
+                                            uint32_t* reach, int64_t tiles, bool staged,
+                                            const float4* shell_tab, int64_t first,
+                                            int64_t step) {
   const int lane = threadIdx.x & 31;
-  const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles;
-       t += wstep) {
+  for (int64_t t = first; t < tiles; t += step) {
     const int64_t ip = t * kTilePoints + lane;
     const bool pv = lane < kTilePoints && ip < pts.n;
     float x = 0.0f, y = 0.0f, z = 0.0f;
@@ -345,6 +337,42 @@ __global__ void __launch_bounds__(kReachThreads)
   }
 }
 
+// The shells' centres and radii^2 into shared memory.
+__device__ __forceinline__ void stage_shells(const BasisDev& b, float4* shell_tab) {
+  for (int s = threadIdx.x; s < b.shell_num; s += blockDim.x) {
+    const int A = b.shell_nuc[s];
+    shell_tab[s] = make_float4(b.nucl_hi[3 * A], b.nucl_hi[3 * A + 1], b.nucl_hi[3 * A + 2],
+                               b.shell_r2_f[s]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kReachThreads)
+    tile_reach_kernel(BasisDev b, PointsDev pts, uint32_t* reach, int64_t tiles, int staged) {
+  extern __shared__ float4 shell_tab[];  // [shell] (X, Y, Z, r2max), float
+  griddep_wait();
+  if (staged) stage_shells(b, shell_tab);
+  const int64_t warps = blockDim.x >> 5;
+  reach_tiles(b, pts, reach, tiles, staged != 0, shell_tab,
+              blockIdx.x * warps + (threadIdx.x >> 5), (int64_t)gridDim.x * warps);
+}
+
+// Several problems: blockIdx.y is the problem; a problem's table is staged
+// when it has at most `cap` shells.
+__global__ void __launch_bounds__(kReachThreads)
+    tile_reach_batch_kernel(const AOProblem* probs, int cap) {
+  extern __shared__ float4 shell_tab[];
+  griddep_wait();
+  const AOProblem& P = probs[blockIdx.y];
+  if (P.out.reach == nullptr) return;
+  const int64_t tiles = (P.p.n + kTilePoints - 1) / kTilePoints;
+  const bool staged = P.b.shell_num <= cap;
+  if (staged) stage_shells(P.b, shell_tab);
+  const int64_t warps = blockDim.x >> 5;
+  reach_tiles(P.b, P.p, P.out.reach, tiles, staged, shell_tab,
+              blockIdx.x * warps + (threadIdx.x >> 5), (int64_t)gridDim.x * warps);
+}
+
 cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* reach,
                               int64_t tiles, cudaStream_t s) {
   const int staged = b.shell_num <= kReachSmemShells ? 1 : 0;
@@ -358,6 +386,24 @@ cudaError_t launch_tile_reach(const BasisDev& b, const PointsDev& p, uint32_t* r
   const int64_t blocks = want < 4 * (int64_t)f.sms ? want : 4 * (int64_t)f.sms;
   return launch_pdl(tile_reach_kernel, (unsigned)(blocks > 0 ? blocks : 1), kReachThreads, smem, s,
                     b, p, reach, tiles, staged);
+}
+
+cudaError_t launch_tile_reach_batch_impl(const AOProblem* d_probs, int nprob, int64_t max_tiles,
+                                         int max_shells, cudaStream_t s) {
+  if (nprob < 1 || nprob > 65535 || max_tiles == 0) return cudaSuccess;
+  const int cap = max_shells < kReachSmemShells ? max_shells : kReachSmemShells;
+  const size_t smem = sizeof(float4) * (size_t)cap;
+  KernelFacts f;
+  cudaError_t e = kernel_facts<tile_reach_batch_kernel>(sizeof(float4) * kReachSmemShells,
+                                                        kReachThreads, &f);
+  if (e != cudaSuccess) return e;
+  // about four blocks per SM over all problems, each walking its problem's tiles
+  int64_t gx = (4 * (int64_t)f.sms + nprob - 1) / nprob;
+  const int64_t want = (max_tiles + 7) / 8;
+  if (gx > want) gx = want;
+  if (gx < 1) gx = 1;
+  return launch_pdl(tile_reach_batch_kernel, dim3((unsigned)gx, (unsigned)nprob), kReachThreads,
+                    smem, s, d_probs, cap);
 }
 
 template <typename T, bool kSplit, bool kChunked, bool kTiled = false>
@@ -400,6 +446,11 @@ cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n
 }
 
 }  // namespace
+
+cudaError_t launch_tile_reach_batch(const AOProblem* d_probs, int nprob, int64_t max_tiles,
+                                    int max_shells, cudaStream_t s) {
+  return launch_tile_reach_batch_impl(d_probs, nprob, max_tiles, max_shells, s);
+}
 
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s) {

@@ -1,12 +1,15 @@
 // batch.cu -- walkers of several molecules of uneven sizes in one launch.
 //
 // A batch holds contexts that are fully set (basis, MO coefficients, points)
-// in a tensor-core mode.  One run evaluates every molecule's MO vgl with two
-// persistent launches: ao_vgl over a work list of (molecule, AO chunk, point
-// tiles) items, then the tcgen05 contraction over (molecule, M tile, N tile)
-// items, each list ordered longest first (LPT) so that the largest pieces
-// start early and the tail is made of small ones.  The two launches are
-// captured once in a CUDA graph and replayed on later runs; the work lists
+// in a tensor-core mode.  One run evaluates every molecule's MO vgl as the
+// single-molecule path does, each step one launch (or one sort) for all
+// molecules: a spatial order of every molecule's points in one radix sort
+// (problem index above the cell key), the tiles' reach pre-pass, ao_vgl
+// over a work list of (molecule, AO chunk, point tiles) items, then the
+// tcgen05 contraction over (molecule, M tile, N tile) items, the two lists
+// ordered longest first (LPT) so that the largest pieces start early and
+// the tail is made of small ones.  The launches are captured once in a CUDA
+// graph and replayed on later runs; the work lists
 // and per-molecule descriptors (tensor maps, pointers, sizes) live in device
 // memory and are rebuilt only when a shape or pointer changes.  The MMA N
 // of each molecule is chosen below the launch's BN_MAX, which the autotuner
@@ -30,6 +33,11 @@ struct qk_batch_s {
   // device descriptors and work lists
   DevBuf d_ao_probs, d_tc_probs, d_ao_items, d_tc_items, d_flag;
   int64_t n_ao_items = 0, n_tc_items = 0;
+  // the spatial order of all molecules' points
+  DevBuf d_sort, d_sort_probs, d_off;
+  BatchOrder order{};
+  int64_t max_tiles = 0;
+  int max_shells = 0;
   std::vector<uintptr_t> signature;  // what the descriptors were built from
   cudaGraphExec_t graph = nullptr;
   int graph_bn = -1;
@@ -50,6 +58,9 @@ qk_status bcuda(qk_batch b, cudaError_t e, const char* what) {
   return bfail(b, e == cudaErrorMemoryAllocation ? QK_ERR_OUT_OF_MEMORY : QK_ERR_CUDA,
                std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// ao_vgl work items of a batch: about four waves of resident CTAs.
+constexpr int64_t kAoItemsTarget = 3000;
 
 // MMA N for a molecule with n MOs under bn_max: as few N tiles as possible,
 // then the smallest multiple of 16 that covers n in that many tiles.
@@ -76,33 +87,75 @@ qk_status build(qk_batch b, float* const* outs) {
     }
   }
   const int n = (int)b->ctxs.size();
-  std::vector<AOProblem> aop(n);
-  std::vector<TcProblem> tcp(n);
-  std::vector<int4> ao_items, tc_items;
-  std::vector<double> ao_cost, tc_cost;
+  std::vector<ForwardViews> views(n);
+  std::vector<int64_t> off(n + 1, 0);
+  std::vector<SortProblem> sp(n);
   for (int i = 0; i < n; ++i) {
-    ForwardViews v;
+    ForwardViews& v = views[i];
     if (context_cusp_on(b->ctxs[i]))
       return bfail(b, QK_ERR_NOT_IMPLEMENTED,
                    "context " + std::to_string(i) + " has the cusp correction on");
     qk_status st = context_forward_views(b->ctxs[i], &v);
     if (st) return bfail(b, st, "context " + std::to_string(i) + " is not ready");
+    off[i + 1] = off[i] + v.p.n;
+    sp[i].p = v.p;
+    cell_grid(v.box_lo, v.box_hi, &sp[i].lo, &sp[i].inv);
+    sp[i].spatial = v.spatial && v.p.n >= 2 * kTilePoints ? 1 : 0;
+  }
+  const int64_t total = off[n];
+  if (total > INT32_MAX) return bfail(b, QK_ERR_BAD_SIZE, "more than 2^31 points in one batch");
+  {
+    cudaError_t e = b->d_sort.ensure(spatial_order_batch_bytes(total, n));
+    if (e == cudaSuccess) e = b->d_sort_probs.ensure(sizeof(SortProblem) * n);
+    if (e == cudaSuccess) e = b->d_off.ensure(sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_sort_probs.p, sp.data(), sizeof(SortProblem) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_off.p, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "batch point order");
+  }
+  b->order = spatial_order_batch_layout(b->d_sort.p, total, n);
+  // tiles per ao_vgl item: about kAoItemsTarget items over the whole batch,
+  // so that each item loads its chunk's tables once for many tiles
+  int64_t blocks = 0;
+  for (int i = 0; i < n; ++i)
+    blocks += (views[i].p.n + kTilePoints - 1) / kTilePoints * views[i].b.nchunk;
+  const int64_t ao_tiles_per_item = std::max<int64_t>(8, (blocks + kAoItemsTarget - 1) / kAoItemsTarget);
+  b->max_tiles = 0;
+  b->max_shells = 0;
+  std::vector<AOProblem> aop(n);
+  std::vector<TcProblem> tcp(n);
+  std::vector<int4> ao_items, tc_items;
+  std::vector<double> ao_cost, tc_cost;
+  for (int i = 0; i < n; ++i) {
+    ForwardViews& v = views[i];
+    // molecule i's points in the batch order, its AO tensor cut in tiles of
+    // that order, output rows written back through the permutation
+    PointsDev ps = b->order.sorted;
+    ps.n = v.p.n;
+    ps.x += off[i];
+    ps.y += off[i];
+    ps.z += off[i];
+    ps.hi += off[i];
+    ps.lo += off[i];
+    v.ao.perm = b->order.perm + off[i];
     aop[i].b = v.b;
-    aop[i].p = v.p;
+    aop[i].p = ps;
     aop[i].out = v.ao;
-    aop[i].out.reach = nullptr;  // the multi-problem ao_vgl culls tiles itself
+    b->max_tiles = std::max<int64_t>(b->max_tiles, (v.p.n + kTilePoints - 1) / kTilePoints);
+    b->max_shells = std::max(b->max_shells, v.b.shell_num);
     const int bn = pick_bn(v.mo_num, b->bn_max);
     if (!tc_make_problem(b->mode, v.ao, v.kpad, v.c_hi, v.c_lo, v.kpad, v.mo_num, outs[i], bn,
                          5 * v.p.n, &tcp[i]))
       return bfail(b, QK_ERR_CUDA, "tensor map encoding failed");
-    // ao items: 8 point tiles of one chunk each
+    // ao items: one chunk of every stride-th tile (strided, so that each
+    // item samples the whole molecule and items of one molecule cost alike)
     const int64_t tiles = (v.p.n + kTilePoints - 1) / kTilePoints;
-    const int64_t per = 8;
+    const int64_t stride = std::max<int64_t>(1, (tiles + ao_tiles_per_item - 1) / ao_tiles_per_item);
     for (int q = 0; q < v.b.nchunk; ++q)
-      for (int64_t t = 0; t < tiles; t += per) {
-        const int64_t e = std::min(tiles, t + per);
-        ao_items.push_back(make_int4(i, q, (int)t, (int)e));
-        ao_cost.push_back((double)(e - t));
+      for (int64_t t = 0; t < stride && t < tiles; ++t) {
+        ao_items.push_back(make_int4(i, q, (int)t, (int)stride));
+        ao_cost.push_back((double)((tiles - t + stride - 1) / stride));
       }
     // contraction items: every (M tile, N tile); cost ~ K blocks x MMA N
     const int64_t mt = v.ao.rows / kTileRows, nt = (v.mo_num + bn - 1) / bn;
@@ -177,9 +230,21 @@ qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig)
   return QK_SUCCESS;
 }
 
+// The point order, the reach pre-pass and ao_vgl of every molecule.
+cudaError_t launch_ao_side(qk_batch b, cudaStream_t s) {
+  cudaError_t e = launch_spatial_order_batch(b->order, (const SortProblem*)b->d_sort_probs.p,
+                                             (const int64_t*)b->d_off.p, s);
+  if (e == cudaSuccess)
+    e = launch_tile_reach_batch((const AOProblem*)b->d_ao_probs.p, (int)b->ctxs.size(),
+                                b->max_tiles, b->max_shells, s);
+  if (e == cudaSuccess)
+    e = launch_ao_vgl_batch(b->mode == QK_BF16X3, (const AOProblem*)b->d_ao_probs.p,
+                            (const int4*)b->d_ao_items.p, b->n_ao_items, s);
+  return e;
+}
+
 cudaError_t launch_both(qk_batch b, cudaStream_t s) {
-  cudaError_t e = launch_ao_vgl_batch(b->mode == QK_BF16X3, (const AOProblem*)b->d_ao_probs.p,
-                                      (const int4*)b->d_ao_items.p, b->n_ao_items, s);
+  cudaError_t e = launch_ao_side(b, s);
   if (e != cudaSuccess) return e;
   return launch_mo_tc_batch(b->mode, b->bn_max, (const TcProblem*)b->d_tc_probs.p,
                             (const int4*)b->d_tc_items.p, b->n_tc_items, (int*)b->d_flag.p, s);
@@ -321,7 +386,7 @@ qk_status qk_batch_run(qk_batch b, float* const* douts, const int64_t* sizes) {
     e = launch_both(b, b->stream);
   }
   if (e != cudaSuccess) return bcuda(b, e, "batch launch");
-  for (qk_context c : b->ctxs) context_mark_ao_valid(c);
+  for (qk_context c : b->ctxs) context_forget_ao(c);
   return QK_SUCCESS;
 }
 
@@ -359,8 +424,7 @@ qk_status qk_batch_autotune(qk_batch b, float* const* douts, int32_t reps, doubl
     st = prepare(b, douts, nullptr);
     if (st) break;
     // the AO tensors are filled once; only the contraction is timed
-    e = launch_ao_vgl_batch(b->mode == QK_BF16X3, (const AOProblem*)b->d_ao_probs.p,
-                            (const int4*)b->d_ao_items.p, b->n_ao_items, b->stream);
+    e = launch_ao_side(b, b->stream);
     for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
       if (r == 1) e = cudaEventRecord(e0, b->stream);
       if (e == cudaSuccess)

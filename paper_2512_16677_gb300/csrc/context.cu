@@ -1983,18 +1983,16 @@ qk_status context_forward_views(qk_context c, ForwardViews* v) {
   v->elec_num = c->elec_num;
   v->mode = c->mode;
   v->basis_version = c->basis_version;
+  for (int k = 0; k < 3; ++k) {
+    v->box_lo[k] = c->nbox_lo[k];
+    v->box_hi[k] = c->nbox_hi[k];
+  }
+  v->spatial = c->spatial;
   return QK_SUCCESS;
 }
 
 bool context_cusp_on(qk_context c) { return c->cusp_on; }
 
-void context_mark_ao_valid(qk_context c) {
-  c->ao_date = c->date;
-  c->ao_mode = c->mode;
-  c->ao_ws = c->ws_user ? c->ws_user : c->ws_own.p;
-  c->ao_version = c->basis_version;
-  c->ao_sorted = false;  // multi-molecule launches keep the caller's order
-  c->ao_pairs = false;   // and write no zeros for a pair contraction
-}
+void context_forget_ao(qk_context c) { c->ao_date = ~0ull; }
 
 }  // namespace qk

@@ -327,7 +327,8 @@ struct AOProblem {
   AOTensor out;  // chunked layout
 };
 // Persistent ao_vgl over a work list of int4 (problem, chunk, first tile,
-// end tile) on tiled AO tensors (kTilePoints points per tile).  split: bf16
+// tile stride): an item takes tiles first, first + stride, ... of the
+// problem's tiled AO tensor (kTilePoints points per tile).  split: bf16
 // hi/lo planes, else FP32.
 cudaError_t launch_ao_vgl_batch(bool split, const AOProblem* probs, const int4* items,
                                 int64_t n_items, cudaStream_t s);
@@ -370,6 +371,36 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
                                  PointsDev* sorted, cudaStream_t s);
 // Kernel launches launch_spatial_order makes for n points.
 int spatial_order_kernels(int64_t n);
+// Cell grid of the spatial order over a box: cell = (x - lo) * inv per axis.
+void cell_grid(const float box_lo[3], const float box_hi[3], float3* lo, float3* inv);
+// Several problems' points in one spatial order (sort.cu): the key of a
+// point is (problem << cell bits) | its cell key in its problem's own grid,
+// so each problem's points stay contiguous, problem after problem, in the
+// order of a single problem within.
+struct SortProblem {
+  PointsDev p;      // the problem's points, caller order
+  float3 lo, inv;   // its cell grid (cell_grid of its nuclear box)
+  int spatial;      // 0: the problem keeps its caller order
+};
+struct BatchOrder {
+  uint32_t* hist;
+  uint32_t* key[2];
+  int32_t* val[2];
+  PointsDev sorted;  // every problem's points in order, problem j from off[j]; ld = total
+  int32_t* perm;     // slot -> the problem's own point index
+  int64_t total;
+  int nprob, passes;
+};
+size_t spatial_order_batch_bytes(int64_t total, int nprob);
+// Pointers into `scratch` (host arithmetic only).
+BatchOrder spatial_order_batch_layout(void* scratch, int64_t total, int nprob);
+// d_probs [nprob], d_off [nprob + 1] (off[0] = 0, off[nprob] = total) in device memory.
+cudaError_t launch_spatial_order_batch(const BatchOrder& o, const SortProblem* d_probs,
+                                       const int64_t* d_off, cudaStream_t s);
+// Reach pre-pass of several tiled AO problems in one launch (problems whose
+// out.reach is NULL are skipped); max_shells: the largest shell count.
+cudaError_t launch_tile_reach_batch(const AOProblem* d_probs, int nprob, int64_t max_tiles,
+                                    int max_shells, cudaStream_t s);
 
 // MO cusp correction (cusp.cu, Sec. 3.3).
 struct CuspDev {
@@ -438,12 +469,15 @@ struct ForwardViews {
   int64_t kpad, mo_num, walk_num, elec_num;
   int mode;
   uint64_t basis_version;  // bumped by every change of nuclei, basis, cutoff or order
+  float box_lo[3], box_hi[3];  // nuclear box of the spatial point order
+  bool spatial;                // whether the context cuts its tiles from that order
 };
 qk_status context_forward_views(qk_context c, ForwardViews* v);
 // Whether the context applies the MO cusp correction.
 bool context_cusp_on(qk_context c);
-// Record that the AO tensor of the current time stamp is now in the workspace.
-void context_mark_ao_valid(qk_context c);
+// Record that the workspace's AO tensor is not the context's own any more
+// (a multi-molecule launch wrote it in its own point order).
+void context_forget_ao(qk_context c);
 qk_status context_fail(qk_context c, qk_status code, const char* msg);
 
 }  // namespace qk

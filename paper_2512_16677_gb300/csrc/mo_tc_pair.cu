@@ -655,6 +655,7 @@ cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, cons
   if (mode == QK_BF16X3) {
     switch (bn) {
       case 64: return launch_pair_bn<QK_BF16X3, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 96: return launch_pair_bn<QK_BF16X3, 96>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 128: return launch_pair_bn<QK_BF16X3, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 160: return launch_pair_bn<QK_BF16X3, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 192: return launch_pair_bn<QK_BF16X3, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
@@ -665,6 +666,7 @@ cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, cons
   if (mode == QK_TF32) {
     switch (bn) {
       case 64: return launch_pair_bn<QK_TF32, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      case 96: return launch_pair_bn<QK_TF32, 96>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 128: return launch_pair_bn<QK_TF32, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 160: return launch_pair_bn<QK_TF32, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
       case 192: return launch_pair_bn<QK_TF32, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);

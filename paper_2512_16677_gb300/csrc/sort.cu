@@ -158,6 +158,64 @@ __global__ void gather_points_kernel(PointsDev p, const int32_t* perm, double* x
   }
 }
 
+// ---- several problems in one order
+
+// The problem that global index g falls in: the largest j with off[j] <= g
+// (empty problems share their offset with the next one and are passed over).
+__device__ __forceinline__ int problem_of(const int64_t* off, int nprob, int64_t g) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void batch_cell_key_kernel(const SortProblem* probs, const int64_t* off, int nprob,
+                                      int64_t total, uint32_t* key) {
+  griddep_wait();
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int j = problem_of(off, nprob, g);
+    const SortProblem& P = probs[j];
+    const int64_t i = g - off[j];
+    uint32_t cell = 0u;
+    if (P.spatial) {
+      const uint32_t cx = cell_of(P.p.hi[i], P.lo.x, P.inv.x);
+      const uint32_t cy = cell_of(P.p.hi[P.p.ld + i], P.lo.y, P.inv.y);
+      const uint32_t cz = cell_of(P.p.hi[2 * P.p.ld + i], P.lo.z, P.inv.z);
+      cell = spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+    }
+    key[g] = ((uint32_t)j << (3 * kCellBits)) | cell;
+  }
+}
+
+// Sorted copy of every problem's points (slot s holds global point perm[s],
+// of the problem that owns slot s) and the problem-local permutation.
+__global__ void batch_gather_kernel(const SortProblem* probs, const int64_t* off, int nprob,
+                                   int64_t total, const int32_t* perm, double* x, double* y,
+                                   double* z, float* hi, float* lo, int32_t* perm_local) {
+  griddep_wait();
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int j = problem_of(off, nprob, s);
+    const PointsDev& p = probs[j].p;
+    const int64_t i = (int64_t)perm[s] - off[j];
+    x[s] = p.x[i];
+    y[s] = p.y[i];
+    z[s] = p.z[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      hi[k * total + s] = p.hi[k * p.ld + i];
+      lo[k * total + s] = p.lo[k * p.ld + i];
+    }
+    perm_local[s] = (int32_t)i;
+  }
+}
+
 unsigned grid_for(int64_t n) {
   const int64_t b = (n + 255) / 256;
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -166,6 +224,16 @@ unsigned grid_for(int64_t n) {
 int sort_blocks(int64_t n) { return (int)((n + kSortBlock - 1) / kSortBlock); }
 
 }  // namespace
+
+void cell_grid(const float box_lo[3], const float box_hi[3], float3* lo, float3* inv) {
+  const float span = (float)(1 << kCellBits);
+  lo->x = box_lo[0];
+  lo->y = box_lo[1];
+  lo->z = box_lo[2];
+  inv->x = span / fmaxf(box_hi[0] - box_lo[0], 1e-3f);
+  inv->y = span / fmaxf(box_hi[1] - box_lo[1], 1e-3f);
+  inv->z = span / fmaxf(box_hi[2] - box_lo[2], 1e-3f);
+}
 
 size_t spatial_order_bytes(int64_t n) {
   const auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -210,13 +278,7 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
   *perm_out = val[kPasses & 1];  // where the last pass leaves the values
   if (n == 0) return cudaSuccess;
   float3 lo, inv;
-  const float span = (float)(1 << kCellBits);
-  lo.x = box_lo[0];
-  lo.y = box_lo[1];
-  lo.z = box_lo[2];
-  inv.x = span / fmaxf(box_hi[0] - box_lo[0], 1e-3f);
-  inv.y = span / fmaxf(box_hi[1] - box_lo[1], 1e-3f);
-  inv.z = span / fmaxf(box_hi[2] - box_lo[2], 1e-3f);
+  cell_grid(box_lo, box_hi, &lo, &inv);
   // each kernel waits for its predecessor's results first thing
   // (programmatic dependent launches: only the launch latency overlaps)
   cudaError_t e = launch_pdl(cell_key_kernel, grid_for(n), 256, 0, s, p, lo, inv, key[0]);
@@ -235,6 +297,83 @@ cudaError_t launch_spatial_order(const PointsDev& p, const float box_lo[3],
   if (e == cudaSuccess)
     e = launch_pdl(gather_points_kernel, grid_for(n), 256, 0, s, p, (const int32_t*)*perm_out, x,
                    x + n, x + 2 * n, hi, hi + 3 * n);
+  return e;
+}
+
+namespace {
+int problem_bits(int nprob) {
+  int b = 0;
+  while (b < 31 && ((int64_t)1 << b) < nprob) ++b;
+  return b;
+}
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+size_t spatial_order_batch_bytes(int64_t total, int nprob) {
+  (void)nprob;
+  return al256(sizeof(uint32_t) * (size_t)kBins * sort_blocks(total)) +
+         2 * al256(sizeof(uint32_t) * total) + 3 * al256(sizeof(int32_t) * total) +
+         al256(3 * sizeof(double) * total) + al256(6 * sizeof(float) * total);
+}
+
+BatchOrder spatial_order_batch_layout(void* scratch, int64_t total, int nprob) {
+  BatchOrder o{};
+  unsigned char* w = (unsigned char*)scratch;
+  o.hist = (uint32_t*)w;
+  w += al256(sizeof(uint32_t) * (size_t)kBins * sort_blocks(total));
+  for (int k = 0; k < 2; ++k) {
+    o.key[k] = (uint32_t*)w;
+    w += al256(sizeof(uint32_t) * total);
+  }
+  for (int k = 0; k < 2; ++k) {
+    o.val[k] = (int32_t*)w;
+    w += al256(sizeof(int32_t) * total);
+  }
+  o.perm = (int32_t*)w;
+  w += al256(sizeof(int32_t) * total);
+  double* x = (double*)w;
+  w += al256(3 * sizeof(double) * total);
+  float* hi = (float*)w;
+  o.sorted.n = total;
+  o.sorted.x = x;
+  o.sorted.y = x + total;
+  o.sorted.z = x + 2 * total;
+  o.sorted.hi = hi;
+  o.sorted.lo = hi + 3 * total;
+  o.sorted.ld = total;
+  o.total = total;
+  o.nprob = nprob;
+  const int bits = 3 * kCellBits + problem_bits(nprob);
+  o.passes = (bits + kDigitBits - 1) / kDigitBits;
+  return o;
+}
+
+cudaError_t launch_spatial_order_batch(const BatchOrder& o, const SortProblem* d_probs,
+                                       const int64_t* d_off, cudaStream_t s) {
+  const int64_t n = o.total;
+  if (n == 0) return cudaSuccess;
+  if (3 * kCellBits + problem_bits(o.nprob) > 32) return cudaErrorInvalidValue;
+  const int nb = sort_blocks(n);
+  cudaError_t e = launch_pdl(batch_cell_key_kernel, grid_for(n), 256, 0, s, d_probs, d_off,
+                             o.nprob, n, o.key[0]);
+  for (int pass = 0; pass < o.passes && e == cudaSuccess; ++pass) {
+    const int in = pass & 1, out = in ^ 1;
+    e = launch_pdl(digit_count_kernel, nb, kSortThreads, 0, s, (const uint32_t*)o.key[in], n,
+                   kDigitBits * pass, nb, o.hist);
+    if (e == cudaSuccess)
+      e = launch_pdl(exclusive_scan_kernel, 1, kScanThreads, 0, s, o.hist, (int64_t)kBins * nb);
+    if (e == cudaSuccess)
+      e = launch_pdl(digit_scatter_kernel, nb, kSortThreads, 0, s, (const uint32_t*)o.key[in],
+                     (const int32_t*)(pass == 0 ? nullptr : o.val[in]), o.key[out], o.val[out], n,
+                     kDigitBits * pass, nb, (const uint32_t*)o.hist);
+  }
+  if (e == cudaSuccess) {
+    double* x = const_cast<double*>(o.sorted.x);
+    float* hi = const_cast<float*>(o.sorted.hi);
+    e = launch_pdl(batch_gather_kernel, grid_for(n), 256, 0, s, d_probs, d_off, o.nprob, n,
+                   (const int32_t*)o.val[o.passes & 1], x, x + n, x + 2 * n, hi, hi + 3 * n,
+                   o.perm);
+  }
   return e;
 }
 

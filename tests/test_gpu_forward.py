@@ -417,3 +417,38 @@ def test_sm_pairs_same_values_as_single_sm(orc, cfg, mode):
     assert_within(mode, outs[True], ref, size, "organic pairs")
     diff = np.abs(outs[True] - outs[False]) / (size + 1e-300)
     assert float(diff.max()) <= 1e-6, float(diff.max())
+
+
+_WIDTH_REF = {}
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("mo_num", [40, 72, 120, 150, 180, 250])
+def test_sm_pairs_every_tile_width(orc, cfg, mode, mo_num):
+    """Every MMA N the contraction picks for up to 256 MOs (64, 96, 128,
+    160, 192, 256: one N tile) on pairs of SMs: the first mo_num MOs of the
+    organic chain on 47 tiles, against the oracle and the single-SM kernel."""
+    import dataclasses
+
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(2, walk_num=2)
+    mm = m.with_points(m.points[:47 * 25 - 3])
+    if "full" not in _WIDTH_REF:
+        _WIDTH_REF["full"] = orc.mo_vgl(mm)
+    ref_full, size_full = _WIDTH_REF["full"]
+    mk = dataclasses.replace(mm, mo_coef=np.ascontiguousarray(mm.mo_coef[:mo_num]))
+    ref, size = ref_full[..., :mo_num], size_full[..., :mo_num]
+    outs = {}
+    for pairs in (True, False):
+        c = qmckl.Context(mode)
+        c.set_molecule(mk)
+        c.set_sm_pairs(pairs)
+        c.set_points_device(torch.from_numpy(mk.coord).cuda())
+        out = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        c.synchronize()
+        outs[pairs] = out.double().cpu().numpy().reshape(-1, 5, mo_num)
+        c.close()
+    assert_within(mode, outs[True], ref, size, f"pairs, {mo_num} MOs")
+    diff = np.abs(outs[True] - outs[False]) / (size + 1e-300)
+    assert float(diff.max()) <= 1e-6, float(diff.max())
