@@ -138,6 +138,10 @@ struct qk_context_s {
   uint64_t mo_version = 0;  // bumped by every upload of C
   DevBuf d_ct;              // C^T bf16 hi/lo planes for the split-bf16 adjoint
   uint64_t ct_version = ~0ull;
+  // C blocked for the pair contraction (per upload of C, tile width and mode)
+  DevBuf d_cpair;
+  uint64_t cpair_version = ~0ull;
+  int cpair_bn = 0, cpair_mode = -1;
   std::vector<cudaEvent_t> range_done;  // one per output range of a host call
   DevBuf d_flag;
   DevBuf bwd_own;
@@ -758,10 +762,21 @@ qk_status contract(qk_context c, const AOTensor& ao, int64_t M, void* dout) {
       const void* b_hi = split ? (const void*)c->c_hi : (const void*)c->c32p;
       const void* b_lo = split ? (const void*)c->c_lo : nullptr;
       const TcConfig cfg = tc_default_config(c->mode, N);
-      if (ao.pair_zero && cfg.bn >= 64 && cfg.bn % 32 == 0)
-        e = launch_mo_tc_pair(c->mode, ao, KP, b_hi, b_lo, KP, N, (float*)dout, cfg.bn,
+      if (ao.pair_zero && cfg.bn >= 64 && cfg.bn % 32 == 0) {
+        // C blocked for the pair kernel, once per upload of C and tile width
+        if (c->cpair_version != c->mo_version || c->cpair_bn != cfg.bn ||
+            c->cpair_mode != c->mode) {
+          e = c->d_cpair.ensure(pair_c_bytes(c->mode, N, KP, cfg.bn));
+          if (e == cudaSuccess)
+            e = launch_pair_c(c->mode, b_hi, b_lo, KP, N, KP, cfg.bn, c->d_cpair.p, c->stream);
+          if (e != cudaSuccess) return cuda_fail(c, e, "blocked C");
+          c->cpair_version = c->mo_version;
+          c->cpair_bn = cfg.bn;
+          c->cpair_mode = c->mode;
+        }
+        e = launch_mo_tc_pair(c->mode, ao, KP, c->d_cpair.p, N, (float*)dout, cfg.bn,
                               (int*)c->d_flag.p, c->stream, M);
-      else
+      } else
         e = launch_mo_tc(c->mode, ao, KP, b_hi, b_lo, KP, N, (float*)dout, cfg,
                          (int*)c->d_flag.p, c->stream, M);
     }

@@ -290,11 +290,19 @@ cudaError_t launch_mo_sparse64(const AOTensor& ao, const double* C, int64_t ldc,
 // Default tile configuration for a problem shape.
 TcConfig tc_default_config(int mode, int64_t mo_num);
 // The same contraction on pairs of SMs (mo_tc_pair.cu): tiled vgl AO tensors
-// only (25 points per tile, written with pair_zero), MMA N = bn (64, 128,
-// 160, 192 or 256) per pair of tiles; D[out_rows][mo] float.
-cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
-                              const void* c_lo, int64_t ldc, int64_t mo_num, float* out, int bn,
-                              int* err_flag, cudaStream_t s, int64_t out_rows);
+// only (25 points per tile, written with pair_zero), MMA N = bn (64, 96,
+// 128, 160, 192 or 256) per pair of tiles; D[out_rows][mo] float.  C comes
+// blocked (launch_pair_c): for each half h of an N tile (the rows one CTA
+// of the pair multiplies, bn / 2 of them, zero-padded) and each K block, a
+// contiguous [planes][bn / 2][128 bytes] block, so that each stage's C
+// copy is one contiguous box.
+size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn);
+// c_hi / c_lo: [mo][ldc] bf16 planes (QK_BF16X3) or c_hi [mo][ldc] FP32 (QK_TF32).
+cudaError_t launch_pair_c(int mode, const void* c_hi, const void* c_lo, int64_t ldc,
+                          int64_t mo_num, int64_t ao_num, int bn, void* c_blk, cudaStream_t s);
+cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_blk,
+                              int64_t mo_num, float* out, int bn, int* err_flag, cudaStream_t s,
+                              int64_t out_rows);
 
 // One contraction problem of a multi-problem launch (device-resident; the
 // tensor maps, 64-byte aligned by their type, are written by the host

@@ -33,6 +33,8 @@
 // the caller's error word and raises the CTA's abort flag.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "tc_common.cuh"
 
 namespace qk {
@@ -76,8 +78,7 @@ constexpr int stages_for_pair(int mode, int bn) {
 template <int BN>
 struct PairSched {
   CUtensorMap a;       // blocked AO tensor: 3-D map over its column slices (one box = one K block)
-  CUtensorMap b;       // C, box BN / 2 rows
-  CUtensorMap b_last;  // C, box last_bn / 2 rows (last N tile, when last_bn < BN)
+  CUtensorMap b;       // blocked C: 3-D map over its [BN / 2][128-byte] slices (box = one block)
   int last_bn;
   float* D;
   const uint8_t* mask;  // [m tiles][mask_ld(nchunk)]
@@ -252,12 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // groups (bits 4-7).
     const bool a_warp = warp == 4;
     if (lane == 0) {
-      if (a_warp) {
-        tma_prefetch_map(&sc.a);
-      } else {
-        tma_prefetch_map(&sc.b);
-        if (sc.last_bn != BN) tma_prefetch_map(&sc.b_last);
-      }
+      tma_prefetch_map(a_warp ? &sc.a : &sc.b);
     }
     auto load_groups = [&](int64_t p, uint32_t (&g)[kMaxWin]) {
       const int mp = (int)(p / sc.n_tiles);
@@ -289,7 +285,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int mt_own = 2 * mp + (int)rank;
       const bool last_n = nt == sc.n_tiles - 1 && sc.last_bn != BN;
       const int bn = last_n ? sc.last_bn : BN;
-      const CUtensorMap* bmap = last_n ? &sc.b_last : &sc.b;
       // the pair-tile's last live K block (-1: none)
       int lastkb = -1;
 #pragma unroll
@@ -302,7 +297,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (lastkb >= sc.num_kb) lastkb = sc.num_kb - 1;
-      const uint32_t cta_bytes = TR::kPlanes * (S::A_BYTES + (uint32_t)(bn / 2) * kRowBytes);
+      // a C block is always BN / 2 rows (the last N tile's are zero-padded)
+      const uint32_t cta_bytes = S::STAGE_BYTES;
       const uint32_t bn_bits = (uint32_t)(bn >> 4) << kStageBnShift;
       uint32_t flags = kStageFirst;
       auto stage = [&](int kb, uint32_t steps, bool own_live, bool last) -> bool {
@@ -332,11 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int z = own_live ? blocked_slice<MODE>(mt_own, kb, sc.nchunk) : sc.zero_slice;
             tma_load_3d_pair(dst, &sc.a, bar, 0, 0, z);
           } else {
-            const int row = (int)(nt * BN + (int)rank * (bn / 2));
-            if constexpr (TR::kPlanes == 2)
-              tma_load_3d_pair(dst, bmap, bar, kb * TR::kBK, row, 0);
-            else
-              tma_load_2d_pair(dst, bmap, bar, kb * TR::kBK, row);
+            const int z = ((2 * nt + (int)rank) * sc.num_kb + kb) * TR::kPlanes;
+            tma_load_3d_pair(dst, &sc.b, bar, 0, 0, z);
           }
         }
         return true;
@@ -391,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t my_tiles =
         total > cluster ? (total - 1 - cluster) / nclusters + 1 : 0;
     const uint64_t d0 = sw128_desc(base);
-    uint32_t it = 0, i = 0, b = 0, dacc = tmem, idesc = 0, bhalf = 0;
+    uint32_t it = 0, i = 0, b = 0, dacc = tmem, idesc = 0;
     bool first = true, in_tile = false, ok = true;
     while ((int64_t)i < my_tiles) {
       const int s = it % STAGES;
@@ -414,14 +407,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         dacc = tmem + b * ACC;
         const int bn = (int)((info >> kStageBnShift) << 4);
         idesc = make_idesc(TR::kFmt, 2 * kBM, bn);
-        bhalf = (uint32_t)(bn / 2);
         first = true;
       }
       tc_fence_after();
       const uint64_t da = d0 + ((uint64_t)(s * S::STAGE_BYTES) >> 4);
       const uint64_t da_lo = da + (S::A_BYTES >> 4);
       const uint64_t db = da + ((TR::kPlanes * S::A_BYTES) >> 4);
-      const uint64_t db_lo = db + ((bhalf * kRowBytes) >> 4);
+      // the C block's lo plane follows BN / 2 rows of hi (padded on the last N tile)
+      const uint64_t db_lo = db + (((uint32_t)(BN / 2) * kRowBytes) >> 4);
 #pragma unroll
       for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
         if (!((info >> kk) & 1u)) continue;
@@ -579,35 +572,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int MODE, int BN>
-cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, const void* c_lo,
-                           int64_t ldc, int64_t N, float* out, int64_t out_rows, int* err_flag,
-                           cudaStream_t s) {
+cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_blk, int64_t N, float* out,
+                           int64_t out_rows, int* err_flag, cudaStream_t s) {
   constexpr int ST = stages_for_pair(MODE, BN);
   using S = PairShape<MODE, BN, ST>;
   using TR = TcTraits<MODE>;
-  const bool f32 = MODE == QK_TF32;
   const int64_t M = ao.rows;
   if (M == 0 || N == 0) return cudaSuccess;
   if (M > INT32_MAX / 2 || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
   if (!ao.tiled || !ao.blocked || M % kBM != 0 || ao.comps == 1) return cudaErrorInvalidValue;
-  if (K > (int64_t)ao.nchunk * kChunkAO) return cudaErrorInvalidValue;
+  if (K > (int64_t)ao.nchunk * kChunkAO || K % kChunkAO != 0) return cudaErrorInvalidValue;
   PairSched<BN> sc;
   const int64_t n_tiles = (N + BN - 1) / BN;
   // the last N tile multiplies only the MOs it has, rounded up to 16 (halves
   // of whole 8-row groups)
   sc.last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
   const int64_t nblocks = M / kBM * ao.nchunk;
-  if (2 * nblocks + 2 > INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t num_kb = K / TR::kBK;
+  if (2 * nblocks + 2 > INT32_MAX || 2 * n_tiles * num_kb * TR::kPlanes > INT32_MAX)
+    return cudaErrorInvalidValue;
   if (!make_map_blocked(&sc.a, ao.a, TR::kPlanes == 2, nblocks)) return cudaErrorInvalidValue;
-  if (TR::kPlanes == 2) {
-    if (!make_map_planes(&sc.b, c_hi, c_lo, K, N, ldc, TR::kBK, BN / 2))
-      return cudaErrorInvalidValue;
-    if (sc.last_bn != BN &&
-        !make_map_planes(&sc.b_last, c_hi, c_lo, K, N, ldc, TR::kBK, sc.last_bn / 2))
-      return cudaErrorInvalidValue;
-  } else {
-    if (!make_map(&sc.b, c_hi, f32, K, N, ldc, TR::kBK, BN / 2)) return cudaErrorInvalidValue;
-    if (sc.last_bn != BN && !make_map(&sc.b_last, c_hi, f32, K, N, ldc, TR::kBK, sc.last_bn / 2))
+  {
+    // blocked C: slices of BN / 2 rows x 128 bytes, box = the planes of one block
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    const cuuint64_t w = 128 / (TR::kPlanes == 2 ? 2 : 4);
+    cuuint64_t dims[3] = {w, (cuuint64_t)(BN / 2), (cuuint64_t)(2 * n_tiles * num_kb * TR::kPlanes)};
+    cuuint64_t strides[2] = {128, (cuuint64_t)(BN / 2) * 128};
+    cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)(BN / 2), (cuuint32_t)TR::kPlanes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&sc.b,
+            TR::kPlanes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+            3, const_cast<void*>(c_blk), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   sc.D = out;
@@ -618,7 +616,7 @@ cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, cons
   sc.zero_slice = (int)(2 * nblocks);
   sc.m_tiles = (int)(M / kBM);
   sc.n_tiles = (int)n_tiles;
-  sc.num_kb = (int)((K + TR::kBK - 1) / TR::kBK);
+  sc.num_kb = (int)num_kb;
   sc.nchunk = ao.nchunk;
   sc.total = ((sc.m_tiles + 1) / 2) * n_tiles;
   auto kern = mo_tc_pair_kernel<MODE, BN, ST>;
@@ -647,33 +645,99 @@ cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_hi, cons
   return cudaLaunchKernelEx(&cfg, kern, sc, err_flag);
 }
 
+// Blocked C of one (half, K block): [planes][BN / 2][w] with w = 128 bytes of
+// elements; half h = 2 nt + r holds rows nt BN + r bn_t / 2 .. + bn_t / 2 of
+// C (bn_t the tile's MMA N), zeros past them and past the last MO.
+template <typename E>
+__global__ void pair_c_kernel(const E* c_hi, const E* c_lo, int64_t ldc, int64_t N, int bn,
+                              int last_bn, int64_t n_tiles, int64_t num_kb, int planes,
+                              E* out) {
+  constexpr int w = 128 / (int)sizeof(E);
+  const int hb = bn / 2;
+  const int64_t total = 2 * n_tiles * num_kb * planes * hb * w;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % w);
+    int64_t t = i / w;
+    const int r = (int)(t % hb);
+    t /= hb;
+    const int p = (int)(t % planes);
+    t /= planes;
+    const int64_t kb = t % num_kb;
+    const int64_t h = t / num_kb;
+    const int64_t nt = h / 2;
+    const int bnt = nt == n_tiles - 1 ? last_bn : bn;
+    const int64_t row = nt * bn + (h & 1) * (bnt / 2) + r;
+    E v = E(0.0f);
+    if (r < bnt / 2 && row < N) v = (p ? c_lo : c_hi)[row * ldc + kb * w + c];
+    out[i] = v;
+  }
+}
+
+int pair_last_bn(int64_t N, int bn) {
+  const int64_t n_tiles = (N + bn - 1) / bn;
+  return (int)((N - (n_tiles - 1) * bn + 15) / 16 * 16);
+}
+
 }  // namespace
 
-cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_hi,
-                              const void* c_lo, int64_t ldc, int64_t mo_num, float* out, int bn,
-                              int* err_flag, cudaStream_t s, int64_t out_rows) {
+size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn) {
+  const int64_t n_tiles = (mo_num + bn - 1) / bn;
+  const int64_t kb = mode == QK_TF32 ? ao_num / 32 : ao_num / 64;
+  const int planes = mode == QK_BF16X3 ? 2 : 1;
+  return (size_t)(2 * n_tiles * kb * planes) * (size_t)(bn / 2) * 128;
+}
+
+cudaError_t launch_pair_c(int mode, const void* c_hi, const void* c_lo, int64_t ldc,
+                          int64_t mo_num, int64_t ao_num, int bn, void* c_blk, cudaStream_t s) {
+  if (bn % 16 != 0 || bn < 32 || bn > 256 || ao_num % kChunkAO != 0) return cudaErrorInvalidValue;
+  const int64_t n_tiles = (mo_num + bn - 1) / bn;
+  const int last_bn = pair_last_bn(mo_num, bn);
+  const int64_t elems = (int64_t)pair_c_bytes(mode, mo_num, ao_num, bn) / (mode == QK_TF32 ? 4 : 2);
+  const unsigned grid = (unsigned)std::min<int64_t>((elems + 255) / 256, 4096);
+  if (elems == 0) return cudaSuccess;
+  if (mode == QK_BF16X3) {
+    pair_c_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
+        (const __nv_bfloat16*)c_hi, (const __nv_bfloat16*)c_lo, ldc, mo_num, bn, last_bn, n_tiles,
+        ao_num / 64, 2, (__nv_bfloat16*)c_blk);
+  } else if (mode == QK_TF32) {
+    pair_c_kernel<float><<<grid, 256, 0, s>>>((const float*)c_hi, nullptr, ldc, mo_num, bn,
+                                              last_bn, n_tiles, ao_num / 32, 1, (float*)c_blk);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_blk,
+                              int64_t mo_num, float* out, int bn, int* err_flag, cudaStream_t s,
+                              int64_t out_rows) {
+#define QK_PAIR_CASE(M_, B_)                                                                   \
+  case B_:                                                                                     \
+    return launch_pair_bn<M_, B_>(ao, ao_num, c_blk, mo_num, out, out_rows, err_flag, s);
   if (mode == QK_BF16X3) {
     switch (bn) {
-      case 64: return launch_pair_bn<QK_BF16X3, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 96: return launch_pair_bn<QK_BF16X3, 96>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 128: return launch_pair_bn<QK_BF16X3, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 160: return launch_pair_bn<QK_BF16X3, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 192: return launch_pair_bn<QK_BF16X3, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 256: return launch_pair_bn<QK_BF16X3, 256>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      QK_PAIR_CASE(QK_BF16X3, 64)
+      QK_PAIR_CASE(QK_BF16X3, 96)
+      QK_PAIR_CASE(QK_BF16X3, 128)
+      QK_PAIR_CASE(QK_BF16X3, 160)
+      QK_PAIR_CASE(QK_BF16X3, 192)
+      QK_PAIR_CASE(QK_BF16X3, 256)
       default: return cudaErrorInvalidValue;
     }
   }
   if (mode == QK_TF32) {
     switch (bn) {
-      case 64: return launch_pair_bn<QK_TF32, 64>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 96: return launch_pair_bn<QK_TF32, 96>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 128: return launch_pair_bn<QK_TF32, 128>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 160: return launch_pair_bn<QK_TF32, 160>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 192: return launch_pair_bn<QK_TF32, 192>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
-      case 256: return launch_pair_bn<QK_TF32, 256>(ao, ao_num, c_hi, c_lo, ldc, mo_num, out, out_rows, err_flag, s);
+      QK_PAIR_CASE(QK_TF32, 64)
+      QK_PAIR_CASE(QK_TF32, 96)
+      QK_PAIR_CASE(QK_TF32, 128)
+      QK_PAIR_CASE(QK_TF32, 160)
+      QK_PAIR_CASE(QK_TF32, 192)
+      QK_PAIR_CASE(QK_TF32, 256)
       default: return cudaErrorInvalidValue;
     }
   }
+#undef QK_PAIR_CASE
   return cudaErrorInvalidValue;
 }
 
