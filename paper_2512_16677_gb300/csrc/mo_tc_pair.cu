@@ -60,16 +60,16 @@ struct PairShape {
   static constexpr int NBUF = 512 / ACC > 4 ? 4 : (int)(512 / ACC);
   static constexpr uint32_t TMEM_ALLOC = tmem_cols<NBUF * ACC>();
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2 * NBUF);
-  static_assert(SMEM + kEpiBytes + 64 <= kSmemLimit, "shared memory budget");
+  static_assert(SMEM + kEpiBytes + 512 <= kSmemLimit, "shared memory budget");
   static_assert(BN % 16 == 0, "MMA N: multiple of 16 (halves of whole 8-row groups)");
   static_assert(BN >= 32 && BN <= 256, "MMA N of a pair: 32..256");
 };
 
 constexpr int stages_for_pair(int mode, int bn) {
-  return (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+  return (int)((kSmemLimit - kEpiBytes - 1024 - 1024) /
                ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn / 2) * kRowBytes)) > 8
              ? 8
-             : (int)((kSmemLimit - kEpiBytes - 1024 - 512) /
+             : (int)((kSmemLimit - kEpiBytes - 1024 - 1024) /
                      ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn / 2) * kRowBytes));
 }
 
@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ uint32_t stage_info[STAGES];
+  __shared__ uint16_t elist[2][64];  // producers' stage lists (one 32-chunk window each)
   __shared__ __align__(16) float epi[4][32][32];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -247,10 +248,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // and the stage's byte count), warp 6 the C blocks: the copies one thread
     // issues complete one after another, so the two operands of a stage come
     // from two warps.  All four producers of a pair walk the same stage
-    // sequence: the union of the pair's live K blocks.  The two mask rows of a pair-tile are read one
-    // pair-tile ahead, a byte per lane and 32-chunk window, and kept in
-    // registers: per chunk the union groups (bits 0-3) and this CTA's own
-    // groups (bits 4-7).
+    // sequence: the union of the pair's live K blocks.  The two mask rows of
+    // a pair-tile are read one pair-tile ahead, a byte per lane and 32-chunk
+    // window, and kept in registers: per chunk the union groups (bits 0-3)
+    // and this CTA's own groups (bits 4-7).
     const bool a_warp = warp == 4;
     if (lane == 0) {
       tma_prefetch_map(a_warp ? &sc.a : &sc.b);
@@ -271,9 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         g[w] = (o | r) | (o << 4);
       }
     };
+    // The stages of one 32-chunk window as a list in shared memory (built by
+    // the whole warp), walked by lane 0 alone: the per-stage work of a
+    // producer is then a wait, a word and a copy, with no warp-wide step.
+    // Entry: K block (bits 0-9), its live k-steps (bits 10-13), the block
+    // live in this CTA's own tile (bit 14); never 0.
+    uint16_t* list = elist[a_warp ? 0 : 1];
     uint32_t gnext[kMaxWin];
     if (cluster < total) load_groups(cluster, gnext);
-    uint32_t it = 0;
+    uint32_t it = 0;  // stages taken (lane 0)
     bool ok = true;
     for (int64_t p = cluster; p < total && ok; p += nclusters) {
       uint32_t gcur[kMaxWin];
@@ -301,24 +308,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t cta_bytes = S::STAGE_BYTES;
       const uint32_t bn_bits = (uint32_t)(bn >> 4) << kStageBnShift;
       uint32_t flags = kStageFirst;
-      auto stage = [&](int kb, uint32_t steps, bool own_live, bool last) -> bool {
+      // one stage (lane 0): wait for the slot, post the stage word (leader's
+      // AO producer), issue this CTA's copy of the operand
+      auto stage = [&](int kb, uint32_t steps, bool own_live) -> bool {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         ++it;
-        bool got = true;
-        if (lane == 0) got = mbar_wait(empty_bar(s), ph ^ 1u, abort_v);
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) {
-          if (lane == 0) flag_error(err_flag, abort_v, 1);
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
+          flag_error(err_flag, abort_v, 1);
           return false;
         }
-        if (a_warp && leader && lane == 0) {
-          stage_info[s] = steps | flags | bn_bits | (last ? kStageLast : 0u);
+        if (a_warp && leader) {
+          stage_info[s] = steps | flags | bn_bits | (kb == lastkb ? kStageLast : 0u);
           mbar_expect_tx(full_bar(s), kb >= 0 ? 2u * cta_bytes : 0u);
         }
         flags = 0;
-        __syncwarp();
-        if (kb >= 0 && lane == 0) {
+        if (kb >= 0) {
           const uint32_t bar = map_to_rank(full_bar(s), 0);  // the leader's full[s]
           const uint32_t dst = base + s * S::STAGE_BYTES + (a_warp ? 0u : TR::kPlanes * S::A_BYTES);
           // own AO block (one contiguous box), or zeros from past the
@@ -335,38 +340,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         return true;
       };
       if (lastkb < 0) {
-        ok = stage(-1, 0u, false, true);
+        if (lane == 0) ok = stage(-1, 0u, false);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
         continue;
       }
 #pragma unroll 1
       for (int w = 0; w < nwin && ok; ++w) {
         const uint32_t g = pick_window(gcur, w);
-        unsigned live = __ballot_sync(0xffffffffu, (g & 0xFu) != 0u);
-        while (live && ok) {
-          const int j = __ffs(live) - 1;
-          live &= live - 1u;
-          const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
-          const bool own_live = (gj >> 4) != 0u;
-          if constexpr (kPer == 1) {
-            // the next live chunk's AO block of this tile into L2 now, so
-            // that its copy into the ring (a stage later) does not wait on HBM
-            const int jn = live ? __ffs(live) - 1 : 0;
-            const uint32_t gn = __shfl_sync(0xffffffffu, g, jn);
-            if (a_warp && live && lane == 2 && (gn >> 4) != 0u)
-              tma_prefetch_l2_3d(&sc.a, 0, 0, blocked_slice<MODE>(mt_own, 32 * w + jn, sc.nchunk));
-          }
+        const int q = 32 * w + lane;
+        const uint32_t own = (g >> 4) != 0u ? 1u << 14 : 0u;
+        uint32_t e[2] = {0u, 0u};
 #pragma unroll
-          for (int h = 0; h < kPer; ++h) {
-            uint32_t steps = gj & 0xFu;
-            if constexpr (kPer == 2) {
-              const uint32_t hh = (gj >> (2 * h)) & 3u;
-              steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+        for (int h = 0; h < kPer; ++h) {
+          uint32_t steps = g & 0xFu;
+          if constexpr (kPer == 2) {
+            const uint32_t hh = (g >> (2 * h)) & 3u;
+            steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+          }
+          const int kb = q * kPer + h;
+          if (steps && kb < sc.num_kb) e[h] = (uint32_t)kb | (steps << 10) | own;
+        }
+        const unsigned b0 = __ballot_sync(0xffffffffu, e[0] != 0u);
+        const unsigned b1 = __ballot_sync(0xffffffffu, e[1] != 0u);
+        const unsigned lt = (1u << lane) - 1u;
+        const int pos = __popc(b0 & lt) + __popc(b1 & lt);
+        if (e[0]) list[pos] = (uint16_t)e[0];
+        if (e[1]) list[pos + (e[0] ? 1 : 0)] = (uint16_t)e[1];
+        const int n_e = __popc(b0) + __popc(b1);
+        __syncwarp();
+        if (lane == 0) {
+          for (int k = 0; k < n_e && ok; ++k) {
+            const uint32_t v = list[k];
+            if constexpr (kPer == 1) {
+              // the next entry's own AO block into L2 now, so that its copy
+              // into the ring (a stage later) does not wait on HBM
+              if (a_warp && k + 1 < n_e) {
+                const uint32_t vn = list[k + 1];
+                if (vn & (1u << 14))
+                  tma_prefetch_l2_3d(&sc.a, 0, 0,
+                                     blocked_slice<MODE>(mt_own, (int)(vn & 0x3FFu), sc.nchunk));
+              }
             }
-            const int kb = (32 * w + j) * kPer + h;
-            if (!steps || !ok || kb >= sc.num_kb) continue;
-            ok = stage(kb, steps, own_live, kb == lastkb);
+            ok = stage((int)(v & 0x3FFu), (v >> 10) & 0xFu, (v >> 14) & 1u);
           }
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);  // also: the list may be rewritten
       }
     }
     if (a_warp && leader && lane == 0 && *abort_v) {
