@@ -369,6 +369,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n_e = __popc(b0) + __popc(b1);
         __syncwarp();
         if (lane == 0) {
+          if constexpr (kPer == 1) {
+            // the window's first own AO block into L2 as soon as the list is known
+            if (a_warp && n_e > 0 && (list[0] & (1u << 14)))
+              tma_prefetch_l2_3d(&sc.a, 0, 0,
+                                 blocked_slice<MODE>(mt_own, (int)(list[0] & 0x3FFu), sc.nchunk));
+          }
           for (int k = 0; k < n_e && ok; ++k) {
             const uint32_t v = list[k];
             if constexpr (kPer == 1) {
