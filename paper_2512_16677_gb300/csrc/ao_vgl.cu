@@ -441,8 +441,7 @@ cudaError_t launch_ao_batch(const AOProblem* probs, const int4* items, int64_t n
   if (n_items == 0) return cudaSuccess;
   const int occ = f.occ < 1 ? 1 : f.occ, sms = f.sms;
   const int64_t grid = n_items < (int64_t)sms * occ ? n_items : (int64_t)sms * occ;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(probs, items, n_items);
-  return cudaGetLastError();
+  return launch_pdl(kern, (unsigned)grid, kThreads, smem, s, probs, items, n_items);
 }
 
 }  // namespace

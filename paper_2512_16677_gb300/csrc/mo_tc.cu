@@ -702,8 +702,7 @@ cudaError_t launch_batch_bn(const TcProblem* probs, const int4* items, int64_t n
   cudaError_t e = persistent_grid<mo_tc_kernel<MODE, BN_MAX, ST, BatchSched>>(
       S::SMEM, S::TMEM_ALLOC, n_items, &grid);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)grid, kThreads, S::SMEM, s>>>(sc, err_flag);
-  return cudaGetLastError();
+  return launch_pdl(kern, (unsigned)grid, kThreads, S::SMEM, s, sc, err_flag);
 }
 
 template <int MODE>
