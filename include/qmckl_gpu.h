@@ -428,9 +428,17 @@ qk_status qk_batch_set_stream(qk_batch b, void* stream);
    replay it; 0: plain launches. */
 qk_status qk_batch_set_graph(qk_batch b, int32_t enable);
 
+/* 1 (default): the batch's contraction multiplies pairs of point tiles on
+   pairs of SMs (tcgen05.mma.cta_group::2), as qk_set_sm_pairs does for one
+   context; 0: one tile per SM.  Both give the same values.  Takes effect at
+   the next run (descriptors and graph are rebuilt).  Sec. 3.2's one-GEMM
+   contraction; the pairing is a GPU execution choice with no counterpart
+   in the paper. */
+qk_status qk_batch_set_sm_pairs(qk_batch b, int32_t enable);
+
 /* Largest MMA N of the contraction (64, 96, 128, 160, 192 or 256; default
    160).  Each molecule uses the smallest multiple of 16 that covers its MOs
-   in the fewest N tiles under this bound. */
+   in the fewest N tiles under this bound (at least 32 on pairs of SMs). */
 qk_status qk_batch_set_tile(qk_batch b, int32_t bn_max);
 qk_status qk_batch_get_tile(qk_batch b, int32_t* bn_max);
 

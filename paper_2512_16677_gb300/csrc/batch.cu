@@ -6,7 +6,8 @@
 // molecules: a spatial order of every molecule's points in one radix sort
 // (problem index above the cell key), the tiles' reach pre-pass, ao_vgl
 // over a work list of (molecule, AO chunk, point tiles) items, then the
-// tcgen05 contraction over (molecule, M tile, N tile) items, the two lists
+// tcgen05 contraction over (molecule, M-tile pair, N tile) items on pairs of
+// SMs (or (molecule, M tile, N tile) on single SMs), the two lists
 // ordered longest first (LPT) so that the largest pieces start early and
 // the tail is made of small ones.  The launches are captured once in a CUDA
 // graph and replayed on later runs; the work lists
@@ -35,6 +36,11 @@ struct qk_batch_s {
   int64_t n_ao_items = 0, n_tc_items = 0;
   // the spatial order of all molecules' points
   DevBuf d_sort, d_sort_probs, d_off;
+  // contraction on pairs of SMs: per molecule C blocked with halves of
+  // bn_max / 2 rows, and the pair problem descriptors
+  bool sm_pairs = true;
+  std::vector<DevBuf> d_cpair;
+  DevBuf d_pair_probs;
   BatchOrder order{};
   int64_t max_tiles = 0;
   int max_shells = 0;
@@ -125,6 +131,8 @@ qk_status build(qk_batch b, float* const* outs) {
   b->max_shells = 0;
   std::vector<AOProblem> aop(n);
   std::vector<TcProblem> tcp(n);
+  std::vector<PairProblem> pp(b->sm_pairs ? n : 0);
+  if (b->sm_pairs) b->d_cpair.resize(n);
   std::vector<int4> ao_items, tc_items;
   std::vector<double> ao_cost, tc_cost;
   for (int i = 0; i < n; ++i) {
@@ -142,12 +150,27 @@ qk_status build(qk_batch b, float* const* outs) {
     aop[i].b = v.b;
     aop[i].p = ps;
     aop[i].out = v.ao;
+    // pairs multiply tiles 2i and 2i + 1 over the union of their live
+    // groups: ao_vgl writes zeros into the groups the partner may light
+    aop[i].out.pair_zero = b->sm_pairs;
     b->max_tiles = std::max<int64_t>(b->max_tiles, (v.p.n + kTilePoints - 1) / kTilePoints);
     b->max_shells = std::max(b->max_shells, v.b.shell_num);
-    const int bn = pick_bn(v.mo_num, b->bn_max);
-    if (!tc_make_problem(b->mode, v.ao, v.kpad, v.c_hi, v.c_lo, v.kpad, v.mo_num, outs[i], bn,
-                         5 * v.p.n, &tcp[i]))
+    int bn = pick_bn(v.mo_num, b->bn_max);
+    if (b->sm_pairs) {
+      bn = std::max(bn, 32);  // the pair kernel's smallest MMA N
+      const int half = b->bn_max / 2;
+      cudaError_t e = b->d_cpair[i].ensure(pair_c_bytes(b->mode, v.mo_num, v.kpad, bn, half));
+      if (e == cudaSuccess)
+        e = launch_pair_c(b->mode, v.c_hi, v.c_lo, v.kpad, v.mo_num, v.kpad, bn, half,
+                          b->d_cpair[i].p, b->stream);
+      if (e != cudaSuccess) return bcuda(b, e, "blocked C");
+      if (!tc_make_pair_problem(b->mode, v.ao, v.kpad, b->d_cpair[i].p, v.mo_num, outs[i], bn,
+                                b->bn_max, 5 * v.p.n, &pp[i]))
+        return bfail(b, QK_ERR_CUDA, "tensor map encoding failed");
+    } else if (!tc_make_problem(b->mode, v.ao, v.kpad, v.c_hi, v.c_lo, v.kpad, v.mo_num, outs[i],
+                                bn, 5 * v.p.n, &tcp[i])) {
       return bfail(b, QK_ERR_CUDA, "tensor map encoding failed");
+    }
     // ao items: one chunk of every stride-th tile (strided, so that each
     // item samples the whole molecule and items of one molecule cost alike)
     const int64_t tiles = (v.p.n + kTilePoints - 1) / kTilePoints;
@@ -157,12 +180,15 @@ qk_status build(qk_batch b, float* const* outs) {
         ao_items.push_back(make_int4(i, q, (int)t, (int)stride));
         ao_cost.push_back((double)((tiles - t + stride - 1) / stride));
       }
-    // contraction items: every (M tile, N tile); cost ~ K blocks x MMA N
+    // contraction items: every (M tile, N tile), or every (M-tile pair, N
+    // tile); cost ~ K blocks x MMA N
     const int64_t mt = v.ao.rows / kTileRows, nt = (v.mo_num + bn - 1) / bn;
-    for (int64_t m = 0; m < mt; ++m)
+    const int64_t nm = b->sm_pairs ? (mt + 1) / 2 : mt;
+    const int nkb = b->sm_pairs ? pp[i].num_kb : tcp[i].num_kb;
+    for (int64_t m = 0; m < nm; ++m)
       for (int64_t k = 0; k < nt; ++k) {
         tc_items.push_back(make_int4(i, (int)m, (int)k, 0));
-        tc_cost.push_back((double)tcp[i].num_kb * bn);
+        tc_cost.push_back((double)nkb * bn);
       }
   }
   // longest first (stable: N tiles of one M tile stay adjacent)
@@ -178,6 +204,9 @@ qk_status build(qk_batch b, float* const* outs) {
   lpt(tc_items, tc_cost);
   cudaError_t e = b->d_ao_probs.ensure(sizeof(AOProblem) * n);
   if (e == cudaSuccess) e = b->d_tc_probs.ensure(sizeof(TcProblem) * n);
+  if (e == cudaSuccess && b->sm_pairs) e = b->d_pair_probs.ensure(sizeof(PairProblem) * n);
+  if (e == cudaSuccess && b->sm_pairs)
+    e = cudaMemcpy(b->d_pair_probs.p, pp.data(), sizeof(PairProblem) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = b->d_ao_items.ensure(sizeof(int4) * std::max<size_t>(1, ao_items.size()));
   if (e == cudaSuccess) e = b->d_tc_items.ensure(sizeof(int4) * std::max<size_t>(1, tc_items.size()));
   if (e == cudaSuccess) e = b->d_flag.ensure(256);
@@ -202,6 +231,7 @@ qk_status build(qk_batch b, float* const* outs) {
 qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig) {
   sig->clear();
   sig->push_back((uintptr_t)b->bn_max);
+  sig->push_back((uintptr_t)b->sm_pairs);
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     ForwardViews v;
     if (context_cusp_on(b->ctxs[i]))
@@ -225,6 +255,7 @@ qk_status signature(qk_batch b, float* const* outs, std::vector<uintptr_t>* sig)
     sig->push_back((uintptr_t)v.b.chunk);
     sig->push_back((uintptr_t)v.c_hi);
     sig->push_back((uintptr_t)v.mo_num);
+    sig->push_back((uintptr_t)v.mo_version);  // C is blocked per upload for pairs
     sig->push_back((uintptr_t)outs[i]);
   }
   return QK_SUCCESS;
@@ -243,11 +274,19 @@ cudaError_t launch_ao_side(qk_batch b, cudaStream_t s) {
   return e;
 }
 
+cudaError_t launch_contraction(qk_batch b, int bn_max, cudaStream_t s) {
+  if (b->sm_pairs)
+    return launch_mo_tc_pair_batch(b->mode, bn_max, (const PairProblem*)b->d_pair_probs.p,
+                                   (const int4*)b->d_tc_items.p, b->n_tc_items, (int*)b->d_flag.p,
+                                   s);
+  return launch_mo_tc_batch(b->mode, bn_max, (const TcProblem*)b->d_tc_probs.p,
+                            (const int4*)b->d_tc_items.p, b->n_tc_items, (int*)b->d_flag.p, s);
+}
+
 cudaError_t launch_both(qk_batch b, cudaStream_t s) {
   cudaError_t e = launch_ao_side(b, s);
   if (e != cudaSuccess) return e;
-  return launch_mo_tc_batch(b->mode, b->bn_max, (const TcProblem*)b->d_tc_probs.p,
-                            (const int4*)b->d_tc_items.p, b->n_tc_items, (int*)b->d_flag.p, s);
+  return launch_contraction(b, b->bn_max, s);
 }
 
 qk_status prepare(qk_batch b, float* const* outs, const int64_t* sizes) {
@@ -341,6 +380,12 @@ qk_status qk_batch_set_graph(qk_batch b, int32_t enable) {
   return QK_SUCCESS;
 }
 
+qk_status qk_batch_set_sm_pairs(qk_batch b, int32_t enable) {
+  if (!b) return QK_ERR_NULL_POINTER;
+  b->sm_pairs = enable != 0;
+  return QK_SUCCESS;
+}
+
 qk_status qk_batch_set_tile(qk_batch b, int32_t bn_max) {
   if (!b) return QK_ERR_NULL_POINTER;
   bool known = false;
@@ -427,10 +472,7 @@ qk_status qk_batch_autotune(qk_batch b, float* const* douts, int32_t reps, doubl
     e = launch_ao_side(b, b->stream);
     for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
       if (r == 1) e = cudaEventRecord(e0, b->stream);
-      if (e == cudaSuccess)
-        e = launch_mo_tc_batch(b->mode, bn, (const TcProblem*)b->d_tc_probs.p,
-                               (const int4*)b->d_tc_items.p, b->n_tc_items, (int*)b->d_flag.p,
-                               b->stream);
+      if (e == cudaSuccess) e = launch_contraction(b, bn, b->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);

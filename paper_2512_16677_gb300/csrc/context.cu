@@ -141,7 +141,7 @@ struct qk_context_s {
   // C blocked for the pair contraction (per upload of C, tile width and mode)
   DevBuf d_cpair;
   uint64_t cpair_version = ~0ull;
-  int cpair_bn = 0, cpair_mode = -1;
+  int cpair_bn = 0, cpair_half = 0, cpair_mode = -1;
   std::vector<cudaEvent_t> range_done;  // one per output range of a host call
   DevBuf d_flag;
   DevBuf bwd_own;
@@ -763,18 +763,10 @@ qk_status contract(qk_context c, const AOTensor& ao, int64_t M, void* dout) {
       const void* b_lo = split ? (const void*)c->c_lo : nullptr;
       const TcConfig cfg = tc_default_config(c->mode, N);
       if (ao.pair_zero && cfg.bn >= 64 && cfg.bn % 32 == 0) {
-        // C blocked for the pair kernel, once per upload of C and tile width
-        if (c->cpair_version != c->mo_version || c->cpair_bn != cfg.bn ||
-            c->cpair_mode != c->mode) {
-          e = c->d_cpair.ensure(pair_c_bytes(c->mode, N, KP, cfg.bn));
-          if (e == cudaSuccess)
-            e = launch_pair_c(c->mode, b_hi, b_lo, KP, N, KP, cfg.bn, c->d_cpair.p, c->stream);
-          if (e != cudaSuccess) return cuda_fail(c, e, "blocked C");
-          c->cpair_version = c->mo_version;
-          c->cpair_bn = cfg.bn;
-          c->cpair_mode = c->mode;
-        }
-        e = launch_mo_tc_pair(c->mode, ao, KP, c->d_cpair.p, N, (float*)dout, cfg.bn,
+        const void* cblk = nullptr;
+        qk_status st = context_pair_c(c, cfg.bn, cfg.bn / 2, &cblk);
+        if (st) return st;
+        e = launch_mo_tc_pair(c->mode, ao, KP, cblk, N, (float*)dout, cfg.bn,
                               (int*)c->d_flag.p, c->stream, M);
       } else
         e = launch_mo_tc(c->mode, ao, KP, b_hi, b_lo, KP, N, (float*)dout, cfg,
@@ -2003,11 +1995,34 @@ qk_status context_forward_views(qk_context c, ForwardViews* v) {
     v->box_hi[k] = c->nbox_hi[k];
   }
   v->spatial = c->spatial;
+  v->mo_version = c->mo_version;
   return QK_SUCCESS;
 }
 
 bool context_cusp_on(qk_context c) { return c->cusp_on; }
 
 void context_forget_ao(qk_context c) { c->ao_date = ~0ull; }
+
+qk_status context_pair_c(qk_context c, int bn, int half_rows, const void** out) {
+  qk_status st = ensure_mo(c);
+  if (st) return st;
+  if (c->cpair_version != c->mo_version || c->cpair_bn != bn || c->cpair_half != half_rows ||
+      c->cpair_mode != c->mode) {
+    const bool split = c->mode == QK_BF16X3;
+    const void* b_hi = split ? (const void*)c->c_hi : (const void*)c->c32p;
+    const void* b_lo = split ? (const void*)c->c_lo : nullptr;
+    cudaError_t e = c->d_cpair.ensure(pair_c_bytes(c->mode, c->mo_num, c->kpad, bn, half_rows));
+    if (e == cudaSuccess)
+      e = launch_pair_c(c->mode, b_hi, b_lo, c->kpad, c->mo_num, c->kpad, bn, half_rows,
+                        c->d_cpair.p, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "blocked C");
+    c->cpair_version = c->mo_version;
+    c->cpair_bn = bn;
+    c->cpair_half = half_rows;
+    c->cpair_mode = c->mode;
+  }
+  *out = c->d_cpair.p;
+  return QK_SUCCESS;
+}
 
 }  // namespace qk

@@ -296,13 +296,36 @@ TcConfig tc_default_config(int mode, int64_t mo_num);
 // of the pair multiplies, bn / 2 of them, zero-padded) and each K block, a
 // contiguous [planes][bn / 2][128 bytes] block, so that each stage's C
 // copy is one contiguous box.
-size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn);
+// half_rows: the rows each half block holds (bn / 2 for a launch of MMA N
+// bn; a multi-problem launch pads every problem's halves to bn_max / 2).
+size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn, int half_rows);
 // c_hi / c_lo: [mo][ldc] bf16 planes (QK_BF16X3) or c_hi [mo][ldc] FP32 (QK_TF32).
 cudaError_t launch_pair_c(int mode, const void* c_hi, const void* c_lo, int64_t ldc,
-                          int64_t mo_num, int64_t ao_num, int bn, void* c_blk, cudaStream_t s);
+                          int64_t mo_num, int64_t ao_num, int bn, int half_rows, void* c_blk,
+                          cudaStream_t s);
 cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_blk,
                               int64_t mo_num, float* out, int bn, int* err_flag, cudaStream_t s,
                               int64_t out_rows);
+// One problem of a multi-problem pair launch (device-resident; the tensor
+// maps, 64-byte aligned by their type, are written by the host).
+struct PairProblem {
+  CUtensorMap a, b;      // blocked AO tensor; blocked C with halves of bn_max / 2 rows
+  const uint8_t* mask;   // [tiles][mask_ld(nchunk)]
+  const int32_t* perm;   // slot -> point (NULL: identity)
+  float* D;              // [M][N] output
+  int64_t M, N;          // output rows (5 * points) and columns
+  int m_tiles, n_tiles, num_kb, nchunk;
+  int bn, last_bn;       // MMA N of the N tiles and of the last one
+  int zero_slice;        // a slice past the AO tensor's end
+};
+// Fill a PairProblem (host): the AO tensor written with pair_zero, C blocked
+// by launch_pair_c(bn, bn_max / 2); bn <= bn_max.
+bool tc_make_pair_problem(int mode, const AOTensor& ao, int64_t K, const void* c_blk, int64_t N,
+                          float* out, int bn, int bn_max, int64_t out_rows, PairProblem* p);
+// Persistent pair launch over a work list of int4 (problem, M-tile pair, N tile, 0).
+cudaError_t launch_mo_tc_pair_batch(int mode, int bn_max, const PairProblem* probs,
+                                    const int4* items, int64_t n_items, int* err_flag,
+                                    cudaStream_t s);
 
 // One contraction problem of a multi-problem launch (device-resident; the
 // tensor maps, 64-byte aligned by their type, are written by the host
@@ -479,10 +502,15 @@ struct ForwardViews {
   uint64_t basis_version;  // bumped by every change of nuclei, basis, cutoff or order
   float box_lo[3], box_hi[3];  // nuclear box of the spatial point order
   bool spatial;                // whether the context cuts its tiles from that order
+  uint64_t mo_version;         // bumped by every upload of C
 };
 qk_status context_forward_views(qk_context c, ForwardViews* v);
 // Whether the context applies the MO cusp correction.
 bool context_cusp_on(qk_context c);
+// C blocked for the pair contraction at MMA N bn with halves of half_rows
+// rows (built on the context's stream once per upload of C, tile shape and
+// mode; *out stays valid until the next call with another shape).
+qk_status context_pair_c(qk_context c, int bn, int half_rows, const void** out);
 // Record that the workspace's AO tensor is not the context's own any more
 // (a multi-molecule launch wrote it in its own point order).
 void context_forget_ao(qk_context c);

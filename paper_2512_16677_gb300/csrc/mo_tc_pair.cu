@@ -73,20 +73,86 @@ constexpr int stages_for_pair(int mode, int bn) {
                      ((mode == QK_BF16X3 ? 2 : 1) * (kBM + bn / 2) * kRowBytes));
 }
 
-// One launch over the tiled AO tensor: pair-tile p -> (M tile pair p / n_tiles,
-// N tile p % n_tiles); CTA rank r of the cluster owns M tile 2 (p / n_tiles) + r.
+// One pair-tile as the roles see it: M tiles 2 mp (leader) and 2 mp + 1
+// (partner) of a problem, N tile nt.
+struct PairTile {
+  const CUtensorMap* a;  // blocked AO tensor: 3-D map over its column slices (one box = one K block)
+  const CUtensorMap* b;  // blocked C: 3-D map over its [BN / 2][128-byte] slices
+  const uint8_t* mask;   // [m tiles][mask_ld(nchunk)]
+  const int32_t* perm;   // slot -> point (NULL: identity)
+  float* D;
+  int64_t M, N;          // output rows (5 points) and columns
+  int mp, nt;            // M-tile pair and N tile
+  int n0, bn;            // first output column and MMA N of the tile
+  int m_tiles, num_kb, nchunk;
+  int zero_slice;        // a slice past the AO tensor's end: its box reads zeros
+};
+
+// One problem: pair-tile p -> (M tile pair p / n_tiles, N tile p % n_tiles).
 template <int BN>
 struct PairSched {
-  CUtensorMap a;       // blocked AO tensor: 3-D map over its column slices (one box = one K block)
-  CUtensorMap b;       // blocked C: 3-D map over its [BN / 2][128-byte] slices (box = one block)
-  int last_bn;
+  CUtensorMap a, b;
+  int last_bn;           // MMA N of the last N tile (the MOs left, rounded up to 16)
   float* D;
-  const uint8_t* mask;  // [m tiles][mask_ld(nchunk)]
-  const int32_t* perm;  // slot -> point (NULL: identity)
-  int64_t M, N;         // output rows (5 points) and columns
-  int zero_slice;       // a slice past the tensor's end: its box reads zeros
-  int m_tiles, n_tiles, num_kb, nchunk;
-  int64_t total;        // pair-tiles
+  const uint8_t* mask;
+  const int32_t* perm;
+  int64_t M, N;
+  int zero_slice, m_tiles, n_tiles, num_kb, nchunk;
+  int64_t total;         // pair-tiles
+  __device__ __forceinline__ int64_t count() const { return total; }
+  __device__ __forceinline__ void prefetch_map(bool a_side) const {
+    tma_prefetch_map(a_side ? &a : &b);
+  }
+  __device__ __forceinline__ PairTile tile(int64_t p) const {
+    PairTile x;
+    x.mp = (int)(p / n_tiles);
+    x.nt = (int)(p - (int64_t)x.mp * n_tiles);
+    x.bn = x.nt == n_tiles - 1 ? last_bn : BN;
+    x.n0 = x.nt * BN;
+    x.a = &a;
+    x.b = &b;
+    x.mask = mask;
+    x.perm = perm;
+    x.D = D;
+    x.M = M;
+    x.N = N;
+    x.m_tiles = m_tiles;
+    x.num_kb = num_kb;
+    x.nchunk = nchunk;
+    x.zero_slice = zero_slice;
+    return x;
+  }
+};
+
+// Several problems: a work list of (problem, M-tile pair, N tile) over
+// descriptors in global memory (tensor maps written by the host).
+struct PairBatchSched {
+  const PairProblem* probs;
+  const int4* items;
+  int64_t n_items;
+  __device__ __forceinline__ int64_t count() const { return n_items; }
+  __device__ __forceinline__ void prefetch_map(bool) const {}  // maps differ per problem
+  __device__ __forceinline__ PairTile tile(int64_t p) const {
+    const int4 it = items[p];
+    const PairProblem& P = probs[it.x];
+    PairTile x;
+    x.mp = it.y;
+    x.nt = it.z;
+    x.bn = x.nt == P.n_tiles - 1 ? P.last_bn : P.bn;
+    x.n0 = x.nt * P.bn;
+    x.a = &P.a;
+    x.b = &P.b;
+    x.mask = P.mask;
+    x.perm = P.perm;
+    x.D = P.D;
+    x.M = P.M;
+    x.N = P.N;
+    x.m_tiles = P.m_tiles;
+    x.num_kb = P.num_kb;
+    x.nchunk = P.nchunk;
+    x.zero_slice = P.zero_slice;
+    return x;
+  }
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -172,16 +238,9 @@ constexpr int kb_per_chunk() {
   return TcTraits<MODE>::kBK == 64 ? 1 : 2;
 }
 
-// Whether the tile's mask row holds a live group (whole warp).
-__device__ __forceinline__ bool row_live(const uint8_t* row, int nq, int lane) {
-  bool live = false;
-  for (int q = lane; q < nq; q += 32) live |= (row[q] & 0xFu) != 0u;
-  return __any_sync(0xffffffffu, live);
-}
-
-template <int MODE, int BN, int STAGES>
+template <int MODE, int BN, int STAGES, class Sched>
 __global__ void __launch_bounds__(kThreads, 1)
-    mo_tc_pair_kernel(const __grid_constant__ PairSched<BN> sc, int* err_flag) {
+    mo_tc_pair_kernel(const __grid_constant__ Sched sc, int* err_flag) {
   using S = PairShape<MODE, BN, STAGES>;
   using TR = TcTraits<MODE>;
   constexpr uint32_t ACC = S::ACC;
@@ -236,11 +295,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_slot;
   griddep_wait();
 
-  const int64_t total = sc.total;
-  const int mld = mask_ld(sc.nchunk);
-
-  const int nq = (sc.num_kb + kPer - 1) / kPer;  // chunks (the last may be half one)
-  const int nwin = (nq + 31) / 32;                 // 32-chunk windows of a mask row
+  const int64_t total = sc.count();
+  // chunks of a tile's K range (the last may be half one) and the 32-chunk
+  // windows of its mask row
+  auto chunks_of = [&](const PairTile& x) { return (x.num_kb + kPer - 1) / kPer; };
 
   if (warp == 4 || warp == 6) {
     // ------------------------------------------------ TMA producers (both CTAs)
@@ -253,14 +311,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // window, and kept in registers: per chunk the union groups (bits 0-3)
     // and this CTA's own groups (bits 4-7).
     const bool a_warp = warp == 4;
-    if (lane == 0) {
-      tma_prefetch_map(a_warp ? &sc.a : &sc.b);
-    }
-    auto load_groups = [&](int64_t p, uint32_t (&g)[kMaxWin]) {
-      const int mp = (int)(p / sc.n_tiles);
-      const int mo = 2 * mp + (int)rank, mr = 2 * mp + 1 - (int)rank;
-      const uint8_t* own_row = mo < sc.m_tiles ? sc.mask + (int64_t)mo * mld : nullptr;
-      const uint8_t* par_row = mr < sc.m_tiles ? sc.mask + (int64_t)mr * mld : nullptr;
+    if (lane == 0) sc.prefetch_map(a_warp);
+    auto load_groups = [&](const PairTile& x, uint32_t (&g)[kMaxWin]) {
+      const int nq = chunks_of(x), nwin = (nq + 31) / 32;
+      const int mld = mask_ld(x.nchunk);
+      const int mo = 2 * x.mp + (int)rank, mr = 2 * x.mp + 1 - (int)rank;
+      const uint8_t* own_row = mo < x.m_tiles ? x.mask + (int64_t)mo * mld : nullptr;
+      const uint8_t* par_row = mr < x.m_tiles ? x.mask + (int64_t)mr * mld : nullptr;
 #pragma unroll
       for (int w = 0; w < kMaxWin; ++w) {
         const int q = 32 * w + lane;
@@ -279,19 +336,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     // live in this CTA's own tile (bit 14); never 0.
     uint16_t* list = elist[a_warp ? 0 : 1];
     uint32_t gnext[kMaxWin];
-    if (cluster < total) load_groups(cluster, gnext);
+    PairTile xnext{};
+    if (cluster < total) {
+      xnext = sc.tile(cluster);
+      load_groups(xnext, gnext);
+    }
     uint32_t it = 0;  // stages taken (lane 0)
     bool ok = true;
     for (int64_t p = cluster; p < total && ok; p += nclusters) {
       uint32_t gcur[kMaxWin];
 #pragma unroll
       for (int w = 0; w < kMaxWin; ++w) gcur[w] = gnext[w];
-      if (p + nclusters < total) load_groups(p + nclusters, gnext);
-      const int mp = (int)(p / sc.n_tiles);
-      const int nt = (int)(p - (int64_t)mp * sc.n_tiles);
-      const int mt_own = 2 * mp + (int)rank;
-      const bool last_n = nt == sc.n_tiles - 1 && sc.last_bn != BN;
-      const int bn = last_n ? sc.last_bn : BN;
+      const PairTile x = xnext;
+      if (p + nclusters < total) {
+        xnext = sc.tile(p + nclusters);
+        load_groups(xnext, gnext);
+      }
+      const int nwin = (chunks_of(x) + 31) / 32;
+      const int nt = x.nt;
+      const int mt_own = 2 * x.mp + (int)rank;
+      const int bn = x.bn;
       // the pair-tile's last live K block (-1: none)
       int lastkb = -1;
 #pragma unroll
@@ -303,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           lastkb = (32 * w + j) * kPer + ((kPer == 2 && (gj & 0xCu)) ? 1 : 0);
         }
       }
-      if (lastkb >= sc.num_kb) lastkb = sc.num_kb - 1;
+      if (lastkb >= x.num_kb) lastkb = x.num_kb - 1;
       // a C block is always BN / 2 rows (the last N tile's are zero-padded)
       const uint32_t cta_bytes = S::STAGE_BYTES;
       const uint32_t bn_bits = (uint32_t)(bn >> 4) << kStageBnShift;
@@ -330,11 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           // tensor's end when the block is dead in this CTA's tile; own half
           // of the C block
           if (a_warp) {
-            const int z = own_live ? blocked_slice<MODE>(mt_own, kb, sc.nchunk) : sc.zero_slice;
-            tma_load_3d_pair(dst, &sc.a, bar, 0, 0, z);
+            const int z = own_live ? blocked_slice<MODE>(mt_own, kb, x.nchunk) : x.zero_slice;
+            tma_load_3d_pair(dst, x.a, bar, 0, 0, z);
           } else {
-            const int z = ((2 * nt + (int)rank) * sc.num_kb + kb) * TR::kPlanes;
-            tma_load_3d_pair(dst, &sc.b, bar, 0, 0, z);
+            const int z = ((2 * nt + (int)rank) * x.num_kb + kb) * TR::kPlanes;
+            tma_load_3d_pair(dst, x.b, bar, 0, 0, z);
           }
         }
         return true;
@@ -358,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
           }
           const int kb = q * kPer + h;
-          if (steps && kb < sc.num_kb) e[h] = (uint32_t)kb | (steps << 10) | own;
+          if (steps && kb < x.num_kb) e[h] = (uint32_t)kb | (steps << 10) | own;
         }
         const unsigned b0 = __ballot_sync(0xffffffffu, e[0] != 0u);
         const unsigned b1 = __ballot_sync(0xffffffffu, e[1] != 0u);
@@ -372,8 +436,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if constexpr (kPer == 1) {
             // the window's first own AO block into L2 as soon as the list is known
             if (a_warp && n_e > 0 && (list[0] & (1u << 14)))
-              tma_prefetch_l2_3d(&sc.a, 0, 0,
-                                 blocked_slice<MODE>(mt_own, (int)(list[0] & 0x3FFu), sc.nchunk));
+              tma_prefetch_l2_3d(x.a, 0, 0,
+                                 blocked_slice<MODE>(mt_own, (int)(list[0] & 0x3FFu), x.nchunk));
           }
           for (int k = 0; k < n_e && ok; ++k) {
             const uint32_t v = list[k];
@@ -383,8 +447,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (a_warp && k + 1 < n_e) {
                 const uint32_t vn = list[k + 1];
                 if (vn & (1u << 14))
-                  tma_prefetch_l2_3d(&sc.a, 0, 0,
-                                     blocked_slice<MODE>(mt_own, (int)(vn & 0x3FFu), sc.nchunk));
+                  tma_prefetch_l2_3d(x.a, 0, 0,
+                                     blocked_slice<MODE>(mt_own, (int)(vn & 0x3FFu), x.nchunk));
               }
             }
             ok = stage((int)(v & 0x3FFu), (v >> 10) & 0xFu, (v >> 14) & 1u);
@@ -486,37 +550,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     // permutation) and the tile's live flag are read one pair-tile ahead.
     // The leader's accumulator-free barrier gets this warp's arrival as soon
     // as its last TMEM load of the tile has completed.
-    auto load_setup = [&](int64_t p, int64_t (&orow)[8], uint32_t& livebits) {
-      const int mp = (int)(p / sc.n_tiles);
-      const int mt = 2 * mp + (int)rank;
+    auto load_setup = [&](const PairTile& x, int64_t (&orow)[8], uint32_t& livebits) {
+      const int mt = 2 * x.mp + (int)rank;
       const int64_t row0 = (int64_t)mt * (5 * kTilePoints);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int loc = warp * 32 + 4 * k + (lane >> 3);
         const int64_t lin = row0 + loc;
-        orow[k] = (mt < sc.m_tiles && loc < 5 * kTilePoints && lin < sc.M)
-                      ? (sc.perm ? 5 * (int64_t)sc.perm[lin / 5] + lin % 5 : lin)
+        orow[k] = (mt < x.m_tiles && loc < 5 * kTilePoints && lin < x.M)
+                      ? (x.perm ? 5 * (int64_t)x.perm[lin / 5] + lin % 5 : lin)
                       : -1;
       }
       livebits = 0u;
-      if (mt < sc.m_tiles) {
-        const uint8_t* row = sc.mask + (int64_t)mt * mld;
+      if (mt < x.m_tiles) {
+        const uint8_t* row = x.mask + (int64_t)mt * mask_ld(x.nchunk);
+        const int nq = chunks_of(x);
         for (int q = lane; q < nq; q += 32) livebits |= (uint32_t)row[q] & 0xFu;
       }
     };
     int64_t onext[8];
     uint32_t lnext = 0u;
-    if (cluster < total) load_setup(cluster, onext, lnext);
+    PairTile xnext{};
+    if (cluster < total) {
+      xnext = sc.tile(cluster);
+      load_setup(xnext, onext, lnext);
+    }
     float(*stg)[32] = epi[warp];
-    const int64_t N = sc.N;
-    const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(sc.D) & 15) == 0;
     uint32_t i = 0;
     for (int64_t p = cluster; p < total; p += nclusters, ++i) {
       int64_t orow[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) orow[k] = onext[k];
       const uint32_t lcur = lnext;
-      if (p + nclusters < total) load_setup(p + nclusters, onext, lnext);
+      const PairTile x = xnext;
+      if (p + nclusters < total) {
+        xnext = sc.tile(p + nclusters);
+        load_setup(xnext, onext, lnext);
+      }
+      const int64_t N = x.N;
+      const bool vec = (N % 4) == 0 && (reinterpret_cast<uintptr_t>(x.D) & 15) == 0;
       const uint32_t b = i % NBUF;
       const long long t0 = clock64();
       bool ok = true;
@@ -531,16 +603,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      const int nt = (int)(p % sc.n_tiles);
-      const bool last_n = nt == sc.n_tiles - 1 && sc.last_bn != BN;
-      const int bn = last_n ? sc.last_bn : BN;
-      const int n0 = nt * BN;
+      const int bn = x.bn;
+      const int n0 = x.n0;
       const bool any_live = __any_sync(0xffffffffu, lcur != 0u);
       const uint32_t tbase = tmem + b * ACC + ((uint32_t)(warp * 32) << 16);
       const int cq = lane & 7;
       float* rowp[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) rowp[k] = sc.D + (orow[k] >= 0 ? orow[k] : 0) * N;
+      for (int k = 0; k < 8; ++k) rowp[k] = x.D + (orow[k] >= 0 ? orow[k] : 0) * N;
 #pragma unroll 1
       for (int c = 0; c < bn; c += 32) {
         const bool two = c + 16 < bn;
@@ -595,62 +665,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int MODE, int BN>
-cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_blk, int64_t N, float* out,
-                           int64_t out_rows, int* err_flag, cudaStream_t s) {
+// The blocked C as a 3-D map: slices of `hb` rows x 128 bytes, box = the
+// planes of one block.
+template <int MODE>
+bool make_map_pair_c(CUtensorMap* m, const void* c_blk, int hb, int64_t nslices) {
+  using TR = TcTraits<MODE>;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t w = 128 / (TR::kPlanes == 2 ? 2 : 4);
+  cuuint64_t dims[3] = {w, (cuuint64_t)hb, (cuuint64_t)nslices};
+  cuuint64_t strides[2] = {128, (cuuint64_t)hb * 128};
+  cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)hb, (cuuint32_t)TR::kPlanes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, TR::kPlanes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+             3, const_cast<void*>(c_blk), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// One persistent launch: one CTA per SM (TMEM is taken whole), in pairs.
+template <int MODE, int BN, class Sched>
+cudaError_t launch_pair_kernel(const Sched& sc, int64_t total, int* err_flag, cudaStream_t s) {
   constexpr int ST = stages_for_pair(MODE, BN);
   using S = PairShape<MODE, BN, ST>;
-  using TR = TcTraits<MODE>;
-  const int64_t M = ao.rows;
-  if (M == 0 || N == 0) return cudaSuccess;
-  if (M > INT32_MAX / 2 || K > INT32_MAX || N > INT32_MAX) return cudaErrorInvalidValue;
-  if (!ao.tiled || !ao.blocked || M % kBM != 0 || ao.comps == 1) return cudaErrorInvalidValue;
-  if (K > (int64_t)ao.nchunk * kChunkAO || K % kChunkAO != 0) return cudaErrorInvalidValue;
-  PairSched<BN> sc;
-  const int64_t n_tiles = (N + BN - 1) / BN;
-  // the last N tile multiplies only the MOs it has, rounded up to 16 (halves
-  // of whole 8-row groups)
-  sc.last_bn = (int)((N - (n_tiles - 1) * BN + 15) / 16 * 16);
-  const int64_t nblocks = M / kBM * ao.nchunk;
-  const int64_t num_kb = K / TR::kBK;
-  if (2 * nblocks + 2 > INT32_MAX || 2 * n_tiles * num_kb * TR::kPlanes > INT32_MAX)
-    return cudaErrorInvalidValue;
-  if (!make_map_blocked(&sc.a, ao.a, TR::kPlanes == 2, nblocks)) return cudaErrorInvalidValue;
-  {
-    // blocked C: slices of BN / 2 rows x 128 bytes, box = the planes of one block
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorInvalidValue;
-    const cuuint64_t w = 128 / (TR::kPlanes == 2 ? 2 : 4);
-    cuuint64_t dims[3] = {w, (cuuint64_t)(BN / 2), (cuuint64_t)(2 * n_tiles * num_kb * TR::kPlanes)};
-    cuuint64_t strides[2] = {128, (cuuint64_t)(BN / 2) * 128};
-    cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)(BN / 2), (cuuint32_t)TR::kPlanes};
-    cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&sc.b,
-            TR::kPlanes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-            3, const_cast<void*>(c_blk), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
-  sc.D = out;
-  sc.mask = ao.mask;
-  sc.perm = ao.perm;
-  sc.M = out_rows;
-  sc.N = N;
-  sc.zero_slice = (int)(2 * nblocks);
-  sc.m_tiles = (int)(M / kBM);
-  sc.n_tiles = (int)n_tiles;
-  sc.num_kb = (int)num_kb;
-  sc.nchunk = ao.nchunk;
-  sc.total = ((sc.m_tiles + 1) / 2) * n_tiles;
-  auto kern = mo_tc_pair_kernel<MODE, BN, ST>;
+  if (total == 0) return cudaSuccess;
+  auto kern = mo_tc_pair_kernel<MODE, BN, ST, Sched>;
   KernelFacts f;
-  cudaError_t e = kernel_facts<mo_tc_pair_kernel<MODE, BN, ST>>(S::SMEM, kThreads, &f);
+  cudaError_t e = kernel_facts<mo_tc_pair_kernel<MODE, BN, ST, Sched>>(S::SMEM, kThreads, &f);
   if (e != cudaSuccess) return e;
   if (f.occ < 1) return cudaErrorInvalidConfiguration;
-  // one CTA per SM (TMEM is taken whole), pairs of SMs, persistent
   int64_t clusters = f.sms / 2;
-  if (clusters > sc.total) clusters = sc.total;
+  if (clusters > total) clusters = total;
   if (clusters < 1) clusters = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * clusters));
@@ -669,15 +714,67 @@ cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_blk, int
   return cudaLaunchKernelEx(&cfg, kern, sc, err_flag);
 }
 
-// Blocked C of one (half, K block): [planes][BN / 2][w] with w = 128 bytes of
-// elements; half h = 2 nt + r holds rows nt BN + r bn_t / 2 .. + bn_t / 2 of
-// C (bn_t the tile's MMA N), zeros past them and past the last MO.
+// Checks and the shared fields of one problem (single or batch).
+template <int MODE>
+bool pair_problem_fields(const AOTensor& ao, int64_t K, int64_t N, int bn, int bn_max,
+                         const void* c_blk, CUtensorMap* a, CUtensorMap* b, int* last_bn,
+                         int* zero_slice, int* m_tiles, int* n_tiles, int* num_kb) {
+  using TR = TcTraits<MODE>;
+  const int64_t M = ao.rows;
+  if (M > INT32_MAX / 2 || K > INT32_MAX || N > INT32_MAX) return false;
+  if (!ao.tiled || !ao.blocked || M % kBM != 0 || ao.comps == 1) return false;
+  if (K > (int64_t)ao.nchunk * kChunkAO || K % kChunkAO != 0) return false;
+  if (bn % 16 != 0 || bn < 32 || bn > bn_max) return false;
+  const int64_t nt = (N + bn - 1) / bn;
+  const int64_t nblocks = M / kBM * ao.nchunk;
+  const int64_t kbs = K / TR::kBK;
+  if (2 * nblocks + 2 > INT32_MAX || 2 * nt * kbs * TR::kPlanes > INT32_MAX) return false;
+  if (!make_map_blocked(a, ao.a, TR::kPlanes == 2, nblocks)) return false;
+  if (!make_map_pair_c<MODE>(b, c_blk, bn_max / 2, 2 * nt * kbs * TR::kPlanes)) return false;
+  // the last N tile multiplies only the MOs it has, rounded up to 16 (halves
+  // of whole 8-row groups)
+  *last_bn = (int)((N - (nt - 1) * bn + 15) / 16 * 16);
+  *zero_slice = (int)(2 * nblocks);
+  *m_tiles = (int)(M / kBM);
+  *n_tiles = (int)nt;
+  *num_kb = (int)kbs;
+  return true;
+}
+
+template <int MODE, int BN>
+cudaError_t launch_pair_bn(const AOTensor& ao, int64_t K, const void* c_blk, int64_t N, float* out,
+                           int64_t out_rows, int* err_flag, cudaStream_t s) {
+  if (ao.rows == 0 || N == 0) return cudaSuccess;
+  PairSched<BN> sc;
+  if (!pair_problem_fields<MODE>(ao, K, N, BN, BN, c_blk, &sc.a, &sc.b, &sc.last_bn,
+                                 &sc.zero_slice, &sc.m_tiles, &sc.n_tiles, &sc.num_kb))
+    return cudaErrorInvalidValue;
+  sc.D = out;
+  sc.mask = ao.mask;
+  sc.perm = ao.perm;
+  sc.M = out_rows;
+  sc.N = N;
+  sc.nchunk = ao.nchunk;
+  sc.total = (int64_t)((sc.m_tiles + 1) / 2) * sc.n_tiles;
+  return launch_pair_kernel<MODE, BN>(sc, sc.total, err_flag, s);
+}
+
+template <int MODE, int BN>
+cudaError_t launch_pair_batch_bn(const PairProblem* probs, const int4* items, int64_t n_items,
+                                 int* err_flag, cudaStream_t s) {
+  PairBatchSched sc{probs, items, n_items};
+  return launch_pair_kernel<MODE, BN>(sc, n_items, err_flag, s);
+}
+
+// Blocked C of one (half, K block): [planes][hb][w] with w = 128 bytes of
+// elements; half h = 2 nt + r holds rows nt bn + r bn_t / 2 .. + bn_t / 2 of
+// C (bn_t the tile's MMA N, bn_t / 2 <= hb), zeros past them and past the
+// last MO.
 template <typename E>
 __global__ void pair_c_kernel(const E* c_hi, const E* c_lo, int64_t ldc, int64_t N, int bn,
-                              int last_bn, int64_t n_tiles, int64_t num_kb, int planes,
+                              int last_bn, int hb, int64_t n_tiles, int64_t num_kb, int planes,
                               E* out) {
   constexpr int w = 128 / (int)sizeof(E);
-  const int hb = bn / 2;
   const int64_t total = 2 * n_tiles * num_kb * planes * hb * w;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -705,32 +802,91 @@ int pair_last_bn(int64_t N, int bn) {
 
 }  // namespace
 
-size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn) {
+size_t pair_c_bytes(int mode, int64_t mo_num, int64_t ao_num, int bn, int half_rows) {
   const int64_t n_tiles = (mo_num + bn - 1) / bn;
   const int64_t kb = mode == QK_TF32 ? ao_num / 32 : ao_num / 64;
   const int planes = mode == QK_BF16X3 ? 2 : 1;
-  return (size_t)(2 * n_tiles * kb * planes) * (size_t)(bn / 2) * 128;
+  return (size_t)(2 * n_tiles * kb * planes) * (size_t)half_rows * 128;
 }
 
 cudaError_t launch_pair_c(int mode, const void* c_hi, const void* c_lo, int64_t ldc,
-                          int64_t mo_num, int64_t ao_num, int bn, void* c_blk, cudaStream_t s) {
-  if (bn % 16 != 0 || bn < 32 || bn > 256 || ao_num % kChunkAO != 0) return cudaErrorInvalidValue;
+                          int64_t mo_num, int64_t ao_num, int bn, int half_rows, void* c_blk,
+                          cudaStream_t s) {
+  if (bn % 16 != 0 || bn < 32 || bn > 256 || ao_num % kChunkAO != 0 || 2 * half_rows < bn ||
+      half_rows % 8 != 0)
+    return cudaErrorInvalidValue;
   const int64_t n_tiles = (mo_num + bn - 1) / bn;
   const int last_bn = pair_last_bn(mo_num, bn);
-  const int64_t elems = (int64_t)pair_c_bytes(mode, mo_num, ao_num, bn) / (mode == QK_TF32 ? 4 : 2);
+  const int64_t elems =
+      (int64_t)pair_c_bytes(mode, mo_num, ao_num, bn, half_rows) / (mode == QK_TF32 ? 4 : 2);
   const unsigned grid = (unsigned)std::min<int64_t>((elems + 255) / 256, 4096);
   if (elems == 0) return cudaSuccess;
   if (mode == QK_BF16X3) {
     pair_c_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
-        (const __nv_bfloat16*)c_hi, (const __nv_bfloat16*)c_lo, ldc, mo_num, bn, last_bn, n_tiles,
-        ao_num / 64, 2, (__nv_bfloat16*)c_blk);
+        (const __nv_bfloat16*)c_hi, (const __nv_bfloat16*)c_lo, ldc, mo_num, bn, last_bn,
+        half_rows, n_tiles, ao_num / 64, 2, (__nv_bfloat16*)c_blk);
   } else if (mode == QK_TF32) {
     pair_c_kernel<float><<<grid, 256, 0, s>>>((const float*)c_hi, nullptr, ldc, mo_num, bn,
-                                              last_bn, n_tiles, ao_num / 32, 1, (float*)c_blk);
+                                              last_bn, half_rows, n_tiles, ao_num / 32, 1,
+                                              (float*)c_blk);
   } else {
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+bool tc_make_pair_problem(int mode, const AOTensor& ao, int64_t K, const void* c_blk, int64_t N,
+                          float* out, int bn, int bn_max, int64_t out_rows, PairProblem* p) {
+  bool ok;
+  if (mode == QK_BF16X3)
+    ok = pair_problem_fields<QK_BF16X3>(ao, K, N, bn, bn_max, c_blk, &p->a, &p->b, &p->last_bn,
+                                        &p->zero_slice, &p->m_tiles, &p->n_tiles, &p->num_kb);
+  else if (mode == QK_TF32)
+    ok = pair_problem_fields<QK_TF32>(ao, K, N, bn, bn_max, c_blk, &p->a, &p->b, &p->last_bn,
+                                      &p->zero_slice, &p->m_tiles, &p->n_tiles, &p->num_kb);
+  else
+    ok = false;
+  if (!ok) return false;
+  p->mask = ao.mask;
+  p->perm = ao.perm;
+  p->D = out;
+  p->M = out_rows;
+  p->N = N;
+  p->nchunk = ao.nchunk;
+  p->bn = bn;
+  return true;
+}
+
+cudaError_t launch_mo_tc_pair_batch(int mode, int bn_max, const PairProblem* probs,
+                                    const int4* items, int64_t n_items, int* err_flag,
+                                    cudaStream_t s) {
+#define QK_PAIR_BATCH_CASE(M_, B_) \
+  case B_:                         \
+    return launch_pair_batch_bn<M_, B_>(probs, items, n_items, err_flag, s);
+  if (mode == QK_BF16X3) {
+    switch (bn_max) {
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 64)
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 96)
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 128)
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 160)
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 192)
+      QK_PAIR_BATCH_CASE(QK_BF16X3, 256)
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (mode == QK_TF32) {
+    switch (bn_max) {
+      QK_PAIR_BATCH_CASE(QK_TF32, 64)
+      QK_PAIR_BATCH_CASE(QK_TF32, 96)
+      QK_PAIR_BATCH_CASE(QK_TF32, 128)
+      QK_PAIR_BATCH_CASE(QK_TF32, 160)
+      QK_PAIR_BATCH_CASE(QK_TF32, 192)
+      QK_PAIR_BATCH_CASE(QK_TF32, 256)
+      default: return cudaErrorInvalidValue;
+    }
+  }
+#undef QK_PAIR_BATCH_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mo_tc_pair(int mode, const AOTensor& ao, int64_t ao_num, const void* c_blk,

@@ -87,6 +87,7 @@ SIGNATURES = {
     "qk_batch_last_error": [_P, ctypes.c_char_p, _I64],
     "qk_batch_set_stream": [_P, _P],
     "qk_batch_set_graph": [_P, _I32],
+    "qk_batch_set_sm_pairs": [_P, _I32],
     "qk_batch_set_tile": [_P, _I32],
     "qk_batch_get_tile": [_P, ctypes.POINTER(_I32)],
     "qk_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)],
@@ -601,6 +602,9 @@ class Batch:
 
     def set_graph(self, enable: bool):
         self._check(self.lib.qk_batch_set_graph(self.h, 1 if enable else 0), "set_graph")
+
+    def set_sm_pairs(self, enable: bool):
+        self._check(self.lib.qk_batch_set_sm_pairs(self.h, 1 if enable else 0), "set_sm_pairs")
 
     def set_tile(self, bn_max: int):
         self._check(self.lib.qk_batch_set_tile(self.h, bn_max), "set_tile")

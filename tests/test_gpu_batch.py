@@ -119,3 +119,25 @@ def test_batch_follows_a_cutoff_change(orc, cfg):
         ref = single.double().cpu().numpy().reshape(-1, 5, m.mo_num)
         got = o.double().cpu().numpy().reshape(-1, 5, m.mo_num)
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.abs(ref).max()
+
+
+def test_batch_pairs_equal_single_sm(orc, cfg):
+    """The batch's contraction on pairs of SMs (the default: M-tile pairs of
+    each molecule, C blocked per molecule) and on single SMs multiply the
+    same live blocks; the pair's extra k-steps add exact zeros.  Every
+    molecule against the oracle and the two against each other."""
+    from paper_2512_16677_gb300 import qmckl
+    mols = cfg(4, walk_num=8)
+    coords = [torch.from_numpy(m.coord).cuda() for m in mols]
+    ctxs = _contexts(mols, coords)
+    res = {}
+    for pairs in (True, False):
+        b = qmckl.Batch(ctxs)
+        b.set_sm_pairs(pairs)
+        outs = b.run()
+        b.synchronize()
+        res[pairs] = [o.double().cpu().numpy().reshape(-1, 5, m.mo_num) for o, m in zip(outs, mols)]
+        if pairs:
+            _check_all(orc, mols, outs, n=16, seed=4)
+    for m, a, s in zip(mols, res[True], res[False]):
+        assert np.max(np.abs(a - s)) <= 1e-6 * np.abs(s).max(), m.name
