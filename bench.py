@@ -541,10 +541,14 @@ def measure_batch(args, world):
     coords = [torch.from_numpy(m.coord).cuda() for m in mols]
     moved = [c + 0.05 for c in coords]
     ctxs = []
+    nnz = []
     for m, c in zip(mols, coords):
         ctx = qmckl.Context("bf16x3")
         ctx.set_molecule(m)
         ctx.set_points_device(c)
+        ctx.mo_vgl_device()            # once on its own: the molecule's exact sparsity
+        torch.cuda.synchronize()
+        nnz.append(ctx.sparsity_stats()[1])
         ctxs.append(ctx)
     b = qmckl.Batch(ctxs)
     bn, tune_ms = b.autotune(reps=3)
@@ -574,7 +578,31 @@ def measure_batch(args, world):
             "evals_per_step": evals, "points": sum(m.point_num for m in mols),
             "ms_per_step": ms, "value": world * evals / (ms * 1e-3), "unit": UNIT,
             "autotuned_bn_max": bn, "autotune_contraction_ms": tune_ms, "cuda_graph": True,
-            "launches_per_step": _batch_launches(len(mols))}
+            "launches_per_step": _batch_launches(len(mols)),
+            "roofline": batch_roofline(mols, nnz, tune_ms, load_peaks()[0])}
+
+
+def batch_roofline(mols, nnz, ms, peaks):
+    """The batch contraction (one launch over every molecule) against the
+    roofline of its algorithmic work: per molecule the sparse count
+    2 * 5 * N_mo * sum_p nnz_AO(p) (one product), over the bytes it must
+    move (nonzero AO entries in two bf16 planes, C once, the FP32 output).
+    nnz per molecule comes from the molecule's own evaluation."""
+    fl = sum(2.0 * 5 * m.mo_num * z for m, z in zip(mols, nnz))
+    nbytes = sum(4.0 * 5 * z + 4.0 * m.mo_num * m.ao_num + 4.0 * 5 * m.point_num * m.mo_num
+                 for m, z in zip(mols, nnz))
+    t = ms * 1e-3
+    hbm = peaks["hbm_gbs"]
+    tensor = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    t_hbm, t_tc = nbytes / (hbm * 1e9), fl / (tensor * 1e12)
+    bound = "hbm" if t_hbm >= t_tc else "tensor"
+    ent = {"kernel": "batch contraction", "algorithmic_flops": fl, "algorithmic_bytes": nbytes,
+           "hbm": {"achieved": nbytes / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": t_hbm / t},
+           "tensor": {"achieved": fl / t / 1e12, "peak": tensor, "unit": "TFLOP/s",
+                      "frac": t_tc / t},
+           "bound": bound, "ms_per_launch": ms}
+    ent.update({k: ent[bound][k] for k in ("achieved", "peak", "unit", "frac")})
+    return ent
 
 
 def _time_steps(fn, steps, warmup=2):

@@ -79,3 +79,23 @@ def test_accuracy_and_common_bar(orc, cfg, monkeypatch):
     res = {"accuracy": acc, "fp32_path": {"ms_per_step": 30.0}, "ms_per_step": 1.0}
     cb = bench.common_bar(res, "bf16x3")
     assert cb["bar"] == 5e-5 and cb["both_meet"] and cb["speedup"] == 30.0
+
+
+def test_batch_roofline_sums_molecules():
+    """The batch contraction's roofline entry: flops and bytes are the sums
+    of each molecule's sparse count and its bytes, the fractions are those
+    over the launch time, and the bound is the longer floor."""
+    from types import SimpleNamespace
+    mols = [SimpleNamespace(mo_num=100, ao_num=400, point_num=1000),
+            SimpleNamespace(mo_num=50, ao_num=200, point_num=3000)]
+    nnz = [20000, 90000]
+    peaks = {"hbm_gbs": 8000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1600.0}
+    r = bench.batch_roofline(mols, nnz, 0.5, peaks)
+    fl = 2 * 5 * (100 * 20000 + 50 * 90000)
+    by = (20 * 20000 + 4 * 100 * 400 + 20 * 1000 * 100) + (20 * 90000 + 4 * 50 * 200 + 20 * 3000 * 50)
+    assert r["algorithmic_flops"] == pytest.approx(fl)
+    assert r["algorithmic_bytes"] == pytest.approx(by)
+    assert r["hbm"]["frac"] == pytest.approx(by / 8e12 / 5e-4)
+    assert r["tensor"]["frac"] == pytest.approx(fl / 1.6e15 / 5e-4)
+    assert r["bound"] == ("hbm" if by / 8e12 >= fl / 1.6e15 else "tensor")
+    assert r["frac"] == r[r["bound"]]["frac"]
