@@ -533,14 +533,19 @@ qk_status ensure_cusp(qk_context c) {
 }
 
 // Adds the cusp correction to MO rows D of the points p (caller's order).
-qk_status apply_cusp(qk_context c, const PointsDev& p, void* D) {
+// The cusp correction on D at points p; `whole`: p are the context's current
+// points, whose spatial order (when they have one) the sphere search walks.
+qk_status apply_cusp(qk_context c, const PointsDev& p, void* D, bool whole = false) {
   if (!c->cusp_on) return QK_SUCCESS;
   cudaError_t e = c->d_cusp_list.ensure(cusp_list_bytes(p.n));
   if (e != cudaSuccess) return cuda_fail(c, e, "cusp point list");
+  const bool sorted = whole && c->perm && c->sort_date == c->date && c->psort.n == p.n;
   {
-    TimedLaunch t(c, 2);
-    e = launch_cusp_apply(c->bdev, c->cudev, p, c->mo_num, c->c64, c->c32, c->ldc, c->cusp_f64,
-                          c->cusp_f32, c->mode == QK_FP64, D, c->d_cusp_list.p, c->stream);
+    TimedLaunch t(c, 2, 2);
+    e = launch_cusp_apply(c->bdev, c->cudev, p, sorted ? &c->psort : nullptr,
+                          sorted ? c->perm : nullptr, c->mo_num, c->c64, c->c32, c->ldc,
+                          c->cusp_f64, c->cusp_f32, c->mode == QK_FP64, D, c->d_cusp_list.p,
+                          c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "cusp correction");
   return QK_SUCCESS;
@@ -1567,14 +1572,14 @@ qk_status qk_get_mo_vgl_device(qk_context c, void* dout, int64_t size) {
     c->fused_date = c->date;
     c->fused_lists = lp;
     c->ao_date = ~0ull;  // no AO tensor was written
-    return apply_cusp(c, c->pdev, dout);
+    return apply_cusp(c, c->pdev, dout, true);
   }
   AOTensor ao{};
   st = provide_ao(c, &ao);
   if (st) return st;
   st = contract(c, ao, M, dout);
   if (st) return st;
-  return apply_cusp(c, c->pdev, dout);
+  return apply_cusp(c, c->pdev, dout, true);
 }
 
 qk_status qk_get_mo_vgl(qk_context c, void* out, int64_t size) {

@@ -13,9 +13,9 @@
 //   3. one thread per (A, i): g, g', g'' of the s part at rc_A with the same
 //      Eq. 3 screening as the MO evaluation, then the 4 x 4 solve.
 // Correction (after the contraction, on the output rows in the caller's
-// point order): pass 1 lists the points inside a sphere (one thread per
-// point); pass 2 gives each listed point a CTA whose warps split the MOs
-// and add
+// point order): pass 1 lists the points inside a sphere (a warp per 32
+// points of the spatial order, spheres culled against the tile's box);
+// pass 2 gives each listed point a CTA whose warps split the MOs and add
 //   value      -g + p(rho)
 //   gradient   (p'(rho)/rho + 2 G_1) d,          d/d rho of an s AO is -2 rho M S_1
 //   Laplacian  (2 f_1/rho + 6 f_2 + 12 f_3 rho) - (4 rho^2 G_2 - 6 G_1)
@@ -205,37 +205,75 @@ __device__ __forceinline__ void correct_columns(const BasisDev& b, const CuspDev
   row[4 * mo_num] += lapp - lapg;
 }
 
-// Pass 1, one thread per point: which spheres hold the point (an FP32
-// prefilter on the float coordinates, nuclei read as warp-wide broadcasts,
-// then the exact FP64 test rho < rc).  A point inside 1..3 spheres is listed
-// once as (point, nuclei ascending, -1 padding); a point inside more is
-// listed once as (point, -2, -2, -2) and pass 2 tests every nucleus for it.
+// Pass 1: which spheres hold each point, one warp per 32 consecutive points
+// of a scan order (the spatial order when the points have one; perm maps a
+// scan slot to the point's index in the output order).  A point inside
+// 1..3 spheres is listed once as (point, nuclei ascending, -1 padding); a
+// point inside more is listed once as (point, -2, -2, -2) and pass 2 tests
+// every nucleus for it.  The tile's bounding box (float
+// coordinates) is tested against every sphere, lanes over nuclei; only the
+// spheres that reach the box are tested point by point (the same FP32
+// prefilter and exact FP64 test as above).  The distance from a nucleus to
+// the box never exceeds the distance to a point inside it, also after
+// rounding (each term is the same or a smaller float difference and float
+// sums are monotone), so the cull drops no point that the prefilter keeps.
 __global__ void __launch_bounds__(256)
-    cusp_find_kernel(BasisDev b, CuspDev cu, PointsDev p, int4* list, int* count) {
-  for (int64_t ip = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ip < p.n;
-       ip += (int64_t)gridDim.x * blockDim.x) {
-    const float xf = p.hi[ip], yf = p.hi[p.ld + ip], zf = p.hi[2 * p.ld + ip];
+    cusp_find_tiles_kernel(BasisDev b, CuspDev cu, PointsDev q, const int32_t* perm,
+                           int4* list, int* count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tiles = (q.n + 31) / 32;
+  const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles;
+       t += wstep) {
+    const int64_t sl = t * 32 + lane;
+    const bool pv = sl < q.n;
+    float xf = 0.0f, yf = 0.0f, zf = 0.0f;
+    if (pv) {
+      xf = q.hi[sl];
+      yf = q.hi[q.ld + sl];
+      zf = q.hi[2 * q.ld + sl];
+    }
+    float lo[3], hi[3];
+    warp_box(pv, xf, yf, zf, lo, hi);
     int found[3] = {-1, -1, -1};
     int nfound = 0;
-    for (int a = 0; a < b.nucl_num; ++a) {
-      const float rcf = cu.rc_f[a];
-      const float ex = xf - b.nucl_hi[3 * a], ey = yf - b.nucl_hi[3 * a + 1],
-                  ez = zf - b.nucl_hi[3 * a + 2];
-      // this far out the point is outside whatever the rounding (the float
-      // coordinates are exact to ~1e-7 relative, r^2 to 1e-5 bohr^2 here)
-      if (!(rcf > 0.0f && ex * ex + ey * ey + ez * ez <= rcf * rcf * 1.001f + 1e-4f)) continue;
-      const double dx = __dsub_rn(p.x[ip], b.nucl_xyz[3 * a]);
-      const double dy = __dsub_rn(p.y[ip], b.nucl_xyz[3 * a + 1]);
-      const double dz = __dsub_rn(p.z[ip], b.nucl_xyz[3 * a + 2]);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                  __dmul_rn(dz, dz));
-      if (!(r2 < cu.rc[a] * cu.rc[a])) continue;
-      if (nfound < 3) found[nfound] = a;
-      ++nfound;
+    for (int a0 = 0; a0 < b.nucl_num; a0 += 32) {
+      const int a = a0 + lane;
+      bool cand = false;
+      if (a < b.nucl_num) {
+        const float rcf = cu.rc_f[a];
+        const float c[3] = {b.nucl_hi[3 * a], b.nucl_hi[3 * a + 1], b.nucl_hi[3 * a + 2]};
+        float d2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float e = fmaxf(0.0f, fmaxf(lo[k] - c[k], c[k] - hi[k]));
+          d2 += e * e;
+        }
+        cand = rcf > 0.0f && d2 <= rcf * rcf * 1.001f + 1e-4f;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, cand);
+      while (m) {
+        const int A = a0 + __ffs(m) - 1;
+        m &= m - 1u;
+        if (!pv) continue;
+        const float rcf = cu.rc_f[A];
+        const float ex = xf - b.nucl_hi[3 * A], ey = yf - b.nucl_hi[3 * A + 1],
+                    ez = zf - b.nucl_hi[3 * A + 2];
+        if (!(ex * ex + ey * ey + ez * ez <= rcf * rcf * 1.001f + 1e-4f)) continue;
+        const double dx = __dsub_rn(q.x[sl], b.nucl_xyz[3 * A]);
+        const double dy = __dsub_rn(q.y[sl], b.nucl_xyz[3 * A + 1]);
+        const double dz = __dsub_rn(q.z[sl], b.nucl_xyz[3 * A + 2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                    __dmul_rn(dz, dz));
+        if (!(r2 < cu.rc[A] * cu.rc[A])) continue;
+        if (nfound < 3) found[nfound] = A;
+        ++nfound;
+      }
     }
-    if (nfound == 0) continue;
-    const int4 it = nfound <= 3 ? make_int4((int)ip, found[0], found[1], found[2])
-                                : make_int4((int)ip, -2, -2, -2);
+    if (!pv || nfound == 0) continue;
+    const int ip = perm ? perm[sl] : (int)sl;
+    const int4 it = nfound <= 3 ? make_int4(ip, found[0], found[1], found[2])
+                                : make_int4(ip, -2, -2, -2);
     list[atomicAdd(count, 1)] = it;
   }
 }
@@ -248,6 +286,7 @@ __global__ void __launch_bounds__(256)
     cusp_apply_list_kernel(BasisDev b, CuspDev cu, PointsDev p, int64_t mo_num, const T* C,
                            int64_t ldc, const T* f, T* D, const int4* list, const int* count) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  griddep_wait();  // the list is the previous kernel's output
   const int n = *count;
   for (int e = blockIdx.x; e < n; e += gridDim.x) {
     const int4 it = list[e];
@@ -309,7 +348,8 @@ cudaError_t launch_cusp_setup(const BasisDev& b, const CuspDev& cu, int64_t mo_n
 size_t cusp_list_bytes(int64_t n) { return sizeof(int4) * (size_t)(n > 0 ? n : 1) + 256; }
 
 cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const PointsDev& p,
-                              int64_t mo_num, const double* C64, const float* C32, int64_t ldc32,
+                              const PointsDev* scan, const int32_t* perm, int64_t mo_num,
+                              const double* C64, const float* C32, int64_t ldc32,
                               const double* f64, const float* f32, bool f64_out, void* D,
                               void* scratch, cudaStream_t s) {
   if (p.n == 0 || mo_num == 0) return cudaSuccess;
@@ -317,19 +357,20 @@ cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const Points
   int4* list = (int4*)((unsigned char*)scratch + 256);
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (p.n + 255) / 256;  // one thread per point
-  const unsigned g = (unsigned)(blocks < 4096 ? blocks : 4096);
+  const PointsDev& q = scan ? *scan : p;
+  if (q.n != p.n) return cudaErrorInvalidValue;
+  // a warp per 32 scan-order points, eight warps per block
+  const int64_t blocks = ((q.n + 31) / 32 + 7) / 8;
+  const unsigned g = (unsigned)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
   const unsigned g2 = (unsigned)(8 * device_sms());
-  if (f64_out) {
-    cusp_find_kernel<<<g, 256, 0, s>>>(b, cu, p, list, count);
-    cusp_apply_list_kernel<double><<<g2, 256, 0, s>>>(b, cu, p, mo_num, C64, b.ao_num, f64,
-                                                      (double*)D, list, count);
-  } else {
-    cusp_find_kernel<<<g, 256, 0, s>>>(b, cu, p, list, count);
-    cusp_apply_list_kernel<float><<<g2, 256, 0, s>>>(b, cu, p, mo_num, C32, ldc32, f32,
-                                                     (float*)D, list, count);
-  }
-  return cudaGetLastError();
+  cusp_find_tiles_kernel<<<g, 256, 0, s>>>(b, cu, q, scan ? perm : nullptr, list, count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (f64_out)
+    return launch_pdl(cusp_apply_list_kernel<double>, g2, 256, 0, s, b, cu, p, mo_num, C64,
+                      (int64_t)b.ao_num, f64, (double*)D, (const int4*)list, (const int*)count);
+  return launch_pdl(cusp_apply_list_kernel<float>, g2, 256, 0, s, b, cu, p, mo_num, C32, ldc32,
+                    f32, (float*)D, (const int4*)list, (const int*)count);
 }
 
 }  // namespace qk

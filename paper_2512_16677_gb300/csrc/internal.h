@@ -448,10 +448,13 @@ cudaError_t launch_cusp_setup(const BasisDev& b, const CuspDev& cu, int64_t mo_n
                               cudaStream_t s);
 // Adds the correction to D [points][5][mo] (FP64 or FP32) at the points.
 // FP64 output: C64 [mo][ao] and f64; FP32 output: C32 [mo][ldc32] and f32.
-// scratch: cusp_list_bytes(p.n) bytes of device memory.
+// scratch: cusp_list_bytes(p.n) bytes of device memory.  scan (optional):
+// the same points in another order (the spatial order), perm[slot] = the
+// point's index in p; the sphere search walks tiles of that order.
 size_t cusp_list_bytes(int64_t n);
 cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const PointsDev& p,
-                              int64_t mo_num, const double* C64, const float* C32, int64_t ldc32,
+                              const PointsDev* scan, const int32_t* perm, int64_t mo_num,
+                              const double* C64, const float* C32, int64_t ldc32,
                               const double* f64, const float* f32, bool f64_out, void* D,
                               void* scratch, cudaStream_t s);
 
