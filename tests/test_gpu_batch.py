@@ -141,3 +141,29 @@ def test_batch_pairs_equal_single_sm(orc, cfg):
             _check_all(orc, mols, outs, n=16, seed=4)
     for m, a, s in zip(mols, res[True], res[False]):
         assert np.max(np.abs(a - s)) <= 1e-6 * np.abs(s).max(), m.name
+
+
+def test_batch_tf32_pairs(orc, cfg):
+    """TF32 batch (pair contraction over FP32 blocked C): every molecule
+    within the TF32 bar of the oracle and equal to its own context."""
+    from paper_2512_16677_gb300 import qmckl
+    mols = cfg(4, walk_num=4)[:5]
+    ctxs = []
+    for m in mols:
+        ctx = qmckl.Context("tf32")
+        ctx.set_molecule(m)
+        ctx.set_points_device(torch.from_numpy(m.coord).cuda())
+        ctxs.append(ctx)
+    b = qmckl.Batch(ctxs)
+    outs = b.run()
+    b.synchronize()
+    rng = np.random.default_rng(6)
+    for c, m, o in zip(ctxs, mols, outs):
+        got = o.double().cpu().numpy().reshape(-1, 5, m.mo_num)
+        idx = np.sort(rng.choice(m.point_num, min(12, m.point_num), replace=False))
+        ref, size = orc.mo_vgl(m, points=m.points[idx])
+        assert_within("tf32", got[idx], ref, size, m.name)
+        single = c.mo_vgl_device()
+        torch.cuda.synchronize()
+        s = single.double().cpu().numpy().reshape(-1, 5, m.mo_num)
+        assert np.max(np.abs(got - s)) <= 1e-5 * np.abs(s).max(), m.name
