@@ -8,9 +8,11 @@
 // consecutive 25-point tiles, one per CTA), and each CTA stages only half of
 // the C tile (N / 2 rows).  Per SM a pipeline stage then carries the AO
 // block (32 KB, one contiguous box of the blocked layout) and half the C
-// block (20 KB at N = 160) instead of the whole C block (40 KB), so four
-// stages fit where three did, and every C byte fetched from L2 serves twice
-// the MMA work.
+// block (20 KB at N = 160, one contiguous box of C blocked per half N tile
+// and K block) instead of the whole C block (40 KB), so four stages fit
+// where three did, and every C byte fetched from L2 serves twice the MMA
+// work.  The kernel takes a scheduler: one problem (pair-tile p -> M-tile
+// pair, N tile), or a work list over several molecules' problems.
 //
 // The two tiles of a pair share one K sequence: the union of their live AO
 // blocks and 16-AO column groups.  A block dead in this CTA's own tile is
@@ -23,6 +25,9 @@
 //              the own half of the C block (a thread's copies complete one
 //              after another, so each operand gets its own issuing warp); the
 //              copies of both CTAs complete on the leader CTA's full barrier.
+//              Each warp builds a 32-chunk window's stage list, one lane walks
+//              it (wait, stage word, copy) and prefetches the next own AO
+//              block into L2.
 //   warp 5     TMEM allocation (cta_group::2, both CTAs); lane 0 of the
 //              leader issues the MMAs and commits them to both CTAs'
 //              barriers (multicast).
