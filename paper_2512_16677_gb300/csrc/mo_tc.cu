@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ uint32_t stage_info[STAGES];  // producer -> MMA, per stage (see kStageFirst)
+  __shared__ uint16_t elist[64];           // producer's stage list (one 32-chunk window)
   __shared__ __align__(16) float epi[4][32][kEpiPitch];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
@@ -272,12 +273,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // and tells the MMA thread, per stage, which k-steps to issue and where
     // tiles begin and end; a tile with no live block still takes one stage
     // (no copies, no MMAs) so that the MMA thread walks stages only.  The
-    // lanes read the mask bytes of 32 chunks at once; lane 0 takes the
-    // barriers and lanes 0 and 1 issue the stage's two copies (AO, C; each
-    // both planes in QK_BF16X3) together.
+    // warp reads the mask bytes of 32 chunks at once and writes that
+    // window's stages as a list in shared memory (entry: K block, bits
+    // 0-9; its live k-steps, bits 10-13); lanes 0 and 1 walk the list
+    // together, lane 0 taking the barriers and the AO copy, lane 1 the C
+    // copy (each both planes in QK_BF16X3).
     constexpr int kPer = kb_per_chunk<MODE>();  // K blocks per chunk
     if (lane == 0) sched.prefetch_maps();
-    uint32_t it = 0;
+    uint32_t it = 0;  // stages taken (lanes 0 and 1)
     bool ok = true;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const TileInfo x = sched.tile(t);
@@ -300,31 +303,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (lastkb >= x.num_kb) lastkb = x.num_kb - 1;  // no mask, odd K block count
       // this lane's copy of a stage: lane 0 the AO tile, lane 1 the C tile
-      const bool copier = lane < 2;
       const CUtensorMap* map = lane ? x.b : x.a;
       const uint32_t dst_off = lane ? TR::kPlanes * S::A_BYTES : 0u;
       const int row0 = lane ? x.n0 : x.m0;
       const uint32_t bn_bits = (uint32_t)(x.bn >> 4) << kStageBnShift;  // on every stage
       uint32_t flags = kStageFirst;
-      // one stage: wait for the slot, post the stage word, issue the copies
-      auto stage = [&](int kb, uint32_t steps, bool last) -> bool {
+      // one stage (lanes 0 and 1): wait for the slot, post the stage word
+      // (lane 0), issue this lane's copy
+      auto stage = [&](int kb, uint32_t steps) -> bool {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         ++it;
-        bool got = true;
-        if (lane == 0) got = mbar_wait(empty_bar(s), ph ^ 1u, abort_v);
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) {
-          if (lane == 0) flag_error(err_flag, abort_v, 1);
+        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
+          flag_error(err_flag, abort_v, 1);
           return false;
         }
         if (lane == 0) {
-          stage_info[s] = steps | flags | bn_bits | (last ? kStageLast : 0u);
+          stage_info[s] = steps | flags | bn_bits | (kb == lastkb ? kStageLast : 0u);
           mbar_expect_tx(full_bar(s), kb >= 0 ? bytes : 0u);
         }
         flags = 0;
-        __syncwarp();
-        if (kb >= 0 && copier) {
+        if (kb >= 0) {
           const uint32_t dst = base + s * S::STAGE_BYTES + dst_off;
           if (lane == 0 && x.ablocked)
             tma_load_3d(dst, map, full_bar(s), 0, 0,
@@ -337,39 +336,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         return true;
       };
       if (lastkb < 0) {
-        ok = stage(-1, 0u, true);
+        if (lane < 2) ok = stage(-1, 0u);
+        ok = __all_sync(0xffffffffu, ok);
         continue;
       }
       for (int q0 = 0; q0 < nq && ok; q0 += 32) {
         const uint32_t g = groups_of(q0 + lane);
-        unsigned live = __ballot_sync(0xffffffffu, g != 0u);
-        while (live && ok) {
-          const int j = __ffs(live) - 1;
-          live &= live - 1u;
-          const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
-          // the AO block of the next live chunk into L2 now, so that its copy
-          // into the ring (a stage later) does not wait on HBM
-          if constexpr (kPer == 1) {
-            if (live && lane == 2) {
-              const int kn = q0 + __ffs(live) - 1;
-              if (x.ablocked)
-                tma_prefetch_l2_3d(x.a, 0, 0, blocked_slice<MODE>(x.m0 / kBM, kn, x.nchunk));
-              else
-                tma_prefetch_l2_3d(x.a, kn * TR::kBK, x.m0, 0);
-            }
-          }
+        uint32_t e[2] = {0u, 0u};
 #pragma unroll
-          for (int h = 0; h < kPer; ++h) {
-            uint32_t steps = gj;
-            if constexpr (kPer == 2) {
-              const uint32_t hh = (gj >> (2 * h)) & 3u;
-              steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+        for (int h = 0; h < kPer; ++h) {
+          uint32_t steps = g;
+          if constexpr (kPer == 2) {
+            const uint32_t hh = (g >> (2 * h)) & 3u;
+            steps = (hh & 1u ? 0x3u : 0u) | (hh & 2u ? 0xCu : 0u);
+          }
+          const int kb = (q0 + lane) * kPer + h;
+          if (steps && kb < x.num_kb) e[h] = (uint32_t)kb | (steps << 10);
+        }
+        const unsigned b0 = __ballot_sync(0xffffffffu, e[0] != 0u);
+        const unsigned b1 = __ballot_sync(0xffffffffu, e[1] != 0u);
+        const unsigned lt = (1u << lane) - 1u;
+        const int pos = __popc(b0 & lt) + __popc(b1 & lt);
+        if (e[0]) elist[pos] = (uint16_t)e[0];
+        if (e[1]) elist[pos + (e[0] ? 1 : 0)] = (uint16_t)e[1];
+        const int n_e = __popc(b0) + __popc(b1);
+        __syncwarp();
+        if (lane < 2) {
+          for (int k = 0; k < n_e && ok; ++k) {
+            const uint32_t v = elist[k];
+            // the next entry's AO block into L2 now, so that its copy into
+            // the ring (a stage later) does not wait on HBM
+            if constexpr (kPer == 1) {
+              if (lane == 0 && k + 1 < n_e) {
+                const int kn = (int)(elist[k + 1] & 0x3FFu);
+                if (x.ablocked)
+                  tma_prefetch_l2_3d(x.a, 0, 0, blocked_slice<MODE>(x.m0 / kBM, kn, x.nchunk));
+                else
+                  tma_prefetch_l2_3d(x.a, kn * TR::kBK, x.m0, 0);
+              }
             }
-            const int kb = (q0 + j) * kPer + h;
-            if (!steps || !ok || kb >= x.num_kb) continue;
-            ok = stage(kb, steps, kb == lastkb);
+            ok = stage((int)(v & 0x3FFu), (v >> 10) & 0xFu);
           }
         }
+        ok = __all_sync(0xffffffffu, ok);  // also: the list may be rewritten
       }
     }
     if (lane == 0 && *abort_v) {
