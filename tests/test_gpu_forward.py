@@ -452,3 +452,26 @@ def test_sm_pairs_every_tile_width(orc, cfg, mode, mo_num):
     assert_within(mode, outs[True], ref, size, f"pairs, {mo_num} MOs")
     diff = np.abs(outs[True] - outs[False]) / (size + 1e-300)
     assert float(diff.max()) <= 1e-6, float(diff.max())
+
+
+def test_spatial_order_is_the_stable_morton_sort(cfg):
+    """The device's point order (one radix sort of the cell keys) equals a
+    stable sort of the same keys done here: cells of a 32^3 grid over the
+    nuclear box +- 4 bohr, from the float coordinates, bits of the three
+    cell indices interleaved x, y, z from the lowest."""
+    m = cfg(2, walk_num=16)
+    c = _ctx(m, "bf16x3")
+    c.mo_vgl_device()
+    torch.cuda.synchronize()
+    perm, _ = c.tile_layout()
+    pts = m.points.astype(np.float32)
+    lo = (m.nucl_coord.min(axis=0) - 4.0).astype(np.float32)
+    hi = (m.nucl_coord.max(axis=0) + 4.0).astype(np.float32)
+    inv = (np.float32(32.0) / np.maximum(hi - lo, np.float32(1e-3))).astype(np.float32)
+    f = (pts - lo) * inv
+    cell = np.where(f <= 0, 0, np.where(f >= 31, 31, np.trunc(f))).astype(np.uint32)
+    key = np.zeros(len(pts), dtype=np.uint32)
+    for bit in range(5):
+        for axis in range(3):
+            key |= ((cell[:, axis] >> bit) & 1) << (3 * bit + axis)
+    np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
