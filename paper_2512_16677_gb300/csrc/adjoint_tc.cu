@@ -32,40 +32,74 @@ __device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16&
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// FP32 [rows][cols] (row stride lds) -> bf16 hi/lo [rows][ld], padding zero.
+// FP32 [rows][cols] (row stride lds) -> bf16 hi/lo [rows][ld] (ld even), padding zero.
 __global__ void split_rows_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
                                   int64_t lds, int64_t ld, __nv_bfloat16* __restrict__ hi,
                                   __nv_bfloat16* __restrict__ lo) {
-  const int64_t n = rows * ld;
+  // two adjacent columns per thread (ld is even), stored as bf16 pairs
+  const int64_t n = rows * ld / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / ld, c = i % ld;
-    split(c < cols ? src[r * lds + c] : 0.0f, hi[i], lo[i]);
+    const int64_t r = 2 * i / ld, c = 2 * i % ld;
+    const float* row = src + r * lds;
+    __nv_bfloat162 hp, lp;
+    split(c < cols ? row[c] : 0.0f, hp.x, lp.x);
+    split(c + 1 < cols ? row[c + 1] : 0.0f, hp.y, lp.y);
+    reinterpret_cast<__nv_bfloat162*>(hi)[i] = hp;
+    reinterpret_cast<__nv_bfloat162*>(lo)[i] = lp;
   }
 }
 
 // FP32 [rows][cols] (row stride lds) -> transposed bf16 hi/lo [cols][ldt]
-// (ldt >= rows, columns past rows zero), through 32 x 32 shared tiles.
+// (ldt >= rows and even, columns past rows zero), through 64 x 64 shared tiles.
 __global__ void __launch_bounds__(256)
     transpose_split_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
-                           int64_t lds, int64_t ldt, __nv_bfloat16* __restrict__ hi,
+                           int64_t lds, int64_t ldt, bool vec, __nv_bfloat16* __restrict__ hi,
                            __nv_bfloat16* __restrict__ lo) {
-  __shared__ float t[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
-  for (int k = ty; k < 32; k += 8) {
-    const int64_t r = r0 + k, c = c0 + tx;
-    t[k][tx] = (r < rows && c < cols) ? src[r * lds + c] : 0.0f;
+  // 64 x 64 tile: rows r0.. of src become columns of out[c][r] = src[r][c].
+  // Loads are float4 along src rows (16 threads per row) when the rows are
+  // 16-byte aligned; stores are bf16 pairs, one warp per output row, so each
+  // warp instruction writes 128 contiguous bytes of each plane.  Columns
+  // r in [rows, ldt) are written as zeros (ldt is even).
+  __shared__ float t[64][65];
+  const int64_t r0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 64;
+  const int q = threadIdx.x & 15, rr = threadIdx.x >> 4;  // 16 x 16 threads
+  if (vec && c0 + 64 <= cols) {
+    for (int k = rr; k < 64; k += 16) {
+      const int64_t r = r0 + k;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) v = __ldg(reinterpret_cast<const float4*>(src + r * lds + c0) + q);
+      t[k][4 * q] = v.x;
+      t[k][4 * q + 1] = v.y;
+      t[k][4 * q + 2] = v.z;
+      t[k][4 * q + 3] = v.w;
+    }
+  } else {
+    for (int k = rr; k < 64; k += 16) {
+      const int64_t r = r0 + k;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t c = c0 + 16 * j + q;
+        t[k][16 * j + q] = (r < rows && c < cols) ? src[r * lds + c] : 0.0f;
+      }
+    }
   }
   __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
-    const int64_t c = c0 + k, r = r0 + tx;  // out[c][r] = src[r][c]
-    if (c < cols && r < ldt) {
-      __nv_bfloat16 h, l;
-      split(t[tx][k], h, l);
-      hi[c * ldt + r] = h;
-      lo[c * ldt + r] = l;
-    }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t r = r0 + 2 * lane;
+  for (int k = w; k < 64; k += 8) {
+    const int64_t c = c0 + k;
+    if (c >= cols || r >= ldt) continue;
+    __nv_bfloat16 h0, l0, h1, l1;
+    split(t[2 * lane][k], h0, l0);
+    split(t[2 * lane + 1][k], h1, l1);
+    __nv_bfloat162 hp, lp;
+    hp.x = h0;
+    hp.y = h1;
+    lp.x = l0;
+    lp.y = l1;
+    *reinterpret_cast<__nv_bfloat162*>(hi + c * ldt + r) = hp;
+    *reinterpret_cast<__nv_bfloat162*>(lo + c * ldt + r) = lp;
   }
 }
 
@@ -166,11 +200,17 @@ cudaError_t launch_adjoint_tc(const float* W, int64_t rows, int64_t mo_num, cons
       (const __nv_bfloat16*)((const unsigned char*)ct + up256(sizeof(__nv_bfloat16) * ao_num * ldw));
 
   // operands in bf16 hi/lo planes
-  split_rows_kernel<<<grid_for(rows * ldw), 256, 0, s>>>(W, rows, mo_num, mo_num, ldw, w_hi, w_lo);
-  const dim3 tw((unsigned)((R + 31) / 32), (unsigned)((mo_num + 31) / 32));
-  transpose_split_kernel<<<tw, 256, 0, s>>>(W, rows, mo_num, mo_num, R, wt_hi, wt_lo);
-  const dim3 ta((unsigned)((R + 31) / 32), (unsigned)((ao_num + 31) / 32));
-  transpose_split_kernel<<<ta, 256, 0, s>>>(ao, rows, ao_num, ld_ao, R, at_hi, at_lo);
+  split_rows_kernel<<<grid_for(rows * ldw / 2), 256, 0, s>>>(W, rows, mo_num, mo_num, ldw, w_hi,
+                                                            w_lo);
+  auto aligned16 = [](const float* q, int64_t ld) {
+    return ((uintptr_t)q & 15) == 0 && ld % 4 == 0;
+  };
+  const dim3 tw((unsigned)((R + 63) / 64), (unsigned)((mo_num + 63) / 64));
+  transpose_split_kernel<<<tw, 256, 0, s>>>(W, rows, mo_num, mo_num, R, aligned16(W, mo_num),
+                                            wt_hi, wt_lo);
+  const dim3 ta((unsigned)((R + 63) / 64), (unsigned)((ao_num + 63) / 64));
+  transpose_split_kernel<<<ta, 256, 0, s>>>(ao, rows, ao_num, ld_ao, R, aligned16(ao, ld_ao),
+                                            at_hi, at_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
