@@ -141,15 +141,29 @@ __global__ void __launch_bounds__(kThreads)
     partial[((int64_t)blockIdx.y * b.shell_num + ch.x) * 3 + i] = s_acc[i];
 }
 
-// Shell totals: sum over the point-tile blocks in a fixed order.  Shells not
-// touched by any block (none here: every chunk writes all its shells) stay 0.
-__global__ void dR_shell_sum_kernel(const double* partial, int blocks, int shell_num,
-                                    double* shell_tot) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= shell_num * 3) return;
+// Shell totals: sum over the point-tile blocks in a fixed order.  A CTA of
+// 32 x 16 threads covers 32 (shell, axis) columns: row ty sums the blocks
+// ty, ty + 16, ... in order, then the 16 row sums are added in order, so
+// the result does not depend on the schedule.  Shells not touched by any
+// block (none here: every chunk writes all its shells) stay 0.
+constexpr int kSumCols = 32, kSumRows = 16;
+__global__ void __launch_bounds__(kSumCols * kSumRows)
+    dR_shell_sum_kernel(const double* partial, int blocks, int shell_num, double* shell_tot) {
+  __shared__ double red[kSumRows][kSumCols];
+  const int tx = threadIdx.x % kSumCols, ty = threadIdx.x / kSumCols;
+  const int i = blockIdx.x * kSumCols + tx;
+  const int n = shell_num * 3;
   double s = 0.0;
-  for (int y = 0; y < blocks; ++y) s += partial[(int64_t)y * shell_num * 3 + i];
-  shell_tot[i] = s;
+  if (i < n)
+    for (int y = ty; y < blocks; y += kSumRows) s += partial[(int64_t)y * n + i];
+  red[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSumRows; ++k) t += red[k][tx];
+    shell_tot[i] = t;
+  }
 }
 
 // dR[A][j] = - sum over shells of A (in shell order).
@@ -190,8 +204,8 @@ cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode, c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   double* shell_tot = partial + (size_t)3 * b.shell_num * blocks;
-  dR_shell_sum_kernel<<<(b.shell_num * 3 + 255) / 256, 256, 0, s>>>(partial, blocks,
-                                                                    b.shell_num, shell_tot);
+  dR_shell_sum_kernel<<<(b.shell_num * 3 + kSumCols - 1) / kSumCols, kSumCols * kSumRows, 0, s>>>(
+      partial, blocks, b.shell_num, shell_tot);
   dR_nucleus_sum_kernel<<<(b.nucl_num * 3 + 255) / 256, 256, 0, s>>>(
       shell_tot, b.shell_nuc, b.shell_num, b.nucl_num, d_dR);
   return cudaGetLastError();
