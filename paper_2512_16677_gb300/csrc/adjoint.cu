@@ -38,6 +38,83 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// The gradient terms of shell s at point ip: g += sum over the shell's AOs
+// j of M_j (Abar_v grad chi + sum_i Abar_i grad d_i chi + Abar_lap grad lap
+// chi), with ab0 the Abar entry (value component) of the shell's first AO
+// and ld the distance between components.
+template <typename T>
+__device__ __forceinline__ void dR_point_shell(const BasisDev& b, const PointsDev& pts,
+                                               int64_t ip, int s, const T* ab0, int64_t ld,
+                                               T Tthr, T g[3]) {
+  using A = Arith<T>;
+  T dx, dy, dz;
+  A::diff(b, pts, ip, b.shell_nuc[s], dx, dy, dz);
+  const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
+  T S0 = T(0), S1 = T(0), S2 = T(0), S3 = T(0);
+  if (r2 < A::r2max(b, s)) {
+    const int k0 = b.shell_prim0[s];
+    const int k1 = k0 + b.shell_nprim[s];
+    for (int k = k0; k < k1; ++k) {
+      const T gm = A::gam(b, k);
+      const T t = A::mul(gm, r2);
+      if (!(t < Tthr)) break;
+      const T ce = A::coef(b, k) * A::ex(-t);
+      S0 += ce;
+      S1 += gm * ce;
+      S2 += gm * gm * ce;
+      S3 += gm * gm * gm * ce;
+    }
+  }
+  if (S0 == T(0) && S1 == T(0) && S2 == T(0) && S3 == T(0)) return;
+  const int l = b.shell_l[s];
+  const int ao0 = b.shell_ao0[s];
+  const int nc = (l + 1) * (l + 2) / 2;
+  const T d[3] = {dx, dy, dz};
+  const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
+  const T k1 = T(2 * (2 * l + 3));
+  for (int j = 0; j < nc; ++j) {
+    const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
+    // 1-D factors of P and their derivatives up to third order
+    const T X[4] = {sel4(a, T(1), dx, x2, x2 * dx), sel4(a, T(0), T(1), T(2) * dx, T(3) * x2),
+                    sel4(a, T(0), T(0), T(2), T(6) * dx), sel4(a, T(0), T(0), T(0), T(6))};
+    const T Y[4] = {sel4(bb, T(1), dy, y2, y2 * dy), sel4(bb, T(0), T(1), T(2) * dy, T(3) * y2),
+                    sel4(bb, T(0), T(0), T(2), T(6) * dy), sel4(bb, T(0), T(0), T(0), T(6))};
+    const T Z[4] = {sel4(c, T(1), dz, z2, z2 * dz), sel4(c, T(0), T(1), T(2) * dz, T(3) * z2),
+                    sel4(c, T(0), T(0), T(2), T(6) * dz), sel4(c, T(0), T(0), T(0), T(6))};
+    const T P = X[0] * Y[0] * Z[0];
+    const T Pi[3] = {X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1]};
+    // Pij[i][j] symmetric
+    const T Pxx = X[2] * Y[0] * Z[0], Pyy = X[0] * Y[2] * Z[0], Pzz = X[0] * Y[0] * Z[2];
+    const T Pxy = X[1] * Y[1] * Z[0], Pxz = X[1] * Y[0] * Z[1], Pyz = X[0] * Y[1] * Z[1];
+    const T Pij[3][3] = {{Pxx, Pxy, Pxz}, {Pxy, Pyy, Pyz}, {Pxz, Pyz, Pzz}};
+    const T lapP = Pxx + Pyy + Pzz;
+    const T lapPj[3] = {X[3] * Y[0] * Z[0] + X[1] * Y[2] * Z[0] + X[1] * Y[0] * Z[2],
+                        X[2] * Y[1] * Z[0] + X[0] * Y[3] * Z[0] + X[0] * Y[1] * Z[2],
+                        X[2] * Y[0] * Z[1] + X[0] * Y[2] * Z[1] + X[0] * Y[0] * Z[3]};
+    const T M = A::aofac(b, ao0 + j);
+    const T* ab = ab0 + j;
+    const T Av = ab[0], Ag[3] = {ab[ld], ab[2 * ld], ab[3 * ld]}, Al = ab[4 * ld];
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) {
+      const T dj = d[jj];
+      T G = Av * (Pi[jj] * S0 - T(2) * dj * P * S1);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T h = Pij[i][jj] * S0 - T(2) * (d[i] * Pi[jj] + dj * Pi[i]) * S1 +
+                    T(4) * d[i] * dj * P * S2 - (i == jj ? T(2) * P * S1 : T(0));
+        G += Ag[i] * h;
+      }
+      const T tl = lapPj[jj] * S0 - T(2) * dj * lapP * S1 - k1 * Pi[jj] * S1 +
+                   (T(2) * k1 + T(8)) * dj * P * S2 + T(4) * r2 * Pi[jj] * S2 -
+                   T(8) * r2 * dj * P * S3;
+      G += Al * tl;
+      g[jj] += M * G;
+    }
+  }
+}
+
+// Abar dense [5P][ld] in the points' order: CTA (chunk, point-tile block y)
+// over point tiles y, y + gridDim.y, ...
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     adjoint_dR_kernel(BasisDev b, PointsDev pts, const T* __restrict__ abar, int64_t ld,
@@ -60,74 +137,51 @@ __global__ void __launch_bounds__(kThreads)
       const int64_t ip = p0 + pl;
       const int s = ch.x + sl;
       T g[3] = {T(0), T(0), T(0)};
-      if (ip < pts.n) {
-        T dx, dy, dz;
-        A::diff(b, pts, ip, b.shell_nuc[s], dx, dy, dz);
-        const T r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
-        T S0 = T(0), S1 = T(0), S2 = T(0), S3 = T(0);
-        if (r2 < A::r2max(b, s)) {
-          const int k0 = b.shell_prim0[s];
-          const int k1 = k0 + b.shell_nprim[s];
-          for (int k = k0; k < k1; ++k) {
-            const T gm = A::gam(b, k);
-            const T t = A::mul(gm, r2);
-            if (!(t < Tthr)) break;
-            const T ce = A::coef(b, k) * A::ex(-t);
-            S0 += ce;
-            S1 += gm * ce;
-            S2 += gm * gm * ce;
-            S3 += gm * gm * gm * ce;
-          }
-        }
-        if (S0 != T(0) || S1 != T(0) || S2 != T(0) || S3 != T(0)) {
-          const int l = b.shell_l[s];
-          const int ao0 = b.shell_ao0[s];
-          const int nc = (l + 1) * (l + 2) / 2;
-          const T d[3] = {dx, dy, dz};
-          const T x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
-          const T k1 = T(2 * (2 * l + 3));
-          const T* row = abar + 5 * ip * ld;
-          for (int j = 0; j < nc; ++j) {
-            const int a = c_pow[l][j][0], bb = c_pow[l][j][1], c = c_pow[l][j][2];
-            // 1-D factors of P and their derivatives up to third order
-            const T X[4] = {sel4(a, T(1), dx, x2, x2 * dx), sel4(a, T(0), T(1), T(2) * dx, T(3) * x2),
-                            sel4(a, T(0), T(0), T(2), T(6) * dx), sel4(a, T(0), T(0), T(0), T(6))};
-            const T Y[4] = {sel4(bb, T(1), dy, y2, y2 * dy), sel4(bb, T(0), T(1), T(2) * dy, T(3) * y2),
-                            sel4(bb, T(0), T(0), T(2), T(6) * dy), sel4(bb, T(0), T(0), T(0), T(6))};
-            const T Z[4] = {sel4(c, T(1), dz, z2, z2 * dz), sel4(c, T(0), T(1), T(2) * dz, T(3) * z2),
-                            sel4(c, T(0), T(0), T(2), T(6) * dz), sel4(c, T(0), T(0), T(0), T(6))};
-            const T P = X[0] * Y[0] * Z[0];
-            const T Pi[3] = {X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1]};
-            // Pij[i][j] symmetric
-            const T Pxx = X[2] * Y[0] * Z[0], Pyy = X[0] * Y[2] * Z[0], Pzz = X[0] * Y[0] * Z[2];
-            const T Pxy = X[1] * Y[1] * Z[0], Pxz = X[1] * Y[0] * Z[1], Pyz = X[0] * Y[1] * Z[1];
-            const T Pij[3][3] = {{Pxx, Pxy, Pxz}, {Pxy, Pyy, Pyz}, {Pxz, Pyz, Pzz}};
-            const T lapP = Pxx + Pyy + Pzz;
-            const T lapPj[3] = {X[3] * Y[0] * Z[0] + X[1] * Y[2] * Z[0] + X[1] * Y[0] * Z[2],
-                                X[2] * Y[1] * Z[0] + X[0] * Y[3] * Z[0] + X[0] * Y[1] * Z[2],
-                                X[2] * Y[0] * Z[1] + X[0] * Y[2] * Z[1] + X[0] * Y[0] * Z[3]};
-            const T M = A::aofac(b, ao0 + j);
-            const T* ab = row + ao0 + j;
-            const T Av = ab[0], Ag[3] = {ab[ld], ab[2 * ld], ab[3 * ld]}, Al = ab[4 * ld];
+      if (ip < pts.n) dR_point_shell(b, pts, ip, s, abar + 5 * ip * ld + b.shell_ao0[s], ld, Tthr, g);
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) {
-              const T dj = d[jj];
-              T G = Av * (Pi[jj] * S0 - T(2) * dj * P * S1);
+      for (int jj = 0; jj < 3; ++jj) g[jj] = warp_sum(g[jj]);
+      if (lane == 0) {
 #pragma unroll
-              for (int i = 0; i < 3; ++i) {
-                const T h = Pij[i][jj] * S0 - T(2) * (d[i] * Pi[jj] + dj * Pi[i]) * S1 +
-                            T(4) * d[i] * dj * P * S2 - (i == jj ? T(2) * P * S1 : T(0));
-                G += Ag[i] * h;
-              }
-              const T tl = lapPj[jj] * S0 - T(2) * dj * lapP * S1 - k1 * Pi[jj] * S1 +
-                           (T(2) * k1 + T(8)) * dj * P * S2 + T(4) * r2 * Pi[jj] * S2 -
-                           T(8) * r2 * dj * P * S3;
-              G += Al * tl;
-              g[jj] += M * G;
-            }
-          }
-        }
+        for (int jj = 0; jj < 3; ++jj) s_acc[3 * sl + jj] += (double)g[jj];
       }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ns * 3; i += kThreads)
+    partial[((int64_t)blockIdx.y * b.shell_num + ch.x) * 3 + i] = s_acc[i];
+}
+
+// Abar in live (tile, chunk) blocks [tiles][nchunk][128][64] (FP32), the
+// points in the tiles' order (25 per tile, rows 5 j + c): CTA (chunk,
+// block y) over the tiles y, y + gridDim.y, ... where the chunk is live.
+__global__ void __launch_bounds__(kThreads)
+    adjoint_dR_blocked_kernel(BasisDev b, PointsDev pts, const float* __restrict__ abar,
+                              const uint8_t* __restrict__ mask, int64_t tiles,
+                              double* __restrict__ partial) {
+  using A = Arith<float>;
+  __shared__ double s_acc[kChunkAO * 3];
+  const int q = blockIdx.x;
+  const int4 ch = b.chunk[q];
+  const int ns = ch.y - ch.x;
+  for (int i = threadIdx.x; i < kChunkAO * 3; i += kThreads) s_acc[i] = 0.0;
+  __syncthreads();
+  const float Tthr = A::thr(b);
+  const int lane = threadIdx.x & 31;
+  const int mld = mask_ld(b.nchunk);
+
+  for (int64_t t = blockIdx.y; t < tiles; t += gridDim.y) {
+    if (!(mask[t * mld + q] & 0xFu)) continue;  // no AO of the chunk reaches the tile
+    const float* blk = abar + (t * b.nchunk + q) * (int64_t)(kTileRows * kChunkAO);
+    // one shell per warp iteration; lanes past the tile's 25 points idle
+    for (int idx = threadIdx.x; idx < kPT * ns; idx += kThreads) {
+      const int pl = idx % kPT;
+      const int sl = idx / kPT;
+      const int64_t ip = t * kTilePoints + pl;
+      const int s = ch.x + sl;
+      float g[3] = {0.0f, 0.0f, 0.0f};
+      if (pl < kTilePoints && ip < pts.n)
+        dR_point_shell(b, pts, ip, s, blk + 5 * pl * kChunkAO + (b.shell_ao0[s] - ch.z),
+                       (int64_t)kChunkAO, Tthr, g);
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) g[jj] = warp_sum(g[jj]);
       if (lane == 0) {
@@ -166,16 +220,30 @@ __global__ void __launch_bounds__(kSumCols * kSumRows)
   }
 }
 
-// dR[A][j] = - sum over shells of A (in shell order).
+// dR[A][j] = - sum over shells of A: a warp per (A, j), lane i adding the
+// shells i, i + 32, ... of A in order, then a fixed shuffle tree.
 __global__ void dR_nucleus_sum_kernel(const double* shell_tot, const int* shell_nuc,
                                       int shell_num, int nucl_num, double* dR) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nucl_num * 3) return;
-  const int A = i / 3, j = i % 3;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nucl_num * 3) return;  // whole warps leave together
+  const int A = w / 3, j = w % 3;
   double s = 0.0;
-  for (int sh = 0; sh < shell_num; ++sh)
+  for (int sh = lane; sh < shell_num; sh += 32)
     if (shell_nuc[sh] == A) s += shell_tot[3 * sh + j];
-  dR[i] = -s;
+  s = warp_sum(s);
+  if (lane == 0) dR[w] = -s;
+}
+
+// Partials [blocks][shell][3] -> shell totals -> d_dR [nucl][3].
+cudaError_t reduce_dR(const BasisDev& b, double* partial, int blocks, double* d_dR,
+                      cudaStream_t s) {
+  double* shell_tot = partial + (size_t)3 * b.shell_num * blocks;
+  dR_shell_sum_kernel<<<(b.shell_num * 3 + kSumCols - 1) / kSumCols, kSumCols * kSumRows, 0, s>>>(
+      partial, blocks, b.shell_num, shell_tot);
+  dR_nucleus_sum_kernel<<<(b.nucl_num * 3 + 7) / 8, 256, 0, s>>>(shell_tot, b.shell_nuc,
+                                                                 b.shell_num, b.nucl_num, d_dR);
+  return cudaGetLastError();
 }
 
 int tile_blocks(int64_t point_num) {
@@ -203,12 +271,22 @@ cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode, c
                                                        n_ptiles);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  double* shell_tot = partial + (size_t)3 * b.shell_num * blocks;
-  dR_shell_sum_kernel<<<(b.shell_num * 3 + kSumCols - 1) / kSumCols, kSumCols * kSumRows, 0, s>>>(
-      partial, blocks, b.shell_num, shell_tot);
-  dR_nucleus_sum_kernel<<<(b.nucl_num * 3 + 255) / 256, 256, 0, s>>>(
-      shell_tot, b.shell_nuc, b.shell_num, b.nucl_num, d_dR);
-  return cudaGetLastError();
+  return reduce_dR(b, partial, blocks, d_dR, s);
+}
+
+cudaError_t launch_adjoint_dR_blocked(const BasisDev& b, const PointsDev& p, const float* abar,
+                                      const uint8_t* mask, double* partial, double* d_dR,
+                                      cudaStream_t s) {
+  // point-tile blocks as for the dense kernel (the partial buffer's size);
+  // never more than the 25-point tiles
+  const int blocks = tile_blocks(p.n);
+  const int64_t tiles = (p.n + kTilePoints - 1) / kTilePoints;
+  if (b.nchunk == 0 || p.n == 0) return cudaSuccess;
+  dim3 grid((unsigned)b.nchunk, (unsigned)blocks);
+  adjoint_dR_blocked_kernel<<<grid, kThreads, 0, s>>>(b, p, abar, mask, tiles, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return reduce_dR(b, partial, blocks, d_dR, s);
 }
 
 }  // namespace qk

@@ -114,6 +114,7 @@ struct qk_context_s {
   void* ao_ws = nullptr;
   bool ao_sorted = false;
   bool ao_pairs = false;  // the AO tensor holds the zeros a pair contraction reads
+  bool ao_zeroed = false;  // its dead groups of live blocks hold zeros (adjoint)
   // host-output staging, device error word, backward scratch
   DevBuf d_out;
   cudaStream_t copy_stream = nullptr;   // device -> host copies of output ranges
@@ -136,7 +137,7 @@ struct qk_context_s {
   double* cusp_f64 = nullptr;
   float* cusp_f32 = nullptr;
   uint64_t mo_version = 0;  // bumped by every upload of C
-  DevBuf d_ct;              // C^T bf16 hi/lo planes for the split-bf16 adjoint
+  DevBuf d_ct;              // C^T bf16 hi/lo planes (chunked order) for the split-bf16 adjoint
   uint64_t ct_version = ~0ull;
   // C blocked for the pair contraction (per upload of C, tile width and mode)
   DevBuf d_cpair;
@@ -668,6 +669,7 @@ void mark_ao(qk_context c, const AOTensor& ao, bool sorted) {
   c->ao_version = c->basis_version;
   c->ao_sorted = sorted;
   c->ao_pairs = ao.pair_zero;
+  c->ao_zeroed = false;
 }
 
 // Whether the device path cuts its tiles from a spatial point order.
@@ -1691,8 +1693,10 @@ qk_status qk_get_timing(qk_context c, double* ms, int64_t* launches, int32_t n) 
 
 namespace {
 
-// Layout of the backward scratch: recomputed AO tensor, Abar (both
-// [5P][ld]), split-K partials of dL/dC, then the dR partials.
+// Layout of the backward scratch.  FP64 / FP32: recomputed AO tensor, Abar
+// (both [5P][ld]), split-K partials of dL/dC, then the dR partials.
+// Split bf16: the block-sparse products' scratch (the AO tensor is the
+// forward's, in the workspace), then the dR partials.
 struct BwdLayout {
   size_t ao, abar, dc, dr, total;
   int k_split;
@@ -1701,6 +1705,14 @@ struct BwdLayout {
 
 BwdLayout bwd_layout(qk_context c) {
   BwdLayout L{};
+  if (c->mode == QK_BF16X3) {
+    L.tc = true;
+    L.dc = 0;
+    L.dr = align_up(adjoint_sparse_scratch_bytes(c->point_num, (int)c->chunks.size(), c->mo_num),
+                    256);
+    L.total = L.dr + align_up(adjoint_dR_partial_bytes(c->bdev, c->point_num), 256);
+    return L;
+  }
   const bool f64 = c->mode == QK_FP64;
   const size_t es = f64 ? sizeof(double) : sizeof(float);
   const int64_t rows = 5 * c->point_num, ld = round_up8(c->ao_num);
@@ -1713,12 +1725,10 @@ BwdLayout bwd_layout(qk_context c) {
   if (ks > kmax) ks = kmax;
   if (ks < 1) ks = 1;
   L.k_split = (int)ks;
-  L.tc = c->mode == QK_BF16X3;
   L.ao = 0;
   L.abar = align_up(rows * ld * es, 256);
   L.dc = L.abar + align_up(rows * ld * es, 256);
-  L.dr = L.dc + (L.tc ? align_up(adjoint_tc_scratch_bytes(rows, c->mo_num, c->ao_num), 256)
-                      : align_up((size_t)ks * c->mo_num * c->ao_num * es, 256));
+  L.dr = L.dc + align_up((size_t)ks * c->mo_num * c->ao_num * es, 256);
   L.total = L.dr + align_up(adjoint_dR_partial_bytes(c->bdev, c->point_num), 256);
   return L;
 }
@@ -1886,6 +1896,13 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
   st = ensure_mo(c);
   if (st) return st;
   const BwdLayout L = bwd_layout(c);
+  // split bf16: the forward's AO tensor of the current points (computed
+  // here if the last forward pass did not leave it in the workspace)
+  AOTensor fao{};
+  if (L.tc) {
+    st = provide_ao(c, &fao);
+    if (st) return st;
+  }
   // scratch: behind the forward's AO tensor in the caller's workspace when it
   // is large enough, else library-owned
   unsigned char* base = nullptr;
@@ -1909,27 +1926,26 @@ qk_status qk_mo_vgl_backward_device(qk_context c, const void* dW, int64_t size, 
   double* drp = (double*)(base + L.dr);
   cudaError_t e;
   TimedLaunch timer(c, 2);
-  // 1. AO values recomputed, not kept from the forward pass
-  e = launch_ao_vgl(c->bdev, c->pdev, f64 ? QK_FP64 : QK_FP32, ao, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "backward ao_vgl");
   if (L.tc) {
-    // 2-3. split bf16 on the tensor cores: Abar = W . C and dL/dC = W^T . AO
+    // split bf16 on the tensor cores over the live blocks of the forward's
+    // AO tensor: dL/dC = W^T . AO, Abar = W . C at the live blocks, dL/dR
     if (c->ct_version != c->mo_version || !c->d_ct.p) {
-      e = c->d_ct.ensure(adjoint_tc_ct_bytes(N, K));
-      if (e == cudaSuccess) e = launch_adjoint_ct_split(c->c64, N, K, c->d_ct.p, c->stream);
+      const int nq = (int)c->chunks.size();
+      e = c->d_ct.ensure(adjoint_sparse_ctk_bytes(nq, N));
+      if (e == cudaSuccess) e = launch_adjoint_ctk_split(c->c64p, N, nq, c->d_ct.p, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "backward C^T planes");
       c->ct_version = c->mo_version;
     }
-    e = launch_adjoint_tc((const float*)dW, rows, N, (const float*)ao.a, ld, K, c->d_ct.p,
-                          (float*)abar, d_dC, c->bdev.ao_caller, dcp, (int*)c->d_flag.p,
-                          c->stream);
+    const PointsDev& tp = c->ao_sorted ? c->psort : c->pdev;  // the tiles' points
+    e = launch_adjoint_sparse(c->bdev, tp, fao, (const float*)dW, N, c->d_ct.p, !c->ao_zeroed,
+                              d_dC, d_dR, base + L.dc, drp, (int*)c->d_flag.p, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "backward tensor-core products");
-    if (d_dR) {
-      e = launch_adjoint_dR(c->bdev, c->pdev, QK_FP32, abar, K, drp, d_dR, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "backward dL/dR");
-    }
+    c->ao_zeroed = true;
     return QK_SUCCESS;
   }
+  // 1. AO values recomputed, not kept from the forward pass
+  e = launch_ao_vgl(c->bdev, c->pdev, f64 ? QK_FP64 : QK_FP32, ao, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward ao_vgl");
   // 2. Abar[row][k] = sum_i W[row][i] C[i][k]
   if (f64)
     e = launch_gemm_f64(rows, K, N, (const double*)dW, N, 1, c->c64, 1, K, (double*)abar, ld, 1,

@@ -479,6 +479,31 @@ cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
                               const void* abar, int64_t ld, double* partial, double* d_dR,
                               cudaStream_t s);
 size_t adjoint_dR_partial_bytes(const BasisDev& b, int64_t point_num);
+// The same from Abar in live (tile, chunk) blocks [tiles][nchunk][128][64]
+// (FP32) of the blocked AO tensor whose mask is `mask`; p: the points in the
+// tiles' order.
+cudaError_t launch_adjoint_dR_blocked(const BasisDev& b, const PointsDev& p, const float* abar,
+                                      const uint8_t* mask, double* partial, double* d_dR,
+                                      cudaStream_t s);
+
+// Split-bf16 adjoint over the forward's blocked AO tensor (adjoint_sparse.cu).
+// ctk: C^T hi/lo planes in the chunked column order, made from C [mo][kpad]
+// (FP64) by launch_adjoint_ctk_split (adjoint_sparse_ctk_bytes).  Then, for
+// W [P][5][mo] (FP32, the caller's points), the AO tensor `ao` (tiled,
+// blocked, bf16 hi/lo, mask; ao.perm the tiles' points) and p the points in
+// the tiles' order: d_dC [mo][ao] (FP64, the caller's AO order; NULL: not
+// formed) and d_dR [nucl][3] (NULL: not formed).  zero_groups: zero the
+// dead groups of live blocks first (once per AO tensor: the forward leaves
+// them unwritten).  scratch: adjoint_sparse_scratch_bytes; dr_partial:
+// adjoint_dR_partial_bytes.
+size_t adjoint_sparse_ctk_bytes(int nchunk, int64_t mo_num);
+cudaError_t launch_adjoint_ctk_split(const double* C64p, int64_t mo_num, int nchunk, void* ctk,
+                                     cudaStream_t s);
+size_t adjoint_sparse_scratch_bytes(int64_t point_num, int nchunk, int64_t mo_num);
+cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const AOTensor& ao,
+                                  const float* W, int64_t mo_num, const void* ctk, bool zero_groups,
+                                  double* d_dC, double* d_dR, void* scratch, double* dr_partial,
+                                  int* err_flag, cudaStream_t s);
 
 // Fused AO + MO evaluation (split-bf16): live-chunk lists per 25-point tile,
 // then one persistent kernel that builds AO blocks in shared memory and

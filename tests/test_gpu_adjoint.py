@@ -5,7 +5,8 @@ Error metric: |gpu - oracle| / size, with the oracle's term-wise size of
 each gradient entry (the same cancellation-aware normwise idea as the
 forward).  FP64 bar 1e-12.  The fp32 mode (and tf32, which shares it) runs
 the adjoint products as FP32 SIMT GEMMs; bf16x3 runs them on the tensor
-cores in split bf16.  Each carries the per-output bar of ADJ_TOL.
+cores in split bf16 over the live blocks of the forward's AO tensor.  Each
+carries the per-output bar of ADJ_TOL.
 """
 import json
 import os
@@ -25,7 +26,8 @@ pytestmark = pytest.mark.gpu
 # bf16x3: every product term of Abar = W C and dL/dC = W^T AO loses at most
 #   3 * 2^-18 = 1.1e-5 of |w||x| to the split (dropped lo*lo, residuals of
 #   both splits); the AO tensor keeps the FP32 forward's bar (3e-5); the FP32
-#   tensor-core accumulation over slices of <= ~4000 rows adds ~1e-5 in
+#   tensor-core accumulation over slices of <= 4096 rows (32 tiles; more
+#   only past 64 MB of partials, far above these cases) adds ~1e-5 in
 #   practice, then slices are summed in FP64 -> dL/dC 1e-4.  dL/dR_nuc takes
 #   Abar (1.1e-5) through the same FP32 third-derivative kernel as fp32 ->
 #   2e-4.
@@ -95,6 +97,50 @@ def test_adjoint_chain_full_size_sparse_weights(orc, cfg, mode):
     W[idx] = synth.random_weights(rng, idx.size, m.mo_num)
     dC, dR, sC, sR = orc.adjoint(m, W[idx], points=m.points[idx], sizes=True)
     _check("chain50_full_sparse", mode, _gpu_grad(m, W, mode), (dC, dR), (sC, sR))
+
+
+def test_split_bf16_adjoint_organic_two_n_tiles(orc, cfg):
+    """Organic chain, 8 walkers (4800 points, 192 tiles), 1650 AOs in 27
+    chunks (an odd count: the last chunk pair has one chunk) and 300 MOs (two
+    N tiles of the dL/dC product), loss weights on 64 sampled points."""
+    m = cfg(2, walk_num=8)
+    rng = np.random.default_rng(48)
+    idx = np.sort(rng.choice(m.point_num, 64, replace=False))
+    W = np.zeros((m.point_num, 5, m.mo_num))
+    W[idx] = synth.random_weights(rng, idx.size, m.mo_num)
+    dC, dR, sC, sR = orc.adjoint(m, W[idx], points=m.points[idx], sizes=True)
+    _check("organic_8w_sparse", "bf16x3", _gpu_grad(m, W, "bf16x3"), (dC, dR), (sC, sR))
+
+
+def test_split_bf16_adjoint_reuses_the_forward_ao(cfg):
+    """The split-bf16 backward over the forward's own AO tensor (right after a
+    forward pass), again (its dead groups already zeroed), and on a fresh
+    context that computes the AO tensor for the backward: bit for bit equal."""
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(3, walk_num=4)
+    W = synth.random_weights(np.random.default_rng(49), m.point_num, m.mo_num)
+    dW = torch.from_numpy(W.reshape(m.walk_num, m.elec_num, 5, m.mo_num)).float().cuda()
+    coord = torch.from_numpy(m.coord).cuda()
+    c = qmckl.Context("bf16x3")
+    c.set_molecule(m)
+    c.set_points_device(coord)
+    c.mo_vgl_device()
+    first = [t.cpu().numpy() for t in c.backward_device(dW)]
+    second = [t.cpu().numpy() for t in c.backward_device(dW)]
+    fresh = [t.cpu().numpy() for t in _gpu_grad_t(m, dW)]
+    for a, b, f in zip(first, second, fresh):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, f)
+
+
+def _gpu_grad_t(m, dW):
+    from paper_2512_16677_gb300 import qmckl
+    c = qmckl.Context("bf16x3")
+    c.set_molecule(m)
+    c.set_points_device(torch.from_numpy(m.coord).cuda())
+    out = c.backward_device(dW)
+    torch.cuda.synchronize()
+    return out
 
 
 def test_adjoint_vs_gpu_finite_differences(cfg):
