@@ -154,44 +154,82 @@ __global__ void __launch_bounds__(kThreads)
 // Abar in live (tile, chunk) blocks [tiles][nchunk][128][64] (FP32), the
 // points in the tiles' order (25 per tile, rows 5 j + c): CTA (chunk,
 // block y) over the tiles y, y + gridDim.y, ... where the chunk is live.
-__global__ void __launch_bounds__(kThreads)
+// Per tile the (point, shell) pairs that pass the radius test are listed
+// first, so that the threads take only pairs with work (about a third of a
+// live block's pairs on a chain); each pair's gradient goes to its own
+// shared slot and the slots are added per shell in point order.
+constexpr int kBlkThreads = 256;
+__global__ void __launch_bounds__(kBlkThreads, 3)
     adjoint_dR_blocked_kernel(BasisDev b, PointsDev pts, const float* __restrict__ abar,
                               const uint8_t* __restrict__ mask, int64_t tiles,
                               double* __restrict__ partial) {
   using A = Arith<float>;
-  __shared__ double s_acc[kChunkAO * 3];
+  __shared__ double s_acc[kMaxShellsChunk * 3];
+  __shared__ float gbuf[kMaxShellsChunk][kTilePoints][3];
+  __shared__ uint16_t list[kMaxShellsChunk * kTilePoints];
+  __shared__ int cnt;
   const int q = blockIdx.x;
   const int4 ch = b.chunk[q];
   const int ns = ch.y - ch.x;
-  for (int i = threadIdx.x; i < kChunkAO * 3; i += kThreads) s_acc[i] = 0.0;
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < kMaxShellsChunk * 3; i += kBlkThreads) s_acc[i] = 0.0;
   const float Tthr = A::thr(b);
-  const int lane = threadIdx.x & 31;
   const int mld = mask_ld(b.nchunk);
 
   for (int64_t t = blockIdx.y; t < tiles; t += gridDim.y) {
     if (!(mask[t * mld + q] & 0xFu)) continue;  // no AO of the chunk reaches the tile
     const float* blk = abar + (t * b.nchunk + q) * (int64_t)(kTileRows * kChunkAO);
-    // one shell per warp iteration; lanes past the tile's 25 points idle
-    for (int idx = threadIdx.x; idx < kPT * ns; idx += kThreads) {
-      const int pl = idx % kPT;
-      const int sl = idx / kPT;
-      const int64_t ip = t * kTilePoints + pl;
+    __syncthreads();  // the previous tile's slots are summed
+    if (tid == 0) cnt = 0;
+    for (int i = tid; i < ns * kTilePoints * 3; i += kBlkThreads) (&gbuf[0][0][0])[i] = 0.0f;
+    __syncthreads();
+    // pairs that pass the radius test (the same test the gradient makes)
+    for (int base = 0; base < ns * kTilePoints; base += kBlkThreads) {
+      const int idx = base + tid;
+      bool pass = false;
+      int pl = 0, sl = 0;
+      if (idx < ns * kTilePoints) {
+        pl = idx % kTilePoints;
+        sl = idx / kTilePoints;
+        const int64_t ip = t * kTilePoints + pl;
+        if (ip < pts.n) {
+          const int s = ch.x + sl;
+          float dx, dy, dz;
+          A::diff(b, pts, ip, b.shell_nuc[s], dx, dy, dz);
+          const float r2 = A::add(A::add(A::mul(dx, dx), A::mul(dy, dy)), A::mul(dz, dz));
+          pass = r2 < A::r2max(b, s);
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      int at = 0;
+      if (lane == 0 && bal) at = atomicAdd(&cnt, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (pass) list[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(pl | (sl << 5));
+    }
+    __syncthreads();
+    const int n_pairs = cnt;
+    for (int k = tid; k < n_pairs; k += kBlkThreads) {
+      const int e = list[k];
+      const int pl = e & 31, sl = e >> 5;
       const int s = ch.x + sl;
       float g[3] = {0.0f, 0.0f, 0.0f};
-      if (pl < kTilePoints && ip < pts.n)
-        dR_point_shell(b, pts, ip, s, blk + 5 * pl * kChunkAO + (b.shell_ao0[s] - ch.z),
-                       (int64_t)kChunkAO, Tthr, g);
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) g[jj] = warp_sum(g[jj]);
-      if (lane == 0) {
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) s_acc[3 * sl + jj] += (double)g[jj];
-      }
+      dR_point_shell(b, pts, t * kTilePoints + pl, s,
+                     blk + 5 * pl * kChunkAO + (b.shell_ao0[s] - ch.z), (int64_t)kChunkAO, Tthr, g);
+      gbuf[sl][pl][0] = g[0];
+      gbuf[sl][pl][1] = g[1];
+      gbuf[sl][pl][2] = g[2];
+    }
+    __syncthreads();
+    for (int i = tid; i < ns * 3; i += kBlkThreads) {
+      const int sl = i / 3, ax = i % 3;
+      float sum = 0.0f;
+#pragma unroll 5
+      for (int pl = 0; pl < kTilePoints; ++pl) sum += gbuf[sl][pl][ax];
+      s_acc[i] += (double)sum;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < ns * 3; i += kThreads)
+  for (int i = tid; i < ns * 3; i += kBlkThreads)
     partial[((int64_t)blockIdx.y * b.shell_num + ch.x) * 3 + i] = s_acc[i];
 }
 
@@ -283,7 +321,7 @@ cudaError_t launch_adjoint_dR_blocked(const BasisDev& b, const PointsDev& p, con
   const int64_t tiles = (p.n + kTilePoints - 1) / kTilePoints;
   if (b.nchunk == 0 || p.n == 0) return cudaSuccess;
   dim3 grid((unsigned)b.nchunk, (unsigned)blocks);
-  adjoint_dR_blocked_kernel<<<grid, kThreads, 0, s>>>(b, p, abar, mask, tiles, partial);
+  adjoint_dR_blocked_kernel<<<grid, kBlkThreads, 0, s>>>(b, p, abar, mask, tiles, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return reduce_dR(b, partial, blocks, d_dR, s);

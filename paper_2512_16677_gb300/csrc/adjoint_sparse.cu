@@ -370,31 +370,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // dL/dC [mo][ao] (FP64, the caller's AO order) = sum over slices of the
-// partials in a fixed order: a CTA of 32 x 16 threads takes one AO and 32
-// MOs; row ty adds the slices ty, ty + 16, ... in order (reads along the
-// MOs), then the 16 row sums are added in order.
-constexpr int kRedCols = 32, kRedRows = 16;
-__global__ void __launch_bounds__(kRedCols * kRedRows)
-    reduce_dct_kernel(const float* __restrict__ part, int slices, int64_t kpad, int ldp,
-                      int64_t mo, const int* ao_shell, const int* shell_chunk, const int4* chunk,
-                      const int* ao_caller, int64_t ao_num, double* __restrict__ dC) {
-  __shared__ double red[kRedRows][kRedCols];
-  const int mblocks = (int)((mo + kRedCols - 1) / kRedCols);
-  const int64_t a = blockIdx.x / mblocks;  // internal AO index
-  const int tx = threadIdx.x % kRedCols, ty = threadIdx.x / kRedCols;
-  const int64_t m = (int64_t)(blockIdx.x % mblocks) * kRedCols + tx;
-  const int q = shell_chunk[ao_shell[a]];
-  const int64_t k = (int64_t)q * kChunkAO + (a - chunk[q].z);
-  double s = 0.0;
-  if (m < mo)
-    for (int z = ty; z < slices; z += kRedRows) s += (double)part[((int64_t)z * kpad + k) * ldp + m];
-  red[ty][tx] = s;
-  __syncthreads();
-  if (ty == 0 && m < mo) {
-    double t = 0.0;
-#pragma unroll
-    for (int r = 0; r < kRedRows; ++r) t += red[r][tx];
-    dC[m * ao_num + (ao_caller ? ao_caller[a] : a)] = t;
+// partials, in slice order: a thread per (AO, MO), MOs fastest (reads along
+// a partial's rows), the slices' loads unrolled.
+__global__ void reduce_dct_kernel(const float* __restrict__ part, int slices, int64_t kpad,
+                                  int ldp, int64_t mo, const int* ao_shell,
+                                  const int* shell_chunk, const int4* chunk, const int* ao_caller,
+                                  int64_t ao_num, double* __restrict__ dC) {
+  const int64_t n = mo * ao_num;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = i / mo, m = i % mo;  // a: internal AO index
+    const int q = shell_chunk[ao_shell[a]];
+    const int64_t k = (int64_t)q * kChunkAO + (a - chunk[q].z);
+    const float* src = part + k * ldp + m;
+    const int64_t stride = kpad * ldp;
+    double s = 0.0;
+#pragma unroll 8
+    for (int z = 0; z < slices; ++z) s += (double)src[z * stride];
+    dC[m * ao_num + (ao_caller ? ao_caller[a] : a)] = s;
   }
 }
 
@@ -405,12 +398,35 @@ constexpr uint32_t kAbB = 2 * 64 * 128;         // C^T rows of a chunk, one K bl
 constexpr uint32_t kAbStage = kAbA + kAbB;
 constexpr int kAbStages = 4;
 constexpr int kAbBuf = 4;                       // 64-column accumulators
-constexpr size_t kAbSmem = 1024 + (size_t)kAbStages * kAbStage + 8 * (2 * kAbStages + 2 * kAbBuf);
+constexpr uint32_t kAbStg = 2 * 32 * 128;       // per epilogue warp: 32 rows x 64 FP32, two halves
+constexpr size_t kAbSmem =
+    1024 + (size_t)kAbStages * kAbStage + 4 * kAbStg + 8 * (2 * kAbStages + 2 * kAbBuf);
 static_assert(kAbSmem <= kSmemCap, "shared memory budget");
+
+// Tiled TMA store of a box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          (uint64_t)map),
+      "r"(src), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// The stores committed so far have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// The stores committed so far are complete.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 
 struct AbParams {
   CUtensorMap w;        // W tile rows hi/lo: box (64 MOs, 128 rows, 2 planes)
   CUtensorMap c;        // C^T hi/lo [kpad][ldw]: box (64 MOs, 64 AOs, 2 planes)
+  CUtensorMap out;      // Abar blocks as rows of 64 FP32: box (32 columns, 32 rows), 128B swizzle
   const uint8_t* mask;
   float* abar;          // blocks [tiles][nchunk][128][64]
   int nchunk, tiles, num_kb;
@@ -574,6 +590,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue (warps 0-3)
+    // Warp w's 32 rows of a block go TMEM -> shared (two 32-column halves in
+    // the 128-byte swizzled layout: 16-byte piece j of row r at j ^ (r & 7),
+    // free of bank conflicts) -> global by two tensor stores; the staging
+    // buffer is reused once the previous item's stores have read it.
+    const uint32_t stg = base + kAbStages * kAbStage + warp * kAbStg;
     uint32_t i = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
@@ -594,23 +615,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (!ok) break;
         tc_fence_after();
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
         const uint32_t tb = tmem + b * 64 + ((uint32_t)(warp * 32) << 16);
-        float* dst = P.abar + (((int64_t)t * P.nchunk + q) * kTileRows + 32 * warp + lane) * 64;
 #pragma unroll
-        for (int c = 0; c < 64; c += 32) {
+        for (int h = 0; h < 2; ++h) {
           float v[32];
-          tmem_ld16x2(tb + c, v, true);
+          tmem_ld16x2(tb + 32 * h, v, true);
+          const uint32_t rowp = stg + h * (kAbStg / 2) + lane * 128;
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            reinterpret_cast<float4*>(dst + c)[j] =
-                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             rowp + (uint32_t)((j ^ (lane & 7)) * 16)),
+                         "f"(v[4 * j]), "f"(v[4 * j + 1]), "f"(v[4 * j + 2]), "f"(v[4 * j + 3])
+                         : "memory");
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(b));
+        if (lane == 0) {
+          mbar_arrive(tempty_bar(b));
+          const int row0 = ((t * P.nchunk + q) * kTileRows) + 32 * warp;
+          tma_store_2d(&P.out, stg, 0, row0);
+          tma_store_2d(&P.out, stg + kAbStg / 2, 32, row0);
+          bulk_commit();
+        }
         ++i;
       }
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -709,8 +743,7 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
   if (!ao.tiled || !ao.blocked || !ao.a_lo || !ao.mask) return cudaErrorInvalidValue;
   const int nchunk = ao.nchunk;
   const int64_t tiles = (P + kTilePoints - 1) / kTilePoints;
-  if (tiles > INT32_MAX / kTileRows || (int64_t)nchunk * tiles * 2 > INT32_MAX ||
-      mo_num > INT32_MAX)
+  if ((int64_t)nchunk * tiles * kTileRows > INT32_MAX || mo_num > INT32_MAX)
     return cudaErrorInvalidValue;
   const int64_t ldw = (mo_num + 7) / 8 * 8;
   const int64_t ldp = up16(mo_num);
@@ -779,8 +812,7 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
       default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    const int64_t mblocks = (mo_num + kRedCols - 1) / kRedCols;
-    reduce_dct_kernel<<<(unsigned)(b.ao_num * mblocks), kRedCols * kRedRows, 0, s>>>(
+    reduce_dct_kernel<<<grid_for(mo_num * b.ao_num), 256, 0, s>>>(
         part, L.slices, kpad, (int)ldp, mo_num, b.ao_shell, b.shell_chunk, b.chunk, b.ao_caller,
         b.ao_num, d_dC);
     e = cudaGetLastError();
@@ -794,6 +826,18 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
   if (!make_map_planes(&ap.w, w_hi, w_lo, ldw, tiles * kTileRows, ldw, 64, kTileRows))
     return cudaErrorInvalidValue;
   if (!make_map_planes(&ap.c, c_hi, c_lo, ldw, kpad, ldw, 64, 64)) return cudaErrorInvalidValue;
+  {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {64, (cuuint64_t)(tiles * nchunk * kTileRows)};
+    cuuint64_t strides[1] = {64 * sizeof(float)};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&ap.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, abar, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   ap.mask = ao.mask;
   ap.abar = abar;
   ap.nchunk = nchunk;
