@@ -690,18 +690,24 @@ def measure_adjoint(args):
                "products_flops": flops, "products_tflops": flops / (mb * 1e-3) / 1e12}
         if mode == "bf16x3":
             tensor = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-            # what the backward must move at least: W in, the recomputed AO
-            # tensor out and back (FP32), Abar out and back (FP32), dL/dC
-            nbytes = 4.0 * rows * mol.mo_num + 2 * 4.0 * rows * mol.ao_num * 2 + \
+            # what the block-sparse backward must move at least: W in (FP32),
+            # the forward's live AO blocks in (bf16 hi + lo, 32 KB each),
+            # Abar at the live blocks out and back (FP32, 32 KB each), dL/dC
+            live, total, _ = ctx.block_stats()
+            blk = 128 * 64 * 4.0
+            nbytes = 4.0 * rows * mol.mo_num + live * blk + 2 * live * blk + \
                 8.0 * mol.mo_num * mol.ao_num
+            ent["live_blocks"] = live
+            ent["total_blocks"] = total
             ent["roofline"] = {
                 "bound": "hbm", "achieved": nbytes / (mb * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": nbytes / (mb * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "algorithmic_bytes": nbytes,
                 "tensor": {"achieved": flops / (mb * 1e-3) / 1e12, "peak": tensor,
                            "unit": "TFLOP/s", "frac": flops / (mb * 1e-3) / 1e12 / tensor},
-                "note": "whole backward (AO recompute, operand splits, both products, dR kernel) "
-                        "against the bytes its FP32 AO and Abar tensors must move"}
+                "note": "whole backward (W gather and split, dL/dC and Abar products over the "
+                        "live blocks, dR kernel) against the bytes W, the live AO blocks and "
+                        "the live Abar blocks must move"}
         res[mode] = ent
         ctx.close()
     return res

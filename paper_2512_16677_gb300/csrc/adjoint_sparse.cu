@@ -238,8 +238,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t bytes = S::A_BYTES + (uint32_t)na * kAtom;
       uint32_t it = 0;
       bool ok = true;
+      uint32_t nxt = t0 < t1 ? live_of(t0) : 0u;
       for (int t = t0; t < t1 && ok; ++t) {
-        const uint32_t lv = live_of(t);
+        const uint32_t lv = nxt;
+        nxt = t + 1 < t1 ? live_of(t + 1) : 0u;  // the next tile's mask bytes, early
         if (!lv) continue;
         const int z0 = (lv & 0xFu) ? 2 * (t * P.nchunk + q0) : P.zero_slice;
         const int z1 = (lv >> 4) ? 2 * (t * P.nchunk + q1) : P.zero_slice;
@@ -277,8 +279,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = make_idesc(1u, kBM, bn) | kAMajorMN | kBMajorMN;
       uint32_t it = 0;
       bool first = true;
+      uint32_t nxt = t0 < t1 ? live_of(t0) : 0u;
       for (int t = t0; t < t1; ++t) {
-        if (!live_of(t)) continue;
+        const uint32_t lv = nxt;
+        nxt = t + 1 < t1 ? live_of(t + 1) : 0u;  // the next tile's mask bytes, early
+        if (!lv) continue;
         bool ok = true;
         for (int h = 0; h < 2; ++h) {
           const int s = it % ST;
@@ -432,6 +437,31 @@ struct AbParams {
   int nchunk, tiles, num_kb;
 };
 
+// Live chunks 64 w .. 64 w + 63 of tile t as bits, from up to four 16-byte
+// loads of the mask row (rows are mask_ld bytes, 16-byte aligned; bytes
+// past the last chunk are never written and are masked off).
+__device__ __forceinline__ uint64_t live_window(const uint8_t* mask, int nchunk, int t, int w) {
+  const int mld = mask_ld(nchunk);
+  const uint4* row = reinterpret_cast<const uint4*>(mask + (int64_t)t * mld + 64 * w);
+  const int nv = (mld - 64 * w) / 16;
+  uint4 x[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) x[v] = v < nv ? row[v] : make_uint4(0u, 0u, 0u, 0u);
+  uint64_t bits = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint32_t wd[4] = {x[v].x, x[v].y, x[v].z, x[v].w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int by = 0; by < 4; ++by)
+        if ((wd[k] >> (8 * by)) & 0xFu) bits |= 1ull << (16 * v + 4 * k + by);
+  }
+  const int valid = nchunk - 64 * w;
+  if (valid < 64) bits &= (1ull << valid) - 1ull;
+  return bits;
+}
+
 // Persistent: CTA c walks tiles c, c + gridDim.x, ... and, in each, its
 // live chunks; a (tile, chunk) item takes num_kb stages (K = MOs in blocks
 // of 64) and one of kAbBuf TMEM accumulators, so that the epilogue of an
@@ -455,7 +485,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   volatile int* abort_v = &abort_flag;
-  const int mld = mask_ld(P.nchunk);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAbStages; ++s) {
@@ -489,25 +518,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       tma_prefetch_map(&P.c);
       uint32_t it = 0;
       bool ok = true;
+      uint64_t cur = (int)blockIdx.x < P.tiles ? live_window(P.mask, P.nchunk, blockIdx.x, 0) : 0;
       for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        const uint8_t* row = P.mask + (int64_t)t * mld;
-        for (int q = 0; q < P.nchunk && ok; ++q) {
-          if (!(row[q] & 0xFu)) continue;
-          for (int kb = 0; kb < P.num_kb; ++kb) {
-            const int s = it % kAbStages;
-            const uint32_t ph = (it / kAbStages) & 1u;
-            ++it;
-            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
-              flag_error(err_flag, abort_v, 1);
-              ok = false;
-              break;
+        const int tn = t + gridDim.x;
+        const uint64_t nxt = tn < P.tiles ? live_window(P.mask, P.nchunk, tn, 0) : 0;  // early
+        for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
+          uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
+          while (bits && ok) {
+            const int q = 64 * w + __ffsll((long long)bits) - 1;
+            bits &= bits - 1ull;
+            for (int kb = 0; kb < P.num_kb; ++kb) {
+              const int s = it % kAbStages;
+              const uint32_t ph = (it / kAbStages) & 1u;
+              ++it;
+              if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_v)) {
+                flag_error(err_flag, abort_v, 1);
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(full_bar(s), kAbStage);
+              const uint32_t st = base + s * kAbStage;
+              tma_load_3d(st, &P.w, full_bar(s), 64 * kb, t * kTileRows, 0);
+              tma_load_3d(st + kAbA, &P.c, full_bar(s), 64 * kb, 64 * q, 0);
             }
-            mbar_expect_tx(full_bar(s), kAbStage);
-            const uint32_t st = base + s * kAbStage;
-            tma_load_3d(st, &P.w, full_bar(s), 64 * kb, t * kTileRows, 0);
-            tma_load_3d(st + kAbA, &P.c, full_bar(s), 64 * kb, 64 * q, 0);
           }
         }
+        cur = nxt;
       }
       if (*abort_v) {
         const uint32_t first = it > (uint32_t)kAbStages ? it - kAbStages : 0u;
@@ -526,10 +562,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0, i = 0;
       bool ok = true, in_item = false;
       uint32_t b = 0;
+      uint64_t cur = (int)blockIdx.x < P.tiles ? live_window(P.mask, P.nchunk, blockIdx.x, 0) : 0;
       for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        const uint8_t* row = P.mask + (int64_t)t * mld;
-        for (int q = 0; q < P.nchunk && ok; ++q) {
-          if (!(row[q] & 0xFu)) continue;
+        const int tn = t + gridDim.x;
+        const uint64_t nxt = tn < P.tiles ? live_window(P.mask, P.nchunk, tn, 0) : 0;  // early
+        for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
+        uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
+        while (bits && ok) {
+          bits &= bits - 1ull;
           b = i % kAbBuf;
           if (!mbar_wait(tempty_bar(b), ((i / kAbBuf) & 1u) ^ 1u, abort_v)) {
             flag_error(err_flag, abort_v, 2);
@@ -567,6 +607,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           in_item = false;
           ++i;
         }
+        }
+        cur = nxt;
       }
       if (!ok) {
         // aborted: the MMAs in flight finish before TMEM is freed
@@ -597,10 +639,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t stg = base + kAbStages * kAbStage + warp * kAbStg;
     uint32_t i = 0;
     bool ok = true;
+    uint64_t cur = (int)blockIdx.x < P.tiles ? live_window(P.mask, P.nchunk, blockIdx.x, 0) : 0;
     for (int t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-      const uint8_t* row = P.mask + (int64_t)t * mld;
-      for (int q = 0; q < P.nchunk; ++q) {
-        if (!(row[q] & 0xFu)) continue;
+      const int tn = t + gridDim.x;
+      const uint64_t nxt = tn < P.tiles ? live_window(P.mask, P.nchunk, tn, 0) : 0;  // early
+      for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
+      uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
+      while (bits) {
+        const int q = 64 * w + __ffsll((long long)bits) - 1;
+        bits &= bits - 1ull;
         const uint32_t b = i % kAbBuf;
         const long long c0 = clock64();
         bool got = true;
@@ -642,6 +689,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++i;
       }
+      }
+      cur = nxt;
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -765,9 +814,9 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
     zero_dead_groups_kernel<<<(unsigned)std::min<int64_t>(blocks, 8 * device_sms()), 256, 0, s>>>(
         (__nv_bfloat16*)ao.a, ao.mask, tiles, nchunk);
   }
-  gather_split_w_kernel<<<(unsigned)std::min<int64_t>((tiles * kTileRows + 7) / 8,
-                                                      16 * (int64_t)device_sms()),
-                          256, 0, s>>>(W, ao.perm, P, mo_num, ldw, tiles, w_hi, w_lo);
+  // a warp per row (the row's point index, then its W row: two dependent loads)
+  gather_split_w_kernel<<<(unsigned)std::min<int64_t>((tiles * kTileRows + 7) / 8, 1 << 20), 256,
+                          0, s>>>(W, ao.perm, P, mo_num, ldw, tiles, w_hi, w_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 

@@ -458,21 +458,6 @@ cudaError_t launch_cusp_apply(const BasisDev& b, const CuspDev& cu, const Points
                               const double* f64, const float* f32, bool f64_out, void* D,
                               void* scratch, cudaStream_t s);
 
-// Split-bf16 adjoint products (adjoint_tc.cu): C^T hi/lo planes of C [mo][ao]
-// (FP64) into `ct` (adjoint_tc_ct_bytes); then, for W [rows][mo] (FP32) and
-// the AO tensor [rows][ld_ao] (FP32, caller's-order columns remapped by
-// col_map on output), Abar [rows][ao] (FP32) = W . C and, unless d_dC is
-// NULL, d_dC [mo][ao] (FP64) = W^T . AO, on the tensor cores, in `scratch`
-// of adjoint_tc_scratch_bytes.
-size_t adjoint_tc_ct_bytes(int64_t mo_num, int64_t ao_num);
-cudaError_t launch_adjoint_ct_split(const double* C64, int64_t mo_num, int64_t ao_num,
-                                    void* ct, cudaStream_t s);
-size_t adjoint_tc_scratch_bytes(int64_t rows, int64_t mo_num, int64_t ao_num);
-cudaError_t launch_adjoint_tc(const float* W, int64_t rows, int64_t mo_num, const float* ao,
-                              int64_t ld_ao, int64_t ao_num, const void* ct, float* abar,
-                              double* d_dC, const int* col_map, void* scratch, int* err_flag,
-                              cudaStream_t s);
-
 // Adjoint dR kernel: dR partials from Abar [5P][ld] (value type T) at the
 // points, reduced into d_dR [nucl][3] (FP64).
 cudaError_t launch_adjoint_dR(const BasisDev& b, const PointsDev& p, int mode,
