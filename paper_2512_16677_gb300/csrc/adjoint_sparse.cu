@@ -94,7 +94,17 @@ __global__ void zero_dead_groups_kernel(__nv_bfloat16* ao, const uint8_t* mask, 
 // in the AO tensor's tile rows: row 128 t + 5 j + c holds component c of
 // point perm[25 t + j] (perm NULL: that point itself).  Rows 125..127 of a
 // tile, rows past the last point and columns past mo are zero.  A warp per
-// row, lanes over column pairs (ldw is even), stored as bf16 pairs.
+// row, lanes over column pairs (ldw is even), stored as bf16 pairs; the
+// next row's point index is loaded while the current row is copied.
+__device__ __forceinline__ const float* w_row(const float* W, const int32_t* perm, int64_t P,
+                                              int64_t mo, int64_t row) {
+  const int j = (int)(row % kTileRows);
+  if (j >= 5 * kTilePoints) return nullptr;
+  const int64_t s = row / kTileRows * kTilePoints + j / 5;
+  if (s >= P) return nullptr;
+  return W + (5 * (perm ? (int64_t)perm[s] : s) + j % 5) * mo;
+}
+
 __global__ void gather_split_w_kernel(const float* __restrict__ W, const int32_t* __restrict__ perm,
                                       int64_t P, int64_t mo, int64_t ldw, int64_t tiles,
                                       __nv_bfloat16* __restrict__ hi,
@@ -102,27 +112,32 @@ __global__ void gather_split_w_kernel(const float* __restrict__ W, const int32_t
   const int lane = threadIdx.x & 31;
   const int64_t rows = tiles * kTileRows;
   const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows;
-       row += step) {
-    const int j = (int)(row % kTileRows);
-    const float* src = nullptr;
-    if (j < 5 * kTilePoints) {
-      const int64_t s = row / kTileRows * kTilePoints + j / 5;
-      if (s < P) src = W + (5 * (perm ? (int64_t)perm[s] : s) + j % 5) * mo;
-    }
+  const bool pairs = (mo & 1) == 0;  // rows start on 8-byte boundaries: float2 loads
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const float* src = row < rows ? w_row(W, perm, P, mo, row) : nullptr;
+  for (; row < rows; row += step) {
+    const int64_t nrow = row + step;
+    const float* nsrc = nrow < rows ? w_row(W, perm, P, mo, nrow) : nullptr;
     __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(hi + row * ldw);
     __nv_bfloat162* ol = reinterpret_cast<__nv_bfloat162*>(lo + row * ldw);
     for (int64_t c = 2 * lane; c < ldw; c += 64) {
       float v0 = 0.0f, v1 = 0.0f;
-      if (src) {
-        if (c < mo) v0 = src[c];
-        if (c + 1 < mo) v1 = src[c + 1];
+      if (src && c < mo) {
+        if (pairs) {
+          const float2 v = *reinterpret_cast<const float2*>(src + c);
+          v0 = v.x;
+          v1 = v.y;
+        } else {
+          v0 = src[c];
+          if (c + 1 < mo) v1 = src[c + 1];
+        }
       }
       const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
       const float2 hf = __bfloat1622float2(h);
       oh[c / 2] = h;
       ol[c / 2] = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
     }
+    src = nsrc;
   }
 }
 
@@ -398,11 +413,15 @@ __global__ void reduce_dct_kernel(const float* __restrict__ part, int slices, in
 
 // ------------------------------------------------------------ Abar blocks --
 
+// An Abar item is one tile and up to kAbGroup of its live chunks: one MMA
+// of N = 64 per chunk multiplies the tile's W rows by the chunks' C^T rows.
+constexpr int kAbGroup = 4;
 constexpr uint32_t kAbA = 2 * kTileRows * 128;  // W rows of a tile, one K block, hi + lo
-constexpr uint32_t kAbB = 2 * 64 * 128;         // C^T rows of a chunk, one K block, hi + lo
+constexpr uint32_t kAbPlane = 64 * 128;         // C^T rows of a chunk, one K block, one plane
+constexpr uint32_t kAbB = 2 * kAbGroup * kAbPlane;  // hi rows of the group, then lo rows
 constexpr uint32_t kAbStage = kAbA + kAbB;
-constexpr int kAbStages = 4;
-constexpr int kAbBuf = 4;                       // 64-column accumulators
+constexpr int kAbStages = 2;
+constexpr int kAbBuf = 2;                       // accumulators of kAbGroup x 64 columns
 constexpr uint32_t kAbStg = 2 * 32 * 128;       // per epilogue warp: 32 rows x 64 FP32, two halves
 constexpr size_t kAbSmem =
     1024 + (size_t)kAbStages * kAbStage + 4 * kAbStg + 8 * (2 * kAbStages + 2 * kAbBuf);
@@ -430,7 +449,7 @@ __device__ __forceinline__ void bulk_wait_all() {
 
 struct AbParams {
   CUtensorMap w;        // W tile rows hi/lo: box (64 MOs, 128 rows, 2 planes)
-  CUtensorMap c;        // C^T hi/lo [kpad][ldw]: box (64 MOs, 64 AOs, 2 planes)
+  CUtensorMap c;        // C^T hi/lo [kpad][ldw]: box (64 MOs, 64 AOs, 1 plane)
   CUtensorMap out;      // Abar blocks as rows of 64 FP32: box (32 columns, 32 rows), 128B swizzle
   const uint8_t* mask;
   float* abar;          // blocks [tiles][nchunk][128][64]
@@ -462,25 +481,39 @@ __device__ __forceinline__ uint64_t live_window(const uint8_t* mask, int nchunk,
   return bits;
 }
 
+// The next item's chunks: up to kAbGroup of the live chunks left in bits
+// (window w), lowest first; returns their count.
+__device__ __forceinline__ int take_group(uint64_t& bits, int w, int* q) {
+  int n = 0;
+  while (bits && n < kAbGroup) {
+    q[n++] = 64 * w + __ffsll((long long)bits) - 1;
+    bits &= bits - 1ull;
+  }
+  return n;
+}
+
 // Persistent: CTA c walks tiles c, c + gridDim.x, ... and, in each, its
-// live chunks; a (tile, chunk) item takes num_kb stages (K = MOs in blocks
-// of 64) and one of kAbBuf TMEM accumulators, so that the epilogue of an
-// item overlaps the MMAs of the next ones.  The three roles enumerate the
-// items from the mask in the same order.
+// live chunks in groups of up to kAbGroup; an item (tile, group) takes
+// num_kb stages (K = MOs in blocks of 64) and one of kAbBuf TMEM
+// accumulators, so that the epilogue of an item overlaps the MMAs of the
+// next.  The three roles enumerate the items from the mask in the same
+// order.
+//   full[s] / empty[s]   stage s loaded / read by the MMAs
 //   tfull[b]  accumulator b complete            (MMA -> epilogue, commit)
-//   tempty[b] accumulator b stored              (epilogue warps -> MMA)
+//   tempty[b] accumulator b read out            (epilogue warps -> MMA)
 __global__ void __launch_bounds__(kThreads, 1)
     abar_kernel(const __grid_constant__ AbParams P, int* err_flag) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t bar0 = base + kAbStages * kAbStage;
+  const uint32_t bar0 = base + kAbStages * kAbStage + 4 * kAbStg;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kAbStages + s); };
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * kAbStages + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * kAbStages + kAbBuf + b); };
-  constexpr uint32_t kTmem = tmem_cols<kAbBuf * 64>();
+  constexpr uint32_t kAcc = kAbGroup * 64;
+  constexpr uint32_t kTmem = tmem_cols<kAbBuf * kAcc>();
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -525,8 +558,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
           uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
           while (bits && ok) {
-            const int q = 64 * w + __ffsll((long long)bits) - 1;
-            bits &= bits - 1ull;
+            int q[kAbGroup];
+            const int n = take_group(bits, w, q);
             for (int kb = 0; kb < P.num_kb; ++kb) {
               const int s = it % kAbStages;
               const uint32_t ph = (it / kAbStages) & 1u;
@@ -536,10 +569,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = false;
                 break;
               }
-              mbar_expect_tx(full_bar(s), kAbStage);
+              mbar_expect_tx(full_bar(s), kAbA + 2u * n * kAbPlane);
               const uint32_t st = base + s * kAbStage;
               tma_load_3d(st, &P.w, full_bar(s), 64 * kb, t * kTileRows, 0);
-              tma_load_3d(st + kAbA, &P.c, full_bar(s), 64 * kb, 64 * q, 0);
+              for (int j = 0; j < n; ++j) {
+                tma_load_3d(st + kAbA + j * kAbPlane, &P.c, full_bar(s), 64 * kb, 64 * q[j], 0);
+                tma_load_3d(st + kAbA + (kAbGroup + j) * kAbPlane, &P.c, full_bar(s), 64 * kb,
+                            64 * q[j], 1);
+              }
             }
           }
         }
@@ -558,7 +595,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 5) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(1u, kBM, 64);
       uint32_t it = 0, i = 0;
       bool ok = true, in_item = false;
       uint32_t b = 0;
@@ -567,46 +603,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int tn = t + gridDim.x;
         const uint64_t nxt = tn < P.tiles ? live_window(P.mask, P.nchunk, tn, 0) : 0;  // early
         for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
-        uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
-        while (bits && ok) {
-          bits &= bits - 1ull;
-          b = i % kAbBuf;
-          if (!mbar_wait(tempty_bar(b), ((i / kAbBuf) & 1u) ^ 1u, abort_v)) {
-            flag_error(err_flag, abort_v, 2);
-            ok = false;
-            break;
-          }
-          in_item = true;
-          const uint32_t dacc = tmem + b * 64;
-          for (int kb = 0; kb < P.num_kb; ++kb) {
-            const int s = it % kAbStages;
-            const uint32_t ph = (it / kAbStages) & 1u;
-            ++it;
-            if (!mbar_wait(full_bar(s), ph, abort_v)) {
+          uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
+          while (bits && ok) {
+            int q[kAbGroup];
+            const int n = take_group(bits, w, q);
+            b = i % kAbBuf;
+            if (!mbar_wait(tempty_bar(b), ((i / kAbBuf) & 1u) ^ 1u, abort_v)) {
               flag_error(err_flag, abort_v, 2);
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint32_t st = base + s * kAbStage;
-            const uint64_t a_hi = sw128_desc(st);
-            const uint64_t a_lo = sw128_desc(st + kAbA / 2);
-            const uint64_t b_hi = sw128_desc(st + kAbA);
-            const uint64_t b_lo = sw128_desc(st + kAbA + kAbB / 2);
+            in_item = true;
+            const uint32_t dacc = tmem + b * kAcc;
+            const uint32_t idesc = make_idesc(1u, kBM, 64 * n);
+            for (int kb = 0; kb < P.num_kb; ++kb) {
+              const int s = it % kAbStages;
+              const uint32_t ph = (it / kAbStages) & 1u;
+              ++it;
+              if (!mbar_wait(full_bar(s), ph, abort_v)) {
+                flag_error(err_flag, abort_v, 2);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t st = base + s * kAbStage;
+              const uint64_t a_hi = sw128_desc(st);
+              const uint64_t a_lo = sw128_desc(st + kAbA / 2);
+              const uint64_t b_hi = sw128_desc(st + kAbA);
+              const uint64_t b_lo = sw128_desc(st + kAbA + kAbGroup * kAbPlane);
 #pragma unroll
-            for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
-              const uint64_t ko = (uint64_t)(kk * kUmmaKBytes) >> 4;
-              umma<QK_BF16X3>(dacc, a_hi + ko, b_hi + ko, idesc, (kb | kk) ? 1u : 0u);
-              umma<QK_BF16X3>(dacc, a_hi + ko, b_lo + ko, idesc, 1u);
-              umma<QK_BF16X3>(dacc, a_lo + ko, b_hi + ko, idesc, 1u);
+              for (int kk = 0; kk < kRowBytes / kUmmaKBytes; ++kk) {
+                const uint64_t ko = (uint64_t)(kk * kUmmaKBytes) >> 4;
+                umma<QK_BF16X3>(dacc, a_hi + ko, b_hi + ko, idesc, (kb | kk) ? 1u : 0u);
+                umma<QK_BF16X3>(dacc, a_hi + ko, b_lo + ko, idesc, 1u);
+                umma<QK_BF16X3>(dacc, a_lo + ko, b_hi + ko, idesc, 1u);
+              }
+              umma_commit(empty_bar(s));
             }
-            umma_commit(empty_bar(s));
+            if (!ok) break;
+            umma_commit(tfull_bar(b));
+            in_item = false;
+            ++i;
           }
-          if (!ok) break;
-          umma_commit(tfull_bar(b));
-          in_item = false;
-          ++i;
-        }
         }
         cur = nxt;
       }
@@ -632,10 +670,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue (warps 0-3)
-    // Warp w's 32 rows of a block go TMEM -> shared (two 32-column halves in
-    // the 128-byte swizzled layout: 16-byte piece j of row r at j ^ (r & 7),
-    // free of bank conflicts) -> global by two tensor stores; the staging
-    // buffer is reused once the previous item's stores have read it.
+    // Per chunk of an item, warp w's 32 rows of the block go TMEM -> shared
+    // (two 32-column halves in the 128-byte swizzled layout: 16-byte piece j
+    // of row r at j ^ (r & 7), free of bank conflicts) -> global by two
+    // tensor stores; the staging buffer is reused once the previous stores
+    // have read it.
     const uint32_t stg = base + kAbStages * kAbStage + warp * kAbStg;
     uint32_t i = 0;
     bool ok = true;
@@ -644,51 +683,55 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int tn = t + gridDim.x;
       const uint64_t nxt = tn < P.tiles ? live_window(P.mask, P.nchunk, tn, 0) : 0;  // early
       for (int w = 0; 64 * w < P.nchunk && ok; ++w) {
-      uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
-      while (bits) {
-        const int q = 64 * w + __ffsll((long long)bits) - 1;
-        bits &= bits - 1ull;
-        const uint32_t b = i % kAbBuf;
-        const long long c0 = clock64();
-        bool got = true;
-        while (!mbar_try_wait(tfull_bar(b), (i / kAbBuf) & 1u)) {
-          if (clock64() - c0 > kWaitCycles) {
-            got = false;
-            break;
+        uint64_t bits = w == 0 ? cur : live_window(P.mask, P.nchunk, t, w);
+        while (bits) {
+          int q[kAbGroup];
+          const int n = take_group(bits, w, q);
+          const uint32_t b = i % kAbBuf;
+          const long long c0 = clock64();
+          bool got = true;
+          while (!mbar_try_wait(tfull_bar(b), (i / kAbBuf) & 1u)) {
+            if (clock64() - c0 > kWaitCycles) {
+              got = false;
+              break;
+            }
           }
-        }
-        if (!got) flag_error(err_flag, abort_v, 3);
-        ok = __all_sync(0xffffffffu, got) && !*abort_v;
-        __syncwarp();
-        if (!ok) break;
-        tc_fence_after();
-        if (lane == 0) bulk_wait_read_all();
-        __syncwarp();
-        const uint32_t tb = tmem + b * 64 + ((uint32_t)(warp * 32) << 16);
+          if (!got) flag_error(err_flag, abort_v, 3);
+          ok = __all_sync(0xffffffffu, got) && !*abort_v;
+          __syncwarp();
+          if (!ok) break;
+          tc_fence_after();
+          for (int j = 0; j < n; ++j) {
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+            const uint32_t tb = tmem + b * kAcc + 64 * j + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float v[32];
-          tmem_ld16x2(tb + 32 * h, v, true);
-          const uint32_t rowp = stg + h * (kAbStg / 2) + lane * 128;
+            for (int h = 0; h < 2; ++h) {
+              float v[32];
+              tmem_ld16x2(tb + 32 * h, v, true);
+              const uint32_t rowp = stg + h * (kAbStg / 2) + lane * 128;
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
-                             rowp + (uint32_t)((j ^ (lane & 7)) * 16)),
-                         "f"(v[4 * j]), "f"(v[4 * j + 1]), "f"(v[4 * j + 2]), "f"(v[4 * j + 3])
-                         : "memory");
+              for (int k = 0; k < 8; ++k)
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                 rowp + (uint32_t)((k ^ (lane & 7)) * 16)),
+                             "f"(v[4 * k]), "f"(v[4 * k + 1]), "f"(v[4 * k + 2]),
+                             "f"(v[4 * k + 3])
+                             : "memory");
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              const int row0 = ((t * P.nchunk + q[j]) * kTileRows) + 32 * warp;
+              tma_store_2d(&P.out, stg, 0, row0);
+              tma_store_2d(&P.out, stg + kAbStg / 2, 32, row0);
+              bulk_commit();
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty_bar(b));
+          ++i;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(tempty_bar(b));
-          const int row0 = ((t * P.nchunk + q) * kTileRows) + 32 * warp;
-          tma_store_2d(&P.out, stg, 0, row0);
-          tma_store_2d(&P.out, stg + kAbStg / 2, 32, row0);
-          bulk_commit();
-        }
-        ++i;
-      }
       }
       cur = nxt;
     }
@@ -814,9 +857,9 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
     zero_dead_groups_kernel<<<(unsigned)std::min<int64_t>(blocks, 8 * device_sms()), 256, 0, s>>>(
         (__nv_bfloat16*)ao.a, ao.mask, tiles, nchunk);
   }
-  // a warp per row (the row's point index, then its W row: two dependent loads)
-  gather_split_w_kernel<<<(unsigned)std::min<int64_t>((tiles * kTileRows + 7) / 8, 1 << 20), 256,
-                          0, s>>>(W, ao.perm, P, mo_num, ldw, tiles, w_hi, w_lo);
+  gather_split_w_kernel<<<(unsigned)std::min<int64_t>((tiles * kTileRows + 7) / 8,
+                                                      16 * (int64_t)device_sms()),
+                          256, 0, s>>>(W, ao.perm, P, mo_num, ldw, tiles, w_hi, w_lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
@@ -874,7 +917,22 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
   memset(&ap, 0, sizeof(ap));
   if (!make_map_planes(&ap.w, w_hi, w_lo, ldw, tiles * kTileRows, ldw, 64, kTileRows))
     return cudaErrorInvalidValue;
-  if (!make_map_planes(&ap.c, c_hi, c_lo, ldw, kpad, ldw, 64, 64)) return cudaErrorInvalidValue;
+  {
+    // C^T planes as a 3-D map with a one-plane box: the hi rows of a group's
+    // chunks land together, then the lo rows
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    const intptr_t gap = (const char*)c_lo - (const char*)c_hi;
+    cuuint64_t dims[3] = {(cuuint64_t)ldw, (cuuint64_t)kpad, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)(ldw * 2), (cuuint64_t)gap};
+    cuuint32_t box[3] = {64, 64, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (gap <= 0 || gap % 16 != 0 ||
+        enc(&ap.c, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(c_hi), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorInvalidValue;
@@ -896,7 +954,7 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
     KernelFacts f;
     e = kernel_facts<abar_kernel>(kAbSmem, kThreads, &f);
     if (e != cudaSuccess) return e;
-    if (f.occ < 1 || f.occ * (int)tmem_cols<kAbBuf * 64>() > 512)
+    if (f.occ < 1 || f.occ * (int)tmem_cols<kAbBuf * kAbGroup * 64>() > 512)
       return cudaErrorInvalidConfiguration;
     const int64_t g = std::min<int64_t>(tiles, (int64_t)f.sms * f.occ);
     e = launch_pdl(abar_kernel, (unsigned)g, kThreads, kAbSmem, s, ap, err_flag);
