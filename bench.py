@@ -48,7 +48,10 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the uneven multi-molecule batch measurement")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the large-cluster and adjoint measurements")
+                    help="skip the secondary measurements (large cluster, adjoint, cusp, "
+                         "density, single moves)")
+    ap.add_argument("--extra", default="large,adjoint,cusp,density,single_move",
+                    help="comma-separated secondary measurements to run (profiling captures)")
     ap.add_argument("--walkers", type=int, default=None,
                     help="fewer walkers than the workload's 256 (profiling captures only)")
     return ap.parse_args()
@@ -478,11 +481,13 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch:
         res["batch"] = measure_batch(args, world)
     if not args.no_extra:
-        res["large"] = measure_large(args, world)
-        res["adjoint"] = measure_adjoint(args)
-        res["cusp"] = measure_cusp(args)
-        res["density"] = measure_density(args)
-        res["single_move"] = measure_single(args)
+        extras = {"large": lambda: measure_large(args, world), "adjoint": lambda: measure_adjoint(args),
+                  "cusp": lambda: measure_cusp(args), "density": lambda: measure_density(args),
+                  "single_move": lambda: measure_single(args)}
+        for name in [e for e in args.extra.split(",") if e]:
+            if name not in extras:
+                raise SystemExit(f"unknown --extra measurement {name!r}")
+            res[name] = extras[name]()
 
     # end to end through the host-memory C-ABI calls: H2D of the coordinates
     # and D2H of the whole MO vgl tensor inside the timed region
