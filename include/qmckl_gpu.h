@@ -366,10 +366,12 @@ qk_status qk_contract_device(int32_t mode, int64_t M, int64_t N, int64_t K, cons
    refused with QK_ERR_BAD_SIZE before any work is queued.
    The first call on a device looks up the array's device address (once per
    device and CUDA context, with that device current: again after a device
-   reset); make that first call before any stream capture.  All calls share the one array and it keeps the previous call's
+   reset).  All calls share the one array and it keeps the previous call's
    contents (the error word is cleared on every call): calls that overlap on
-   the GPU race, so serialise them (one stream, or events).  Synchronises
-   `stream` to read the error word.  Allocates no device or host memory. */
+   the GPU race, so serialise them (one stream, or events).  Every call
+   synchronises `stream` to read the error word, so no call can be made
+   while that stream is being captured into a CUDA graph.  Allocates no
+   device or host memory. */
 qk_status qk_contract_device_noalloc(int32_t mode, int64_t M, int64_t N, int64_t K,
                                      const float* A, const float* B, float* D, void* stream);
 
