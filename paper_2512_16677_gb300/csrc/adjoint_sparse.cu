@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "tc_common.cuh"
 
@@ -113,11 +114,36 @@ __global__ void gather_split_w_kernel(const float* __restrict__ W, const int32_t
   const int64_t rows = tiles * kTileRows;
   const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5);
   const bool pairs = (mo & 1) == 0;  // rows start on 8-byte boundaries: float2 loads
+  // rows on 16-byte boundaries and whole quads of columns: float4 loads
+  const bool quads = (mo & 3) == 0 && (ldw & 3) == 0 && ((uintptr_t)W & 15) == 0;
   int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const float* src = row < rows ? w_row(W, perm, P, mo, row) : nullptr;
   for (; row < rows; row += step) {
     const int64_t nrow = row + step;
     const float* nsrc = nrow < rows ? w_row(W, perm, P, mo, nrow) : nullptr;
+    if (quads) {
+      // four columns per lane: one 16-byte load, 8 bytes into each plane
+      uint2* oh = reinterpret_cast<uint2*>(hi + row * ldw);
+      uint2* ol = reinterpret_cast<uint2*>(lo + row * ldw);
+      for (int64_t c = 4 * lane; c < ldw; c += 128) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (src && c < mo) v = *reinterpret_cast<const float4*>(src + c);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z, v.w);
+        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+        const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+        const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+        uint2 hw, lw;
+        memcpy(&hw.x, &h0, 4);
+        memcpy(&hw.y, &h1, 4);
+        memcpy(&lw.x, &l0, 4);
+        memcpy(&lw.y, &l1, 4);
+        oh[c / 4] = hw;
+        ol[c / 4] = lw;
+      }
+      src = nsrc;
+      continue;
+    }
     __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(hi + row * ldw);
     __nv_bfloat162* ol = reinterpret_cast<__nv_bfloat162*>(lo + row * ldw);
     for (int64_t c = 2 * lane; c < ldw; c += 64) {
@@ -390,18 +416,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // dL/dC [mo][ao] (FP64, the caller's AO order) = sum over slices of the
-// partials, in slice order: a thread per (AO, MO), MOs fastest (reads along
-// a partial's rows), the slices' loads unrolled.
+// partials, in slice order: a thread per (chunked column k, MO), MOs
+// fastest (reads along a partial's rows), the slices' loads unrolled;
+// padding columns of a chunk are skipped.
 __global__ void reduce_dct_kernel(const float* __restrict__ part, int slices, int64_t kpad,
-                                  int ldp, int64_t mo, const int* ao_shell,
-                                  const int* shell_chunk, const int4* chunk, const int* ao_caller,
+                                  int ldp, int64_t mo, const int4* chunk, const int* ao_caller,
                                   int64_t ao_num, double* __restrict__ dC) {
-  const int64_t n = mo * ao_num;
+  const int64_t n = kpad * mo;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = i / mo, m = i % mo;  // a: internal AO index
-    const int q = shell_chunk[ao_shell[a]];
-    const int64_t k = (int64_t)q * kChunkAO + (a - chunk[q].z);
+    const int64_t k = i / mo, m = i % mo;
+    const int4 ch = chunk[k / kChunkAO];
+    const int a = ch.z + (int)(k % kChunkAO);  // internal AO index
+    if (a >= ch.w) continue;
     const float* src = part + k * ldp + m;
     const int64_t stride = kpad * ldp;
     double s = 0.0;
@@ -904,9 +931,8 @@ cudaError_t launch_adjoint_sparse(const BasisDev& b, const PointsDev& p, const A
       default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    reduce_dct_kernel<<<grid_for(mo_num * b.ao_num), 256, 0, s>>>(
-        part, L.slices, kpad, (int)ldp, mo_num, b.ao_shell, b.shell_chunk, b.chunk, b.ao_caller,
-        b.ao_num, d_dC);
+    reduce_dct_kernel<<<grid_for(mo_num * kpad), 256, 0, s>>>(
+        part, L.slices, kpad, (int)ldp, mo_num, b.chunk, b.ao_caller, b.ao_num, d_dC);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
