@@ -21,7 +21,9 @@
 //     live.  The tiles are cut into slices whose FP32 partials are added in
 //     a fixed order (FP64) by a last small kernel.
 //   * Abar is formed for live (tile, chunk) blocks only: A = the W rows of
-//     the tile (K-major, K = MOs), B = the chunk's rows of C^T (K-major).
+//     the tile (K-major, K = MOs), B = the rows of C^T of up to four live
+//     chunks of the tile (K-major, one MMA of N = 64 per chunk); each block
+//     leaves through swizzled shared-memory staging and TMA tensor stores.
 // The three split products hi.hi + hi.lo + lo.hi accumulate in FP32 in TMEM.
 // Every wait is bounded; a wait that gives up records a code in the error
 // word, stops the pipeline, lets the copies and MMAs in flight finish,
