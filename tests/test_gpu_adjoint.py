@@ -112,6 +112,26 @@ def test_split_bf16_adjoint_organic_two_n_tiles(orc, cfg):
     _check("organic_8w_sparse", "bf16x3", _gpu_grad(m, W, "bf16x3"), (dC, dR), (sC, sR))
 
 
+def test_split_bf16_adjoint_few_points_six_mos(orc, cfg):
+    """30 points of the C/H chain (two tiles, the second holding 5 points;
+    under two tiles the points keep the caller's order) and the first 6 MOs
+    (W rows gathered two columns at a time), against the oracle."""
+    from paper_2512_16677_gb300 import qmckl
+    m = cfg(3, walk_num=1)
+    pts = np.ascontiguousarray(m.points[:30])
+    C = np.ascontiguousarray(m.mo_coef[:6])
+    W = synth.random_weights(np.random.default_rng(50), pts.shape[0], C.shape[0])
+    dC, dR, sC, sR = orc.adjoint(m, W, points=pts, C=C, sizes=True)
+    c = qmckl.Context("bf16x3")
+    c.set_molecule(m)
+    c.set_mo_coefficient(C)
+    c.set_points_device(torch.from_numpy(pts.reshape(1, 30, 3)).cuda())
+    gC, gR = c.backward_device(torch.from_numpy(W.reshape(1, 30, 5, 6)).float().cuda())
+    torch.cuda.synchronize()
+    c.synchronize()
+    _check("chain_30pts_6mo", "bf16x3", (gC.cpu().numpy(), gR.cpu().numpy()), (dC, dR), (sC, sR))
+
+
 def test_split_bf16_adjoint_reuses_the_forward_ao(cfg):
     """The split-bf16 backward over the forward's own AO tensor (right after a
     forward pass), again (its dead groups already zeroed), and on a fresh
