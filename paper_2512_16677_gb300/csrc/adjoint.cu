@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads)
 // live block's pairs on a chain); each pair's gradient goes to its own
 // shared slot and the slots are added per shell in point order.
 constexpr int kBlkThreads = 256;
-__global__ void __launch_bounds__(kBlkThreads, 3)
+__global__ void __launch_bounds__(kBlkThreads, 4)
     adjoint_dR_blocked_kernel(BasisDev b, PointsDev pts, const float* __restrict__ abar,
                               const uint8_t* __restrict__ mask, int64_t tiles,
                               double* __restrict__ partial) {
