@@ -396,8 +396,13 @@ qk_status qk_selftest_wait_timeout(int64_t limit_cycles, int32_t* info);
    points (Sec. 3.6 needs nuclear derivatives of the orbitals up to third
    order).  dW has the mo_vgl layout and element type, in device memory.
    d_dC [mo_num][ao_num] (dL/dC) and d_dR [nucl_num][3] (dL/dR_nuc) are
-   device FP64 arrays; either may be NULL to skip it.  AO values are
-   recomputed (not taken from the forward).  Runs on the context's stream. */
+   device FP64 arrays; either may be NULL to skip it.  QK_FP64 and QK_FP32
+   / QK_TF32 recompute the AO values densely and multiply with SIMT GEMMs.
+   QK_BF16X3 multiplies on the tensor cores over the block-sparse AO tensor
+   of the current points: the one the last forward call left in the
+   workspace, else one computed here (it is kept, as a forward call keeps
+   it); its derivatives for dL/dR_nuc are recomputed.  Runs on the
+   context's stream. */
 qk_status qk_mo_vgl_backward_device(qk_context ctx, const void* dW, int64_t size,
                                     double* d_dC, double* d_dR);
 
