@@ -59,3 +59,30 @@ def _cluster_sample(orc, m, c, mode):
     assert idx.shape[0] >= 256
     _SAMPLE["idx"] = idx
     _SAMPLE["ref"], _SAMPLE["size"] = mo_vgl_threaded(orc, m, m.points[idx])
+
+
+def test_large_cluster_split_bf16_adjoint(orc, cfg):
+    """The split-bf16 backward at the cluster's size: 157 AO chunks (three
+    32-chunk windows of the mask), 2000 MOs (eight N tiles of 256 in dL/dC^T,
+    32 K blocks per Abar item), loss weights on 8 points spread over the
+    walkers, against the oracle's adjoint at those points (the bars of the
+    split-bf16 adjoint)."""
+    from paper_2512_16677_gb300 import qmckl, synth
+    m = cfg(5)
+    rng = np.random.default_rng(51)
+    idx = np.sort(rng.choice(m.point_num, 8, replace=False))
+    Wp = synth.random_weights(rng, idx.size, m.mo_num)
+    dC, dR, sC, sR = orc.adjoint(m, Wp, points=m.points[idx], sizes=True)
+    W = torch.zeros((m.point_num, 5, m.mo_num), dtype=torch.float32)
+    W[torch.from_numpy(idx)] = torch.from_numpy(Wp).float()
+    c = qmckl.Context("bf16x3")
+    c.set_molecule(m)
+    c.set_points_device(torch.from_numpy(m.coord).cuda())
+    c.mo_vgl_device()
+    gC, gR = c.backward_device(W.reshape(m.walk_num, m.elec_num, 5, m.mo_num).cuda())
+    torch.cuda.synchronize()
+    c.synchronize()
+    eC = float(np.max(np.abs(gC.cpu().numpy() - dC) / (sC + 1e-300)))
+    eR = float(np.max(np.abs(gR.cpu().numpy() - dR) / (sR + 1e-300)))
+    assert eC <= 1e-4, f"dL/dC {eC:.3e}"
+    assert eR <= 2e-4, f"dL/dR {eR:.3e}"
