@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kThreads)
 // first, so that the threads take only pairs with work (about a third of a
 // live block's pairs on a chain); each pair's gradient goes to its own
 // shared slot and the slots are added per shell in point order.
-constexpr int kBlkThreads = 256;
-__global__ void __launch_bounds__(kBlkThreads, 4)
+constexpr int kBlkThreads = 128;
+__global__ void __launch_bounds__(kBlkThreads, 8)
     adjoint_dR_blocked_kernel(BasisDev b, PointsDev pts, const float* __restrict__ abar,
                               const uint8_t* __restrict__ mask, int64_t tiles,
                               double* __restrict__ partial) {
