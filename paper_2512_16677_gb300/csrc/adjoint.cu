@@ -17,11 +17,16 @@
 //                       + (4(2l+3) + 8) d_j P S2 + 4 r^2 P_j S2 - 8 r^2 d_j P S3)
 // (the Laplacian of Eq. 1 uses d . grad P = l P for the homogeneous P).
 //
-// One CTA covers 32 points x one AO column chunk; each warp handles the 32
-// points of one shell, reduces over them with shuffles and adds into a
-// per-shell accumulator that only it writes, so the sum order is fixed.
-// Per-CTA shell sums go to a partial buffer; two small kernels then sum the
-// partials over point tiles and over the shells of each nucleus.
+// Dense Abar (FP64, FP32): one CTA covers 32 points x one AO column chunk;
+// each warp handles the 32 points of one shell, reduces over them with
+// shuffles and adds into a per-shell accumulator that only it writes, so
+// the sum order is fixed.  Abar in live (tile, chunk) blocks (split bf16):
+// one CTA per chunk walks the tiles where the chunk is live, lists the
+// (point, shell) pairs inside the shell's radius, gives each its own
+// shared slot and sums the slots per shell in point order.  Either way the
+// per-CTA shell sums go to a partial buffer; two small kernels then sum the
+// partials over point-tile blocks and over the shells of each nucleus, in
+// fixed orders.
 #include "ao_common.cuh"
 
 namespace qk {
