@@ -248,3 +248,23 @@ def test_autograd_function(orc, cfg):
     dC, dR, sC, sR = orc.adjoint(m, W, sizes=True)
     assert np.max(np.abs(C.grad.numpy() - dC) / sC) <= 1e-12
     assert np.max(np.abs(R.grad.numpy() - dR) / sR) <= 1e-12
+
+
+def test_autograd_function_split_bf16(orc, cfg):
+    """torch.autograd through the split-bf16 forward and backward (the
+    backward recomputes the AO tensor at the forward's points): C.grad and
+    R.grad within the split-bf16 adjoint bars of the oracle's adjoint."""
+    from paper_2512_16677_gb300 import autograd, qmckl
+    m = cfg(3, walk_num=1)
+    ctx = qmckl.Context("bf16x3")
+    ctx.set_molecule(m)
+    C = torch.tensor(m.mo_coef, dtype=torch.float64, requires_grad=True)
+    R = torch.tensor(m.nucl_coord, dtype=torch.float64, requires_grad=True)
+    coord = torch.from_numpy(m.coord).cuda()
+    W = synth.random_weights(np.random.default_rng(52), m.point_num, m.mo_num)
+    Wt = torch.from_numpy(W.reshape(m.walk_num, m.elec_num, 5, m.mo_num)).float().cuda()
+    out = autograd.mo_vgl(ctx, C, R, coord)
+    (out * Wt).sum().backward()
+    dC, dR, sC, sR = orc.adjoint(m, W, sizes=True)
+    assert np.max(np.abs(C.grad.numpy() - dC) / (sC + 1e-300)) <= ADJ_TOL["bf16x3"][0]
+    assert np.max(np.abs(R.grad.numpy() - dR) / (sR + 1e-300)) <= ADJ_TOL["bf16x3"][1]
